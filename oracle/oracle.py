@@ -1,0 +1,299 @@
+"""ctypes binding of the FP64 CPU oracle (srmc_oracle.c).
+
+TEST INFRASTRUCTURE ONLY: imported by tests/, by ``__graft_entry__.smoke()``
+and by the ``cpu_baseline`` / ``--impl reference`` legs of ``bench.py``.  The
+product path (``paper_2407_21085_gb300``) never imports this module.
+
+The oracle follows Alg. SRMDP step by step in double precision (see the
+header of srmc_oracle.c for the passage behind every function).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import shutil
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "srmc_oracle.c")
+_HDR = os.path.join(_HERE, "srmc_oracle.h")
+_OUT = os.path.join(_HERE, "_build", "libsrmc_oracle.so")
+DMAX = 8
+PMAX = 24
+MODELS = {"cos": 0, "logistic": 1, "affine": 2}
+BASES = {"lp0": 0, "lp1": 1}
+
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (plain C, OpenMP, no FP contraction)."""
+    os.makedirs(os.path.dirname(_OUT), exist_ok=True)
+    stale = (not os.path.exists(_OUT)
+             or os.path.getmtime(_OUT) < max(os.path.getmtime(_SRC), os.path.getmtime(_HDR)))
+    if force or stale:
+        tmp = _OUT + f".{os.getpid()}.tmp"
+        cmd = ["gcc", "-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-fPIC", "-shared", "-fopenmp",
+               "-ffp-contract=off", "-fno-fast-math", "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _OUT)
+    return _OUT
+
+
+class _Problem(C.Structure):
+    _fields_ = [
+        ("d", C.c_int), ("q", C.c_int), ("N", C.c_int), ("T", C.c_double),
+        ("b", C.c_double * DMAX), ("sigma", C.c_double * (DMAX * DMAX)),
+        ("model", C.c_int), ("params", C.c_double * PMAX),
+        ("cells", C.c_int * DMAX), ("lo", C.c_double * DMAX), ("hi", C.c_double * DMAX),
+        ("mu", C.c_double), ("basis", C.c_int), ("M", C.c_int64),
+        ("seed", C.c_uint64), ("instance", C.c_uint32), ("Cy", C.c_double), ("Cz", C.c_double),
+    ]
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            _lib = _bind(C.CDLL(build()))
+    return _lib
+
+
+def compile_variant(source_text: str, out_path: str):
+    """Compile a modified copy of the oracle source (used by tests that plant a
+    mistake in the oracle to show that the pins catch it) and bind it."""
+    src = out_path + ".c"
+    with open(src, "w") as fh:
+        fh.write(source_text)
+    shutil.copy(_HDR, os.path.join(os.path.dirname(out_path), "srmc_oracle.h"))
+    subprocess.run(["gcc", "-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-fPIC", "-shared", "-fopenmp",
+                    "-ffp-contract=off", "-o", out_path, src, "-lm"], check=True)
+    return _bind(C.CDLL(out_path))
+
+
+def source_text() -> str:
+    with open(_SRC) as fh:
+        return fh.read()
+
+
+def _bind(L):
+    P = C.POINTER(_Problem)
+    u32p = C.POINTER(C.c_uint32)
+    dp = C.POINTER(C.c_double)
+    L.orc_philox4x32_10.argtypes = [u32p, u32p, u32p]
+    L.orc_uniform.argtypes = [C.c_uint32]; L.orc_uniform.restype = C.c_double
+    L.orc_norminv.argtypes = [C.c_double]; L.orc_norminv.restype = C.c_double
+    L.orc_normal_from_word.argtypes = [C.c_uint32]; L.orc_normal_from_word.restype = C.c_double
+    L.orc_draw_word.argtypes = [P, C.c_int, C.c_int64, C.c_int64, C.c_int64]
+    L.orc_draw_word.restype = C.c_uint32
+    L.orc_logistic_cdf.argtypes = [C.c_double, C.c_double]; L.orc_logistic_cdf.restype = C.c_double
+    L.orc_sample_restricted.argtypes = [C.c_double] * 4; L.orc_sample_restricted.restype = C.c_double
+    L.orc_locate_dim.argtypes = [P, C.c_int, C.c_double]; L.orc_locate_dim.restype = C.c_int
+    L.orc_locate.argtypes = [P, dp]; L.orc_locate.restype = C.c_int64
+    L.orc_locate_dim_f32.argtypes = [C.c_float, C.c_float, C.c_float, C.c_int]
+    L.orc_locate_dim_f32.restype = C.c_int
+    L.orc_cell_edges.argtypes = [P, C.c_int, C.c_int, dp, dp]
+    L.orc_stratum_centre.argtypes = [P, C.c_int64, dp]
+    L.orc_start_point.argtypes = [P, C.c_int, C.c_int64, C.c_int64, dp]
+    L.orc_g.argtypes = [P, dp]; L.orc_g.restype = C.c_double
+    L.orc_f.argtypes = [P, C.c_int, dp, C.c_double, dp]; L.orc_f.restype = C.c_double
+    L.orc_lstsq_householder.argtypes = [C.c_int, C.c_int, C.c_int, dp, dp, dp]
+    L.orc_lstsq_householder.restype = C.c_int
+    L.orc_create.argtypes = [P]; L.orc_create.restype = C.c_void_p
+    L.orc_destroy.argtypes = [C.c_void_p]
+    L.orc_row_len.argtypes = [C.c_void_p]; L.orc_row_len.restype = C.c_int
+    L.orc_solve_full.argtypes = [C.c_void_p, C.c_int]; L.orc_solve_full.restype = C.c_int
+    L.orc_fit_lazy.argtypes = [C.c_void_p, C.c_int, C.c_int64]; L.orc_fit_lazy.restype = C.c_int
+    L.orc_fit_one.argtypes = [C.c_void_p, C.c_int, C.c_int64]; L.orc_fit_one.restype = C.c_int64
+    L.orc_row.argtypes = [C.c_void_p, C.c_int, C.c_int64]; L.orc_row.restype = dp
+    L.orc_eval.argtypes = [C.c_void_p, C.c_int, C.c_int64, dp, dp, dp]
+    L.orc_eval.restype = C.c_int64
+    L.orc_fallbacks.argtypes = [C.c_void_p]; L.orc_fallbacks.restype = C.c_int64
+    L.orc_path_steps.argtypes = [C.c_void_p]; L.orc_path_steps.restype = C.c_int64
+    return L
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def to_struct(w) -> _Problem:
+    """Fill the oracle's problem struct from a workload description (any
+    object with the fields of ``paper_2407_21085_gb300.workloads.Workload``)."""
+    p = _Problem()
+    p.d, p.q, p.N, p.T = int(w.d), int(w.q), int(w.N), float(w.T)
+    for l in range(w.d):
+        p.b[l] = float(w.b[l])
+        for r in range(w.q):
+            p.sigma[l * w.q + r] = float(w.sigma[l][r])
+    p.model = MODELS[w.model]
+    for a, v in enumerate(w.params):
+        p.params[a] = float(v)
+    for l in range(w.d):
+        p.cells[l] = int(w.cells[l]); p.lo[l] = float(w.lo[l]); p.hi[l] = float(w.hi[l])
+    p.mu = float(w.mu)
+    p.basis = BASES[w.basis]
+    p.M = int(w.M)
+    p.seed = int(w.seed)
+    p.instance = int(w.instance)
+    p.Cy, p.Cz = float(w.Cy), float(w.Cz)
+    return p
+
+
+# ---- primitives -------------------------------------------------------------
+def philox4x32_10(ctr, key):
+    L = lib()
+    c = (C.c_uint32 * 4)(*[int(v) & 0xFFFFFFFF for v in ctr])
+    k = (C.c_uint32 * 2)(*[int(v) & 0xFFFFFFFF for v in key])
+    o = (C.c_uint32 * 4)()
+    L.orc_philox4x32_10(c, k, o)
+    return tuple(int(v) for v in o)
+
+
+def draw_word(w, i, k, m, n):
+    return int(lib().orc_draw_word(C.byref(to_struct(w)), i, k, m, n))
+
+
+def uniform(word):
+    return lib().orc_uniform(int(word))
+
+
+def norminv(u):
+    return lib().orc_norminv(float(u))
+
+
+def normal_from_word(word):
+    return lib().orc_normal_from_word(int(word))
+
+
+def logistic_cdf(x, mu):
+    return lib().orc_logistic_cdf(float(x), float(mu))
+
+
+def sample_restricted(U, xlo, xhi, mu):
+    return lib().orc_sample_restricted(float(U), float(xlo), float(xhi), float(mu))
+
+
+def locate_dim(w, l, x):
+    return int(lib().orc_locate_dim(C.byref(to_struct(w)), l, float(x)))
+
+
+def locate(w, x):
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    return int(lib().orc_locate(C.byref(to_struct(w)), _dptr(x)))
+
+
+def locate_dim_f32(x, lo, r, cells):
+    return int(lib().orc_locate_dim_f32(float(np.float32(x)), float(np.float32(lo)),
+                                         float(np.float32(r)), int(cells)))
+
+
+def cell_edges(w, l, c):
+    a, b = C.c_double(), C.c_double()
+    lib().orc_cell_edges(C.byref(to_struct(w)), l, c, C.byref(a), C.byref(b))
+    return a.value, b.value
+
+
+def stratum_centre(w, k):
+    x = np.zeros(w.d)
+    lib().orc_stratum_centre(C.byref(to_struct(w)), int(k), _dptr(x))
+    return x
+
+
+def start_point(w, i, k, m):
+    x = np.zeros(w.d)
+    lib().orc_start_point(C.byref(to_struct(w)), int(i), int(k), int(m), _dptr(x))
+    return x
+
+
+def g(w, x):
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    return lib().orc_g(C.byref(to_struct(w)), _dptr(x))
+
+
+def f(w, j, x, y, z):
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    z = np.ascontiguousarray(z, dtype=np.float64)
+    return lib().orc_f(C.byref(to_struct(w)), int(j), _dptr(x), float(y), _dptr(z))
+
+
+def lstsq_householder(A, B):
+    A = np.array(A, dtype=np.float64, order="C")
+    B = np.array(B, dtype=np.float64, order="C")
+    if B.ndim == 1:
+        B = B[:, None]
+    n, p = A.shape
+    r = B.shape[1]
+    X = np.zeros((p, r))
+    rc = lib().orc_lstsq_householder(n, p, r, _dptr(A), _dptr(B), _dptr(X))
+    return X, rc
+
+
+# ---- the scheme -------------------------------------------------------------
+class Oracle:
+    """One oracle context: the raw-basis coefficient rows of every fitted (i,k)."""
+
+    def __init__(self, w, library=None):
+        self.w = w
+        self._p = to_struct(w)
+        self._L = library if library is not None else lib()
+        self._ctx = self._L.orc_create(C.byref(self._p))
+        if not self._ctx:
+            raise ValueError("oracle: invalid problem or out of memory")
+        self.K = int(np.prod(w.cells))
+        self.R = self._L.orc_row_len(self._ctx)
+
+    def close(self):
+        if self._ctx:
+            self._L.orc_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def solve_full(self, nthreads: int = 0) -> None:
+        if self._L.orc_solve_full(self._ctx, int(nthreads)) != 0:
+            raise RuntimeError("oracle: full solve found missing rows")
+
+    def fit_lazy(self, i: int, k: int) -> None:
+        if self._L.orc_fit_lazy(self._ctx, int(i), int(k)) != 0:
+            raise RuntimeError("oracle: lazy fit failed")
+
+    def row(self, i: int, k: int):
+        ptr = self._L.orc_row(self._ctx, int(i), int(k))
+        if not ptr:
+            return None
+        return np.ctypeslib.as_array(ptr, shape=(self.R,)).copy()
+
+    def eval(self, i: int, x):
+        x = np.ascontiguousarray(np.atleast_2d(x), dtype=np.float64)
+        n = x.shape[0]
+        y = np.zeros(n)
+        z = np.zeros((n, self.w.q))
+        miss = self._L.orc_eval(self._ctx, int(i), n, _dptr(x), _dptr(y), _dptr(z))
+        if miss:
+            raise RuntimeError(f"oracle: {miss} points fall in strata not fitted at step {i}")
+        return y, z
+
+    def eval_lazy(self, i: int, x):
+        """Fit every stratum the points fall in (lazily), then evaluate."""
+        x = np.atleast_2d(np.asarray(x, dtype=np.float64))
+        if i < self.w.N:
+            for a in range(x.shape[0]):
+                self.fit_lazy(i, locate(self.w, x[a]))
+        return self.eval(i, x)
+
+    @property
+    def fallbacks(self) -> int:
+        return int(self._L.orc_fallbacks(self._ctx))
+
+    @property
+    def path_steps(self) -> int:
+        return int(self._L.orc_path_steps(self._ctx))

@@ -1,0 +1,106 @@
+/*
+ * srmc_oracle.h -- plain FP64 CPU oracle of the stratified regression Monte
+ * Carlo scheme (SRMDP) for discrete BSDEs.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the
+ * cpu_baseline / reference legs of bench.py may load or call this code.  It
+ * shares no header, helper, table or constant generator with the CUDA path
+ * (paper_2407_21085_gb300/csrc); the two meet only through plain numbers
+ * handed to both by the seeded workload definitions.
+ *
+ * What it computes, with the passage it follows:
+ *   - time grid t_i = i*dt, dt = T/N                               (Sec. 2, eq. MDP)
+ *   - Euler Markov chain X_{j+1} = X_j + b dt + sigma dW_j          (Alg. 2, "Euler dynamics")
+ *   - equal-size hypercube strata, exterior cells infinite          (assumption A_Strat)
+ *   - logistic law nu, restricted law nu_k, inverse-CDF sampler     (assumption A_nu, Alg. 3)
+ *   - fresh, independent clouds C_{i,k} of M paths                  (Def. "Simulations and empirical measures")
+ *   - backward SRMDP recursion: Z-OLS then Y-OLS, truncation T_L    (Alg. SRMDP, eq. PsiM; eq. TL)
+ *   - LP0 as the mean, LP1 by Householder QR of A=[1, x_i]          (Sec. 4.1, eqs. lp0/lp1 explicit)
+ *   - Philox-4x32-10 counter RNG from its published definition      (Salmon, Moraes, Dror, Shaw, SC'11)
+ *   - standard normal by inversion, Phi^{-1}(U), one uniform each
+ *
+ * Parity pins of every function live in tests/test_oracle_*.py.
+ */
+#ifndef SRMC_ORACLE_H
+#define SRMC_ORACLE_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ORC_DMAX 8
+#define ORC_PMAX 24
+
+enum { ORC_MODEL_COS = 0, ORC_MODEL_LOGISTIC = 1, ORC_MODEL_AFFINE = 2 };
+enum { ORC_LP0 = 0, ORC_LP1 = 1 };
+
+/* One SRMC problem: forward SDE, driver/terminal model, grid, strata, basis. */
+typedef struct {
+    int d, q;                       /* dim of X and of W                     */
+    int N;                          /* number of time steps                  */
+    double T;                       /* horizon                               */
+    double b[ORC_DMAX];             /* constant drift                        */
+    double sigma[ORC_DMAX * ORC_DMAX]; /* constant diffusion, row-major d x q */
+    int model;                      /* ORC_MODEL_*                           */
+    double params[ORC_PMAX];        /* model parameters (see srmc_oracle.c)  */
+    int cells[ORC_DMAX];            /* cells per dimension                   */
+    double lo[ORC_DMAX], hi[ORC_DMAX]; /* box; outer cells extend to +-inf   */
+    double mu;                      /* logistic scale                        */
+    int basis;                      /* ORC_LP0 / ORC_LP1                     */
+    int64_t M;                      /* paths per stratum                     */
+    uint64_t seed;                  /* Philox seed                           */
+    uint32_t instance;              /* instance id folded into the key       */
+    double Cy, Cz;                  /* truncation levels; <= 0 disables      */
+} orc_problem;
+
+/* ---- primitives ---------------------------------------------------------- */
+void     orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
+double   orc_uniform(uint32_t w);                 /* (w + 1/2) 2^-32            */
+double   orc_norminv(double u);                   /* Phi^{-1}(u), u in (0,1)    */
+double   orc_normal_from_word(uint32_t w);        /* Phi^{-1}((w+1/2) 2^-32)    */
+uint32_t orc_draw_word(const orc_problem *P, int i, int64_t k, int64_t m, int64_t n);
+double   orc_logistic_cdf(double x, double mu);
+double   orc_sample_restricted(double U, double xlo, double xhi, double mu);
+int      orc_locate_dim(const orc_problem *P, int l, double x);
+int64_t  orc_locate(const orc_problem *P, const double *x);
+int      orc_locate_dim_f32(float x, float lo, float r, int C);
+void     orc_cell_edges(const orc_problem *P, int l, int c, double *xlo, double *xhi);
+void     orc_stratum_cells(const orc_problem *P, int64_t k, int *cells);
+void     orc_stratum_centre(const orc_problem *P, int64_t k, double *x);
+void     orc_start_point(const orc_problem *P, int i, int64_t k, int64_t m, double *x);
+double   orc_g(const orc_problem *P, const double *x);
+double   orc_f(const orc_problem *P, int j, const double *x, double y, const double *z);
+
+/* ---- least squares ------------------------------------------------------- */
+/* Householder QR least squares: A (n x p, row-major), B (n x r) -> X (p x r).
+ * Returns 0 on success, 1 if R is numerically singular.  A and B are
+ * overwritten. */
+int orc_lstsq_householder(int n, int p, int r, double *A, double *B, double *X);
+
+/* ---- the scheme ---------------------------------------------------------- */
+typedef struct orc_ctx orc_ctx;
+orc_ctx *orc_create(const orc_problem *P);
+void     orc_destroy(orc_ctx *C);
+int      orc_row_len(const orc_ctx *C);           /* (1+q)*(dim of basis)        */
+/* Full backward solve, OpenMP over strata with nthreads threads (0 = default). */
+int      orc_solve_full(orc_ctx *C, int nthreads);
+/* Lazy, memoised fit of one (i,k): computes every row it depends on first. */
+int      orc_fit_lazy(orc_ctx *C, int i, int64_t k);
+/* Fit of one (i,k) given that every row of steps > i it visits exists.
+ * Returns the number of rows it was missing (0 on success). */
+int64_t  orc_fit_one(orc_ctx *C, int i, int64_t k);
+/* Raw-basis row (alpha[dimb], beta[q*dimb]) of (i,k); NULL if not computed. */
+const double *orc_row(const orc_ctx *C, int i, int64_t k);
+/* Truncated y_i(x), z_i(x) at n points (row-major n x d); rows must exist.
+ * Returns the number of points whose row is missing. */
+int64_t  orc_eval(orc_ctx *C, int i, int64_t n, const double *x, double *y, double *z);
+/* Number of (i,k) fits that fell back to LP0 because R was singular. */
+int64_t  orc_fallbacks(const orc_ctx *C);
+/* Path-steps simulated so far (diagnostic; one unit = one Euler step). */
+int64_t  orc_path_steps(const orc_ctx *C);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

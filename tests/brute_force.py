@@ -1,0 +1,161 @@
+"""A second, independent restatement of Alg. SRMDP for tiny problems.
+
+Pure Python + numpy/scipy library routines, written straight from the paper
+without looking at the C oracle's structure: its own Philox-4x32-10, the
+normal quantile from scipy (Cephes ndtri), the restricted logistic quantile
+through scipy's logit/expit, and numpy's lstsq for every OLS.  Used only by
+tests, on problems with a handful of strata and paths.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+from scipy import special
+
+MASK = 0xFFFFFFFF
+
+
+def philox(ctr, key, rounds=10):
+    c = list(ctr)
+    k = list(key)
+    for r in range(rounds):
+        if r:
+            k = [(k[0] + 0x9E3779B9) & MASK, (k[1] + 0xBB67AE85) & MASK]
+        p0 = 0xD2511F53 * c[0]
+        p1 = 0xCD9E8D57 * c[2]
+        c = [((p1 >> 32) ^ c[1] ^ k[0]) & MASK, p1 & MASK,
+             ((p0 >> 32) ^ c[3] ^ k[1]) & MASK, p0 & MASK]
+    return c
+
+
+def word(w, i, k, m, n):
+    key = [(w.seed & MASK) ^ w.instance, (w.seed >> 32) & MASK]
+    return philox([n // 4, m, k, i], key)[n % 4]
+
+
+def unif(u32):
+    return (u32 + 0.5) / 2.0 ** 32
+
+
+def normal(u32):
+    return float(special.ndtri(unif(u32)))
+
+
+def cells_of(w, k):
+    out = []
+    for C in w.cells:
+        out.append(k % C)
+        k //= C
+    return out
+
+
+def edges(w, l, c):
+    h = (w.hi[l] - w.lo[l]) / w.cells[l]
+    a = -math.inf if c == 0 else w.lo[l] + c * h
+    b = math.inf if c == w.cells[l] - 1 else w.lo[l] + (c + 1) * h
+    return a, b
+
+
+def start(w, i, k, m):
+    x = np.zeros(w.d)
+    cs = cells_of(w, k)
+    for l in range(w.d):
+        a, b = edges(w, l, cs[l])
+        Fa = 0.0 if a == -math.inf else special.expit(w.mu * a)
+        Fb = 1.0 if b == math.inf else special.expit(w.mu * b)
+        U = unif(word(w, i, k, m, l))
+        x[l] = special.logit(Fa + U * (Fb - Fa)) / w.mu
+    return x
+
+
+def locate(w, x):
+    k, stride = 0, 1
+    for l in range(w.d):
+        h = (w.hi[l] - w.lo[l]) / w.cells[l]
+        c = int(min(max(math.floor((x[l] - w.lo[l]) / h), 0), w.cells[l] - 1))
+        k += c * stride
+        stride *= w.cells[l]
+    return k
+
+
+def g(w, x):
+    if w.model == "cos":
+        return math.cos(x.sum() / math.sqrt(w.d))
+    if w.model == "logistic":
+        e = math.exp(w.T + x.sum())
+        return e / (1 + e)
+    p = w.params
+    return p[0] + float(np.dot(p[1:1 + w.d], x))
+
+
+def f(w, j, x, y, z):
+    t = j * w.T / w.N
+    if w.model == "cos":
+        lam, kap, kapz, s0 = w.params[:4]
+        s = x.sum() / math.sqrt(w.d)
+        e = math.exp(lam * (w.T - t))
+        out = (lam + s0 * s0 / 2) * y + kap * (y * y - (e * math.cos(s)) ** 2)
+        if kapz:
+            out += kapz * (float(np.dot(z, z)) - (s0 * e * math.sin(s)) ** 2)
+        return out
+    if w.model == "logistic":
+        return float(np.sum(z)) * (y - (2 + w.q) / (2 * w.q))
+    p, d = w.params, w.d
+    return p[1 + d] + float(np.dot(p[2 + d:2 + 2 * d], x)) + p[2 + 2 * d] * y
+
+
+def clamp(v, L):
+    return v if L <= 0 else float(np.clip(v, -L, L))
+
+
+def solve(w):
+    """All rows: rows[i][k] = (alpha[p], beta[q, p]) in the raw basis."""
+    N, d, q, M = w.N, w.d, w.q, w.M
+    dt = w.T / N
+    p = 1 if w.basis == "lp0" else d + 1
+    sig = np.array(w.sigma, dtype=float)
+    b = np.array(w.b, dtype=float)
+    rows = [dict() for _ in range(N)]
+
+    def phi(x):
+        return np.array([1.0]) if p == 1 else np.concatenate([[1.0], x])
+
+    def y_and_z(j, x):
+        if j == N:
+            return g(w, x), None
+        al, be = rows[j][locate(w, x)]
+        v = phi(x)
+        return clamp(float(al @ v), w.Cy), np.array([clamp(float(be[l] @ v), w.Cz) for l in range(q)])
+
+    for i in range(N - 1, -1, -1):
+        for k in range(w.K):
+            X0, DW, S1, Y1 = [], [], [], []
+            for m in range(M):
+                x = start(w, i, k, m)
+                X0.append(x.copy())
+                path = [x]
+                incs = []
+                for j in range(i, N):
+                    dw = np.array([math.sqrt(dt) * normal(word(w, i, k, m, d + (j - i) * q + l))
+                                   for l in range(q)])
+                    incs.append(dw)
+                    path.append(path[-1] + b * dt + sig @ dw)
+                S = g(w, path[-1])
+                for j in range(i + 1, N):
+                    xj, xj1 = path[j - i], path[j - i + 1]
+                    yj1, _ = y_and_z(j + 1, xj1)
+                    _, zj = y_and_z(j, xj)
+                    S += f(w, j, xj, yj1, zj) * dt
+                S1.append(S)
+                DW.append(incs[0])
+                Y1.append(y_and_z(i + 1, path[1])[0])
+            A = np.array([phi(x) for x in X0])
+            Bz = np.array([S1[m] * DW[m] / dt for m in range(M)])
+            beta = np.linalg.lstsq(A, Bz, rcond=None)[0].T          # q x p
+            zi = [np.array([clamp(float(beta[l] @ phi(X0[m])), w.Cz) for l in range(q)])
+                  for m in range(M)]
+            By = np.array([S1[m] + f(w, i, X0[m], Y1[m], zi[m]) * dt for m in range(M)])
+            alpha = np.linalg.lstsq(A, By, rcond=None)[0]
+            rows[i][k] = (alpha, beta)
+    return rows, y_and_z
