@@ -1,0 +1,191 @@
+/*
+ * srmc.h -- C ABI of libsrmc, a GB300 (sm_103a) implementation of the
+ * stratified regression Monte Carlo scheme (SRMDP) for discrete-time BSDEs
+ * and semilinear parabolic PDEs (Gobet, Lopez-Salas, Turkedjiev, Vazquez).
+ *
+ * Problem solved (Sec. 1, eqs. fbsde/eds/pde; Sec. 2, eq. MDP): the
+ * multistep-forward dynamic programming equation on the grid t_i = i T/N,
+ *     Y_i    = E_i[ g(X_N) + sum_{j=i}^{N-1} f_j(X_j, Y_{j+1}, Z_j) dt ],
+ *     dt Z_i = E_i[ (g(X_N) + sum_{j=i+1}^{N-1} f_j(X_j, Y_{j+1}, Z_j) dt) dW_i ],
+ * with X the Euler chain X_{j+1} = X_j + b dt + sigma dW_j (Alg. 2), approximated
+ * by Alg. SRMDP: for every time step i = N-1..0 and every hypercube stratum
+ * H_k, draw M fresh paths started from the restricted logistic law nu_k
+ * (assumption A_nu, Alg. 3), simulate them to t_N, and fit the Z-response then
+ * the Y-response by least squares on LP0 (constants) or LP1 (affine functions)
+ * local to H_k (eq. PsiM; Sec. 4.1), truncating the fitted values (eq. TL).
+ *
+ * Conventions for every call:
+ *   - Host arrays passed in are read during the call and copied; the caller
+ *     keeps ownership.
+ *   - "dev" pointers are device memory of the current CUDA device, owned by
+ *     the caller; the library never frees them and never keeps them after
+ *     the call returns (work on them is enqueued on the given stream).
+ *   - "stream" is a cudaStream_t passed as void*; NULL is the legacy default
+ *     stream.  Compute calls are asynchronous on that stream.
+ *   - Errors come back as an srmc_status; srmc_last_error() gives a message
+ *     for the calling thread.  No C++ exception crosses this ABI.
+ *   - Random numbers: Philox-4x32-10 (Salmon et al., SC'11) with
+ *     key = (seed_lo ^ instance, seed_hi) and counter = (n/4, m, k, i) for word
+ *     n of path m of cloud C_{i,k}; words 0..d-1 draw the start point,
+ *     words d + (j-i) q + l the normal of component l of dW_j.  Uniforms are
+ *     U = (w + 1/2) 2^-32 and normals Phi^{-1}(U).  Nothing is stored: a path
+ *     is regenerated from its counter whenever it is needed.
+ */
+#ifndef SRMC_H
+#define SRMC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SRMC_DMAX 8     /* largest dimension d supported                    */
+#define SRMC_PMAX 24    /* length of the model parameter array             */
+
+typedef enum {
+    SRMC_OK = 0,
+    SRMC_ERR_INVALID_ARG = 1,   /* a size, pointer or parameter is out of range */
+    SRMC_ERR_CUDA = 2,          /* a CUDA runtime call failed                   */
+    SRMC_ERR_OOM = 3,           /* device allocation failed                     */
+    SRMC_ERR_UNSUPPORTED = 4,   /* valid input outside what this build supports */
+    SRMC_ERR_STATE = 5          /* call out of order (e.g. step i before i+1)   */
+} srmc_status;
+
+typedef enum { SRMC_LP0 = 0, SRMC_LP1 = 1 } srmc_basis;        /* Sec. 2, (A_Strat) examples */
+typedef enum { SRMC_FP32 = 0, SRMC_FP64 = 1 } srmc_precision;
+
+/* Built-in driver/terminal families.  params[] layouts:
+ *   SRMC_MODEL_COS:      {lam, kap, kapz, s0};  g(x) = cos(s), s = sum_l x_l / sqrt(d),
+ *                        f_j(x,y,z) = (lam + s0^2/2) y + kap (y^2 - u(t_j,x)^2)
+ *                                     + kapz (|z|^2 - s0^2 e^{2 lam (T-t_j)} sin^2 s),
+ *                        u(t,x) = e^{lam (T-t)} cos(s) solves the PDE when sigma = s0 I.
+ *   SRMC_MODEL_LOGISTIC: {} ; the test BSDE of Sec. 5.1: w = exp(t + sum x),
+ *                        g = w(T,x)/(1+w(T,x)), f = (sum_l z_l)(y - (2+q)/(2q)).
+ *   SRMC_MODEL_AFFINE:   {g0, g_1..g_d, f0, f_1..f_d, a}; g = g0 + g.x,
+ *                        f_j(x,y,z) = f0 + f.x + a y. */
+typedef enum { SRMC_MODEL_COS = 0, SRMC_MODEL_LOGISTIC = 1, SRMC_MODEL_AFFINE = 2 } srmc_model;
+
+/* Forward SDE, driver, terminal condition and time grid (Sec. 1-2).
+ * b: [d] constant drift (host).  sigma: [d*q] row-major constant diffusion
+ * (host); this build requires q == d and a diagonal sigma, else
+ * SRMC_ERR_UNSUPPORTED.  params: [n_params <= SRMC_PMAX] (host). */
+typedef struct {
+    int d, q;
+    int N;
+    double T;
+    const double *b;
+    const double *sigma;
+    srmc_model model;
+    const double *params;
+    int n_params;
+} srmc_problem;
+
+/* Strata (assumption A_Strat): the box [lo_l, hi_l) cut into cells[l] equal
+ * cells per dimension, the first and last cell of every dimension extended
+ * to -inf / +inf.  Stratum index k = sum_l c_l prod_{l'<l} cells[l']
+ * (dimension 0 fastest); a point x is in cell c_l = clamp(floor((x_l - lo_l) /
+ * h_l), 0, cells[l]-1), h_l = (hi_l - lo_l)/cells[l], in FP64 (single-precision
+ * paths take the same decision as floor((x_l - lo_l) * r_l), r_l = cells[l] /
+ * (hi_l - lo_l) rounded to float).  mu: scale of the logistic law nu (eq.
+ * logistic).  All arrays host, [d]. */
+typedef struct {
+    const int *cells;
+    const double *lo, *hi;
+    double mu;
+} srmc_strata;
+
+/* Scheme configuration.  M: paths per stratum and step, M >= dim of the basis
+ * (Def. of the clouds).  Cy, Cz: truncation levels of y and of each component
+ * of z (eq. TL, Prop. a.s. bounds); a value <= 0 disables that truncation.
+ * block_threads: threads per stratum block, a multiple of 32 in [32, 256],
+ * or 0 for the library's choice. */
+typedef struct {
+    srmc_basis basis;
+    srmc_precision prec;
+    long long M;
+    unsigned long long seed;
+    unsigned instance;
+    double Cy, Cz;
+    int block_threads;
+} srmc_config;
+
+typedef struct srmc_solver srmc_solver;   /* opaque, library-owned */
+
+/* Validate the problem and allocate the solver's device tables on the
+ * current device: coefficient rows of every (i, k), i < N, in FP64 (and FP32
+ * for the FP32 form), zero-filled.  Errors: SRMC_ERR_INVALID_ARG,
+ * SRMC_ERR_UNSUPPORTED, SRMC_ERR_OOM, SRMC_ERR_CUDA; *out is NULL on error. */
+srmc_status srmc_create(const srmc_problem *problem, const srmc_strata *strata,
+                        const srmc_config *config, srmc_solver **out);
+
+/* Release everything the solver owns.  NULL is accepted. */
+void srmc_destroy(srmc_solver *s);
+
+/* The whole backward recursion of Alg. SRMDP, i = N-1 .. 0, enqueued on
+ * stream: per step one launch over all strata (Z fit, then Y fit).
+ * Asynchronous; results are valid once the stream has reached this point. */
+srmc_status srmc_solve(srmc_solver *s, void *stream);
+
+/* One step i of Alg. SRMDP for all strata.  Requires the rows of steps
+ * i+1..N-1 (enqueued earlier on the same stream); SRMC_ERR_STATE otherwise. */
+srmc_status srmc_solve_step(srmc_solver *s, int i, void *stream);
+
+/* Truncated y_i(x) and z_i(x) (Alg. SRMDP, the fitted functions restricted to
+ * the stratum holding x) at n points.  dev_x: [n][d] double; dev_y: [n]
+ * double; dev_z: [n][q] double (may be NULL).  i == N gives y = g, z = 0.
+ * n == 0 is a no-op. */
+srmc_status srmc_eval(const srmc_solver *s, int i, const double *dev_x, long long n,
+                      double *dev_y, double *dev_z, void *stream);
+
+/* The K stratum centres (centre of the nominal finite cell in every
+ * dimension), written to dev_x: [K][d] double. */
+srmc_status srmc_centres(const srmc_solver *s, double *dev_x, void *stream);
+
+/* Layout of the FP64 coefficient table: row (i,k) holds alpha[p] then
+ * beta[q][p] in the centred basis phi(x) = [1, (x - c_k)/(h/2)], p = 1 (LP0)
+ * or d+1 (LP1), c_k the nominal centre; y_i(x) = T_Cy(alpha . phi(x)).
+ * *dev_y64 / *dev_z64 are borrowed pointers to [N][K][ry] and [N][K][rz]
+ * doubles, valid until srmc_destroy. */
+srmc_status srmc_table(const srmc_solver *s, const double **dev_y64, const double **dev_z64,
+                       int *p, int *ry, int *rz, long long *K);
+
+/* Counters since creation: [0] strata fits that fell back from LP1 to LP0
+ * because the Gram matrix was numerically singular (Cholesky pivot below
+ * 1e-12 of its trace); [1] non-finite coefficients written; [2] stratum-path
+ * steps simulated.  Synchronises the device. */
+srmc_status srmc_stats(const srmc_solver *s, unsigned long long out[3]);
+
+/* ---- the method's primitives, exposed for testing and reuse --------------- */
+
+/* Philox-4x32-10 of n counters: dev_ctr [n][4] uint32, key[2] host, dev_out
+ * [n][4]. */
+srmc_status srmc_philox(const uint32_t *dev_ctr, const uint32_t key[2], long long n,
+                        uint32_t *dev_out, void *stream);
+
+/* Standard normals xi = Phi^{-1}((w + 1/2) 2^-32) of n words; FP64 into
+ * dev_out64 and/or the single-precision form into dev_out32 (either NULL). */
+srmc_status srmc_normals(const uint32_t *dev_words, long long n, double *dev_out64,
+                         float *dev_out32, void *stream);
+
+/* Stratum index of n points: dev_x64 [n][d] double decided in FP64, or
+ * dev_x32 [n][d] float decided in FP32 (exactly one non-NULL). */
+srmc_status srmc_locate(const srmc_solver *s, const double *dev_x64, const float *dev_x32,
+                        long long n, long long *dev_k, void *stream);
+
+/* Start points (Alg. 3) of paths m0..m0+n-1 of cloud C_{i,k} in the solver's
+ * precision, widened to double: dev_x [n][d]. */
+srmc_status srmc_start_points(const srmc_solver *s, int i, long long k, long long m0,
+                              long long n, double *dev_x, void *stream);
+
+/* Message of the last error on this thread ("" if none). */
+const char *srmc_last_error(void);
+
+/* ABI version of this header. */
+int srmc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,81 @@
+"""Build libsrmc.so in-tree for sm_103a with nvcc.
+
+The step kernel is compiled once per dimension D = 1..8 (-DSRMC_STEP_D=D) so
+that per-path state stays in registers; the objects are compiled in parallel
+and linked with the C-ABI translation unit into one shared library under
+``paper_2407_21085_gb300/_build``.
+"""
+from __future__ import annotations
+
+import concurrent.futures as cf
+import os
+import shutil
+import subprocess
+import sys
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+CSRC = os.path.join(HERE, "csrc")
+INCLUDE = os.path.join(os.path.dirname(HERE), "include")
+OUT_DIR = os.path.join(HERE, "_build")
+LIB = os.path.join(OUT_DIR, "libsrmc.so")
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+DIMS = range(1, 9)
+
+
+def _nvcc() -> str:
+    for cand in (shutil.which("nvcc"), "/usr/local/cuda/bin/nvcc"):
+        if cand and os.path.exists(cand):
+            return cand
+    raise RuntimeError("nvcc not found: the CUDA toolkit is required to build libsrmc")
+
+
+def _flags():
+    return ARCH + ["-O3", "-lineinfo", "-std=c++17", "-I", INCLUDE, "-Xcompiler",
+                   "-fPIC,-ffp-contract=off", "--expt-relaxed-constexpr"]
+
+
+def _sources():
+    srcs = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cu", ".cuh", ".h"))]
+    srcs.append(os.path.join(INCLUDE, "srmc.h"))
+    return srcs
+
+
+def _stale() -> bool:
+    if not os.path.exists(LIB):
+        return True
+    t = os.path.getmtime(LIB)
+    return any(os.path.getmtime(s) > t for s in _sources())
+
+
+def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -> str:
+    if not force and not _stale():
+        return LIB
+    os.makedirs(OUT_DIR, exist_ok=True)
+    nvcc = _nvcc()
+    units = [(os.path.join(CSRC, "srmc_step.cu"), os.path.join(OUT_DIR, f"step_d{D}.o"), [f"-DSRMC_STEP_D={D}"])
+             for D in DIMS]
+    for name in sorted(os.listdir(CSRC)):
+        if name.endswith(".cu") and name != "srmc_step.cu":
+            units.append((os.path.join(CSRC, name), os.path.join(OUT_DIR, name[:-3] + ".o"), []))
+
+    def compile_one(u):
+        src, obj, extra = u
+        cmd = [nvcc] + _flags() + extra + ["-c", src, "-o", obj]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"nvcc failed for {os.path.basename(src)} {extra}:\n{r.stderr}")
+        if verbose and r.stderr:
+            sys.stderr.write(r.stderr)
+        return obj
+
+    jobs = jobs or min(len(units), os.cpu_count() or 4)
+    with cf.ThreadPoolExecutor(max_workers=jobs) as ex:
+        objs = list(ex.map(compile_one, units))
+    tmp = LIB + f".{os.getpid()}.tmp"
+    subprocess.run([nvcc] + ARCH + ["-shared", "-o", tmp] + objs, check=True)
+    os.replace(tmp, LIB)
+    return LIB
+
+
+if __name__ == "__main__":
+    print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))

@@ -1,0 +1,509 @@
+// srmc_capi.cu -- the C ABI of libsrmc (include/srmc.h): solver set-up, the
+// backward time loop, evaluation of the fitted functions, and kernels for the
+// method's primitives.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <limits>
+#include <string>
+#include <vector>
+
+#include "../../include/srmc.h"
+#include "srmc_internal.h"
+
+using srmc::Params;
+
+struct srmc_solver {
+    Params P;                   // device pointers inside point to the buffers below
+    int device;
+    bool fp64, lp1;
+    int mv;                     // model variant of the step kernel
+    int threads;
+    int done_from;              // every step >= done_from has been enqueued
+    double *cellF = nullptr;
+    float *cellF_f = nullptr;
+    double *stepc = nullptr;
+    float *stepc_f = nullptr;
+    float *Y32 = nullptr, *Z32 = nullptr;
+    double *Y64 = nullptr, *Z64 = nullptr;
+    unsigned long long *stats = nullptr;
+};
+
+namespace {
+
+thread_local std::string g_last_error;
+
+srmc_status fail(srmc_status st, const std::string &msg)
+{
+    g_last_error = msg;
+    return st;
+}
+
+srmc_status cuda_fail(cudaError_t e, const char *what)
+{
+    return fail(e == cudaErrorMemoryAllocation ? SRMC_ERR_OOM : SRMC_ERR_CUDA,
+                std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define SRMC_CUDA(call, what)                                   \
+    do {                                                        \
+        cudaError_t e_ = (call);                                \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what);      \
+    } while (0)
+
+double logistic_cdf(double x, double mu)
+{
+    if (x == -INFINITY) return 0.0;
+    if (x == INFINITY) return 1.0;
+    return 1.0 / (1.0 + std::exp(-mu * x));
+}
+
+int pad_to(int v, int m) { return (v + m - 1) / m * m; }
+
+void free_all(srmc_solver *s)
+{
+    cudaFree(s->cellF); cudaFree(s->cellF_f); cudaFree(s->stepc); cudaFree(s->stepc_f);
+    cudaFree(s->Y32); cudaFree(s->Z32); cudaFree(s->Y64); cudaFree(s->Z64); cudaFree(s->stats);
+}
+
+cudaError_t launch_step(const srmc_solver *s, int i, cudaStream_t st)
+{
+    const Params &P = s->P;
+    const int grid = (int)(P.K < 2147483647LL ? P.K : 2147483647LL);
+    switch (P.d) {
+    case 1: return srmc::launch_step_d1(P, i, s->fp64, s->lp1, s->mv, grid, s->threads, st);
+    case 2: return srmc::launch_step_d2(P, i, s->fp64, s->lp1, s->mv, grid, s->threads, st);
+    case 3: return srmc::launch_step_d3(P, i, s->fp64, s->lp1, s->mv, grid, s->threads, st);
+    case 4: return srmc::launch_step_d4(P, i, s->fp64, s->lp1, s->mv, grid, s->threads, st);
+    case 5: return srmc::launch_step_d5(P, i, s->fp64, s->lp1, s->mv, grid, s->threads, st);
+    case 6: return srmc::launch_step_d6(P, i, s->fp64, s->lp1, s->mv, grid, s->threads, st);
+    case 7: return srmc::launch_step_d7(P, i, s->fp64, s->lp1, s->mv, grid, s->threads, st);
+    case 8: return srmc::launch_step_d8(P, i, s->fp64, s->lp1, s->mv, grid, s->threads, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+// ---- kernels of the primitives and of the evaluation ----------------------
+
+__global__ void philox_kernel(const uint32_t *ctr, uint32_t k0, uint32_t k1, long long n,
+                              uint32_t *out)
+{
+    for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < n;
+         a += (long long)gridDim.x * blockDim.x) {
+        unsigned c0 = ctr[4 * a], c1 = ctr[4 * a + 1], c2 = ctr[4 * a + 2], c3 = ctr[4 * a + 3];
+        srmc::philox10(c0, c1, c2, c3, k0, k1);
+        out[4 * a] = c0; out[4 * a + 1] = c1; out[4 * a + 2] = c2; out[4 * a + 3] = c3;
+    }
+}
+
+__global__ void normals_kernel(const uint32_t *w, long long n, double *o64, float *o32)
+{
+    for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < n;
+         a += (long long)gridDim.x * blockDim.x) {
+        if (o64) o64[a] = srmc::normal_of(w[a], 0.0);
+        if (o32) o32[a] = srmc::normal_of(w[a], 0.0f);
+    }
+}
+
+__global__ void locate_kernel(const Params P, const double *x64, const float *x32, long long n,
+                              long long *kout)
+{
+    for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < n;
+         a += (long long)gridDim.x * blockDim.x) {
+        long long k = 0;
+        for (int l = 0; l < P.d; ++l) {
+            int c;
+            if (x64) {
+                double t;
+                c = srmc::locate_dim(x64[a * P.d + l], P.lo[l], P.h[l], P.cells[l], t);
+            } else {
+                float t;
+                c = srmc::locate_dim(x32[a * P.d + l], P.lo_f[l], P.r_f[l], P.cells[l], t);
+            }
+            k += (long long)c * P.stride[l];
+        }
+        kout[a] = k;
+    }
+}
+
+__global__ void start_points_kernel(const Params P, bool fp64, int i, long long k, long long m0,
+                                    long long n, double *xout)
+{
+    for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < n;
+         a += (long long)gridDim.x * blockDim.x) {
+        srmc::Words W;
+        W.init((unsigned)(m0 + a), (unsigned)k, (unsigned)i, P.key0, P.key1);
+        long long rem = k;
+        for (int l = 0; l < P.d; ++l) {
+            const int c = (int)(rem % P.cells[l]);
+            rem /= P.cells[l];
+            const int o = 3 * (P.cell_off[l] + c);
+            const unsigned w = W.next();
+            if (fp64)
+                xout[a * P.d + l] = srmc::sample_cell(w, P.cellF[o], P.cellF[o + 1], P.cellF[o + 2], P.mu);
+            else
+                xout[a * P.d + l] = (double)srmc::sample_cell(w, P.cellF_f[o], P.cellF_f[o + 1],
+                                                              P.cellF_f[o + 2], P.inv_mu_f);
+        }
+    }
+}
+
+__global__ void centres_kernel(const Params P, double *x)
+{
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < P.K;
+         k += (long long)gridDim.x * blockDim.x) {
+        long long rem = k;
+        for (int l = 0; l < P.d; ++l) {
+            const int c = (int)(rem % P.cells[l]);
+            rem /= P.cells[l];
+            x[k * P.d + l] = P.lo[l] + ((double)c + 0.5) * P.h[l];
+        }
+    }
+}
+
+__device__ double g_eval(const Params &P, const double *x)
+{
+    double s = 0.0;
+    for (int l = 0; l < P.d; ++l) s += x[l];
+    if (P.model == srmc::MODEL_COS) return cos(s / P.sqrt_d);
+    if (P.model == srmc::MODEL_LOGISTIC) {
+        const double w = exp(P.T + s);
+        return w / (1.0 + w);
+    }
+    double v = P.prm[0];
+    for (int l = 0; l < P.d; ++l) v += P.prm[1 + l] * x[l];
+    return v;
+}
+
+// Truncated y_i, z_i from the FP64 rows, in the centred basis.
+__global__ void eval_kernel(const Params P, int i, const double *x, long long n, double *y,
+                            double *z)
+{
+    for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < n;
+         a += (long long)gridDim.x * blockDim.x) {
+        const double *xa = x + a * P.d;
+        if (i == P.N) {
+            y[a] = g_eval(P, xa);
+            if (z)
+                for (int l = 0; l < P.q; ++l) z[a * P.q + l] = 0.0;
+            continue;
+        }
+        double phi[srmc::DMAX + 1];
+        phi[0] = 1.0;
+        long long k = 0;
+        for (int l = 0; l < P.d; ++l) {
+            double t;
+            const int c = srmc::locate_dim(xa[l], P.lo[l], P.h[l], P.cells[l], t);
+            k += (long long)c * P.stride[l];
+            phi[1 + l] = 2.0 * (t - (double)c) - 1.0;
+        }
+        const long long row = (long long)i * P.K + k;
+        const double *al = P.Y64 + row * P.ry64;
+        double v = al[0];
+        for (int c = 1; c < P.p; ++c) v += al[c] * phi[c];
+        y[a] = fmin(fmax(v, -P.Cy), P.Cy);
+        if (z) {
+            const double *be = P.Z64 + row * P.rz64;
+            for (int l = 0; l < P.q; ++l) {
+                double w = be[l * P.p];
+                for (int c = 1; c < P.p; ++c) w += be[l * P.p + c] * phi[c];
+                z[a * P.q + l] = fmin(fmax(w, -P.Cz), P.Cz);
+            }
+        }
+    }
+}
+
+int grid_for(long long n, int threads)
+{
+    long long g = (n + threads - 1) / threads;
+    if (g < 1) g = 1;
+    if (g > 65535LL * 32) g = 65535LL * 32;
+    return (int)g;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *srmc_last_error(void) { return g_last_error.c_str(); }
+
+int srmc_version(void) { return 1; }
+
+srmc_status srmc_create(const srmc_problem *pr, const srmc_strata *sa, const srmc_config *cf,
+                        srmc_solver **out)
+{
+    if (!out) return fail(SRMC_ERR_INVALID_ARG, "srmc_create: out is NULL");
+    *out = nullptr;
+    if (!pr || !sa || !cf) return fail(SRMC_ERR_INVALID_ARG, "srmc_create: NULL argument");
+    const int d = pr->d, q = pr->q;
+    if (d < 1 || d > SRMC_DMAX) return fail(SRMC_ERR_INVALID_ARG, "d must be in [1, 8]");
+    if (q != d) return fail(SRMC_ERR_UNSUPPORTED, "this build requires q == d");
+    if (pr->N < 1 || pr->N > 1000000) return fail(SRMC_ERR_INVALID_ARG, "N must be in [1, 1e6]");
+    if (!(pr->T > 0.0) || !std::isfinite(pr->T)) return fail(SRMC_ERR_INVALID_ARG, "T must be > 0");
+    if (!pr->b || !pr->sigma) return fail(SRMC_ERR_INVALID_ARG, "b and sigma are required");
+    for (int l = 0; l < d; ++l)
+        for (int r = 0; r < q; ++r)
+            if (l != r && pr->sigma[l * q + r] != 0.0)
+                return fail(SRMC_ERR_UNSUPPORTED, "this build requires a diagonal sigma");
+    if (pr->model < SRMC_MODEL_COS || pr->model > SRMC_MODEL_AFFINE)
+        return fail(SRMC_ERR_INVALID_ARG, "unknown model");
+    if (pr->n_params < 0 || pr->n_params > SRMC_PMAX || (pr->n_params > 0 && !pr->params))
+        return fail(SRMC_ERR_INVALID_ARG, "params: n_params must be in [0, 24]");
+    const int need = pr->model == SRMC_MODEL_COS ? 4 : pr->model == SRMC_MODEL_AFFINE ? 3 + 2 * d : 0;
+    if (pr->n_params < need) return fail(SRMC_ERR_INVALID_ARG, "too few model parameters");
+    if (!sa->cells || !sa->lo || !sa->hi) return fail(SRMC_ERR_INVALID_ARG, "strata arrays are required");
+    if (!(sa->mu > 0.0) || !std::isfinite(sa->mu)) return fail(SRMC_ERR_INVALID_ARG, "mu must be > 0");
+    long long K = 1, cells_total = 0;
+    for (int l = 0; l < d; ++l) {
+        if (sa->cells[l] < 1) return fail(SRMC_ERR_INVALID_ARG, "cells must be >= 1");
+        if (!(sa->lo[l] < sa->hi[l]) || !std::isfinite(sa->lo[l]) || !std::isfinite(sa->hi[l]))
+            return fail(SRMC_ERR_INVALID_ARG, "need finite lo < hi");
+        K *= sa->cells[l];
+        cells_total += sa->cells[l];
+        if (K > 2147483647LL) return fail(SRMC_ERR_INVALID_ARG, "too many strata (K > 2^31-1)");
+    }
+    const int p = cf->basis == SRMC_LP1 ? d + 1 : 1;
+    if (cf->basis != SRMC_LP0 && cf->basis != SRMC_LP1) return fail(SRMC_ERR_INVALID_ARG, "basis");
+    if (cf->prec != SRMC_FP32 && cf->prec != SRMC_FP64) return fail(SRMC_ERR_INVALID_ARG, "precision");
+    if (cf->M < p) return fail(SRMC_ERR_INVALID_ARG, "M must be >= the basis dimension");
+    if (cf->M > 4294967295LL) return fail(SRMC_ERR_INVALID_ARG, "M must be < 2^32");
+    int threads = cf->block_threads;
+    if (threads == 0) threads = cf->M >= 256 ? 256 : (int)((cf->M + 31) / 32 * 32);
+    if (threads < 32 || threads > srmc::MAX_THREADS || threads % 32)
+        return fail(SRMC_ERR_INVALID_ARG, "block_threads must be a multiple of 32 in [32, 256]");
+
+    srmc_solver *s = new srmc_solver();
+    Params &P = s->P;
+    std::memset(&P, 0, sizeof(P));
+    cudaGetDevice(&s->device);
+    s->fp64 = cf->prec == SRMC_FP64;
+    s->lp1 = cf->basis == SRMC_LP1;
+    s->threads = threads;
+    s->done_from = pr->N;
+    P.d = d; P.q = q; P.N = pr->N; P.p = p;
+    P.K = K; P.M = cf->M;
+    P.model = pr->model;
+    const double kapz = pr->model == SRMC_MODEL_COS ? pr->params[2] : 0.0;
+    s->mv = pr->model == SRMC_MODEL_COS ? (kapz != 0.0 ? srmc::MV_COS_Z : srmc::MV_COS)
+          : pr->model == SRMC_MODEL_LOGISTIC ? srmc::MV_LOGISTIC : srmc::MV_AFFINE;
+    P.zin = (s->mv == srmc::MV_COS_Z || s->mv == srmc::MV_LOGISTIC);
+    P.ry32 = pad_to(p, 4); P.rz32 = pad_to(q * p, 4);
+    P.ry64 = pad_to(p, 2); P.rz64 = pad_to(q * p, 2);
+    long long stride = 1;
+    int off = 0;
+    for (int l = 0; l < d; ++l) {
+        P.cells[l] = sa->cells[l];
+        P.stride[l] = stride; stride *= sa->cells[l];
+        P.cell_off[l] = off; off += sa->cells[l];
+        P.lo[l] = sa->lo[l];
+        P.h[l] = (sa->hi[l] - sa->lo[l]) / (double)sa->cells[l];
+        P.b[l] = pr->b[l];
+        P.sig[l] = pr->sigma[l * q + l];
+        P.lo_f[l] = (float)sa->lo[l];
+        P.r_f[l] = (float)((double)sa->cells[l] / (sa->hi[l] - sa->lo[l]));
+        P.b_f[l] = (float)pr->b[l];
+        P.sig_f[l] = (float)P.sig[l];
+    }
+    P.T = pr->T;
+    P.dt = pr->T / (double)pr->N;
+    P.sdt = std::sqrt(P.dt);
+    P.mu = sa->mu;
+    P.sqrt_d = std::sqrt((double)d);
+    P.dt_f = (float)P.dt; P.sdt_f = (float)P.sdt;
+    P.inv_mu_f = (float)(1.0 / sa->mu);
+    P.inv_sqrt_d_f = (float)(1.0 / std::sqrt((double)d));
+    const double inf = std::numeric_limits<double>::infinity();
+    P.Cy = cf->Cy > 0.0 ? cf->Cy : inf;
+    P.Cz = cf->Cz > 0.0 ? cf->Cz : inf;
+    P.Cy_f = (float)P.Cy; P.Cz_f = (float)P.Cz;
+    P.key0 = (unsigned)(cf->seed & 0xFFFFFFFFull) ^ cf->instance;
+    P.key1 = (unsigned)(cf->seed >> 32);
+    for (int a = 0; a < pr->n_params; ++a) { P.prm[a] = pr->params[a]; P.prm_f[a] = (float)pr->params[a]; }
+
+    // Sampler constants of every cell side (Alg. 3): F(x-), 1 - F(x+), F(x+) - F(x-).
+    std::vector<double> cellF(3 * cells_total);
+    std::vector<float> cellF_f(3 * cells_total);
+    for (int l = 0; l < d; ++l)
+        for (int c = 0; c < sa->cells[l]; ++c) {
+            const double h = P.h[l];
+            const double xlo = c == 0 ? -inf : sa->lo[l] + (double)c * h;
+            const double xhi = c == sa->cells[l] - 1 ? inf : sa->lo[l] + (double)(c + 1) * h;
+            const double Flo = logistic_cdf(xlo, sa->mu);
+            const double Fchi = logistic_cdf(-xhi, sa->mu);
+            const double w = xlo > 0.0 ? logistic_cdf(-xlo, sa->mu) - Fchi
+                                       : logistic_cdf(xhi, sa->mu) - Flo;
+            const int o = 3 * (P.cell_off[l] + c);
+            cellF[o] = Flo; cellF[o + 1] = Fchi; cellF[o + 2] = w;
+            cellF_f[o] = (float)Flo; cellF_f[o + 1] = (float)Fchi; cellF_f[o + 2] = (float)w;
+        }
+    // Per-step driver constants of the cos model: kap e_j^2, kapz s0^2 e_j^2.
+    std::vector<double> stepc(2 * (pr->N + 1), 0.0);
+    std::vector<float> stepc_f(2 * (pr->N + 1), 0.0f);
+    if (pr->model == SRMC_MODEL_COS) {
+        const double lam = pr->params[0], kap = pr->params[1], s0 = pr->params[3];
+        for (int j = 0; j <= pr->N; ++j) {
+            const double tj = (double)j * P.dt;
+            const double e = std::exp(lam * (pr->T - tj));
+            stepc[2 * j] = kap * e * e;
+            stepc[2 * j + 1] = kapz * s0 * s0 * e * e;
+            stepc_f[2 * j] = (float)stepc[2 * j];
+            stepc_f[2 * j + 1] = (float)stepc[2 * j + 1];
+        }
+    }
+
+    auto bail = [&](cudaError_t e, const char *what) {
+        free_all(s);
+        delete s;
+        return cuda_fail(e, what);
+    };
+    cudaError_t e;
+    const size_t rows = (size_t)pr->N * (size_t)K;
+    if ((e = cudaMalloc(&s->cellF, sizeof(double) * cellF.size())) != cudaSuccess) return bail(e, "cudaMalloc");
+    if ((e = cudaMalloc(&s->cellF_f, sizeof(float) * cellF_f.size())) != cudaSuccess) return bail(e, "cudaMalloc");
+    if ((e = cudaMalloc(&s->stepc, sizeof(double) * stepc.size())) != cudaSuccess) return bail(e, "cudaMalloc");
+    if ((e = cudaMalloc(&s->stepc_f, sizeof(float) * stepc_f.size())) != cudaSuccess) return bail(e, "cudaMalloc");
+    if ((e = cudaMalloc(&s->Y64, sizeof(double) * rows * P.ry64)) != cudaSuccess) return bail(e, "cudaMalloc Y64");
+    if ((e = cudaMalloc(&s->Z64, sizeof(double) * rows * P.rz64)) != cudaSuccess) return bail(e, "cudaMalloc Z64");
+    if (!s->fp64) {
+        if ((e = cudaMalloc(&s->Y32, sizeof(float) * rows * P.ry32)) != cudaSuccess) return bail(e, "cudaMalloc Y32");
+        if ((e = cudaMalloc(&s->Z32, sizeof(float) * rows * P.rz32)) != cudaSuccess) return bail(e, "cudaMalloc Z32");
+    }
+    if ((e = cudaMalloc(&s->stats, sizeof(unsigned long long) * 4)) != cudaSuccess) return bail(e, "cudaMalloc");
+    if ((e = cudaMemcpy(s->cellF, cellF.data(), sizeof(double) * cellF.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return bail(e, "cudaMemcpy");
+    if ((e = cudaMemcpy(s->cellF_f, cellF_f.data(), sizeof(float) * cellF_f.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return bail(e, "cudaMemcpy");
+    if ((e = cudaMemcpy(s->stepc, stepc.data(), sizeof(double) * stepc.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return bail(e, "cudaMemcpy");
+    if ((e = cudaMemcpy(s->stepc_f, stepc_f.data(), sizeof(float) * stepc_f.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return bail(e, "cudaMemcpy");
+    if ((e = cudaMemset(s->Y64, 0, sizeof(double) * rows * P.ry64)) != cudaSuccess) return bail(e, "cudaMemset");
+    if ((e = cudaMemset(s->Z64, 0, sizeof(double) * rows * P.rz64)) != cudaSuccess) return bail(e, "cudaMemset");
+    if (s->Y32 && (e = cudaMemset(s->Y32, 0, sizeof(float) * rows * P.ry32)) != cudaSuccess) return bail(e, "cudaMemset");
+    if (s->Z32 && (e = cudaMemset(s->Z32, 0, sizeof(float) * rows * P.rz32)) != cudaSuccess) return bail(e, "cudaMemset");
+    if ((e = cudaMemset(s->stats, 0, sizeof(unsigned long long) * 4)) != cudaSuccess) return bail(e, "cudaMemset");
+    P.cellF = s->cellF; P.cellF_f = s->cellF_f; P.stepc = s->stepc; P.stepc_f = s->stepc_f;
+    P.Y32 = s->Y32; P.Z32 = s->Z32; P.Y64 = s->Y64; P.Z64 = s->Z64; P.stats = s->stats;
+    *out = s;
+    g_last_error.clear();
+    return SRMC_OK;
+}
+
+void srmc_destroy(srmc_solver *s)
+{
+    if (!s) return;
+    free_all(s);
+    delete s;
+}
+
+srmc_status srmc_solve_step(srmc_solver *s, int i, void *stream)
+{
+    if (!s) return fail(SRMC_ERR_INVALID_ARG, "srmc_solve_step: NULL solver");
+    if (i < 0 || i >= s->P.N) return fail(SRMC_ERR_INVALID_ARG, "srmc_solve_step: i out of range");
+    if (s->done_from > i + 1) return fail(SRMC_ERR_STATE, "srmc_solve_step: steps > i not solved yet");
+    SRMC_CUDA(launch_step(s, i, (cudaStream_t)stream), "step kernel launch");
+    if (i < s->done_from) s->done_from = i;
+    return SRMC_OK;
+}
+
+srmc_status srmc_solve(srmc_solver *s, void *stream)
+{
+    if (!s) return fail(SRMC_ERR_INVALID_ARG, "srmc_solve: NULL solver");
+    for (int i = s->P.N - 1; i >= 0; --i) {
+        SRMC_CUDA(launch_step(s, i, (cudaStream_t)stream), "step kernel launch");
+    }
+    s->done_from = 0;
+    return SRMC_OK;
+}
+
+srmc_status srmc_eval(const srmc_solver *s, int i, const double *x, long long n, double *y,
+                      double *z, void *stream)
+{
+    if (!s) return fail(SRMC_ERR_INVALID_ARG, "srmc_eval: NULL solver");
+    if (i < 0 || i > s->P.N) return fail(SRMC_ERR_INVALID_ARG, "srmc_eval: i out of range");
+    if (n < 0) return fail(SRMC_ERR_INVALID_ARG, "srmc_eval: n < 0");
+    if (n == 0) return SRMC_OK;
+    if (!x || !y) return fail(SRMC_ERR_INVALID_ARG, "srmc_eval: NULL buffer");
+    if (i < s->P.N && s->done_from > i) return fail(SRMC_ERR_STATE, "srmc_eval: step i not solved");
+    eval_kernel<<<grid_for(n, 128), 128, 0, (cudaStream_t)stream>>>(s->P, i, x, n, y, z);
+    SRMC_CUDA(cudaGetLastError(), "eval kernel launch");
+    return SRMC_OK;
+}
+
+srmc_status srmc_centres(const srmc_solver *s, double *x, void *stream)
+{
+    if (!s || !x) return fail(SRMC_ERR_INVALID_ARG, "srmc_centres: NULL argument");
+    centres_kernel<<<grid_for(s->P.K, 128), 128, 0, (cudaStream_t)stream>>>(s->P, x);
+    SRMC_CUDA(cudaGetLastError(), "centres kernel launch");
+    return SRMC_OK;
+}
+
+srmc_status srmc_table(const srmc_solver *s, const double **y64, const double **z64, int *p,
+                       int *ry, int *rz, long long *K)
+{
+    if (!s) return fail(SRMC_ERR_INVALID_ARG, "srmc_table: NULL solver");
+    if (y64) *y64 = s->Y64;
+    if (z64) *z64 = s->Z64;
+    if (p) *p = s->P.p;
+    if (ry) *ry = s->P.ry64;
+    if (rz) *rz = s->P.rz64;
+    if (K) *K = s->P.K;
+    return SRMC_OK;
+}
+
+srmc_status srmc_stats(const srmc_solver *s, unsigned long long out[3])
+{
+    if (!s || !out) return fail(SRMC_ERR_INVALID_ARG, "srmc_stats: NULL argument");
+    unsigned long long h[4];
+    SRMC_CUDA(cudaDeviceSynchronize(), "srmc_stats: synchronize");
+    SRMC_CUDA(cudaMemcpy(h, s->stats, sizeof(h), cudaMemcpyDeviceToHost), "srmc_stats: copy");
+    out[0] = h[0];
+    out[1] = h[1];
+    long long steps = 0;
+    for (int i = s->done_from; i < s->P.N; ++i) steps += (long long)(s->P.N - i);
+    out[2] = (unsigned long long)(steps * s->P.K * s->P.M);
+    return SRMC_OK;
+}
+
+srmc_status srmc_philox(const uint32_t *ctr, const uint32_t key[2], long long n, uint32_t *out,
+                        void *stream)
+{
+    if (n < 0 || !key) return fail(SRMC_ERR_INVALID_ARG, "srmc_philox: bad argument");
+    if (n == 0) return SRMC_OK;
+    if (!ctr || !out) return fail(SRMC_ERR_INVALID_ARG, "srmc_philox: NULL buffer");
+    philox_kernel<<<grid_for(n, 128), 128, 0, (cudaStream_t)stream>>>(ctr, key[0], key[1], n, out);
+    SRMC_CUDA(cudaGetLastError(), "philox kernel launch");
+    return SRMC_OK;
+}
+
+srmc_status srmc_normals(const uint32_t *w, long long n, double *o64, float *o32, void *stream)
+{
+    if (n < 0) return fail(SRMC_ERR_INVALID_ARG, "srmc_normals: n < 0");
+    if (n == 0) return SRMC_OK;
+    if (!w || (!o64 && !o32)) return fail(SRMC_ERR_INVALID_ARG, "srmc_normals: NULL buffer");
+    normals_kernel<<<grid_for(n, 128), 128, 0, (cudaStream_t)stream>>>(w, n, o64, o32);
+    SRMC_CUDA(cudaGetLastError(), "normals kernel launch");
+    return SRMC_OK;
+}
+
+srmc_status srmc_locate(const srmc_solver *s, const double *x64, const float *x32, long long n,
+                        long long *k, void *stream)
+{
+    if (!s || n < 0) return fail(SRMC_ERR_INVALID_ARG, "srmc_locate: bad argument");
+    if (n == 0) return SRMC_OK;
+    if (!k || (!x64 == !x32)) return fail(SRMC_ERR_INVALID_ARG, "srmc_locate: need exactly one of x64, x32");
+    locate_kernel<<<grid_for(n, 128), 128, 0, (cudaStream_t)stream>>>(s->P, x64, x32, n, k);
+    SRMC_CUDA(cudaGetLastError(), "locate kernel launch");
+    return SRMC_OK;
+}
+
+srmc_status srmc_start_points(const srmc_solver *s, int i, long long k, long long m0, long long n,
+                              double *x, void *stream)
+{
+    if (!s || n < 0 || i < 0 || i >= s->P.N || k < 0 || k >= s->P.K || m0 < 0 ||
+        m0 + n > 4294967296LL)
+        return fail(SRMC_ERR_INVALID_ARG, "srmc_start_points: bad argument");
+    if (n == 0) return SRMC_OK;
+    if (!x) return fail(SRMC_ERR_INVALID_ARG, "srmc_start_points: NULL buffer");
+    start_points_kernel<<<grid_for(n, 128), 128, 0, (cudaStream_t)stream>>>(s->P, s->fp64, i, k, m0, n, x);
+    SRMC_CUDA(cudaGetLastError(), "start points kernel launch");
+    return SRMC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,285 @@
+// srmc_device.cuh -- device building blocks of the SRMDP hot path (sm_103a).
+//
+// Every function here is one step of Alg. SRMDP or of the simulation it
+// relies on; the passage is named beside each.  FP32 and FP64 forms are
+// overloads of the same definition.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+#include <math_constants.h>
+
+namespace srmc {
+
+constexpr int DMAX = 8;
+constexpr int PMAX = 24;
+constexpr int MAX_THREADS = 256;
+constexpr int MAX_WARPS = MAX_THREADS / 32;
+
+enum Model { MODEL_COS = 0, MODEL_LOGISTIC = 1, MODEL_AFFINE = 2 };
+
+// Everything a step launch needs, passed by value as the kernel parameter.
+struct Params {
+    int d, q, N, p;                 // dims, steps, basis dimension
+    int ry32, rz32, ry64, rz64;     // row strides of the coefficient tables
+    long long K, M;
+    int model, zin;
+    int cells[DMAX];
+    long long stride[DMAX];         // stratum index stride of each dimension
+    int cell_off[DMAX];             // offset of dimension l in cellF
+    double lo[DMAX], h[DMAX], b[DMAX], sig[DMAX];
+    float lo_f[DMAX], r_f[DMAX], b_f[DMAX], sig_f[DMAX];
+    double T, dt, sdt, mu, sqrt_d;
+    float dt_f, sdt_f, inv_mu_f, inv_sqrt_d_f;
+    double Cy, Cz;                  // +inf when disabled
+    float Cy_f, Cz_f;
+    unsigned key0, key1;
+    double prm[PMAX];
+    float prm_f[PMAX];
+    const double *cellF;            // [sum cells][3]: F(x-), 1 - F(x+), F(x+) - F(x-)
+    const float *cellF_f;
+    const double *stepc;            // [N+1][2] per-step driver constants
+    const float *stepc_f;
+    float *Y32, *Z32;               // [N][K][ry32], [N][K][rz32]
+    double *Y64, *Z64;              // [N][K][ry64], [N][K][rz64]
+    unsigned long long *stats;      // [0] LP1->LP0 fallbacks, [1] non-finite rows
+};
+
+// ---- Philox-4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) --------------------
+__device__ __forceinline__ void philox10(unsigned &c0, unsigned &c1, unsigned &c2, unsigned &c3,
+                                         unsigned k0, unsigned k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const unsigned hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
+        const unsigned hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
+        const unsigned n0 = hi1 ^ c1 ^ k0;
+        const unsigned n2 = hi0 ^ c3 ^ k1;
+        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+        k0 += 0x9E3779B9u; k1 += 0xBB67AE85u;
+    }
+}
+
+// The word stream of one path of cloud C_{i,k}: counter (n/4, m, k, i).
+// Words are consumed in order; the position is uniform across a warp, so
+// the refill branch does not diverge.
+struct Words {
+    unsigned m, k, i, k0, k1, blk;
+    int pos;
+    unsigned w0, w1, w2, w3;
+    __device__ __forceinline__ void gen()
+    {
+        w0 = blk; w1 = m; w2 = k; w3 = i;
+        philox10(w0, w1, w2, w3, k0, k1);
+    }
+    __device__ __forceinline__ void init(unsigned m_, unsigned k_, unsigned i_, unsigned key0,
+                                         unsigned key1)
+    {
+        m = m_; k = k_; i = i_; k0 = key0; k1 = key1; blk = 0; pos = 0;
+        gen();
+    }
+    __device__ __forceinline__ unsigned next()
+    {
+        if (pos == 4) { ++blk; gen(); pos = 0; }
+        const unsigned r = pos == 0 ? w0 : pos == 1 ? w1 : pos == 2 ? w2 : w3;
+        ++pos;
+        return r;
+    }
+};
+
+// ---- standard normal by inversion: xi = Phi^{-1}((w + 1/2) 2^-32) ----------
+// The upper half is taken from the exact complement (~w + 1/2) 2^-32.
+__device__ __forceinline__ double normal_of(unsigned w, double)
+{
+    const bool up = w >= 0x80000000u;
+    const unsigned v = up ? ~w : w;
+    const double x = normcdfinv(((double)v + 0.5) * 0x1p-32);
+    return up ? -x : x;
+}
+__device__ __forceinline__ float normal_of(unsigned w, float)
+{
+    const bool up = w >= 0x80000000u;
+    const unsigned v = up ? ~w : w;
+    const float x = normcdfinvf(fmaf(__uint2float_rn(v), 0x1p-32f, 0x1p-33f));
+    return up ? -x : x;
+}
+
+// ---- restricted logistic sampler (assumption A_nu, Alg. 3) ------------------
+// x = log(p / qc) / mu, p = F(x-) + U w, qc = 1 - F(x+) + (1 - U) w,
+// w = F(x+) - F(x-): the inverse of the cell's restricted CDF.
+__device__ __forceinline__ double sample_cell(unsigned w, double Flo, double Fchi, double wid,
+                                              double mu)
+{
+    const double U = ((double)w + 0.5) * 0x1p-32;
+    const double Uc = ((double)(~w) + 0.5) * 0x1p-32;
+    const double p = Flo + U * wid;
+    const double qc = Fchi + Uc * wid;
+    return log(p / qc) / mu;
+}
+__device__ __forceinline__ float sample_cell(unsigned w, float Flo, float Fchi, float wid,
+                                             float inv_mu)
+{
+    const float U = fmaf(__uint2float_rn(w), 0x1p-32f, 0x1p-33f);
+    const float Uc = fmaf(__uint2float_rn(~w), 0x1p-32f, 0x1p-33f);
+    const float p = fmaf(U, wid, Flo);
+    const float qc = fmaf(Uc, wid, Fchi);
+    return logf(p / qc) * inv_mu;
+}
+
+// ---- stratum location (assumption A_Strat, half-open cells) ----------------
+// Returns the cell and the cell coordinate t = (x - lo)/h, from which the
+// centred LP1 basis value 2 (t - c) - 1 follows.
+__device__ __forceinline__ int locate_dim(double x, double lo, double h, int C, double &t)
+{
+    t = __ddiv_rn(__dsub_rn(x, lo), h);
+    if (!(t >= 0.0)) return 0;
+    if (t >= (double)C) return C - 1;
+    const int c = (int)floor(t);
+    return c > C - 1 ? C - 1 : c;
+}
+__device__ __forceinline__ int locate_dim(float x, float lo, float r, int C, float &t)
+{
+    t = __fmul_rn(__fsub_rn(x, lo), r);
+    if (!(t >= 0.0f)) return 0;
+    if (t >= (float)C) return C - 1;
+    const int c = (int)floorf(t);
+    return c > C - 1 ? C - 1 : c;
+}
+
+// Precision traits: which parameter copies a form reads.
+template <typename R> struct Form;
+template <> struct Form<double> {
+    __device__ static double lo(const Params &P, int l) { return P.lo[l]; }
+    __device__ static double scale(const Params &P, int l) { return P.h[l]; }   // divide by h
+    __device__ static double b(const Params &P, int l) { return P.b[l]; }
+    __device__ static double sig(const Params &P, int l) { return P.sig[l]; }
+    __device__ static double dt(const Params &P) { return P.dt; }
+    __device__ static double sdt(const Params &P) { return P.sdt; }
+    __device__ static double Cy(const Params &P) { return P.Cy; }
+    __device__ static double Cz(const Params &P) { return P.Cz; }
+    __device__ static double prm(const Params &P, int a) { return P.prm[a]; }
+    __device__ static double mu_arg(const Params &P) { return P.mu; }
+    __device__ static const double *cellF(const Params &P) { return P.cellF; }
+    __device__ static const double *stepc(const Params &P) { return P.stepc; }
+    __device__ static const double *Ytab(const Params &P) { return P.Y64; }
+    __device__ static const double *Ztab(const Params &P) { return P.Z64; }
+    __device__ static int ry(const Params &P) { return P.ry64; }
+    __device__ static int rz(const Params &P) { return P.rz64; }
+};
+template <> struct Form<float> {
+    __device__ static float lo(const Params &P, int l) { return P.lo_f[l]; }
+    __device__ static float scale(const Params &P, int l) { return P.r_f[l]; }  // multiply by r
+    __device__ static float b(const Params &P, int l) { return P.b_f[l]; }
+    __device__ static float sig(const Params &P, int l) { return P.sig_f[l]; }
+    __device__ static float dt(const Params &P) { return P.dt_f; }
+    __device__ static float sdt(const Params &P) { return P.sdt_f; }
+    __device__ static float Cy(const Params &P) { return P.Cy_f; }
+    __device__ static float Cz(const Params &P) { return P.Cz_f; }
+    __device__ static float prm(const Params &P, int a) { return P.prm_f[a]; }
+    __device__ static float mu_arg(const Params &P) { return P.inv_mu_f; }
+    __device__ static const float *cellF(const Params &P) { return P.cellF_f; }
+    __device__ static const float *stepc(const Params &P) { return P.stepc_f; }
+    __device__ static const float *Ytab(const Params &P) { return P.Y32; }
+    __device__ static const float *Ztab(const Params &P) { return P.Z32; }
+    __device__ static int ry(const Params &P) { return P.ry32; }
+    __device__ static int rz(const Params &P) { return P.rz32; }
+};
+
+__device__ __forceinline__ void sincos_r(double s, double *sn, double *cs) { sincos(s, sn, cs); }
+__device__ __forceinline__ void sincos_r(float s, float *sn, float *cs) { sincosf(s, sn, cs); }
+__device__ __forceinline__ double cos_r(double s) { return cos(s); }
+__device__ __forceinline__ float cos_r(float s) { return cosf(s); }
+__device__ __forceinline__ double exp_r(double s) { return exp(s); }
+__device__ __forceinline__ float exp_r(float s) { return expf(s); }
+__device__ __forceinline__ double clamp_r(double v, double L) { return fmin(fmax(v, -L), L); }
+__device__ __forceinline__ float clamp_r(float v, float L) { return fminf(fmaxf(v, -L), L); }
+__device__ __forceinline__ double sqrtd_of(const Params &P, double) { return P.sqrt_d; }
+
+// ---- terminal condition g and driver f_j (Sec. 1, eq. fbsde; models) --------
+template <typename R, int D, int MODEL>
+__device__ __forceinline__ R model_g(const Params &P, const R (&x)[D])
+{
+    R s = x[0];
+#pragma unroll
+    for (int l = 1; l < D; ++l) s += x[l];
+    if (MODEL == MODEL_COS) {
+        if (sizeof(R) == 8) return cos_r(s / (R)P.sqrt_d);
+        return cos_r(s * (R)P.inv_sqrt_d_f);
+    } else if (MODEL == MODEL_LOGISTIC) {
+        const R w = exp_r((R)P.T + s);
+        return w / ((R)1 + w);
+    } else {
+        R v = Form<R>::prm(P, 0);
+#pragma unroll
+        for (int l = 0; l < D; ++l) v += Form<R>::prm(P, 1 + l) * x[l];
+        return v;
+    }
+}
+
+// f_j(x, y, z); z is used only when ZIN.
+template <typename R, int D, int MODEL, bool ZIN>
+__device__ __forceinline__ R model_f(const Params &P, int j, const R (&x)[D], R y, const R *z)
+{
+    if (MODEL == MODEL_COS) {
+        R s = x[0];
+#pragma unroll
+        for (int l = 1; l < D; ++l) s += x[l];
+        s = (sizeof(R) == 8) ? s / (R)P.sqrt_d : s * (R)P.inv_sqrt_d_f;
+        const R lam = Form<R>::prm(P, 0), kap = Form<R>::prm(P, 1), s0 = Form<R>::prm(P, 3);
+        const R *sc = Form<R>::stepc(P) + 2 * j;
+        const R c1 = __ldg(sc), c2 = __ldg(sc + 1);     // kap e_j^2, kapz s0^2 e_j^2
+        R v = (lam + (R)0.5 * s0 * s0) * y + kap * y * y;
+        if (ZIN) {
+            R sn, cs;
+            sincos_r(s, &sn, &cs);
+            R zz = (R)0;
+#pragma unroll
+            for (int l = 0; l < D; ++l) zz += z[l] * z[l];
+            v += Form<R>::prm(P, 2) * zz - c1 * cs * cs - c2 * sn * sn;
+        } else {
+            const R cs = cos_r(s);
+            v -= c1 * cs * cs;
+        }
+        return v;
+    } else if (MODEL == MODEL_LOGISTIC) {
+        R sz = (R)0;
+#pragma unroll
+        for (int l = 0; l < D; ++l) sz += z[l];
+        return sz * (y - (R)(2 + D) / (R)(2 * D));
+    } else {
+        R v = Form<R>::prm(P, 1 + D);
+#pragma unroll
+        for (int l = 0; l < D; ++l) v += Form<R>::prm(P, 2 + D + l) * x[l];
+        return v + Form<R>::prm(P, 2 + 2 * D) * y;
+    }
+}
+
+// ---- table rows ----------------------------------------------------------
+template <int PP>
+__device__ __forceinline__ void load_row(const float *ptr, float (&out)[PP])
+{
+    constexpr int V = (PP + 3) / 4;
+    const float4 *p4 = reinterpret_cast<const float4 *>(ptr);
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        const float4 t = __ldg(p4 + v);
+        if (4 * v + 0 < PP) out[4 * v + 0] = t.x;
+        if (4 * v + 1 < PP) out[4 * v + 1] = t.y;
+        if (4 * v + 2 < PP) out[4 * v + 2] = t.z;
+        if (4 * v + 3 < PP) out[4 * v + 3] = t.w;
+    }
+}
+template <int PP>
+__device__ __forceinline__ void load_row(const double *ptr, double (&out)[PP])
+{
+    constexpr int V = (PP + 1) / 2;
+    const double2 *p2 = reinterpret_cast<const double2 *>(ptr);
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        const double2 t = __ldg(p2 + v);
+        if (2 * v + 0 < PP) out[2 * v + 0] = t.x;
+        if (2 * v + 1 < PP) out[2 * v + 1] = t.y;
+    }
+}
+
+}  // namespace srmc

@@ -1,0 +1,428 @@
+// srmc_step.cu -- one backward step i of Alg. SRMDP for every stratum.
+//
+// Compiled once per dimension D (-DSRMC_STEP_D=D) so that every per-path
+// array lives in registers.  One thread block owns one stratum H_k at a time
+// (grid-stride over k); its threads share the M paths of the cloud C_{i,k}.
+//
+//   phase A  per path m: start point x_i ~ nu_k (Alg. 3), Euler to t_N
+//            (Alg. 2), at every later step locate the stratum of X_{j+1},
+//            read its fitted row and evaluate y_{j+1}(X_{j+1}), z_{j+1}(X_{j+1})
+//            (truncated), accumulate S_{Y,i+1} = g(X_N) + sum_{j>i} f_j dt
+//            (eq. PsiM); add phi phi^T, phi S dW_i/dt, phi S to the moments.
+//   Z fit    Cholesky of the Gram matrix in FP64, beta = G^{-1} r_Z.
+//   phase B  per path: regenerate x_i, dW_i, X_{i+1} from the same counters,
+//            f_i(x_i, y_{i+1}(X_{i+1}), z_i(x_i)) with the new beta (Z before Y),
+//            add phi f_i to the moments.
+//   Y fit    alpha = G^{-1} (r_S + dt r_F); write row (i, k).
+//
+// Moments: FP64 form accumulates in double per thread.  FP32 form
+// accumulates in float per thread over blocks of FLUSH paths, then reduces
+// each entry across the warp and carries the warp sums in double, so the
+// rounding error of a moment does not grow with M.
+#include "srmc_internal.h"
+
+#ifndef SRMC_STEP_D
+#error "compile with -DSRMC_STEP_D=<dimension>"
+#endif
+
+namespace srmc {
+namespace {
+
+constexpr int FLUSH = 8;
+
+template <int E>
+struct Moments64 {
+    double a[E];
+    __device__ void zero() {
+#pragma unroll
+        for (int e = 0; e < E; ++e) a[e] = 0.0;
+    }
+    __device__ void add(int e, double v) { a[e] += v; }
+    __device__ void flush(int) {}
+    // Leaves the warp total of entry e in lane (e & 31), slot e >> 5.
+    __device__ void finish(double (&out)[(E + 31) / 32], int lane) {
+#pragma unroll
+        for (int s = 0; s < (E + 31) / 32; ++s) out[s] = 0.0;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            double v = a[e];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == (e & 31)) out[e >> 5] = v;
+        }
+    }
+};
+
+template <int E>
+struct Moments32 {
+    float a[E];
+    double c[(E + 31) / 32];
+    __device__ void zero() {
+#pragma unroll
+        for (int e = 0; e < E; ++e) a[e] = 0.0f;
+#pragma unroll
+        for (int s = 0; s < (E + 31) / 32; ++s) c[s] = 0.0;
+    }
+    __device__ void add(int e, float v) { a[e] += v; }
+    __device__ void flush(int lane) {
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            float v = a[e];
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == (e & 31)) c[e >> 5] += (double)v;
+            a[e] = 0.0f;
+        }
+    }
+    __device__ void finish(double (&out)[(E + 31) / 32], int lane) {
+        flush(lane);
+#pragma unroll
+        for (int s = 0; s < (E + 31) / 32; ++s) out[s] = c[s];
+    }
+};
+
+template <typename R, int E> struct MomentsOf;
+template <int E> struct MomentsOf<double, E> { using type = Moments64<E>; };
+template <int E> struct MomentsOf<float, E> { using type = Moments32<E>; };
+
+// Block-wide totals of E entries: every warp parks its totals in smem, then
+// threads sum the warps in a fixed order (deterministic).
+template <int E>
+__device__ void block_totals(const double (&lanev)[(E + 31) / 32], double (*red)[E], double *tot,
+                             int lane, int warp, int nwarps)
+{
+#pragma unroll
+    for (int s = 0; s < (E + 31) / 32; ++s) {
+        const int e = s * 32 + lane;
+        if (e < E) red[warp][e] = lanev[s];
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < E; e += blockDim.x) {
+        double v = 0.0;
+        for (int w = 0; w < nwarps; ++w) v += red[w][e];
+        tot[e] = v;
+    }
+    __syncthreads();
+}
+
+// Cholesky factor of the p x p Gram matrix (packed upper triangle, row-major
+// pairs a <= b) into L (row-major p x p).  Returns false if a pivot is below
+// 1e-12 of the trace (numerically singular).
+template <int p>
+__device__ bool cholesky(const double *Gp, double *L)
+{
+    double G[p][p];
+    int e = 0;
+#pragma unroll
+    for (int a = 0; a < p; ++a)
+#pragma unroll
+        for (int b = a; b < p; ++b) { G[a][b] = Gp[e]; G[b][a] = Gp[e]; ++e; }
+    double tr = 0.0;
+#pragma unroll
+    for (int a = 0; a < p; ++a) tr += G[a][a];
+    for (int a = 0; a < p; ++a) {
+        for (int b = 0; b <= a; ++b) {
+            double s = G[a][b];
+            for (int c = 0; c < b; ++c) s -= L[a * p + c] * L[b * p + c];
+            if (a == b) {
+                if (!(s > 1e-12 * tr)) return false;
+                L[a * p + a] = sqrt(s);
+            } else {
+                L[a * p + b] = s / L[b * p + b];
+            }
+        }
+        for (int b = a + 1; b < p; ++b) L[a * p + b] = 0.0;
+    }
+    return true;
+}
+
+template <int p>
+__device__ void chol_solve(const double *L, const double *r, double *x)
+{
+    double y[p];
+    for (int a = 0; a < p; ++a) {
+        double s = r[a];
+        for (int c = 0; c < a; ++c) s -= L[a * p + c] * y[c];
+        y[a] = s / L[a * p + a];
+    }
+    for (int a = p - 1; a >= 0; --a) {
+        double s = y[a];
+        for (int c = a + 1; c < p; ++c) s -= L[c * p + a] * x[c];
+        x[a] = s / L[a * p + a];
+    }
+}
+
+// y_{j}(x), z_{j}(x) from the row of the stratum holding x (truncated), or
+// g(x) when j == N.
+template <typename R, int D, bool LP1, int MODEL, bool ZIN>
+__device__ __forceinline__ void eval_at(const Params &P, int j, const R (&x)[D], R &y, R (&z)[D])
+{
+    constexpr int p = LP1 ? D + 1 : 1;
+    if (j == P.N) {
+        y = model_g<R, D, MODEL>(P, x);
+        return;
+    }
+    long long kk = 0;
+    R phi[p];
+    phi[0] = (R)1;
+#pragma unroll
+    for (int l = 0; l < D; ++l) {
+        R t;
+        const int c = locate_dim(x[l], Form<R>::lo(P, l), Form<R>::scale(P, l), P.cells[l], t);
+        kk += (long long)c * P.stride[l];
+        if (LP1) phi[1 + l] = (R)2 * (t - (R)c) - (R)1;
+    }
+    const long long row = (long long)j * P.K + kk;
+    R a[p];
+    load_row<p>(Form<R>::Ytab(P) + row * Form<R>::ry(P), a);
+    R v = a[0];
+#pragma unroll
+    for (int c = 1; c < p; ++c) v += a[c] * phi[c];
+    y = clamp_r(v, Form<R>::Cy(P));
+    if (ZIN) {
+        R bz[D * p];
+        load_row<D * p>(Form<R>::Ztab(P) + row * Form<R>::rz(P), bz);
+#pragma unroll
+        for (int l = 0; l < D; ++l) {
+            R w = bz[l * p];
+#pragma unroll
+            for (int c = 1; c < p; ++c) w += bz[l * p + c] * phi[c];
+            z[l] = clamp_r(w, Form<R>::Cz(P));
+        }
+    }
+}
+
+template <typename R, int D, bool LP1, int MODEL, bool ZIN>
+__global__ void __launch_bounds__(MAX_THREADS) step_kernel(const Params P, const int i)
+{
+    constexpr int p = LP1 ? D + 1 : 1;
+    constexpr int q = D;
+    constexpr int EG = LP1 ? p * (p + 1) / 2 : 0;
+    constexpr int EZ = q * p;
+    constexpr int EA = EG + EZ + p;
+    constexpr int EB = p;
+    using MA = typename MomentsOf<R, EA>::type;
+    using MB = typename MomentsOf<R, EB>::type;
+
+    __shared__ double redA[MAX_WARPS][EA];
+    __shared__ double totA[EA];
+    __shared__ double redB[MAX_WARPS][EB];
+    __shared__ double totB[EB];
+    __shared__ double Ls[p * p];
+    __shared__ double beta_s[q * p];
+    __shared__ R beta_r[q * p];
+    __shared__ int ok_s;
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const R dt = Form<R>::dt(P), sdt = Form<R>::sdt(P), inv_dt = (R)1 / dt;
+
+    for (long long k = blockIdx.x; k < P.K; k += gridDim.x) {
+        // Cells of H_k and the sampler constants of each of its sides.
+        int cell[D];
+        R Flo[D], Fchi[D], Wd[D];
+        {
+            long long rem = k;
+#pragma unroll
+            for (int l = 0; l < D; ++l) {
+                cell[l] = (int)(rem % P.cells[l]);
+                rem /= P.cells[l];
+                const R *cf = Form<R>::cellF(P) + 3 * (P.cell_off[l] + cell[l]);
+                Flo[l] = __ldg(cf); Fchi[l] = __ldg(cf + 1); Wd[l] = __ldg(cf + 2);
+            }
+        }
+
+        // ---------------- phase A: responses of the Z and Y fits ---------------
+        MA mA;
+        mA.zero();
+        int since_flush = 0;
+        for (long long m0 = 0; m0 < P.M; m0 += blockDim.x) {
+            const long long m = m0 + threadIdx.x;
+            const bool valid = m < P.M;
+            Words W;
+            W.init((unsigned)m, (unsigned)k, (unsigned)i, P.key0, P.key1);
+            R x[D], phi[p], dwi[D], xj[D], zj[D], yn, zn[D];
+            phi[0] = (R)1;
+#pragma unroll
+            for (int l = 0; l < D; ++l) {
+                x[l] = sample_cell(W.next(), Flo[l], Fchi[l], Wd[l], Form<R>::mu_arg(P));
+                if (LP1) {
+                    R t;
+                    if (sizeof(R) == 8) t = (x[l] - (R)P.lo[l]) / (R)P.h[l];
+                    else t = (x[l] - (R)P.lo_f[l]) * (R)P.r_f[l];
+                    phi[1 + l] = (R)2 * (t - (R)cell[l]) - (R)1;
+                }
+            }
+#pragma unroll
+            for (int l = 0; l < D; ++l) {
+                dwi[l] = sdt * normal_of(W.next(), (R)0);
+                xj[l] = x[l] + Form<R>::b(P, l) * dt + Form<R>::sig(P, l) * dwi[l];
+            }
+            eval_at<R, D, LP1, MODEL, ZIN>(P, i + 1, xj, yn, zj);
+            R S = (R)0;
+            for (int j = i + 1; j < P.N; ++j) {
+                R xn[D];
+#pragma unroll
+                for (int l = 0; l < D; ++l) {
+                    const R dw = sdt * normal_of(W.next(), (R)0);
+                    xn[l] = xj[l] + Form<R>::b(P, l) * dt + Form<R>::sig(P, l) * dw;
+                }
+                eval_at<R, D, LP1, MODEL, ZIN>(P, j + 1, xn, yn, zn);
+                S += dt * model_f<R, D, MODEL, ZIN>(P, j, xj, yn, zj);
+#pragma unroll
+                for (int l = 0; l < D; ++l) { xj[l] = xn[l]; zj[l] = zn[l]; }
+            }
+            S += model_g<R, D, MODEL>(P, xj);
+            if (valid) {
+                int e = 0;
+                if (LP1) {
+#pragma unroll
+                    for (int a = 0; a < p; ++a)
+#pragma unroll
+                        for (int b = a; b < p; ++b) mA.add(e++, phi[a] * phi[b]);
+                }
+#pragma unroll
+                for (int l = 0; l < q; ++l) {
+                    const R wz = S * dwi[l] * inv_dt;
+#pragma unroll
+                    for (int a = 0; a < p; ++a) mA.add(EG + l * p + a, phi[a] * wz);
+                }
+#pragma unroll
+                for (int a = 0; a < p; ++a) mA.add(EG + EZ + a, phi[a] * S);
+            }
+            if (++since_flush == FLUSH) { mA.flush(lane); since_flush = 0; }
+        }
+        {
+            double lv[(EA + 31) / 32];
+            mA.finish(lv, lane);
+            block_totals<EA>(lv, redA, totA, lane, warp, nwarps);
+        }
+
+        // ---------------- Z fit (FP64) ------------------------------------------
+        if (threadIdx.x == 0) {
+            const double Md = (double)P.M;
+            bool ok = true;
+            if (LP1) ok = cholesky<p>(totA, Ls);
+            for (int l = 0; l < q; ++l) {
+                if (LP1 && ok) {
+                    chol_solve<p>(Ls, totA + EG + l * p, beta_s + l * p);
+                } else {
+                    for (int a = 0; a < p; ++a)
+                        beta_s[l * p + a] = (a == 0) ? totA[EG + l * p] / Md : 0.0;
+                }
+            }
+            for (int a = 0; a < q * p; ++a) beta_r[a] = (R)beta_s[a];
+            ok_s = ok ? 1 : 0;
+        }
+        __syncthreads();
+
+        // ---------------- phase B: the f_i term of the Y response ----------------
+        MB mB;
+        mB.zero();
+        since_flush = 0;
+        for (long long m0 = 0; m0 < P.M; m0 += blockDim.x) {
+            const long long m = m0 + threadIdx.x;
+            const bool valid = m < P.M;
+            Words W;
+            W.init((unsigned)m, (unsigned)k, (unsigned)i, P.key0, P.key1);
+            R x[D], phi[p], x1[D], y1, z1[D], zi[D];
+            phi[0] = (R)1;
+#pragma unroll
+            for (int l = 0; l < D; ++l) {
+                x[l] = sample_cell(W.next(), Flo[l], Fchi[l], Wd[l], Form<R>::mu_arg(P));
+                if (LP1) {
+                    R t;
+                    if (sizeof(R) == 8) t = (x[l] - (R)P.lo[l]) / (R)P.h[l];
+                    else t = (x[l] - (R)P.lo_f[l]) * (R)P.r_f[l];
+                    phi[1 + l] = (R)2 * (t - (R)cell[l]) - (R)1;
+                }
+            }
+#pragma unroll
+            for (int l = 0; l < D; ++l) {
+                const R dw = sdt * normal_of(W.next(), (R)0);
+                x1[l] = x[l] + Form<R>::b(P, l) * dt + Form<R>::sig(P, l) * dw;
+            }
+            eval_at<R, D, LP1, MODEL, ZIN>(P, i + 1, x1, y1, z1);
+#pragma unroll
+            for (int l = 0; l < q; ++l) {
+                R w = beta_r[l * p];
+#pragma unroll
+                for (int a = 1; a < p; ++a) w += beta_r[l * p + a] * phi[a];
+                zi[l] = clamp_r(w, Form<R>::Cz(P));
+            }
+            const R fi = model_f<R, D, MODEL, ZIN>(P, i, x, y1, zi);
+            if (valid) {
+#pragma unroll
+                for (int a = 0; a < p; ++a) mB.add(a, phi[a] * fi);
+            }
+            if (++since_flush == FLUSH) { mB.flush(lane); since_flush = 0; }
+        }
+        {
+            double lv[(EB + 31) / 32];
+            mB.finish(lv, lane);
+            block_totals<EB>(lv, redB, totB, lane, warp, nwarps);
+        }
+
+        // ---------------- Y fit (FP64) and the row (i, k) -----------------------
+        if (threadIdx.x == 0) {
+            const double Md = (double)P.M;
+            const double dtd = P.dt;
+            double rY[p], alpha[p];
+            for (int a = 0; a < p; ++a) rY[a] = totA[EG + EZ + a] + dtd * totB[a];
+            if (LP1 && ok_s) {
+                chol_solve<p>(Ls, rY, alpha);
+            } else {
+                for (int a = 0; a < p; ++a) alpha[a] = (a == 0) ? rY[0] / Md : 0.0;
+            }
+            const long long row = (long long)i * P.K + k;
+            bool finite = true;
+            for (int a = 0; a < p; ++a) {
+                finite = finite && isfinite(alpha[a]);
+                P.Y64[row * P.ry64 + a] = alpha[a];
+                if (P.Y32) P.Y32[row * P.ry32 + a] = (float)alpha[a];
+            }
+            for (int a = 0; a < q * p; ++a) {
+                finite = finite && isfinite(beta_s[a]);
+                P.Z64[row * P.rz64 + a] = beta_s[a];
+                if (P.Z32) P.Z32[row * P.rz32 + a] = (float)beta_s[a];
+            }
+            if (LP1 && !ok_s) atomicAdd(P.stats + 0, 1ull);
+            if (!finite) atomicAdd(P.stats + 1, 1ull);
+        }
+        __syncthreads();
+    }
+}
+
+template <typename R, bool LP1, int MODEL, bool ZIN>
+cudaError_t launch_one(const Params &P, int i, int grid, int threads, cudaStream_t st)
+{
+    step_kernel<R, SRMC_STEP_D, LP1, MODEL, ZIN><<<grid, threads, 0, st>>>(P, i);
+    return cudaGetLastError();
+}
+
+template <typename R>
+cudaError_t launch_prec(const Params &P, int i, bool lp1, int mv, int grid, int threads,
+                        cudaStream_t st)
+{
+    switch (mv) {
+    case MV_COS:      return lp1 ? launch_one<R, true, MODEL_COS, false>(P, i, grid, threads, st)
+                                 : launch_one<R, false, MODEL_COS, false>(P, i, grid, threads, st);
+    case MV_COS_Z:    return lp1 ? launch_one<R, true, MODEL_COS, true>(P, i, grid, threads, st)
+                                 : launch_one<R, false, MODEL_COS, true>(P, i, grid, threads, st);
+    case MV_LOGISTIC: return lp1 ? launch_one<R, true, MODEL_LOGISTIC, true>(P, i, grid, threads, st)
+                                 : launch_one<R, false, MODEL_LOGISTIC, true>(P, i, grid, threads, st);
+    case MV_AFFINE:   return lp1 ? launch_one<R, true, MODEL_AFFINE, false>(P, i, grid, threads, st)
+                                 : launch_one<R, false, MODEL_AFFINE, false>(P, i, grid, threads, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+cudaError_t SRMC_LAUNCH_STEP_NAME(SRMC_STEP_D)(const Params &P, int i, bool fp64, bool lp1, int mv,
+                                                int grid, int threads, cudaStream_t st)
+{
+    return fp64 ? launch_prec<double>(P, i, lp1, mv, grid, threads, st)
+                : launch_prec<float>(P, i, lp1, mv, grid, threads, st);
+}
+
+}  // namespace srmc

@@ -1,0 +1,222 @@
+"""Python binding of libsrmc (include/srmc.h): argument marshalling only.
+
+Every function keeps the C name; every compute step runs in the library's
+CUDA kernels.  Device buffers are torch tensors (device memory and streams
+only); host buffers are numpy arrays.  There is no CPU fallback: if the
+shared library is missing or fails to load, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libsrmc.so")
+
+SRMC_OK = 0
+STATUS = {0: "SRMC_OK", 1: "SRMC_ERR_INVALID_ARG", 2: "SRMC_ERR_CUDA", 3: "SRMC_ERR_OOM",
+          4: "SRMC_ERR_UNSUPPORTED", 5: "SRMC_ERR_STATE"}
+MODELS = {"cos": 0, "logistic": 1, "affine": 2}
+BASES = {"lp0": 0, "lp1": 1}
+PRECISIONS = {"fp32": 0, "fp64": 1}
+
+
+class SrmcError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class srmc_problem(C.Structure):
+    _fields_ = [("d", C.c_int), ("q", C.c_int), ("N", C.c_int), ("T", C.c_double),
+                ("b", C.POINTER(C.c_double)), ("sigma", C.POINTER(C.c_double)),
+                ("model", C.c_int), ("params", C.POINTER(C.c_double)), ("n_params", C.c_int)]
+
+
+class srmc_strata(C.Structure):
+    _fields_ = [("cells", C.POINTER(C.c_int)), ("lo", C.POINTER(C.c_double)),
+                ("hi", C.POINTER(C.c_double)), ("mu", C.c_double)]
+
+
+class srmc_config(C.Structure):
+    _fields_ = [("basis", C.c_int), ("prec", C.c_int), ("M", C.c_longlong),
+                ("seed", C.c_ulonglong), ("instance", C.c_uint), ("Cy", C.c_double),
+                ("Cz", C.c_double), ("block_threads", C.c_int)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def lib():
+    """Load the in-tree libsrmc.so (raises if it was not built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"libsrmc is not built ({LIB_PATH} missing); run "
+                                   "`python -c 'import __graft_entry__ as g; g.build()'`")
+            L = C.CDLL(LIB_PATH)
+            vp, ll, i_ = C.c_void_p, C.c_longlong, C.c_int
+            L.srmc_create.argtypes = [C.POINTER(srmc_problem), C.POINTER(srmc_strata),
+                                      C.POINTER(srmc_config), C.POINTER(vp)]
+            L.srmc_destroy.argtypes = [vp]; L.srmc_destroy.restype = None
+            L.srmc_solve.argtypes = [vp, vp]
+            L.srmc_solve_step.argtypes = [vp, i_, vp]
+            L.srmc_eval.argtypes = [vp, i_, vp, ll, vp, vp, vp]
+            L.srmc_centres.argtypes = [vp, vp, vp]
+            L.srmc_table.argtypes = [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(i_), C.POINTER(i_),
+                                     C.POINTER(i_), C.POINTER(ll)]
+            L.srmc_stats.argtypes = [vp, C.POINTER(C.c_ulonglong)]
+            L.srmc_philox.argtypes = [vp, C.POINTER(C.c_uint32), ll, vp, vp]
+            L.srmc_normals.argtypes = [vp, ll, vp, vp, vp]
+            L.srmc_locate.argtypes = [vp, vp, vp, ll, vp, vp]
+            L.srmc_start_points.argtypes = [vp, i_, ll, ll, ll, vp, vp]
+            L.srmc_last_error.restype = C.c_char_p
+            L.srmc_version.restype = C.c_int
+            for name in ("srmc_create", "srmc_solve", "srmc_solve_step", "srmc_eval", "srmc_centres",
+                         "srmc_table", "srmc_stats", "srmc_philox", "srmc_normals", "srmc_locate",
+                         "srmc_start_points"):
+                getattr(L, name).restype = C.c_int
+            _lib = L
+    return _lib
+
+
+def _check(status):
+    if status != SRMC_OK:
+        raise SrmcError(status, lib().srmc_last_error().decode())
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _darr(vals):
+    a = (C.c_double * max(1, len(vals)))(*[float(v) for v in vals])
+    return a
+
+
+def exported_symbols():
+    """Names declared in include/srmc.h that the loaded library exports."""
+    L = lib()
+    return [n for n in ("srmc_create", "srmc_destroy", "srmc_solve", "srmc_solve_step", "srmc_eval",
+                        "srmc_centres", "srmc_table", "srmc_stats", "srmc_philox", "srmc_normals",
+                        "srmc_locate", "srmc_start_points", "srmc_last_error", "srmc_version")
+            if hasattr(L, n)]
+
+
+class Solver:
+    """One SRMC problem on the current CUDA device (wraps srmc_create)."""
+
+    def __init__(self, w, block_threads: int = 0):
+        L = lib()
+        self.w = w
+        d, q = w.d, w.q
+        self._b = _darr(w.b)
+        self._sig = _darr([w.sigma[l][r] for l in range(d) for r in range(q)])
+        self._prm = _darr(w.params)
+        self._cells = (C.c_int * d)(*[int(c) for c in w.cells])
+        self._lo = _darr(w.lo)
+        self._hi = _darr(w.hi)
+        pr = srmc_problem(d, q, int(w.N), float(w.T), self._b, self._sig, MODELS[w.model],
+                          self._prm, len(w.params))
+        sa = srmc_strata(self._cells, self._lo, self._hi, float(w.mu))
+        cf = srmc_config(BASES[w.basis], PRECISIONS[w.precision], int(w.M), int(w.seed),
+                         int(w.instance), float(w.Cy), float(w.Cz), int(block_threads))
+        h = C.c_void_p()
+        _check(L.srmc_create(C.byref(pr), C.byref(sa), C.byref(cf), C.byref(h)))
+        self._h = h
+        self.K = int(np.prod(w.cells))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().srmc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    def srmc_solve(self, stream=None):
+        _check(lib().srmc_solve(self._h, _stream(stream)))
+
+    def srmc_solve_step(self, i, stream=None):
+        _check(lib().srmc_solve_step(self._h, int(i), _stream(stream)))
+
+    def srmc_eval(self, i, x, y, z=None, stream=None):
+        _check(lib().srmc_eval(self._h, int(i), _ptr(x), x.shape[0], _ptr(y), _ptr(z), _stream(stream)))
+
+    def srmc_centres(self, x, stream=None):
+        _check(lib().srmc_centres(self._h, _ptr(x), _stream(stream)))
+
+    def srmc_table(self):
+        y, z = C.c_void_p(), C.c_void_p()
+        p, ry, rz, K = C.c_int(), C.c_int(), C.c_int(), C.c_longlong()
+        _check(lib().srmc_table(self._h, C.byref(y), C.byref(z), C.byref(p), C.byref(ry),
+                                C.byref(rz), C.byref(K)))
+        return dict(y64=y.value, z64=z.value, p=p.value, ry=ry.value, rz=rz.value, K=K.value)
+
+    def srmc_stats(self):
+        out = (C.c_ulonglong * 3)()
+        _check(lib().srmc_stats(self._h, out))
+        return dict(fallbacks=int(out[0]), nonfinite=int(out[1]), path_steps=int(out[2]))
+
+    def srmc_locate(self, x, k, stream=None):
+        import torch
+        x64 = x if x.dtype == torch.float64 else None
+        x32 = x if x.dtype == torch.float32 else None
+        _check(lib().srmc_locate(self._h, _ptr(x64), _ptr(x32), x.shape[0], _ptr(k), _stream(stream)))
+
+    def srmc_start_points(self, i, k, m0, x, stream=None):
+        _check(lib().srmc_start_points(self._h, int(i), int(k), int(m0), x.shape[0], _ptr(x),
+                                       _stream(stream)))
+
+    # Convenience on top of the C calls -------------------------------------
+    def centres(self):
+        import torch
+        x = torch.empty((self.K, self.w.d), dtype=torch.float64, device="cuda")
+        self.srmc_centres(x)
+        return x
+
+    def evaluate(self, i, x):
+        import torch
+        y = torch.empty(x.shape[0], dtype=torch.float64, device=x.device)
+        z = torch.empty((x.shape[0], self.w.q), dtype=torch.float64, device=x.device)
+        self.srmc_eval(i, x, y, z)
+        return y, z
+
+
+def srmc_philox(ctr, key, out, stream=None):
+    k = (C.c_uint32 * 2)(int(key[0]) & 0xFFFFFFFF, int(key[1]) & 0xFFFFFFFF)
+    _check(lib().srmc_philox(_ptr(ctr), k, ctr.shape[0], _ptr(out), _stream(stream)))
+
+
+def srmc_normals(words, out64=None, out32=None, stream=None):
+    _check(lib().srmc_normals(_ptr(words), words.shape[0], _ptr(out64), _ptr(out32), _stream(stream)))
+
+
+def srmc_version() -> int:
+    return int(lib().srmc_version())
+
+
+def build(force: bool = False) -> str:
+    from . import build as _b
+    return _b.build(force=force)

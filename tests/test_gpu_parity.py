@@ -1,0 +1,224 @@
+"""GPU solves through the C ABI against the FP64 CPU oracle on the same
+Philox streams.
+
+Tolerances (stated per test): FP64 form |dy|, |dz| <= 1e-10 at stratum
+centres; FP32 form |dy| <= 1e-4 (1 + |y|) and |dz| <= 1e-4 (1 + |z|).
+Full-size workloads are checked on sampled strata of the last steps, which
+the oracle fits lazily (each fit computes every row its paths visit)."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2407_21085_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-10
+TOL32 = 1e-4
+
+
+@pytest.fixture(scope="module")
+def dev():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2407_21085_gb300 import srmc
+    return torch, srmc
+
+
+def _check(w, gy, gz, ry, rz, where=""):
+    if w.precision == "fp64":
+        dy = np.max(np.abs(gy - ry))
+        dz = np.max(np.abs(gz - rz))
+        assert dy <= TOL64 and dz <= TOL64, (where, dy, dz)
+        return dy, dz
+    ey = np.abs(gy - ry) / (1 + np.abs(ry))
+    ez = np.abs(gz - rz) / (1 + np.abs(rz))
+    assert np.max(ey) <= TOL32 and np.max(ez) <= TOL32, (where, np.max(ey), np.max(ez))
+    return np.max(ey), np.max(ez)
+
+
+def _full_parity(dev, orc, w, block_threads=0, points=None):
+    torch, srmc = dev
+    s = srmc.Solver(w, block_threads=block_threads)
+    s.srmc_solve()
+    x = s.centres() if points is None else torch.from_numpy(points).cuda()
+    xn = x.cpu().numpy()
+    o = orc.Oracle(w)
+    o.solve_full(0)
+    worst = (0.0, 0.0)
+    for i in range(w.N + 1):
+        gy, gz = s.evaluate(i, x)
+        ry, rz = o.eval(i, xn)
+        e = _check(w, gy.cpu().numpy(), gz.cpu().numpy(), ry, rz, where=f"step {i}")
+        worst = (max(worst[0], e[0]), max(worst[1], e[1]))
+    st = s.srmc_stats()
+    assert st["nonfinite"] == 0 and st["fallbacks"] == o.fallbacks == 0
+    return s, worst
+
+
+# ---- whole backward solves at sizes the oracle finishes in seconds ----------
+
+def test_cfg1_full_fp64(dev, orc):
+    # d=1, K=32 on [-4,4], N=10, M=1000 (ragged: 1000 = 3*256 + 232), LP1, FP64
+    _full_parity(dev, orc, W.cfg1())
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("basis", ["lp1", "lp0"])
+def test_cfg2_family_reduced(dev, orc, prec, basis):
+    # d=2 cos model (s0=0.3, lam=0.2, kap=0.5), N=8.  The FP32 paths differ
+    # from the FP64 ones by rounding, so now and then a path lands on the other
+    # side of a cell edge; with LP0 the fitted y jumps there by ~|grad u| h, and
+    # one such path moves its stratum's z fit by ~ jump dt |dW_i| / (dt M).
+    # M is chosen so that one edge flip stays inside the FP32 tolerance.
+    if prec == "fp32" and basis == "lp0":
+        w = W.cfg2(C=8, N=8, M=4096, precision=prec, basis=basis)
+    else:
+        w = W.cfg2(C=16, N=8, M=512, precision=prec, basis=basis)
+    _full_parity(dev, orc, w)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_cfg3_family_reduced_with_z_in_driver(dev, orc, prec):
+    # d=4, kapz = 0.2 (the driver reads z_j), 4^4 strata on [-3.5,3.5]^4, N=4, M=256
+    _full_parity(dev, orc, W.cfg3(C=4, N=4, M=256, precision=prec))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_active_truncation(dev, orc, prec):
+    w = W.cfg2(C=8, N=6, M=300, precision=prec, kapz=0.3).replace(Cy=0.8, Cz=0.5)
+    _full_parity(dev, orc, w)
+
+
+@pytest.mark.parametrize("d,C,N,M", [(3, 5, 3, 96), (5, 2, 3, 64), (6, 2, 3, 128), (7, 2, 2, 40), (8, 2, 2, 64)])
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_other_dimensions(dev, orc, d, C, N, M, prec):
+    w = W.cos_model(f"d{d}", d=d, N=N, C=C, a=2.0, M=M, s0=0.3, lam=0.2, kap=0.5, kapz=0.1,
+                    precision=prec)
+    _full_parity(dev, orc, w)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_paper_logistic_model(dev, orc, prec):
+    # The test BSDE of Sec. 5.1 (driver uses sum z), d=3, strata on [-6.5,6.5]^3
+    _full_parity(dev, orc, W.logistic_paper(d=3, N=4, C=3, M=200, precision=prec))
+
+
+# ---- edge cases -------------------------------------------------------------
+
+@pytest.mark.parametrize("M,bt", [(37, 32), (3, 32), (33, 64), (257, 256)])
+def test_ragged_and_minimal_M(dev, orc, M, bt):
+    # M not a multiple of the block, and M equal to the basis dimension (d+1 = 3)
+    _full_parity(dev, orc, W.cfg2(C=4, N=3, M=M, precision="fp64"), block_threads=bt)
+
+
+def test_single_stratum_and_single_step(dev, orc):
+    # K = 1: one cell covering R (nu_k = nu); N = 1: only the terminal step
+    _full_parity(dev, orc, W.cfg1(C=1, N=1, M=500))
+    _full_parity(dev, orc, W.cfg1(C=1, N=3, M=500))
+
+
+def test_block_size_does_not_change_results(dev, orc):
+    torch, srmc = dev
+    w = W.cfg2(C=8, N=4, M=640, precision="fp64")
+    vals = []
+    for bt in (32, 96, 256):
+        s = srmc.Solver(w, block_threads=bt)
+        s.srmc_solve()
+        y, z = s.evaluate(0, s.centres())
+        vals.append((y.cpu().numpy(), z.cpu().numpy()))
+    for y, z in vals[1:]:
+        assert np.max(np.abs(y - vals[0][0])) < 1e-12 and np.max(np.abs(z - vals[0][1])) < 1e-12
+
+
+def test_deterministic(dev):
+    torch, srmc = dev
+    w = W.cfg2(C=16, N=6, M=1024, precision="fp32")
+    out = []
+    for _ in range(2):
+        s = srmc.Solver(w)
+        s.srmc_solve()
+        t = s.srmc_table()
+        y, z = s.evaluate(0, s.centres())
+        out.append((y.cpu().numpy(), z.cpu().numpy()))
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-11), ("fp32", 2e-5)])
+def test_exact_affine_fit(dev, prec, tol):
+    # sigma = 0: y_i is affine and LP1 must reproduce it (exact up to rounding)
+    torch, srmc = dev
+    from tests.test_oracle_scheme import _affine_truth
+    gv, fv = [0.3, -0.7], [0.2, 0.05]
+    w = W.affine(d=2, N=5, C=3, M=64, g0=0.4, gv=gv, f0=-0.3, fv=fv, a=0.6, b=[0.5, -0.25],
+                 s0=0.0, precision=prec)
+    s = srmc.Solver(w)
+    s.srmc_solve()
+    truth = _affine_truth(2, 5, 1.0, 0.4, gv, -0.3, fv, 0.6, [0.5, -0.25])
+    x = np.random.default_rng(0).uniform(-3, 3, size=(64, 2))
+    for i in range(w.N):
+        y, _ = s.evaluate(i, torch.from_numpy(x).cuda())
+        want = truth[i][0] + x @ truth[i][1]
+        assert np.max(np.abs(y.cpu().numpy() - want)) < tol * (1 + np.max(np.abs(want)))
+
+
+def test_invalid_arguments(dev):
+    torch, srmc = dev
+    with pytest.raises(srmc.SrmcError) as e:
+        srmc.Solver(W.cfg2(M=2))                 # M < d + 1
+    assert e.value.status == 1
+    bad = W.cfg2(M=64)
+    bad.sigma = [[0.3, 0.1], [0.0, 0.3]]
+    with pytest.raises(srmc.SrmcError) as e:
+        srmc.Solver(bad)                         # non-diagonal sigma
+    assert e.value.status == 4
+    with pytest.raises(srmc.SrmcError) as e:
+        srmc.Solver(W.cfg2(M=64), block_threads=48)
+    assert e.value.status == 1
+    s = srmc.Solver(W.cfg2(C=4, N=5, M=64))
+    with pytest.raises(srmc.SrmcError) as e:
+        s.srmc_solve_step(2)                     # steps 3, 4 not solved yet
+    assert e.value.status == 5
+    s.srmc_solve_step(4)
+    s.srmc_solve_step(3)
+    s.srmc_solve_step(2)
+    empty = torch.empty((0, 2), dtype=torch.float64, device="cuda")
+    y = torch.empty(0, dtype=torch.float64, device="cuda")
+    s.srmc_eval(2, empty, y)                     # n = 0 is a no-op
+
+
+# ---- full-size workloads, sampled strata of the last steps ------------------
+
+def _sampled_parity(dev, orc, w, steps, n_strata, seed=0):
+    torch, srmc = dev
+    s = srmc.Solver(w)
+    s.srmc_solve()
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(seed)
+    o = orc.Oracle(w)
+    xs_all = s.centres().cpu().numpy()
+    for i in steps:
+        ks = rng.choice(w.K, size=n_strata, replace=False)
+        for k in ks:
+            o.fit_lazy(i, int(k))
+        xs = xs_all[ks]
+        gy, gz = s.evaluate(i, torch.from_numpy(xs).cuda())
+        ry, rz = o.eval(i, xs)
+        _check(w, gy.cpu().numpy(), gz.cpu().numpy(), ry, rz, where=f"step {i}")
+    st = s.srmc_stats()
+    assert st["nonfinite"] == 0
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp64"])
+def test_cfg2_full_size_sampled(dev, orc, prec):
+    # 64x64 strata, N=20, M=4096: the benchmark's launch configuration
+    w = W.cfg2(precision=prec)
+    _sampled_parity(dev, orc, w, steps=[w.N - 1, w.N - 2, w.N - 3], n_strata=4)
+
+
+def test_cfg3_full_size_sampled(dev, orc):
+    # 12^4 strata, N=50, M=16384, kapz=0.2, FP32 form
+    w = W.cfg3()
+    _sampled_parity(dev, orc, w, steps=[w.N - 1, w.N - 2], n_strata=3)
