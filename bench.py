@@ -1,0 +1,321 @@
+"""Benchmark of the SRMC backward solve on GB300.
+
+One step = one whole backward solve of Alg. SRMDP (N step launches over all
+strata) on the selected workload, inputs already resident on the device.
+The metric is stratum-path-steps per second: K M N (N+1) / 2 units per solve.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload cfg2]
+                  [--impl reference] [--no-cpu-baseline]
+
+With N > 1 (torchrun, one process per GPU) every rank solves its own
+independent instance (replicas, weak scaling, no collective on the data
+path); value = units of all ranks / max elapsed over ranks.
+The reference arm (--impl reference) times the FP64 CPU oracle on a bounded
+sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2407_21085_gb300 import workloads as W  # noqa: E402
+
+METRIC = "stratum-path-steps/s"
+UNIT = "path-steps/s"
+L2_FLUSH_BYTES = 512 << 20
+
+
+def flops_per_path_step(d: int) -> float:
+    """Algorithmic FP32 FLOPs of one stratum-path-step (Euler, locate, centre,
+    y and z evaluation, clamps, driver, response update): 2 d^2 + 13 d + 20."""
+    return 2.0 * d * d + 13.0 * d + 20.0
+
+
+def fp32_peak_tflops(sms: int, mhz: float) -> float:
+    """FP32 FMA pipe peak: SMs x 128 lanes x 2 FLOP x clock."""
+    return sms * 128 * 2 * mhz * 1e6 / 1e12
+
+
+def workload(name: str) -> W.Workload:
+    makers = {"cfg1": W.cfg1, "cfg2": W.cfg2, "cfg2_fp64": lambda: W.cfg2(precision="fp64"),
+              "cfg2_lp0": lambda: W.cfg2(basis="lp0"), "cfg3": W.cfg3, "cfg5": W.cfg5}
+    return makers[name]()
+
+
+# ---- distributed plumbing (replicas only) -----------------------------------
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def max_over_ranks(value: float, backend_device=None) -> float:
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return value
+    t = torch.tensor([value], dtype=torch.float64, device=backend_device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier():
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.barrier()
+
+
+# ---- clocks during the timed region -----------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                v = [a.strip() for a in line.split(",")]
+                if len(v) >= 9:
+                    rows.append(v)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[c] for r in rows for c in range(4) if r[5 + c].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---- the GPU arm ---------------------------------------------------------------
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2407_21085_gb300 import srmc
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    if ws > 1 and not dist.is_initialized():
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    props = torch.cuda.get_device_properties(dev)
+    sms = props.multi_processor_count
+
+    w = workload(args.workload).replace(instance=workload(args.workload).instance + 1000 * rank)
+    units = w.path_steps()
+    stream = torch.cuda.current_stream()
+    solver = srmc.Solver(w)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def one_step(events=None):
+        if events is None:
+            solver.srmc_solve(stream)
+            return
+        for i in range(w.N - 1, -1, -1):
+            a, b = events[i]
+            a.record(stream)
+            solver.srmc_solve_step(i, stream)
+            b.record(stream)
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    launch_ms = []
+    step_ms = []
+    barrier()
+    torch.cuda.synchronize()
+    for _ in range(args.steps):
+        flush.fill_(1.0)                     # evict the tables from L2 between steps
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(w.N)]
+        one_step(ev)
+        torch.cuda.synchronize()
+        per = [ev[i][0].elapsed_time(ev[i][1]) for i in range(w.N)]
+        launch_ms.extend(per)
+        step_ms.append(ev[w.N - 1][0].elapsed_time(ev[0][1]))
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    total_ms = sum(step_ms)
+    total_ms_max = max_over_ranks(total_ms, dev)
+    value = units * ws * args.steps / (total_ms_max / 1e3)
+
+    # End to end through the public API with host buffers: create (host
+    # parameters -> device), solve, copy the FP64 coefficient tables to pinned
+    # host memory, destroy.
+    e2e_ms = []
+    h2d = sum(w.cells) * 3 * (8 + 4) + (w.N + 1) * 2 * (8 + 4)
+    info = solver.srmc_table()
+    ny, nz = w.N * w.K * info["ry"], w.N * w.K * info["rz"]
+    host_y = torch.empty(ny, dtype=torch.float64, pin_memory=True)
+    host_z = torch.empty(nz, dtype=torch.float64, pin_memory=True)
+    for r in range(args.e2e_steps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s2 = srmc.Solver(w)
+        s2.srmc_solve(stream)
+        s2.srmc_read_table(host_y, host_z, stream)
+        stream.synchronize()
+        s2.close()
+        if r > 0:
+            e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_max = max_over_ranks(sum(e2e_ms), dev)
+    e2e_value = units * ws * len(e2e_ms) / (e2e_max / 1e3)
+    tab_bytes = (ny + nz) * 8
+
+    # Roofline of the dominant kernel (the step kernel: every launch is one).
+    avg_launch_s = (sum(launch_ms) / len(launch_ms)) / 1e3
+    flops_per_launch = flops_per_path_step(w.d) * units / w.N
+    achieved = flops_per_launch / avg_launch_s / 1e12
+    peak_mhz = 2070.0
+    peak = fp32_peak_tflops(sms, peak_mhz)
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if w.precision == "fp32" else "f64",
+        "data": "synthetic",
+        "config": {"workload": w.name, "d": w.d, "strata": w.K, "N": w.N, "M": w.M, "basis": w.basis,
+                   "precision": w.precision, "model": "cos (u = e^{lam(T-t)} cos(sum x/sqrt d))",
+                   "path_steps_per_solve": units, "l2": "flushed between steps (512 MiB write)",
+                   "parallelism": f"replicas x{ws}"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": args.traffic,
+                     "kernel": "step_kernel", "flops_per_unit": flops_per_path_step(w.d),
+                     "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x {peak_mhz:.0f} MHz"},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": tab_bytes},
+        "gpu_launches": w.N * args.steps,
+        "clocks": clocks,
+    }
+    solver.close()
+    return out, rank, w
+
+
+# ---- the CPU oracle (cpu_baseline leg and the reference arm) -------------------
+def oracle_sample(w: W.Workload, M_sample: int, threads: int):
+    """Time the FP64 oracle's full backward solve of the workload with M
+    reduced to M_sample (all strata, all steps) on `threads` host threads."""
+    from oracle import oracle as o
+    o.build()
+    ws = w.replace(M=M_sample, precision="fp64")
+    t0 = time.perf_counter()
+    orc = o.Oracle(ws)
+    orc.solve_full(threads)
+    dt = time.perf_counter() - t0
+    steps = orc.path_steps
+    orc.close()
+    return steps / dt, dt, f"{w.name} with M={M_sample} (all {w.K} strata, all {w.N} steps), FP64"
+
+
+def cpu_cores():
+    return os.cpu_count() or 1
+
+
+def run_reference(args):
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return None
+    w = workload(args.workload)
+    cores = cpu_cores()
+    M_s = args.ref_M
+    for _ in range(args.warmup):
+        oracle_sample(w, M_s, cores)
+    rates, times = [], []
+    for _ in range(args.steps):
+        r, dt, sample = oracle_sample(w, M_s, cores)
+        rates.append(r)
+        times.append(dt)
+    units = sum(rates[i] * times[i] for i in range(len(rates)))
+    value = units / sum(times)
+    return {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": w.name, "d": w.d, "strata": w.K, "N": w.N, "M": w.M, "basis": w.basis,
+                   "sample_M": M_s},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default="cfg2")
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-M", type=int, default=128, help="M of the bounded oracle sample")
+    ap.add_argument("--ref-M", type=int, default=32, help="M of each reference-arm step")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="DRAM bytes per step-kernel launch from an ncu capture of this kernel")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+
+    if args.impl == "reference":
+        out = run_reference(args)
+        if out is not None:
+            print(json.dumps(out), flush=True)
+        return
+
+    out, rank, w = run_gpu(args)
+    if rank == 0:
+        if not args.no_cpu_baseline and out["n_gpus"] == 1:
+            r, dt, sample = oracle_sample(w, args.cpu_M, cpu_cores())
+            out["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+                                   "sample": sample, "seconds": dt}
+        else:
+            out["cpu_baseline"] = None
+        print(json.dumps(out), flush=True)
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -151,6 +151,12 @@ srmc_status srmc_centres(const srmc_solver *s, double *dev_x, void *stream);
 srmc_status srmc_table(const srmc_solver *s, const double **dev_y64, const double **dev_z64,
                        int *p, int *ry, int *rz, long long *K);
 
+/* Copy the FP64 coefficient tables (layout of srmc_table, all N*K rows) into
+ * caller memory: dst_y [N][K][ry] and dst_z [N][K][rz] doubles, host (pinned
+ * or pageable) or device; either may be NULL.  Asynchronous on stream for
+ * device or pinned destinations; the caller synchronises before reading. */
+srmc_status srmc_read_table(const srmc_solver *s, double *dst_y, double *dst_z, void *stream);
+
 /* Counters since creation: [0] strata fits that fell back from LP1 to LP0
  * because the Gram matrix was numerically singular (Cholesky pivot below
  * 1e-12 of its trace); [1] non-finite coefficients written; [2] stratum-path

@@ -447,6 +447,19 @@ srmc_status srmc_table(const srmc_solver *s, const double **y64, const double **
     return SRMC_OK;
 }
 
+srmc_status srmc_read_table(const srmc_solver *s, double *dst_y, double *dst_z, void *stream)
+{
+    if (!s) return fail(SRMC_ERR_INVALID_ARG, "srmc_read_table: NULL solver");
+    const size_t rows = (size_t)s->P.N * (size_t)s->P.K;
+    if (dst_y)
+        SRMC_CUDA(cudaMemcpyAsync(dst_y, s->Y64, sizeof(double) * rows * s->P.ry64, cudaMemcpyDefault,
+                                  (cudaStream_t)stream), "srmc_read_table: copy y");
+    if (dst_z)
+        SRMC_CUDA(cudaMemcpyAsync(dst_z, s->Z64, sizeof(double) * rows * s->P.rz64, cudaMemcpyDefault,
+                                  (cudaStream_t)stream), "srmc_read_table: copy z");
+    return SRMC_OK;
+}
+
 srmc_status srmc_stats(const srmc_solver *s, unsigned long long out[3])
 {
     if (!s || !out) return fail(SRMC_ERR_INVALID_ARG, "srmc_stats: NULL argument");

@@ -71,6 +71,7 @@ def lib():
             L.srmc_table.argtypes = [vp, C.POINTER(vp), C.POINTER(vp), C.POINTER(i_), C.POINTER(i_),
                                      C.POINTER(i_), C.POINTER(ll)]
             L.srmc_stats.argtypes = [vp, C.POINTER(C.c_ulonglong)]
+            L.srmc_read_table.argtypes = [vp, vp, vp, vp]
             L.srmc_philox.argtypes = [vp, C.POINTER(C.c_uint32), ll, vp, vp]
             L.srmc_normals.argtypes = [vp, ll, vp, vp, vp]
             L.srmc_locate.argtypes = [vp, vp, vp, ll, vp, vp]
@@ -78,7 +79,7 @@ def lib():
             L.srmc_last_error.restype = C.c_char_p
             L.srmc_version.restype = C.c_int
             for name in ("srmc_create", "srmc_solve", "srmc_solve_step", "srmc_eval", "srmc_centres",
-                         "srmc_table", "srmc_stats", "srmc_philox", "srmc_normals", "srmc_locate",
+                         "srmc_table", "srmc_read_table", "srmc_stats", "srmc_philox", "srmc_normals", "srmc_locate",
                          "srmc_start_points"):
                 getattr(L, name).restype = C.c_int
             _lib = L
@@ -112,7 +113,8 @@ def exported_symbols():
     """Names declared in include/srmc.h that the loaded library exports."""
     L = lib()
     return [n for n in ("srmc_create", "srmc_destroy", "srmc_solve", "srmc_solve_step", "srmc_eval",
-                        "srmc_centres", "srmc_table", "srmc_stats", "srmc_philox", "srmc_normals",
+                        "srmc_centres", "srmc_table", "srmc_read_table", "srmc_stats", "srmc_philox",
+                        "srmc_normals",
                         "srmc_locate", "srmc_start_points", "srmc_last_error", "srmc_version")
             if hasattr(L, n)]
 
@@ -173,6 +175,10 @@ class Solver:
         _check(lib().srmc_table(self._h, C.byref(y), C.byref(z), C.byref(p), C.byref(ry),
                                 C.byref(rz), C.byref(K)))
         return dict(y64=y.value, z64=z.value, p=p.value, ry=ry.value, rz=rz.value, K=K.value)
+
+    def srmc_read_table(self, dst_y, dst_z, stream=None):
+        """Copy the FP64 tables into caller tensors (host, pinned or device)."""
+        _check(lib().srmc_read_table(self._h, _ptr(dst_y), _ptr(dst_z), _stream(stream)))
 
     def srmc_stats(self):
         out = (C.c_ulonglong * 3)()
