@@ -49,7 +49,8 @@ def fp32_peak_tflops(sms: int, mhz: float) -> float:
 
 def workload(name: str) -> W.Workload:
     makers = {"cfg1": W.cfg1, "cfg2": W.cfg2, "cfg2_fp64": lambda: W.cfg2(precision="fp64"),
-              "cfg2_lp0": lambda: W.cfg2(basis="lp0"), "cfg3": W.cfg3, "cfg5": W.cfg5}
+              "cfg2_lp0": lambda: W.cfg2(basis="lp0"), "cfg3": W.cfg3, "cfg5": W.cfg5,
+              "cfg5_M1024": lambda: W.cfg5(M=1024, name="cfg5_d6_K262144_N40_M1024")}
     return makers[name]()
 
 

@@ -47,16 +47,22 @@ def _stale() -> bool:
     return any(os.path.getmtime(s) > t for s in _sources())
 
 
-def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -> str:
-    if not force and not _stale():
+def build(force: bool = False, verbose: bool = False, jobs: int | None = None,
+          out_dir: str | None = None, defines=()) -> str:
+    """Compile and link libsrmc.so (into out_dir, default _build/, with extra
+    -D defines for experiments on tuning constants)."""
+    lib = LIB if out_dir is None else os.path.join(out_dir, "libsrmc.so")
+    if out_dir is None and not force and not _stale():
         return LIB
-    os.makedirs(OUT_DIR, exist_ok=True)
+    out = OUT_DIR if out_dir is None else out_dir
+    os.makedirs(out, exist_ok=True)
     nvcc = _nvcc()
-    units = [(os.path.join(CSRC, "srmc_step.cu"), os.path.join(OUT_DIR, f"step_d{D}.o"), [f"-DSRMC_STEP_D={D}"])
-             for D in DIMS]
+    extra_defs = [f"-D{d}" for d in defines]
+    units = [(os.path.join(CSRC, "srmc_step.cu"), os.path.join(out, f"step_d{D}.o"),
+              [f"-DSRMC_STEP_D={D}"] + extra_defs) for D in DIMS]
     for name in sorted(os.listdir(CSRC)):
         if name.endswith(".cu") and name != "srmc_step.cu":
-            units.append((os.path.join(CSRC, name), os.path.join(OUT_DIR, name[:-3] + ".o"), []))
+            units.append((os.path.join(CSRC, name), os.path.join(out, name[:-3] + ".o"), extra_defs))
 
     def compile_one(u):
         src, obj, extra = u
@@ -71,10 +77,10 @@ def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -
     jobs = jobs or min(len(units), os.cpu_count() or 4)
     with cf.ThreadPoolExecutor(max_workers=jobs) as ex:
         objs = list(ex.map(compile_one, units))
-    tmp = LIB + f".{os.getpid()}.tmp"
+    tmp = lib + f".{os.getpid()}.tmp"
     subprocess.run([nvcc] + ARCH + ["-shared", "-o", tmp] + objs, check=True)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -132,13 +132,14 @@ __global__ void start_points_kernel(const Params P, bool fp64, int i, long long 
     for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < n;
          a += (long long)gridDim.x * blockDim.x) {
         srmc::Words W;
-        W.init((unsigned)(m0 + a), (unsigned)k, (unsigned)i, P.key0, P.key1);
+        W.init(P, (unsigned)(m0 + a), (unsigned)k, (unsigned)i);
         long long rem = k;
+        int pos = 0;
         for (int l = 0; l < P.d; ++l) {
             const int c = (int)(rem % P.cells[l]);
             rem /= P.cells[l];
             const int o = 3 * (P.cell_off[l] + c);
-            const unsigned w = W.next();
+            const unsigned w = W.next_dynamic(P, pos);
             if (fp64)
                 xout[a * P.d + l] = srmc::sample_cell(w, P.cellF[o], P.cellF[o + 1], P.cellF[o + 2], P.mu);
             else
@@ -262,6 +263,12 @@ srmc_status srmc_create(const srmc_problem *pr, const srmc_strata *sa, const srm
         cells_total += sa->cells[l];
         if (K > 2147483647LL) return fail(SRMC_ERR_INVALID_ARG, "too many strata (K > 2^31-1)");
     }
+    {
+        const int p_ = cf->basis == SRMC_LP1 ? d + 1 : 1;
+        const long long rmax = (long long)pad_to(q * p_, 4);
+        if ((long long)pr->N * K * rmax >= 4294967296LL)
+            return fail(SRMC_ERR_UNSUPPORTED, "table too large: N K row-length must be < 2^32");
+    }
     const int p = cf->basis == SRMC_LP1 ? d + 1 : 1;
     if (cf->basis != SRMC_LP0 && cf->basis != SRMC_LP1) return fail(SRMC_ERR_INVALID_ARG, "basis");
     if (cf->prec != SRMC_FP32 && cf->prec != SRMC_FP64) return fail(SRMC_ERR_INVALID_ARG, "precision");
@@ -289,7 +296,7 @@ srmc_status srmc_create(const srmc_problem *pr, const srmc_strata *sa, const srm
     P.zin = (s->mv == srmc::MV_COS_Z || s->mv == srmc::MV_LOGISTIC);
     P.ry32 = pad_to(p, 4); P.rz32 = pad_to(q * p, 4);
     P.ry64 = pad_to(p, 2); P.rz64 = pad_to(q * p, 2);
-    long long stride = 1;
+    int stride = 1;
     int off = 0;
     for (int l = 0; l < d; ++l) {
         P.cells[l] = sa->cells[l];
@@ -318,7 +325,15 @@ srmc_status srmc_create(const srmc_problem *pr, const srmc_strata *sa, const srm
     P.Cy_f = (float)P.Cy; P.Cz_f = (float)P.Cz;
     P.key0 = (unsigned)(cf->seed & 0xFFFFFFFFull) ^ cf->instance;
     P.key1 = (unsigned)(cf->seed >> 32);
+    for (int r = 0; r < 10; ++r) {
+        P.rk0[r] = P.key0 + (unsigned)r * 0x9E3779B9u;
+        P.rk1[r] = P.key1 + (unsigned)r * 0xBB67AE85u;
+    }
     for (int a = 0; a < pr->n_params; ++a) { P.prm[a] = pr->params[a]; P.prm_f[a] = (float)pr->params[a]; }
+    if (pr->model == SRMC_MODEL_COS) {
+        P.lin = pr->params[0] + 0.5 * pr->params[3] * pr->params[3];
+        P.lin_f = (float)P.lin;
+    }
 
     // Sampler constants of every cell side (Alg. 3): F(x-), 1 - F(x+), F(x+) - F(x-).
     std::vector<double> cellF(3 * cells_total);

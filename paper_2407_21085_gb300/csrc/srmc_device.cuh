@@ -6,6 +6,7 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 #include <cuda_runtime.h>
 #include <math_constants.h>
 
@@ -25,7 +26,7 @@ struct Params {
     long long K, M;
     int model, zin;
     int cells[DMAX];
-    long long stride[DMAX];         // stratum index stride of each dimension
+    int stride[DMAX];               // stratum index stride of each dimension
     int cell_off[DMAX];             // offset of dimension l in cellF
     double lo[DMAX], h[DMAX], b[DMAX], sig[DMAX];
     float lo_f[DMAX], r_f[DMAX], b_f[DMAX], sig_f[DMAX];
@@ -34,18 +35,35 @@ struct Params {
     double Cy, Cz;                  // +inf when disabled
     float Cy_f, Cz_f;
     unsigned key0, key1;
+    unsigned rk0[10], rk1[10];      // Philox round keys: key + r (0x9E3779B9, 0xBB67AE85)
     double prm[PMAX];
     float prm_f[PMAX];
+    double lin;                     // cos model: lam + s0^2/2
+    float lin_f;
     const double *cellF;            // [sum cells][3]: F(x-), 1 - F(x+), F(x+) - F(x-)
     const float *cellF_f;
     const double *stepc;            // [N+1][2] per-step driver constants
     const float *stepc_f;
-    float *Y32, *Z32;               // [N][K][ry32], [N][K][rz32]
+    float *Y32, *Z32;               // [N][K][ry32], [N][K][rz32]; N K r < 2^32
     double *Y64, *Z64;              // [N][K][ry64], [N][K][rz64]
     unsigned long long *stats;      // [0] LP1->LP0 fallbacks, [1] non-finite rows
 };
 
 // ---- Philox-4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) --------------------
+__device__ __forceinline__ void philox10(unsigned &c0, unsigned &c1, unsigned &c2, unsigned &c3,
+                                         const unsigned (&rk0)[10], const unsigned (&rk1)[10])
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const unsigned hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
+        const unsigned hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
+        const unsigned n0 = hi1 ^ c1 ^ rk0[r];
+        const unsigned n2 = hi0 ^ c3 ^ rk1[r];
+        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+    }
+}
+
+// The same with the round keys derived on the fly from the key (k0, k1).
 __device__ __forceinline__ void philox10(unsigned &c0, unsigned &c1, unsigned &c2, unsigned &c3,
                                          unsigned k0, unsigned k1)
 {
@@ -60,32 +78,58 @@ __device__ __forceinline__ void philox10(unsigned &c0, unsigned &c1, unsigned &c
     }
 }
 
-// The word stream of one path of cloud C_{i,k}: counter (n/4, m, k, i).
-// Words are consumed in order; the position is uniform across a warp, so
-// the refill branch does not diverge.
+// The word stream of one path of cloud C_{i,k}: counter (n/4, m, k, i),
+// word n = position n mod 4 of block n/4.  Callers take words in order with
+// a compile-time phase PH = (index of the first word) mod 4, so that every
+// word is read from a fixed register; a new block is generated whenever
+// the stream crosses a block boundary (FRESH: block 0 is already there).
 struct Words {
-    unsigned m, k, i, k0, k1, blk;
-    int pos;
-    unsigned w0, w1, w2, w3;
-    __device__ __forceinline__ void gen()
+    unsigned m, k, i, blk;
+    unsigned w[4];
+    template <typename PP>
+    __device__ __forceinline__ void gen(const PP &P)
     {
-        w0 = blk; w1 = m; w2 = k; w3 = i;
-        philox10(w0, w1, w2, w3, k0, k1);
+        w[0] = blk; w[1] = m; w[2] = k; w[3] = i;
+        philox10(w[0], w[1], w[2], w[3], P.rk0, P.rk1);
     }
-    __device__ __forceinline__ void init(unsigned m_, unsigned k_, unsigned i_, unsigned key0,
-                                         unsigned key1)
+    template <typename PP>
+    __device__ __forceinline__ void init(const PP &P, unsigned m_, unsigned k_, unsigned i_)
     {
-        m = m_; k = k_; i = i_; k0 = key0; k1 = key1; blk = 0; pos = 0;
-        gen();
+        m = m_; k = k_; i = i_; blk = 0;
+        gen(P);
     }
-    __device__ __forceinline__ unsigned next()
+    template <int PH, int CNT, bool FRESH, typename PP>
+    __device__ __forceinline__ void take(const PP &P, unsigned (&out)[CNT])
     {
-        if (pos == 4) { ++blk; gen(); pos = 0; }
-        const unsigned r = pos == 0 ? w0 : pos == 1 ? w1 : pos == 2 ? w2 : w3;
+#pragma unroll
+        for (int c = 0; c < CNT; ++c) {
+            const int p = (PH + c) & 3;
+            if (p == 0 && !(FRESH && c == 0)) { ++blk; gen(P); }
+            out[c] = w[p];
+        }
+    }
+    // Word at a run-time position (used off the hot loop only).
+    template <typename PP>
+    __device__ __forceinline__ unsigned next_dynamic(const PP &P, int &pos)
+    {
+        if (pos == 4) { ++blk; gen(P); pos = 0; }
+        const unsigned r = pos == 0 ? w[0] : pos == 1 ? w[1] : pos == 2 ? w[2] : w[3];
         ++pos;
         return r;
     }
 };
+
+// Compile-time loop: f(integral_constant<int, g>) for g = G0 .. G-1.
+template <int G0, int G, typename F>
+__device__ __forceinline__ void static_for(F &&f)
+{
+    if constexpr (G0 < G) {
+        f(std::integral_constant<int, G0>{});
+        static_for<G0 + 1, G>(f);
+    }
+}
+
+__host__ __device__ constexpr int gcd_c(int a, int b) { return b == 0 ? a : gcd_c(b, a % b); }
 
 // ---- standard normal by inversion: xi = Phi^{-1}((w + 1/2) 2^-32) ----------
 // The upper half is taken from the exact complement (~w + 1/2) 2^-32.
@@ -96,11 +140,49 @@ __device__ __forceinline__ double normal_of(unsigned w, double)
     const double x = normcdfinv(((double)v + 0.5) * 0x1p-32);
     return up ? -x : x;
 }
+// Single-precision Phi^{-1}: erfinv-style reduction (Giles, "Approximating
+// the erfinv function", GPU Computing Gems, 2010): with y = 2p - 1 and
+// w = -log(4 p (1-p)), Phi^{-1}(p) = y h(w) where h is smooth in w.  h is
+// approximated by degree-9 polynomials in (w - 5/2) for w < 5 and in
+// (sqrt(w) - c) for w >= 5, with coefficients fitted by this project
+// (weighted least squares towards minimax relative error against an FP64
+// Phi^{-1}; max relative error 6e-9 and 9e-8 on the two pieces).  y is
+// formed from the integer complement so that it keeps full relative
+// precision next to p = 1/2.
 __device__ __forceinline__ float normal_of(unsigned w, float)
 {
     const bool up = w >= 0x80000000u;
-    const unsigned v = up ? ~w : w;
-    const float x = normcdfinvf(fmaf(__uint2float_rn(v), 0x1p-32f, 0x1p-33f));
+    const unsigned v = up ? ~w : w;                                     // p <= 1/2
+    const float p = fmaf(__uint2float_rn(v), 0x1p-32f, 0x1p-33f);
+    const float y = fmaf(__uint2float_rn(0x7FFFFFFFu - v), -0x1p-31f, -0x1p-32f);   // 2p - 1
+    const float wv = -__logf(4.0f * (p * (1.0f - p)));
+    float h;
+    if (wv < 5.0f) {
+        const float s = wv - 2.5f;
+        h = -1.243243108e-08f;
+        h = fmaf(h, s, 3.285592243e-08f);
+        h = fmaf(h, s, 6.592648560e-07f);
+        h = fmaf(h, s, -4.897004146e-06f);
+        h = fmaf(h, s, -7.019233635e-06f);
+        h = fmaf(h, s, 3.087856749e-04f);
+        h = fmaf(h, s, -1.771644573e-03f);
+        h = fmaf(h, s, -5.907717161e-03f);
+        h = fmaf(h, s, 3.488020301e-01f);
+        h = fmaf(h, s, 2.123313427e+00f);
+    } else {
+        const float s = sqrtf(wv) - 3.435767889f;
+        h = 6.402532017e-05f;
+        h = fmaf(h, s, -3.551483360e-06f);
+        h = fmaf(h, s, -4.645976005e-04f);
+        h = fmaf(h, s, 9.079263546e-04f);
+        h = fmaf(h, s, -1.158809988e-03f);
+        h = fmaf(h, s, 1.824696665e-03f);
+        h = fmaf(h, s, -3.379537957e-03f);
+        h = fmaf(h, s, 5.249740090e-03f);
+        h = fmaf(h, s, 1.424003482e+00f);
+        h = fmaf(h, s, 4.625601292e+00f);
+    }
+    const float x = y * h;
     return up ? -x : x;
 }
 
@@ -123,7 +205,7 @@ __device__ __forceinline__ float sample_cell(unsigned w, float Flo, float Fchi, 
     const float Uc = fmaf(__uint2float_rn(~w), 0x1p-32f, 0x1p-33f);
     const float p = fmaf(U, wid, Flo);
     const float qc = fmaf(Uc, wid, Fchi);
-    return logf(p / qc) * inv_mu;
+    return __logf(__fdividef(p, qc)) * inv_mu;
 }
 
 // ---- stratum location (assumption A_Strat, half-open cells) ----------------
@@ -140,10 +222,8 @@ __device__ __forceinline__ int locate_dim(double x, double lo, double h, int C, 
 __device__ __forceinline__ int locate_dim(float x, float lo, float r, int C, float &t)
 {
     t = __fmul_rn(__fsub_rn(x, lo), r);
-    if (!(t >= 0.0f)) return 0;
-    if (t >= (float)C) return C - 1;
-    const int c = (int)floorf(t);
-    return c > C - 1 ? C - 1 : c;
+    // fmaxf maps NaN to 0, like the "!(t >= 0)" test of the FP64 form.
+    return (int)fminf(fmaxf(floorf(t), 0.0f), (float)(C - 1));
 }
 
 // Precision traits: which parameter copies a form reads.
@@ -158,6 +238,7 @@ template <> struct Form<double> {
     __device__ static double Cy(const Params &P) { return P.Cy; }
     __device__ static double Cz(const Params &P) { return P.Cz; }
     __device__ static double prm(const Params &P, int a) { return P.prm[a]; }
+    __device__ static double lin(const Params &P) { return P.lin; }
     __device__ static double mu_arg(const Params &P) { return P.mu; }
     __device__ static const double *cellF(const Params &P) { return P.cellF; }
     __device__ static const double *stepc(const Params &P) { return P.stepc; }
@@ -176,6 +257,7 @@ template <> struct Form<float> {
     __device__ static float Cy(const Params &P) { return P.Cy_f; }
     __device__ static float Cz(const Params &P) { return P.Cz_f; }
     __device__ static float prm(const Params &P, int a) { return P.prm_f[a]; }
+    __device__ static float lin(const Params &P) { return P.lin_f; }
     __device__ static float mu_arg(const Params &P) { return P.inv_mu_f; }
     __device__ static const float *cellF(const Params &P) { return P.cellF_f; }
     __device__ static const float *stepc(const Params &P) { return P.stepc_f; }
@@ -186,11 +268,13 @@ template <> struct Form<float> {
 };
 
 __device__ __forceinline__ void sincos_r(double s, double *sn, double *cs) { sincos(s, sn, cs); }
-__device__ __forceinline__ void sincos_r(float s, float *sn, float *cs) { sincosf(s, sn, cs); }
+// The FP32 form takes the SFU versions (error ~1e-6 absolute for the
+// arguments met here, far below the FP32 tolerance of the fits).
+__device__ __forceinline__ void sincos_r(float s, float *sn, float *cs) { __sincosf(s, sn, cs); }
 __device__ __forceinline__ double cos_r(double s) { return cos(s); }
-__device__ __forceinline__ float cos_r(float s) { return cosf(s); }
+__device__ __forceinline__ float cos_r(float s) { return __cosf(s); }
 __device__ __forceinline__ double exp_r(double s) { return exp(s); }
-__device__ __forceinline__ float exp_r(float s) { return expf(s); }
+__device__ __forceinline__ float exp_r(float s) { return __expf(s); }
 __device__ __forceinline__ double clamp_r(double v, double L) { return fmin(fmax(v, -L), L); }
 __device__ __forceinline__ float clamp_r(float v, float L) { return fminf(fmaxf(v, -L), L); }
 __device__ __forceinline__ double sqrtd_of(const Params &P, double) { return P.sqrt_d; }
@@ -225,10 +309,10 @@ __device__ __forceinline__ R model_f(const Params &P, int j, const R (&x)[D], R 
 #pragma unroll
         for (int l = 1; l < D; ++l) s += x[l];
         s = (sizeof(R) == 8) ? s / (R)P.sqrt_d : s * (R)P.inv_sqrt_d_f;
-        const R lam = Form<R>::prm(P, 0), kap = Form<R>::prm(P, 1), s0 = Form<R>::prm(P, 3);
+        const R kap = Form<R>::prm(P, 1);
         const R *sc = Form<R>::stepc(P) + 2 * j;
         const R c1 = __ldg(sc), c2 = __ldg(sc + 1);     // kap e_j^2, kapz s0^2 e_j^2
-        R v = (lam + (R)0.5 * s0 * s0) * y + kap * y * y;
+        R v = Form<R>::lin(P) * y + kap * y * y;        // (lam + s0^2/2) y + kap y^2
         if (ZIN) {
             R sn, cs;
             sincos_r(s, &sn, &cs);

@@ -28,7 +28,7 @@
 namespace srmc {
 namespace {
 
-constexpr int FLUSH = 8;
+constexpr int FLUSH = 16;
 
 template <int E>
 struct Moments64 {
@@ -81,6 +81,49 @@ struct Moments32 {
     }
 };
 
+// FP32 moments for long moment vectors: the path's E products are formed
+// after its time loop and reduced over the warp through a padded 32 x 33
+// shared-memory tile, 32 entries at a time; lane l keeps the running sums
+// of entries 32 c + l in double.  Nothing of size E stays live across the
+// time loop, which keeps the register count (and so the occupancy) of the
+// path simulation independent of E.
+template <int E>
+struct MomentsT {
+    static constexpr int NC = (E + 31) / 32;
+    double c[NC];
+    float *tile;
+    __device__ void zero() {
+#pragma unroll
+        for (int s = 0; s < NC; ++s) c[s] = 0.0;
+    }
+    template <typename F>
+    __device__ __forceinline__ void add_path(F &&entry, int lane) {
+#pragma unroll
+        for (int ch = 0; ch < NC; ++ch) {
+#pragma unroll
+            for (int e2 = 0; e2 < 32; ++e2)
+                if (32 * ch + e2 < E) tile[lane * 33 + e2] = entry(32 * ch + e2);
+            __syncwarp();
+            if (32 * ch + lane < E) {
+                float sum = 0.0f;
+#pragma unroll 8
+                for (int r = 0; r < 32; ++r) sum += tile[r * 33 + lane];
+                c[ch] += (double)sum;
+            }
+            __syncwarp();
+        }
+    }
+    __device__ void finish(double (&out)[NC], int) {
+#pragma unroll
+        for (int s = 0; s < NC; ++s) out[s] = c[s];
+    }
+};
+
+// Position (a, b), a <= b, of entry e of the packed upper triangle of a
+// p x p matrix stored row by row.
+__host__ __device__ constexpr int tri_a(int e, int p) { return e < p ? 0 : 1 + tri_a(e - p, p - 1); }
+__host__ __device__ constexpr int tri_b(int e, int p) { return e < p ? e : 1 + tri_b(e - p, p - 1); }
+
 template <typename R, int E> struct MomentsOf;
 template <int E> struct MomentsOf<double, E> { using type = Moments64<E>; };
 template <int E> struct MomentsOf<float, E> { using type = Moments32<E>; };
@@ -105,24 +148,19 @@ __device__ void block_totals(const double (&lanev)[(E + 31) / 32], double (*red)
     __syncthreads();
 }
 
-// Cholesky factor of the p x p Gram matrix (packed upper triangle, row-major
-// pairs a <= b) into L (row-major p x p).  Returns false if a pivot is below
-// 1e-12 of the trace (numerically singular).
+// Cholesky factor L (row-major p x p, shared memory) of the Gram matrix
+// given as its packed upper triangle (pairs a <= b, row by row).  Returns
+// false if a pivot is below 1e-12 of the trace (numerically singular).  Run
+// by one thread on shared memory so that it adds no registers to the path
+// simulation.
 template <int p>
 __device__ bool cholesky(const double *Gp, double *L)
 {
-    double G[p][p];
-    int e = 0;
-#pragma unroll
-    for (int a = 0; a < p; ++a)
-#pragma unroll
-        for (int b = a; b < p; ++b) { G[a][b] = Gp[e]; G[b][a] = Gp[e]; ++e; }
     double tr = 0.0;
-#pragma unroll
-    for (int a = 0; a < p; ++a) tr += G[a][a];
+    for (int a = 0; a < p; ++a) tr += Gp[a * p - a * (a - 1) / 2];
     for (int a = 0; a < p; ++a) {
         for (int b = 0; b <= a; ++b) {
-            double s = G[a][b];
+            double s = Gp[b * p - b * (b - 1) / 2 + (a - b)];     // G[b][a] = G[a][b]
             for (int c = 0; c < b; ++c) s -= L[a * p + c] * L[b * p + c];
             if (a == b) {
                 if (!(s > 1e-12 * tr)) return false;
@@ -136,17 +174,17 @@ __device__ bool cholesky(const double *Gp, double *L)
     return true;
 }
 
+// Solve L L^T x = r in place in x (shared memory; x may alias r).
 template <int p>
 __device__ void chol_solve(const double *L, const double *r, double *x)
 {
-    double y[p];
     for (int a = 0; a < p; ++a) {
         double s = r[a];
-        for (int c = 0; c < a; ++c) s -= L[a * p + c] * y[c];
-        y[a] = s / L[a * p + a];
+        for (int c = 0; c < a; ++c) s -= L[a * p + c] * x[c];
+        x[a] = s / L[a * p + a];
     }
     for (int a = p - 1; a >= 0; --a) {
-        double s = y[a];
+        double s = x[a];
         for (int c = a + 1; c < p; ++c) s -= L[c * p + a] * x[c];
         x[a] = s / L[a * p + a];
     }
@@ -162,26 +200,26 @@ __device__ __forceinline__ void eval_at(const Params &P, int j, const R (&x)[D],
         y = model_g<R, D, MODEL>(P, x);
         return;
     }
-    long long kk = 0;
+    unsigned kk = 0;
     R phi[p];
     phi[0] = (R)1;
 #pragma unroll
     for (int l = 0; l < D; ++l) {
         R t;
         const int c = locate_dim(x[l], Form<R>::lo(P, l), Form<R>::scale(P, l), P.cells[l], t);
-        kk += (long long)c * P.stride[l];
+        kk += (unsigned)c * (unsigned)P.stride[l];
         if (LP1) phi[1 + l] = (R)2 * (t - (R)c) - (R)1;
     }
-    const long long row = (long long)j * P.K + kk;
+    const unsigned row = (unsigned)j * (unsigned)P.K + kk;     // N K < 2^32 (checked at create)
     R a[p];
-    load_row<p>(Form<R>::Ytab(P) + row * Form<R>::ry(P), a);
+    load_row<p>(Form<R>::Ytab(P) + row * (unsigned)Form<R>::ry(P), a);
     R v = a[0];
 #pragma unroll
     for (int c = 1; c < p; ++c) v += a[c] * phi[c];
     y = clamp_r(v, Form<R>::Cy(P));
     if (ZIN) {
         R bz[D * p];
-        load_row<D * p>(Form<R>::Ztab(P) + row * Form<R>::rz(P), bz);
+        load_row<D * p>(Form<R>::Ztab(P) + row * (unsigned)Form<R>::rz(P), bz);
 #pragma unroll
         for (int l = 0; l < D; ++l) {
             R w = bz[l * p];
@@ -192,8 +230,22 @@ __device__ __forceinline__ void eval_at(const Params &P, int j, const R (&x)[D],
     }
 }
 
+// Blocks per SM the compiler must fit (register budget): FP32 forms of
+// higher dimension would otherwise take > 100 registers and run 2 blocks/SM.
+#ifndef SRMC_MINB_LO
+#define SRMC_MINB_LO 5
+#endif
+#ifndef SRMC_MINB_HI
+#define SRMC_MINB_HI 3
+#endif
+template <typename R, int D>
+struct MinBlocks {
+    static constexpr int value = sizeof(R) == 8 ? 1 : (D <= 2 ? SRMC_MINB_LO : SRMC_MINB_HI);
+};
+
 template <typename R, int D, bool LP1, int MODEL, bool ZIN>
-__global__ void __launch_bounds__(MAX_THREADS) step_kernel(const Params P, const int i)
+__global__ void __launch_bounds__(MAX_THREADS, MinBlocks<R, D>::value)
+step_kernel(const Params P, const int i)
 {
     constexpr int p = LP1 ? D + 1 : 1;
     constexpr int q = D;
@@ -201,8 +253,10 @@ __global__ void __launch_bounds__(MAX_THREADS) step_kernel(const Params P, const
     constexpr int EZ = q * p;
     constexpr int EA = EG + EZ + p;
     constexpr int EB = p;
-    using MA = typename MomentsOf<R, EA>::type;
+    constexpr bool TILE = sizeof(R) == 4 && EA > 24;
+    using MA = typename std::conditional<TILE, MomentsT<EA>, typename MomentsOf<R, EA>::type>::type;
     using MB = typename MomentsOf<R, EB>::type;
+    __shared__ float tiles[TILE ? MAX_WARPS * 32 * 33 : 1];
 
     __shared__ double redA[MAX_WARPS][EA];
     __shared__ double totA[EA];
@@ -234,62 +288,95 @@ __global__ void __launch_bounds__(MAX_THREADS) step_kernel(const Params P, const
         // ---------------- phase A: responses of the Z and Y fits ---------------
         MA mA;
         mA.zero();
+        if constexpr (TILE) mA.tile = tiles + warp * 32 * 33;
         int since_flush = 0;
         for (long long m0 = 0; m0 < P.M; m0 += blockDim.x) {
             const long long m = m0 + threadIdx.x;
             const bool valid = m < P.M;
             Words W;
-            W.init((unsigned)m, (unsigned)k, (unsigned)i, P.key0, P.key1);
-            R x[D], phi[p], dwi[D], xj[D], zj[D], yn, zn[D];
+            W.init(P, (unsigned)m, (unsigned)k, (unsigned)i);
+            R x[D], phi[p], dwi[D], xj[D], zj[D], yn;
             phi[0] = (R)1;
+            {
+                unsigned ws[D];
+                W.template take<0, D, true>(P, ws);
 #pragma unroll
-            for (int l = 0; l < D; ++l) {
-                x[l] = sample_cell(W.next(), Flo[l], Fchi[l], Wd[l], Form<R>::mu_arg(P));
-                if (LP1) {
-                    R t;
-                    if (sizeof(R) == 8) t = (x[l] - (R)P.lo[l]) / (R)P.h[l];
-                    else t = (x[l] - (R)P.lo_f[l]) * (R)P.r_f[l];
-                    phi[1 + l] = (R)2 * (t - (R)cell[l]) - (R)1;
+                for (int l = 0; l < D; ++l) {
+                    x[l] = sample_cell(ws[l], Flo[l], Fchi[l], Wd[l], Form<R>::mu_arg(P));
+                    if (LP1) {
+                        R t;
+                        if (sizeof(R) == 8) t = (x[l] - (R)P.lo[l]) / (R)P.h[l];
+                        else t = (x[l] - (R)P.lo_f[l]) * (R)P.r_f[l];
+                        phi[1 + l] = (R)2 * (t - (R)cell[l]) - (R)1;
+                    }
                 }
             }
+            {
+                unsigned wd[D];
+                W.template take<D % 4, D, false>(P, wd);
 #pragma unroll
-            for (int l = 0; l < D; ++l) {
-                dwi[l] = sdt * normal_of(W.next(), (R)0);
-                xj[l] = x[l] + Form<R>::b(P, l) * dt + Form<R>::sig(P, l) * dwi[l];
+                for (int l = 0; l < D; ++l) {
+                    dwi[l] = sdt * normal_of(wd[l], (R)0);
+                    xj[l] = x[l] + Form<R>::b(P, l) * dt + Form<R>::sig(P, l) * dwi[l];
+                }
             }
             eval_at<R, D, LP1, MODEL, ZIN>(P, i + 1, xj, yn, zj);
             R S = (R)0;
-            for (int j = i + 1; j < P.N; ++j) {
-                R xn[D];
+            // Steps j = i+1 .. N-1 in groups of G, so that the word phase of
+            // every step in a group is a compile-time constant.
+            constexpr int G = 4 / gcd_c(D, 4);
+            for (int j0 = i + 1; j0 < P.N; j0 += G) {
+                static_for<0, G>([&](auto gc) {
+                    constexpr int g = decltype(gc)::value;
+                    const int j = j0 + g;
+                    if (j >= P.N) return;
+                    unsigned wn[D];
+                    W.template take<(D + D * (1 + g)) % 4, D, false>(P, wn);
+                    R xn[D], zn[D];
 #pragma unroll
-                for (int l = 0; l < D; ++l) {
-                    const R dw = sdt * normal_of(W.next(), (R)0);
-                    xn[l] = xj[l] + Form<R>::b(P, l) * dt + Form<R>::sig(P, l) * dw;
-                }
-                eval_at<R, D, LP1, MODEL, ZIN>(P, j + 1, xn, yn, zn);
-                S += dt * model_f<R, D, MODEL, ZIN>(P, j, xj, yn, zj);
+                    for (int l = 0; l < D; ++l) {
+                        const R dw = sdt * normal_of(wn[l], (R)0);
+                        xn[l] = xj[l] + Form<R>::b(P, l) * dt + Form<R>::sig(P, l) * dw;
+                    }
+                    eval_at<R, D, LP1, MODEL, ZIN>(P, j + 1, xn, yn, zn);
+                    S += dt * model_f<R, D, MODEL, ZIN>(P, j, xj, yn, zj);
 #pragma unroll
-                for (int l = 0; l < D; ++l) { xj[l] = xn[l]; zj[l] = zn[l]; }
+                    for (int l = 0; l < D; ++l) { xj[l] = xn[l]; zj[l] = zn[l]; }
+                });
             }
             S += model_g<R, D, MODEL>(P, xj);
-            if (valid) {
-                int e = 0;
-                if (LP1) {
+            if constexpr (TILE) {
+                // entry e of this path's products (0 for lanes past M)
+                const R Sv = valid ? S : (R)0;
+                R wz[q];
 #pragma unroll
-                    for (int a = 0; a < p; ++a)
+                for (int l = 0; l < q; ++l) wz[l] = Sv * dwi[l] * inv_dt;
+                const R g1 = valid ? (R)1 : (R)0;
+                mA.add_path([&](int e) -> float {
+                    if (e < EG) return g1 * phi[tri_a(e, p)] * phi[tri_b(e, p)];
+                    if (e < EG + EZ) return phi[(e - EG) % p] * wz[(e - EG) / p];
+                    return phi[e - EG - EZ] * Sv;
+                }, lane);
+            } else {
+                if (valid) {
+                    int e = 0;
+                    if (LP1) {
 #pragma unroll
-                        for (int b = a; b < p; ++b) mA.add(e++, phi[a] * phi[b]);
+                        for (int a = 0; a < p; ++a)
+#pragma unroll
+                            for (int b = a; b < p; ++b) mA.add(e++, phi[a] * phi[b]);
+                    }
+#pragma unroll
+                    for (int l = 0; l < q; ++l) {
+                        const R wz = S * dwi[l] * inv_dt;
+#pragma unroll
+                        for (int a = 0; a < p; ++a) mA.add(EG + l * p + a, phi[a] * wz);
+                    }
+#pragma unroll
+                    for (int a = 0; a < p; ++a) mA.add(EG + EZ + a, phi[a] * S);
                 }
-#pragma unroll
-                for (int l = 0; l < q; ++l) {
-                    const R wz = S * dwi[l] * inv_dt;
-#pragma unroll
-                    for (int a = 0; a < p; ++a) mA.add(EG + l * p + a, phi[a] * wz);
-                }
-#pragma unroll
-                for (int a = 0; a < p; ++a) mA.add(EG + EZ + a, phi[a] * S);
+                if (++since_flush == FLUSH) { mA.flush(lane); since_flush = 0; }
             }
-            if (++since_flush == FLUSH) { mA.flush(lane); since_flush = 0; }
         }
         {
             double lv[(EA + 31) / 32];
@@ -323,23 +410,31 @@ __global__ void __launch_bounds__(MAX_THREADS) step_kernel(const Params P, const
             const long long m = m0 + threadIdx.x;
             const bool valid = m < P.M;
             Words W;
-            W.init((unsigned)m, (unsigned)k, (unsigned)i, P.key0, P.key1);
+            W.init(P, (unsigned)m, (unsigned)k, (unsigned)i);
             R x[D], phi[p], x1[D], y1, z1[D], zi[D];
             phi[0] = (R)1;
+            {
+                unsigned ws[D];
+                W.template take<0, D, true>(P, ws);
 #pragma unroll
-            for (int l = 0; l < D; ++l) {
-                x[l] = sample_cell(W.next(), Flo[l], Fchi[l], Wd[l], Form<R>::mu_arg(P));
-                if (LP1) {
-                    R t;
-                    if (sizeof(R) == 8) t = (x[l] - (R)P.lo[l]) / (R)P.h[l];
-                    else t = (x[l] - (R)P.lo_f[l]) * (R)P.r_f[l];
-                    phi[1 + l] = (R)2 * (t - (R)cell[l]) - (R)1;
+                for (int l = 0; l < D; ++l) {
+                    x[l] = sample_cell(ws[l], Flo[l], Fchi[l], Wd[l], Form<R>::mu_arg(P));
+                    if (LP1) {
+                        R t;
+                        if (sizeof(R) == 8) t = (x[l] - (R)P.lo[l]) / (R)P.h[l];
+                        else t = (x[l] - (R)P.lo_f[l]) * (R)P.r_f[l];
+                        phi[1 + l] = (R)2 * (t - (R)cell[l]) - (R)1;
+                    }
                 }
             }
+            {
+                unsigned wd[D];
+                W.template take<D % 4, D, false>(P, wd);
 #pragma unroll
-            for (int l = 0; l < D; ++l) {
-                const R dw = sdt * normal_of(W.next(), (R)0);
-                x1[l] = x[l] + Form<R>::b(P, l) * dt + Form<R>::sig(P, l) * dw;
+                for (int l = 0; l < D; ++l) {
+                    const R dw = sdt * normal_of(wd[l], (R)0);
+                    x1[l] = x[l] + Form<R>::b(P, l) * dt + Form<R>::sig(P, l) * dw;
+                }
             }
             eval_at<R, D, LP1, MODEL, ZIN>(P, i + 1, x1, y1, z1);
 #pragma unroll
@@ -366,12 +461,13 @@ __global__ void __launch_bounds__(MAX_THREADS) step_kernel(const Params P, const
         if (threadIdx.x == 0) {
             const double Md = (double)P.M;
             const double dtd = P.dt;
-            double rY[p], alpha[p];
-            for (int a = 0; a < p; ++a) rY[a] = totA[EG + EZ + a] + dtd * totB[a];
+            double *alpha = totB;                      // solved in place
+            for (int a = 0; a < p; ++a) alpha[a] = totA[EG + EZ + a] + dtd * totB[a];
             if (LP1 && ok_s) {
-                chol_solve<p>(Ls, rY, alpha);
+                chol_solve<p>(Ls, alpha, alpha);
             } else {
-                for (int a = 0; a < p; ++a) alpha[a] = (a == 0) ? rY[0] / Md : 0.0;
+                const double m0 = alpha[0] / Md;
+                for (int a = 0; a < p; ++a) alpha[a] = (a == 0) ? m0 : 0.0;
             }
             const long long row = (long long)i * P.K + k;
             bool finite = true;

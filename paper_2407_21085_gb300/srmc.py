@@ -14,7 +14,8 @@ import threading
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_build", "libsrmc.so")
+# SRMC_LIBRARY overrides the path (e.g. to compare two builds of the library).
+LIB_PATH = os.environ.get("SRMC_LIBRARY") or os.path.join(_HERE, "_build", "libsrmc.so")
 
 SRMC_OK = 0
 STATUS = {0: "SRMC_OK", 1: "SRMC_ERR_INVALID_ARG", 2: "SRMC_ERR_CUDA", 3: "SRMC_ERR_OOM",
