@@ -50,7 +50,10 @@ def fp32_peak_tflops(sms: int, mhz: float) -> float:
 def workload(name: str) -> W.Workload:
     makers = {"cfg1": W.cfg1, "cfg2": W.cfg2, "cfg2_fp64": lambda: W.cfg2(precision="fp64"),
               "cfg2_lp0": lambda: W.cfg2(basis="lp0"), "cfg3": W.cfg3, "cfg5": W.cfg5,
-              "cfg5_M1024": lambda: W.cfg5(M=1024, name="cfg5_d6_K262144_N40_M1024")}
+              "cfg5_M1024": lambda: W.cfg5(M=1024, name="cfg5_d6_K262144_N40_M1024"),
+              # reduced-M cases of the same kernels, for profiler captures
+              "cfg3_M2048": lambda: W.cfg3(M=2048, name="cfg3_d4_K20736_N50_M2048"),
+              "cfg5_M512": lambda: W.cfg5(M=512, name="cfg5_d6_K262144_N40_M512")}
     return makers[name]()
 
 
@@ -141,7 +144,7 @@ def run_gpu(args):
     w = workload(args.workload).replace(instance=workload(args.workload).instance + 1000 * rank)
     units = w.path_steps()
     stream = torch.cuda.current_stream()
-    solver = srmc.Solver(w)
+    solver = srmc.Solver(w, block_threads=args.block_threads)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
     def one_step(events=None):
@@ -190,10 +193,10 @@ def run_gpu(args):
     ny, nz = w.N * w.K * info["ry"], w.N * w.K * info["rz"]
     host_y = torch.empty(ny, dtype=torch.float64, pin_memory=True)
     host_z = torch.empty(nz, dtype=torch.float64, pin_memory=True)
-    for r in range(args.e2e_steps + 1):
+    for r in range(args.e2e_steps + 1 if args.e2e_steps > 0 else 0):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        s2 = srmc.Solver(w)
+        s2 = srmc.Solver(w, block_threads=args.block_threads)
         s2.srmc_solve(stream)
         s2.srmc_read_table(host_y, host_z, stream)
         stream.synchronize()
@@ -201,7 +204,7 @@ def run_gpu(args):
         if r > 0:
             e2e_ms.append((time.perf_counter() - t0) * 1e3)
     e2e_max = max_over_ranks(sum(e2e_ms), dev)
-    e2e_value = units * ws * len(e2e_ms) / (e2e_max / 1e3)
+    e2e_value = units * ws * len(e2e_ms) / (e2e_max / 1e3) if e2e_ms else None
     tab_bytes = (ny + nz) * 8
 
     # Roofline of the dominant kernel (the step kernel: every launch is one).
@@ -219,7 +222,7 @@ def run_gpu(args):
         "config": {"workload": w.name, "d": w.d, "strata": w.K, "N": w.N, "M": w.M, "basis": w.basis,
                    "precision": w.precision, "model": "cos (u = e^{lam(T-t)} cos(sum x/sqrt d))",
                    "path_steps_per_solve": units, "l2": "flushed between steps (512 MiB write)",
-                   "parallelism": f"replicas x{ws}"},
+                   "parallelism": f"replicas x{ws}", "block_threads": args.block_threads or "library"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": args.traffic,
                      "kernel": "step_kernel", "flops_per_unit": flops_per_path_step(w.d),
@@ -292,6 +295,7 @@ def main():
     ap.add_argument("--cpu-M", type=int, default=128, help="M of the bounded oracle sample")
     ap.add_argument("--ref-M", type=int, default=32, help="M of each reference-arm step")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--block-threads", type=int, default=0, help="threads per stratum block (0: library)")
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per step-kernel launch from an ncu capture of this kernel")
     args = ap.parse_args()

@@ -82,42 +82,78 @@ struct Moments32 {
 };
 
 // FP32 moments for long moment vectors: the path's E products are formed
-// after its time loop and reduced over the warp through a padded 32 x 33
-// shared-memory tile, 32 entries at a time; lane l keeps the running sums
-// of entries 32 c + l in double.  Nothing of size E stays live across the
-// time loop, which keeps the register count (and so the occupancy) of the
-// path simulation independent of E.
+// after its time loop and summed over the warp by recursive halving
+// (reduce-scatter): in round r every lane keeps one half of its vector and
+// adds the partner's copy of that half, so after five rounds each lane holds
+// LF = E / 32 (rounded up level by level) warp sums, which it adds to running
+// sums in double.  Nothing of size E stays live across the time loop, so the
+// registers of the path simulation do not grow with E, and no shared memory
+// is taken from L1.
+__host__ __device__ constexpr int halve(int L) { return (L + 1) / 2; }
+__host__ __device__ constexpr int rs_len(int E, int r) { return r == 0 ? E : halve(rs_len(E, r - 1)); }
+
 template <int E>
-struct MomentsT {
-    static constexpr int NC = (E + 31) / 32;
-    double c[NC];
-    float *tile;
-    __device__ void zero() {
+struct MomentsRS {
+    static constexpr int LF = rs_len(E, 5);
+    double c[LF];
+    int base;                          // entry index of c[0] held by this lane
+    int rend;                          // end of the real entries of this lane's slice
+    __device__ void zero(int lane) {
 #pragma unroll
-        for (int s = 0; s < NC; ++s) c[s] = 0.0;
-    }
-    template <typename F>
-    __device__ __forceinline__ void add_path(F &&entry, int lane) {
+        for (int s = 0; s < LF; ++s) c[s] = 0.0;
+        // In round r the slice [base, base + L_{r-1}) splits at L_r = rs_len(E, r):
+        // the upper half [base + L_r, ...) ends where the parent's real entries
+        // end; the lower half ends at base + L_r.  Slots past rend are padding.
+        base = 0;
+        rend = E;
 #pragma unroll
-        for (int ch = 0; ch < NC; ++ch) {
-#pragma unroll
-            for (int e2 = 0; e2 < 32; ++e2)
-                if (32 * ch + e2 < E) tile[lane * 33 + e2] = entry(32 * ch + e2);
-            __syncwarp();
-            if (32 * ch + lane < E) {
-                float sum = 0.0f;
-#pragma unroll 8
-                for (int r = 0; r < 32; ++r) sum += tile[r * 33 + lane];
-                c[ch] += (double)sum;
-            }
-            __syncwarp();
+        for (int r = 1; r <= 5; ++r) {
+            const int L = rs_len(E, r);
+            if (lane & (32 >> r)) base += L;
+            else rend = min(rend, base + L);
         }
     }
-    __device__ void finish(double (&out)[NC], int) {
+    template <int L, int O>
+    __device__ __forceinline__ static void round(const float (&v)[L], float (&o)[halve(L)], int lane) {
+        constexpr int H = halve(L);
+        const bool up = (lane & O) != 0;
 #pragma unroll
-        for (int s = 0; s < NC; ++s) out[s] = c[s];
+        for (int k = 0; k < H; ++k) {
+            const float lo = v[k];
+            const float hi = (k + H < L) ? v[k + H] : 0.0f;
+            const float mine = up ? hi : lo;
+            const float other = up ? lo : hi;
+            o[k] = mine + __shfl_xor_sync(0xffffffffu, other, O);
+        }
+    }
+    __device__ __forceinline__ void add_path(const float (&v)[E], int lane) {
+        float a1[rs_len(E, 1)], a2[rs_len(E, 2)], a3[rs_len(E, 3)], a4[rs_len(E, 4)], a5[LF];
+        round<E, 16>(v, a1, lane);
+        round<rs_len(E, 1), 8>(a1, a2, lane);
+        round<rs_len(E, 2), 4>(a2, a3, lane);
+        round<rs_len(E, 3), 2>(a3, a4, lane);
+        round<rs_len(E, 4), 1>(a4, a5, lane);
+#pragma unroll
+        for (int s = 0; s < LF; ++s) c[s] += (double)a5[s];
     }
 };
+
+// Block totals of reduce-scattered moments: lane values go to their entries.
+template <int E, int LF>
+__device__ void block_totals_rs(const double (&c)[LF], int base, int rend, double (*red)[E],
+                                double *tot, int warp, int nwarps)
+{
+#pragma unroll
+    for (int s = 0; s < LF; ++s)
+        if (base + s < rend) red[warp][base + s] = c[s];
+    __syncthreads();
+    for (int e = threadIdx.x; e < E; e += blockDim.x) {
+        double v = 0.0;
+        for (int w = 0; w < nwarps; ++w) v += red[w][e];
+        tot[e] = v;
+    }
+    __syncthreads();
+}
 
 // Position (a, b), a <= b, of entry e of the packed upper triangle of a
 // p x p matrix stored row by row.
@@ -149,44 +185,53 @@ __device__ void block_totals(const double (&lanev)[(E + 31) / 32], double (*red)
 }
 
 // Cholesky factor L (row-major p x p, shared memory) of the Gram matrix
-// given as its packed upper triangle (pairs a <= b, row by row).  Returns
-// false if a pivot is below 1e-12 of the trace (numerically singular).  Run
-// by one thread on shared memory so that it adds no registers to the path
-// simulation.
+// given as its packed upper triangle (pairs a <= b, row by row), computed by
+// one warp (right-looking: pivot by lane 0, column and trailing update spread
+// over the lanes); Linv holds 1 / L[a][a].  Returns false (in every lane) if
+// a pivot is below 1e-12 of the trace: numerically singular.  G is a
+// p x p shared-memory work array.
 template <int p>
-__device__ bool cholesky(const double *Gp, double *L)
+__device__ bool cholesky_warp(const double *Gp, double *G, double *L, double *Linv, int lane)
 {
+    for (int e = lane; e < p * p; e += 32) {
+        const int a = e / p, b = e % p;
+        const int r = a < b ? a : b, c = a < b ? b : a;
+        G[e] = Gp[r * p - r * (r - 1) / 2 + (c - r)];
+        L[e] = 0.0;
+    }
+    __syncwarp();
     double tr = 0.0;
-    for (int a = 0; a < p; ++a) tr += Gp[a * p - a * (a - 1) / 2];
-    for (int a = 0; a < p; ++a) {
-        for (int b = 0; b <= a; ++b) {
-            double s = Gp[b * p - b * (b - 1) / 2 + (a - b)];     // G[b][a] = G[a][b]
-            for (int c = 0; c < b; ++c) s -= L[a * p + c] * L[b * p + c];
-            if (a == b) {
-                if (!(s > 1e-12 * tr)) return false;
-                L[a * p + a] = sqrt(s);
-            } else {
-                L[a * p + b] = s / L[b * p + b];
-            }
+    for (int a = 0; a < p; ++a) tr += G[a * p + a];
+    for (int b = 0; b < p; ++b) {
+        const double piv = G[b * p + b];
+        if (!(piv > 1e-12 * tr)) return false;          // uniform: every lane reads the same value
+        const double ld = sqrt(piv), inv = 1.0 / ld;
+        for (int a = b + 1 + lane; a < p; a += 32) L[a * p + b] = G[a * p + b] * inv;
+        if (lane == 0) { L[b * p + b] = ld; Linv[b] = inv; }
+        __syncwarp();
+        const int m = p - 1 - b;                          // trailing (m x m) lower part
+        for (int t = lane; t < m * m; t += 32) {
+            const int a = b + 1 + t / m, c = b + 1 + t % m;
+            if (c <= a) G[a * p + c] -= L[a * p + b] * L[c * p + b];
         }
-        for (int b = a + 1; b < p; ++b) L[a * p + b] = 0.0;
+        __syncwarp();
     }
     return true;
 }
 
-// Solve L L^T x = r in place in x (shared memory; x may alias r).
+// Solve L L^T x = r (L, Linv from cholesky_warp) into x (may alias r).
 template <int p>
-__device__ void chol_solve(const double *L, const double *r, double *x)
+__device__ void chol_solve(const double *L, const double *Linv, const double *r, double *x)
 {
     for (int a = 0; a < p; ++a) {
         double s = r[a];
         for (int c = 0; c < a; ++c) s -= L[a * p + c] * x[c];
-        x[a] = s / L[a * p + a];
+        x[a] = s * Linv[a];
     }
     for (int a = p - 1; a >= 0; --a) {
         double s = x[a];
         for (int c = a + 1; c < p; ++c) s -= L[c * p + a] * x[c];
-        x[a] = s / L[a * p + a];
+        x[a] = s * Linv[a];
     }
 }
 
@@ -232,11 +277,12 @@ __device__ __forceinline__ void eval_at(const Params &P, int j, const R (&x)[D],
 
 // Blocks per SM the compiler must fit (register budget): FP32 forms of
 // higher dimension would otherwise take > 100 registers and run 2 blocks/SM.
+// (Measured on GB300: 5 blocks for d <= 2 and 4 for d >= 3 are best.)
 #ifndef SRMC_MINB_LO
 #define SRMC_MINB_LO 5
 #endif
 #ifndef SRMC_MINB_HI
-#define SRMC_MINB_HI 3
+#define SRMC_MINB_HI 4
 #endif
 template <typename R, int D>
 struct MinBlocks {
@@ -253,16 +299,17 @@ step_kernel(const Params P, const int i)
     constexpr int EZ = q * p;
     constexpr int EA = EG + EZ + p;
     constexpr int EB = p;
-    constexpr bool TILE = sizeof(R) == 4 && EA > 24;
-    using MA = typename std::conditional<TILE, MomentsT<EA>, typename MomentsOf<R, EA>::type>::type;
+    constexpr bool RS = sizeof(R) == 4 && EA > 24;
+    using MA = typename std::conditional<RS, MomentsRS<EA>, typename MomentsOf<R, EA>::type>::type;
     using MB = typename MomentsOf<R, EB>::type;
-    __shared__ float tiles[TILE ? MAX_WARPS * 32 * 33 : 1];
 
     __shared__ double redA[MAX_WARPS][EA];
     __shared__ double totA[EA];
     __shared__ double redB[MAX_WARPS][EB];
     __shared__ double totB[EB];
     __shared__ double Ls[p * p];
+    __shared__ double Gw[p * p];
+    __shared__ double Linv[p];
     __shared__ double beta_s[q * p];
     __shared__ R beta_r[q * p];
     __shared__ int ok_s;
@@ -287,8 +334,7 @@ step_kernel(const Params P, const int i)
 
         // ---------------- phase A: responses of the Z and Y fits ---------------
         MA mA;
-        mA.zero();
-        if constexpr (TILE) mA.tile = tiles + warp * 32 * 33;
+        if constexpr (RS) mA.zero(lane); else mA.zero();
         int since_flush = 0;
         for (long long m0 = 0; m0 < P.M; m0 += blockDim.x) {
             const long long m = m0 + threadIdx.x;
@@ -345,18 +391,22 @@ step_kernel(const Params P, const int i)
                 });
             }
             S += model_g<R, D, MODEL>(P, xj);
-            if constexpr (TILE) {
-                // entry e of this path's products (0 for lanes past M)
-                const R Sv = valid ? S : (R)0;
-                R wz[q];
+            if constexpr (RS) {
+                // this path's products (zero for lanes past M)
+                const float Sv = valid ? (float)S : 0.0f;
+                const float g1 = valid ? 1.0f : 0.0f;
+                float v[EA];
 #pragma unroll
-                for (int l = 0; l < q; ++l) wz[l] = Sv * dwi[l] * inv_dt;
-                const R g1 = valid ? (R)1 : (R)0;
-                mA.add_path([&](int e) -> float {
-                    if (e < EG) return g1 * phi[tri_a(e, p)] * phi[tri_b(e, p)];
-                    if (e < EG + EZ) return phi[(e - EG) % p] * wz[(e - EG) / p];
-                    return phi[e - EG - EZ] * Sv;
-                }, lane);
+                for (int e = 0; e < EG; ++e) v[e] = g1 * phi[tri_a(e, p)] * phi[tri_b(e, p)];
+#pragma unroll
+                for (int l = 0; l < q; ++l) {
+                    const float wz = Sv * (float)dwi[l] * (float)inv_dt;
+#pragma unroll
+                    for (int a = 0; a < p; ++a) v[EG + l * p + a] = (float)phi[a] * wz;
+                }
+#pragma unroll
+                for (int a = 0; a < p; ++a) v[EG + EZ + a] = (float)phi[a] * Sv;
+                mA.add_path(v, lane);
             } else {
                 if (valid) {
                     int e = 0;
@@ -378,27 +428,31 @@ step_kernel(const Params P, const int i)
                 if (++since_flush == FLUSH) { mA.flush(lane); since_flush = 0; }
             }
         }
-        {
+        if constexpr (RS) {
+            block_totals_rs<EA>(mA.c, mA.base, mA.rend, redA, totA, warp, nwarps);
+        } else {
             double lv[(EA + 31) / 32];
             mA.finish(lv, lane);
             block_totals<EA>(lv, redA, totA, lane, warp, nwarps);
         }
 
-        // ---------------- Z fit (FP64) ------------------------------------------
-        if (threadIdx.x == 0) {
+        // ---------------- Z fit (FP64, one warp) -----------------------------
+        if (warp == 0) {
             const double Md = (double)P.M;
             bool ok = true;
-            if (LP1) ok = cholesky<p>(totA, Ls);
-            for (int l = 0; l < q; ++l) {
+            if (LP1) ok = cholesky_warp<p>(totA, Gw, Ls, Linv, lane);
+            __syncwarp();
+            for (int l = lane; l < q; l += 32) {
                 if (LP1 && ok) {
-                    chol_solve<p>(Ls, totA + EG + l * p, beta_s + l * p);
+                    chol_solve<p>(Ls, Linv, totA + EG + l * p, beta_s + l * p);
                 } else {
-                    for (int a = 0; a < p; ++a)
-                        beta_s[l * p + a] = (a == 0) ? totA[EG + l * p] / Md : 0.0;
+                    const double m0 = totA[EG + l * p] / Md;
+                    for (int a = 0; a < p; ++a) beta_s[l * p + a] = (a == 0) ? m0 : 0.0;
                 }
             }
-            for (int a = 0; a < q * p; ++a) beta_r[a] = (R)beta_s[a];
-            ok_s = ok ? 1 : 0;
+            __syncwarp();
+            for (int a = lane; a < q * p; a += 32) beta_r[a] = (R)beta_s[a];
+            if (lane == 0) ok_s = ok ? 1 : 0;
         }
         __syncthreads();
 
@@ -464,7 +518,7 @@ step_kernel(const Params P, const int i)
             double *alpha = totB;                      // solved in place
             for (int a = 0; a < p; ++a) alpha[a] = totA[EG + EZ + a] + dtd * totB[a];
             if (LP1 && ok_s) {
-                chol_solve<p>(Ls, alpha, alpha);
+                chol_solve<p>(Ls, Linv, alpha, alpha);
             } else {
                 const double m0 = alpha[0] / Md;
                 for (int a = 0; a < p; ++a) alpha[a] = (a == 0) ? m0 : 0.0;
