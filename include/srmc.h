@@ -124,8 +124,10 @@ srmc_status srmc_create(const srmc_problem *problem, const srmc_strata *strata,
 void srmc_destroy(srmc_solver *s);
 
 /* The whole backward recursion of Alg. SRMDP, i = N-1 .. 0, enqueued on
- * stream: per step one launch over all strata (Z fit, then Y fit).
- * Asynchronous; results are valid once the stream has reached this point. */
+ * stream: per step one launch over all strata (Z fit, then Y fit).  The N
+ * launches are captured once into a CUDA graph (on a private stream, at the
+ * first call) and replayed on `stream` by every call.  Asynchronous; results
+ * are valid once the stream has reached this point. */
 srmc_status srmc_solve(srmc_solver *s, void *stream);
 
 /* One step i of Alg. SRMDP for all strata.  Requires the rows of steps
@@ -156,6 +158,16 @@ srmc_status srmc_table(const srmc_solver *s, const double **dev_y64, const doubl
  * or pageable) or device; either may be NULL.  Asynchronous on stream for
  * device or pinned destinations; the caller synchronises before reading. */
 srmc_status srmc_read_table(const srmc_solver *s, double *dst_y, double *dst_z, void *stream);
+
+/* Error of the fitted functions against the closed-form solution of the
+ * model at the K stratum centres, for every step i = 0..N-1 (the metric of
+ * the benchmark plan; Sec. 5.1 uses the same comparison at nu-distributed
+ * points).  dev_out: [N][4] doubles: max_k |y_i - u|, mean_k (y_i - u)^2,
+ * max_k max_l |z_i,l - z*_l|, mean_k |z_i - z*|^2.  Cos model: u = e^{lam(T-t)}
+ * cos(s), z* = -s0 e^{lam(T-t)} sin(s) / sqrt(d) (sigma = s0 I); logistic model
+ * (Sec. 5.1): u = w/(1+w), z*_l = w/(1+w)^2.  SRMC_ERR_UNSUPPORTED for the
+ * affine model.  Requires a finished solve. */
+srmc_status srmc_closed_form_error(const srmc_solver *s, double *dev_out, void *stream);
 
 /* Counters since creation: [0] strata fits that fell back from LP1 to LP0
  * because the Gram matrix was numerically singular (Cholesky pivot below

@@ -27,6 +27,8 @@ struct srmc_solver {
     float *Y32 = nullptr, *Z32 = nullptr;
     double *Y64 = nullptr, *Z64 = nullptr;
     unsigned long long *stats = nullptr;
+    cudaStream_t cap_stream = nullptr;   // private stream for graph capture
+    cudaGraphExec_t graph = nullptr;     // the N step launches of one solve
 };
 
 namespace {
@@ -62,6 +64,8 @@ int pad_to(int v, int m) { return (v + m - 1) / m * m; }
 
 void free_all(srmc_solver *s)
 {
+    if (s->graph) cudaGraphExecDestroy(s->graph);
+    if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
     cudaFree(s->cellF); cudaFree(s->cellF_f); cudaFree(s->stepc); cudaFree(s->stepc_f);
     cudaFree(s->Y32); cudaFree(s->Z32); cudaFree(s->Y64); cudaFree(s->Z64); cudaFree(s->stats);
 }
@@ -420,10 +424,106 @@ srmc_status srmc_solve_step(srmc_solver *s, int i, void *stream)
 srmc_status srmc_solve(srmc_solver *s, void *stream)
 {
     if (!s) return fail(SRMC_ERR_INVALID_ARG, "srmc_solve: NULL solver");
-    for (int i = s->P.N - 1; i >= 0; --i) {
-        SRMC_CUDA(launch_step(s, i, (cudaStream_t)stream), "step kernel launch");
+    if (!s->graph) {
+        if (!s->cap_stream)
+            SRMC_CUDA(cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking), "graph stream");
+        cudaGraph_t g = nullptr;
+        SRMC_CUDA(cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+        cudaError_t le = cudaSuccess;
+        for (int i = s->P.N - 1; i >= 0 && le == cudaSuccess; --i) le = launch_step(s, i, s->cap_stream);
+        cudaError_t ce = cudaStreamEndCapture(s->cap_stream, &g);
+        if (le != cudaSuccess) { if (g) cudaGraphDestroy(g); return cuda_fail(le, "step kernel capture"); }
+        if (ce != cudaSuccess) return cuda_fail(ce, "end capture");
+        cudaError_t ie = cudaGraphInstantiate(&s->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (ie != cudaSuccess) { s->graph = nullptr; return cuda_fail(ie, "graph instantiate"); }
     }
+    SRMC_CUDA(cudaGraphLaunch(s->graph, (cudaStream_t)stream), "graph launch");
     s->done_from = 0;
+    return SRMC_OK;
+}
+
+namespace {
+__device__ void closed_form(const Params &P, int i, const double *x, double &u, double *zs)
+{
+    const double t = (double)i * P.dt;
+    double sx = 0.0;
+    for (int l = 0; l < P.d; ++l) sx += x[l];
+    if (P.model == srmc::MODEL_COS) {
+        const double e = exp(P.prm[0] * (P.T - t));
+        const double s = sx / P.sqrt_d;
+        u = e * cos(s);
+        for (int l = 0; l < P.q; ++l) zs[l] = -P.prm[3] * e * sin(s) / P.sqrt_d;
+    } else {
+        const double w = exp(t + sx);
+        u = w / (1.0 + w);
+        for (int l = 0; l < P.q; ++l) zs[l] = w / ((1.0 + w) * (1.0 + w));
+    }
+}
+
+// One block per step: errors of y_i, z_i at every stratum centre.
+__global__ void closed_form_error_kernel(const Params P, double *out)
+{
+    const int i = blockIdx.x;
+    double ymax = 0.0, ysq = 0.0, zmax = 0.0, zsq = 0.0;
+    for (long long k = threadIdx.x; k < P.K; k += blockDim.x) {
+        double x[srmc::DMAX], phi[srmc::DMAX + 1], zs[srmc::DMAX], u;
+        long long rem = k;
+        phi[0] = 1.0;
+        for (int l = 0; l < P.d; ++l) {
+            const int c = (int)(rem % P.cells[l]);
+            rem /= P.cells[l];
+            x[l] = P.lo[l] + ((double)c + 0.5) * P.h[l];
+            phi[1 + l] = 0.0;                    // centre of the nominal cell
+        }
+        closed_form(P, i, x, u, zs);
+        const long long row = (long long)i * P.K + k;
+        const double *al = P.Y64 + row * P.ry64;
+        double v = al[0];
+        for (int c = 1; c < P.p; ++c) v += al[c] * phi[c];
+        const double dy = fmin(fmax(v, -P.Cy), P.Cy) - u;
+        ymax = fmax(ymax, fabs(dy));
+        ysq += dy * dy;
+        const double *be = P.Z64 + row * P.rz64;
+        for (int l = 0; l < P.q; ++l) {
+            double w = be[l * P.p];
+            for (int c = 1; c < P.p; ++c) w += be[l * P.p + c] * phi[c];
+            const double dz = fmin(fmax(w, -P.Cz), P.Cz) - zs[l];
+            zmax = fmax(zmax, fabs(dz));
+            zsq += dz * dz;
+        }
+    }
+    __shared__ double red[4][32];
+    for (int o = 16; o > 0; o >>= 1) {
+        ymax = fmax(ymax, __shfl_xor_sync(0xffffffffu, ymax, o));
+        ysq += __shfl_xor_sync(0xffffffffu, ysq, o);
+        zmax = fmax(zmax, __shfl_xor_sync(0xffffffffu, zmax, o));
+        zsq += __shfl_xor_sync(0xffffffffu, zsq, o);
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) { red[0][warp] = ymax; red[1][warp] = ysq; red[2][warp] = zmax; red[3][warp] = zsq; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0, b = 0, c = 0, e = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            a = fmax(a, red[0][w]); b += red[1][w]; c = fmax(c, red[2][w]); e += red[3][w];
+        }
+        out[4 * i + 0] = a;
+        out[4 * i + 1] = b / (double)P.K;
+        out[4 * i + 2] = c;
+        out[4 * i + 3] = e / (double)P.K;
+    }
+}
+}  // namespace
+
+srmc_status srmc_closed_form_error(const srmc_solver *s, double *out, void *stream)
+{
+    if (!s || !out) return fail(SRMC_ERR_INVALID_ARG, "srmc_closed_form_error: NULL argument");
+    if (s->P.model == srmc::MODEL_AFFINE)
+        return fail(SRMC_ERR_UNSUPPORTED, "srmc_closed_form_error: no closed form for the affine model");
+    if (s->done_from > 0) return fail(SRMC_ERR_STATE, "srmc_closed_form_error: solve not finished");
+    closed_form_error_kernel<<<s->P.N, 256, 0, (cudaStream_t)stream>>>(s->P, out);
+    SRMC_CUDA(cudaGetLastError(), "closed form error kernel launch");
     return SRMC_OK;
 }
 

@@ -73,6 +73,7 @@ def lib():
                                      C.POINTER(i_), C.POINTER(ll)]
             L.srmc_stats.argtypes = [vp, C.POINTER(C.c_ulonglong)]
             L.srmc_read_table.argtypes = [vp, vp, vp, vp]
+            L.srmc_closed_form_error.argtypes = [vp, vp, vp]
             L.srmc_philox.argtypes = [vp, C.POINTER(C.c_uint32), ll, vp, vp]
             L.srmc_normals.argtypes = [vp, ll, vp, vp, vp]
             L.srmc_locate.argtypes = [vp, vp, vp, ll, vp, vp]
@@ -80,7 +81,8 @@ def lib():
             L.srmc_last_error.restype = C.c_char_p
             L.srmc_version.restype = C.c_int
             for name in ("srmc_create", "srmc_solve", "srmc_solve_step", "srmc_eval", "srmc_centres",
-                         "srmc_table", "srmc_read_table", "srmc_stats", "srmc_philox", "srmc_normals", "srmc_locate",
+                         "srmc_table", "srmc_read_table", "srmc_closed_form_error", "srmc_stats", "srmc_philox",
+                         "srmc_normals", "srmc_locate",
                          "srmc_start_points"):
                 getattr(L, name).restype = C.c_int
             _lib = L
@@ -114,7 +116,8 @@ def exported_symbols():
     """Names declared in include/srmc.h that the loaded library exports."""
     L = lib()
     return [n for n in ("srmc_create", "srmc_destroy", "srmc_solve", "srmc_solve_step", "srmc_eval",
-                        "srmc_centres", "srmc_table", "srmc_read_table", "srmc_stats", "srmc_philox",
+                        "srmc_centres", "srmc_table", "srmc_read_table", "srmc_closed_form_error",
+                        "srmc_stats", "srmc_philox",
                         "srmc_normals",
                         "srmc_locate", "srmc_start_points", "srmc_last_error", "srmc_version")
             if hasattr(L, n)]
@@ -180,6 +183,16 @@ class Solver:
     def srmc_read_table(self, dst_y, dst_z, stream=None):
         """Copy the FP64 tables into caller tensors (host, pinned or device)."""
         _check(lib().srmc_read_table(self._h, _ptr(dst_y), _ptr(dst_z), _stream(stream)))
+
+    def srmc_closed_form_error(self, out, stream=None):
+        _check(lib().srmc_closed_form_error(self._h, _ptr(out), _stream(stream)))
+
+    def closed_form_error(self):
+        """[N][4] (max|dy|, mean dy^2, max|dz|, mean |dz|^2) at the centres, as numpy."""
+        import torch
+        out = torch.empty((self.w.N, 4), dtype=torch.float64, device="cuda")
+        self.srmc_closed_form_error(out)
+        return out.cpu().numpy()
 
     def srmc_stats(self):
         out = (C.c_ulonglong * 3)()

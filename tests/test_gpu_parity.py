@@ -222,3 +222,58 @@ def test_cfg3_full_size_sampled(dev, orc):
     # 12^4 strata, N=50, M=16384, kapz=0.2, FP32 form
     w = W.cfg3()
     _sampled_parity(dev, orc, w, steps=[w.N - 1, w.N - 2], n_strata=3)
+
+
+def test_graph_solve_equals_step_launches(dev):
+    # srmc_solve replays a captured graph of the N launches; srmc_solve_step
+    # launches them one by one: the tables must be identical.
+    torch, srmc = dev
+    w = W.cfg2(C=8, N=5, M=300)
+    a = srmc.Solver(w)
+    a.srmc_solve()
+    a.srmc_solve()                               # a second replay of the same graph
+    b = srmc.Solver(w)
+    for i in range(w.N - 1, -1, -1):
+        b.srmc_solve_step(i)
+    t = a.srmc_table()
+    ny, nz = w.N * w.K * t["ry"], w.N * w.K * t["rz"]
+    ya, za = torch.empty(ny, dtype=torch.float64, device="cuda"), torch.empty(nz, dtype=torch.float64, device="cuda")
+    yb, zb = torch.empty_like(ya), torch.empty_like(za)
+    a.srmc_read_table(ya, za)
+    b.srmc_read_table(yb, zb)
+    torch.cuda.synchronize()
+    assert torch.equal(ya, yb) and torch.equal(za, zb)
+
+
+@pytest.mark.parametrize("model", ["cos", "logistic"])
+def test_closed_form_error_kernel(dev, model):
+    # The on-device error reduction equals the same statistics computed on the
+    # host from srmc_eval at the centres and the closed form of the model.
+    torch, srmc = dev
+    if model == "cos":
+        w = W.cfg2(C=16, N=6, M=512, kapz=0.1)
+    else:
+        w = W.logistic_paper(d=2, N=5, C=8, M=400)
+    s = srmc.Solver(w)
+    s.srmc_solve()
+    err = s.closed_form_error()
+    x = s.centres()
+    xn = x.cpu().numpy()
+    for i in range(w.N):
+        y, z = s.evaluate(i, x)
+        y, z = y.cpu().numpy(), z.cpu().numpy()
+        t = i * w.dt
+        if model == "cos":
+            lam, s0 = w.params[0], w.params[3]
+            sv = xn.sum(1) / math.sqrt(w.d)
+            u = math.exp(lam * (1 - t)) * np.cos(sv)
+            zs = np.repeat((-s0 * math.exp(lam * (1 - t)) * np.sin(sv) / math.sqrt(w.d))[:, None], w.d, 1)
+        else:
+            om = np.exp(t + xn.sum(1))
+            u = om / (1 + om)
+            zs = np.repeat((om / (1 + om) ** 2)[:, None], w.d, 1)
+        want = [np.max(np.abs(y - u)), np.mean((y - u) ** 2), np.max(np.abs(z - zs)),
+                np.mean(np.sum((z - zs) ** 2, axis=1))]
+        assert np.allclose(err[i], want, rtol=1e-9, atol=1e-14), (i, err[i], want)
+    # the fitted solution is close to the closed form (scheme + time-discretisation error)
+    assert err[:, 0].max() < 0.1
