@@ -114,6 +114,13 @@ def _bind(L):
     L.orc_eval.restype = C.c_int64
     L.orc_fallbacks.argtypes = [C.c_void_p]; L.orc_fallbacks.restype = C.c_int64
     L.orc_path_steps.argtypes = [C.c_void_p]; L.orc_path_steps.restype = C.c_int64
+    L.orc_set_control.argtypes = [C.c_void_p, dp]; L.orc_set_control.restype = C.c_int
+    fp = C.POINTER(C.c_float)
+    L.orc_mlp_nparams.argtypes = [C.c_int, C.c_int]; L.orc_mlp_nparams.restype = C.c_int
+    L.orc_bf16.argtypes = [C.c_double]; L.orc_bf16.restype = C.c_float
+    L.orc_mlp_eval.argtypes = [fp, C.c_int, C.c_int, C.c_int, dp, dp, dp]
+    L.orc_mlp_loss_grad.argtypes = [fp, C.c_int, C.c_int, C.c_int, C.c_int64, dp, dp, dp]
+    L.orc_mlp_loss_grad.restype = C.c_double
     return L
 
 
@@ -290,6 +297,15 @@ class Oracle:
                 self.fit_lazy(i, locate(self.w, x[a]))
         return self.eval(i, x)
 
+    def set_control(self, rows):
+        """Control rows [N][K][q][p] (centred basis) or None."""
+        if rows is None:
+            self._L.orc_set_control(self._ctx, None)
+            return
+        self._control = np.ascontiguousarray(rows, dtype=np.float64)
+        if self._L.orc_set_control(self._ctx, _dptr(self._control)) != 0:
+            raise MemoryError("oracle: control rows")
+
     @property
     def fallbacks(self) -> int:
         return int(self._L.orc_fallbacks(self._ctx))
@@ -297,3 +313,43 @@ class Oracle:
     @property
     def path_steps(self) -> int:
         return int(self._L.orc_path_steps(self._ctx))
+
+
+# ---- the MLP of the learned control variate ---------------------------------
+def mlp_nparams(nin, H):
+    return int(lib().orc_mlp_nparams(nin, H))
+
+
+def bf16(v):
+    return float(lib().orc_bf16(float(v)))
+
+
+def _fptr(a):
+    return a.ctypes.data_as(C.POINTER(C.c_float))
+
+
+def mlp_eval(params, nin, H, a, bf16_round=False):
+    """u and the input gradient at the rows of a (n x nin)."""
+    prm = np.ascontiguousarray(params, dtype=np.float32)
+    a = np.ascontiguousarray(np.atleast_2d(a), dtype=np.float64)
+    n = a.shape[0]
+    u = np.zeros(n)
+    g = np.zeros((n, nin))
+    L = lib()
+    for s in range(n):
+        uu = C.c_double()
+        gg = np.zeros(nin)
+        L.orc_mlp_eval(_fptr(prm), nin, H, int(bf16_round), _dptr(a[s]), C.byref(uu), _dptr(gg))
+        u[s] = uu.value
+        g[s] = gg
+    return u, g
+
+
+def mlp_loss_grad(params, nin, H, a, y, bf16_round=False):
+    prm = np.ascontiguousarray(params, dtype=np.float32)
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    g = np.zeros(mlp_nparams(nin, H))
+    loss = lib().orc_mlp_loss_grad(_fptr(prm), nin, H, int(bf16_round), a.shape[0], _dptr(a),
+                                   _dptr(y), _dptr(g))
+    return loss, g

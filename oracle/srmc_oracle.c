@@ -346,6 +346,7 @@ int orc_lstsq_householder(int n, int p, int r, double *A, double *B, double *X)
 /* ------------------------------------------------------------------------ */
 struct orc_ctx {
     orc_problem P;
+    double *control;    /* [N][K][q][dimb] centred-basis control rows, or NULL */
     int64_t K;          /* number of strata                                 */
     int dimb;           /* basis dimension: 1 (LP0) or d+1 (LP1)            */
     int R;              /* row length (1+q)*dimb                            */
@@ -374,12 +375,46 @@ orc_ctx *orc_create(const orc_problem *P)
 void orc_destroy(orc_ctx *C)
 {
     if (!C) return;
+    free(C->control);
     free(C->rows);
     free(C->done);
     free(C);
 }
 
 int orc_row_len(const orc_ctx *C) { return C->R; }
+
+int orc_set_control(orc_ctx *C, const double *rows)
+{
+    free(C->control);
+    C->control = NULL;
+    if (!rows) return 0;
+    size_t n = (size_t)C->P.N * (size_t)C->K * (size_t)C->P.q * (size_t)C->dimb;
+    C->control = (double *)malloc(sizeof(double) * n);
+    if (!C->control) return 1;
+    memcpy(C->control, rows, sizeof(double) * n);
+    return 0;
+}
+
+/* zc_j(x) . dw for a point x of stratum k (control rows in the centred basis
+ * [1, (x - c_k)/(h/2)], values truncated at C_z). */
+static double control_dot(const orc_ctx *C, int j, int64_t k, const double *x, const double *dw)
+{
+    const orc_problem *P = &C->P;
+    const int p = C->dimb;
+    double phi[ORC_DMAX + 1], ctr[ORC_DMAX];
+    orc_stratum_centre(P, k, ctr);
+    phi[0] = 1.0;
+    if (p > 1)
+        for (int l = 0; l < P->d; ++l) phi[1 + l] = (x[l] - ctr[l]) / (0.5 * cell_width(P, l));
+    const double *row = C->control + ((size_t)j * (size_t)C->K + (size_t)k) * (size_t)(P->q * p);
+    double s = 0.0;
+    for (int l = 0; l < P->q; ++l) {
+        double v = 0.0;
+        for (int c = 0; c < p; ++c) v += row[l * p + c] * phi[c];
+        s += trunc_L(v, P->Cz) * dw[l];
+    }
+    return s;
+}
 int64_t orc_fallbacks(const orc_ctx *C) { return C->fallbacks; }
 int64_t orc_path_steps(const orc_ctx *C) { return C->path_steps; }
 
@@ -444,6 +479,8 @@ static int64_t fit_impl(orc_ctx *C, int i, int64_t k, int lazy)
     double *DW = (double *)malloc(sizeof(double) * (size_t)(M * q));   /* Delta W_i */
     double *S1 = (double *)malloc(sizeof(double) * (size_t)M);         /* S_{Y,i+1} */
     double *Y1 = (double *)malloc(sizeof(double) * (size_t)M);         /* y_{i+1}(x_{i+1}) */
+    double *CZ = (double *)calloc((size_t)M, sizeof(double));          /* sum_{j>i} zc_j.dW_j */
+    double *CI = (double *)calloc((size_t)M, sizeof(double));          /* zc_i(x_i).dW_i */
     double *A = (double *)malloc(sizeof(double) * (size_t)(M * p));
     double *B = (double *)malloc(sizeof(double) * (size_t)(M * (q > 1 ? q : 1)));
     double *coef = (double *)malloc(sizeof(double) * (size_t)(p * (q > 1 ? q : 1)));
@@ -467,6 +504,10 @@ static int64_t fit_impl(orc_ctx *C, int i, int64_t k, int lazy)
                 xn[l] = v;
             }
             steps++;
+            if (C->control) {
+                const double cd = control_dot(C, j, j == i ? k : orc_locate(P, x), x, dw);
+                if (j == i) CI[m] = cd; else CZ[m] += cd;
+            }
             if (j + 1 == N) {
                 yn = orc_g(P, xn);
             } else {
@@ -493,14 +534,14 @@ static int64_t fit_impl(orc_ctx *C, int i, int64_t k, int lazy)
         /* Z: OLS of S_{Y,i+1} Delta W_i / dt on L_{Z,k}. */
         for (int64_t m = 0; m < M; ++m) {
             basis(C, X0 + m * d, A + m * p);
-            for (int l = 0; l < q; ++l) B[m * q + l] = S1[m] * DW[m * q + l] / dt;
+            for (int l = 0; l < q; ++l) B[m * q + l] = (S1[m] - CZ[m]) * DW[m * q + l] / dt;
         }
         if (p == 1 || orc_lstsq_householder((int)M, p, q, A, B, coef)) {
             /* LP0, eq. lp0 explicit: the mean (also the fallback). */
             if (p > 1) fell_back = 1;
             for (int l = 0; l < q; ++l) {
                 double s = 0.0;
-                for (int64_t m = 0; m < M; ++m) s += S1[m] * DW[m * q + l] / dt;
+                for (int64_t m = 0; m < M; ++m) s += (S1[m] - CZ[m]) * DW[m * q + l] / dt;
                 for (int c = 0; c < p; ++c) coef[c * q + l] = (c == 0) ? s / (double)M : 0.0;
             }
         }
@@ -518,7 +559,7 @@ static int64_t fit_impl(orc_ctx *C, int i, int64_t k, int lazy)
                 zi[l] = trunc_L(w, P->Cz);
             }
             for (int c = 0; c < p; ++c) A[m * p + c] = phi[c];
-            B[m] = S1[m] + orc_f(P, i, X0 + m * d, Y1[m], zi) * dt;
+            B[m] = S1[m] + orc_f(P, i, X0 + m * d, Y1[m], zi) * dt - CZ[m] - CI[m];
         }
         double ysum = 0.0;
         for (int64_t m = 0; m < M; ++m) ysum += B[m];
@@ -537,7 +578,7 @@ static int64_t fit_impl(orc_ctx *C, int i, int64_t k, int lazy)
 #pragma omp atomic
     C->path_steps += steps;
 
-    free(X0); free(DW); free(S1); free(Y1); free(A); free(B); free(coef);
+    free(X0); free(DW); free(S1); free(Y1); free(CZ); free(CI); free(A); free(B); free(coef);
     return missing;
 }
 
@@ -586,4 +627,115 @@ int64_t orc_eval(orc_ctx *C, int i, int64_t n, const double *x, double *y, doubl
         eval_row(C, row, xa, y + a, z + a * P->q);
     }
     return missing;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Small MLP u(a) with SiLU activations, forward, input gradient and the    */
+/* gradient of the mean squared error (plain backpropagation).              */
+/* ------------------------------------------------------------------------ */
+int orc_mlp_nparams(int nin, int H) { return H * nin + H + H * H + H + H + 1; }
+
+float orc_bf16(double v)
+{
+    float f = (float)v;
+    uint32_t b;
+    memcpy(&b, &f, 4);
+    b += 0x7FFFu + ((b >> 16) & 1u);        /* round to nearest, ties to even */
+    b &= 0xFFFF0000u;
+    memcpy(&f, &b, 4);
+    return f;
+}
+
+static double rnd(double v, int bf16) { return bf16 ? (double)orc_bf16(v) : v; }
+static double sigm(double z) { return 1.0 / (1.0 + exp(-z)); }
+
+typedef struct {
+    const float *W1, *b1, *W2, *b2, *w3, *b3;
+} mlp_view;
+
+static mlp_view mlp_split(const float *prm, int nin, int H)
+{
+    mlp_view v;
+    v.W1 = prm; v.b1 = v.W1 + H * nin; v.W2 = v.b1 + H; v.b2 = v.W2 + H * H; v.w3 = v.b2 + H;
+    v.b3 = v.w3 + H;
+    return v;
+}
+
+/* Forward pass keeping what the backward passes need. */
+static double mlp_forward(const mlp_view *m, int nin, int H, int bf16, const double *a, double *ar,
+                          double *z1, double *h1r, double *z2, double *h2)
+{
+    for (int c = 0; c < nin; ++c) ar[c] = rnd(a[c], bf16);
+    for (int o = 0; o < H; ++o) {
+        double s = 0.0;
+        for (int c = 0; c < nin; ++c) s += rnd(m->W1[o * nin + c], bf16) * ar[c];
+        z1[o] = s + m->b1[o];
+        h1r[o] = rnd(z1[o] * sigm(z1[o]), bf16);
+    }
+    double u = m->b3[0];
+    for (int o = 0; o < H; ++o) {
+        double s = 0.0;
+        for (int c = 0; c < H; ++c) s += rnd(m->W2[o * H + c], bf16) * h1r[c];
+        z2[o] = s + m->b2[o];
+        h2[o] = z2[o] * sigm(z2[o]);
+        u += (double)m->w3[o] * h2[o];
+    }
+    return u;
+}
+
+static double dsilu(double z) { double sg = sigm(z); return sg * (1.0 + z * (1.0 - sg)); }
+
+void orc_mlp_eval(const float *prm, int nin, int H, int bf16, const double *a, double *u,
+                  double *grad_a)
+{
+    mlp_view m = mlp_split(prm, nin, H);
+    double ar[64], z1[256], h1r[256], z2[256], h2[256], gz2[256], gz1[256];
+    *u = mlp_forward(&m, nin, H, bf16, a, ar, z1, h1r, z2, h2);
+    if (!grad_a) return;
+    for (int o = 0; o < H; ++o) gz2[o] = rnd((double)m.w3[o] * dsilu(z2[o]), bf16);
+    for (int c = 0; c < H; ++c) {
+        double s = 0.0;
+        for (int o = 0; o < H; ++o) s += gz2[o] * rnd(m.W2[o * H + c], bf16);
+        gz1[c] = rnd(s * dsilu(z1[c]), bf16);
+    }
+    for (int c = 0; c < nin; ++c) {
+        double s = 0.0;
+        for (int o = 0; o < H; ++o) s += gz1[o] * rnd(m.W1[o * nin + c], bf16);
+        grad_a[c] = s;
+    }
+}
+
+double orc_mlp_loss_grad(const float *prm, int nin, int H, int bf16, int64_t n, const double *a,
+                         const double *y, double *grad)
+{
+    mlp_view m = mlp_split(prm, nin, H);
+    const int P = orc_mlp_nparams(nin, H);
+    double *gW1 = grad, *gb1 = gW1 + H * nin, *gW2 = gb1 + H, *gb2 = gW2 + H * H, *gw3 = gb2 + H;
+    double *gb3 = gw3 + H;
+    for (int q = 0; q < P; ++q) grad[q] = 0.0;
+    double loss = 0.0;
+    double ar[64], z1[256], h1r[256], z2[256], h2[256], gz2[256], gz1[256];
+    for (int64_t s = 0; s < n; ++s) {
+        double u = mlp_forward(&m, nin, H, bf16, a + s * nin, ar, z1, h1r, z2, h2);
+        double r = u - y[s];
+        loss += r * r;
+        double du = 2.0 * r / (double)n;
+        gb3[0] += du;
+        for (int o = 0; o < H; ++o) {
+            gw3[o] += du * h2[o];
+            gz2[o] = rnd(du * (double)m.w3[o] * dsilu(z2[o]), bf16);
+            gb2[o] += gz2[o];
+        }
+        for (int o = 0; o < H; ++o)
+            for (int c = 0; c < H; ++c) gW2[o * H + c] += gz2[o] * h1r[c];
+        for (int c = 0; c < H; ++c) {
+            double t = 0.0;
+            for (int o = 0; o < H; ++o) t += gz2[o] * rnd(m.W2[o * H + c], bf16);
+            gz1[c] = rnd(t * dsilu(z1[c]), bf16);
+            gb1[c] += gz1[c];
+        }
+        for (int o = 0; o < H; ++o)
+            for (int c = 0; c < nin; ++c) gW1[o * nin + c] += gz1[o] * ar[c];
+    }
+    return loss / (double)n;
 }

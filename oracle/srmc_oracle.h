@@ -95,10 +95,31 @@ const double *orc_row(const orc_ctx *C, int i, int64_t k);
 /* Truncated y_i(x), z_i(x) at n points (row-major n x d); rows must exist.
  * Returns the number of points whose row is missing. */
 int64_t  orc_eval(orc_ctx *C, int i, int64_t n, const double *x, double *y, double *z);
+/* Control variate (a martingale control subtracted from the responses):
+ * rows [N][K][q][p] in the centred basis phi = [1, (x - c_k)/(h/2)] give
+ * zc_j(x) = T_Cz(beta . phi(x)) for x in stratum k; the Y response loses
+ * sum_{j>=i} zc_j(X_j).dW_j and the Z response sum_{j>i} zc_j(X_j).dW_j.
+ * Both have zero conditional mean given x_i, so the fitted functions keep
+ * their expectation.  The rows are copied; NULL removes the control. */
+int      orc_set_control(orc_ctx *C, const double *rows);
+
 /* Number of (i,k) fits that fell back to LP0 because R was singular. */
 int64_t  orc_fallbacks(const orc_ctx *C);
 /* Path-steps simulated so far (diagnostic; one unit = one Euler step). */
 int64_t  orc_path_steps(const orc_ctx *C);
+
+/* ---- small MLP u(a), a = (t, x_1..x_d): nin -> H -> H -> 1, SiLU ----------
+ * Parameter vector (float): W1 [H][nin], b1 [H], W2 [H][H], b2 [H], w3 [H], b3.
+ * bf16 != 0 rounds to bfloat16 (nearest even) exactly where the GPU kernels
+ * feed tensor-core operands: the inputs, W1, h1, W2, and in the backward pass
+ * g_z2 and g_z1; everything else is FP64. */
+int    orc_mlp_nparams(int nin, int H);
+float  orc_bf16(double v);
+void   orc_mlp_eval(const float *prm, int nin, int H, int bf16, const double *a, double *u,
+                    double *grad_a);
+/* Mean squared error (1/n) sum (u(a_s) - y_s)^2 and its gradient (nparams). */
+double orc_mlp_loss_grad(const float *prm, int nin, int H, int bf16, int64_t n, const double *a,
+                         const double *y, double *grad);
 
 #ifdef __cplusplus
 }

@@ -171,3 +171,66 @@ def affine(d: int, N: int, C: int, M: int, g0: float, gv, f0: float, fv, a: floa
 
 
 ALL = {"cfg1": cfg1, "cfg2": cfg2, "cfg3": cfg3, "cfg5": cfg5}
+
+
+# ---- inputs of the control-variate form ---------------------------------------
+def centres(w: Workload):
+    """Stratum centres [K][d] (centre of the nominal finite cell), k with
+    dimension 0 fastest."""
+    import numpy as np
+    idx = np.arange(w.K)
+    out = np.zeros((w.K, w.d))
+    for l in range(w.d):
+        c = idx % w.cells[l]
+        idx = idx // w.cells[l]
+        h = (w.hi[l] - w.lo[l]) / w.cells[l]
+        out[:, l] = w.lo[l] + (c + 0.5) * h
+    return out
+
+
+def control_rows(w: Workload, fn):
+    """Tabulate a control function fn(t, X[n][d]) -> [n][q] on the strata as
+    rows [N][K][q][p] in the centred basis [1, (x - c_k)/(h/2)]: the value at
+    the centre and, for LP1, central differences at c +- (h/4) e_m (a step of
+    one unit of the centred coordinate)."""
+    import numpy as np
+    p = 1 if w.basis == "lp0" else w.d + 1
+    ctr = centres(w)
+    h = (np.array(w.hi) - np.array(w.lo)) / np.array(w.cells)
+    rows = np.zeros((w.N, w.K, w.q, p))
+    for j in range(w.N):
+        t = j * w.T / w.N
+        rows[j, :, :, 0] = fn(t, ctr)
+        if p > 1:
+            for m in range(w.d):
+                e = np.zeros(w.d)
+                e[m] = h[m] / 4
+                rows[j, :, :, 1 + m] = fn(t, ctr + e) - fn(t, ctr - e)
+    return rows
+
+
+def closed_form_z(w: Workload):
+    """z*(t, x) = s0 grad u of the cos family (-s0 e^{lam(T-t)} sin(s)/sqrt(d)
+    in every component) as a function for control_rows."""
+    import numpy as np
+    lam, s0 = w.params[0], w.params[3]
+
+    def fn(t, X):
+        s = X.sum(axis=1) / math.sqrt(w.d)
+        v = -s0 * np.exp(lam * (w.T - t)) * np.sin(s) / math.sqrt(w.d)
+        return np.repeat(v[:, None], w.q, axis=1)
+    return fn
+
+
+def random_smooth_z(w: Workload, seed: int = 0, scale: float = 0.3):
+    """A seeded smooth function R^d -> R^q (a few random Fourier modes), used as
+    an arbitrary control in unbiasedness tests."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    F = rng.normal(size=(4, w.d))
+    A = rng.normal(size=(4, w.q)) * scale
+    ph = rng.uniform(0, 2 * math.pi, size=4)
+
+    def fn(t, X):
+        return np.cos(X @ F.T + ph + t) @ A
+    return fn
