@@ -159,6 +159,65 @@ srmc_status srmc_table(const srmc_solver *s, const double **dev_y64, const doubl
  * device or pinned destinations; the caller synchronises before reading. */
 srmc_status srmc_read_table(const srmc_solver *s, double *dst_y, double *dst_z, void *stream);
 
+/* Martingale control variate (an extension of Alg. SRMDP, not in the
+ * paper): with rows beta_{j,k} installed, every response of cloud C_{i,k}
+ * loses the control built from zc_j(x) = T_Cz(beta_{j,k} . phi(x)), x in H_k:
+ * the Y response loses sum_{j>=i} zc_j(X_j).dW_j and the Z response
+ * sum_{j>i} zc_j(X_j).dW_j.  Both terms have zero conditional mean given
+ * x_i (dW_j is independent of everything known at t_j), so the fitted
+ * functions keep their expectation while the response variance drops when
+ * zc approximates the true z = sigma^T grad u.  rows: [N][K][q][p] doubles,
+ * host or device memory, centred basis phi = [1, (x - c_k)/(h/2)]; copied
+ * (synchronously).  LP1 solvers only (SRMC_ERR_UNSUPPORTED otherwise). */
+srmc_status srmc_set_control(srmc_solver *s, const double *rows);
+
+/* Remove the control variate (the plain scheme again). */
+srmc_status srmc_clear_control(srmc_solver *s);
+
+/* Copy the installed control rows ([N][K][q][p] doubles) into caller memory
+ * (host or device); SRMC_ERR_STATE if no control is installed. */
+srmc_status srmc_read_control(const srmc_solver *s, double *rows);
+
+/* ---- learned control variate: a small MLP u_theta(t, x) -------------------
+ * (an extension of the paper's scheme).  Architecture: a = (t, x_1..x_d)
+ * (n_in = d + 1 <= 15) -> 64 -> 64 -> 1 with SiLU activations.  Parameters
+ * (FP32 master copy, float vector): W1 [64][n_in], b1 [64], W2 [64][64],
+ * b2 [64], w3 [64], b3.  The kernels run the two 64-wide layers on BF16
+ * tensor-core tiles with FP32 accumulation: inputs, W1, h1, W2 (and in the
+ * backward passes g_z2, g_z1) are rounded to bfloat16, everything else is
+ * FP32.  Training: mean squared error, Adam (beta1 0.9, beta2 0.999). */
+typedef struct srmc_mlp srmc_mlp;   /* opaque, library-owned */
+
+/* Create on the current device with seeded initial weights (uniform
+ * +-sqrt(6/fan_in), biases 0).  hidden must be 64. */
+srmc_status srmc_mlp_create(int n_in, int hidden, unsigned long long seed, srmc_mlp **out);
+void srmc_mlp_destroy(srmc_mlp *m);
+int srmc_mlp_nparams(const srmc_mlp *m);
+/* Parameter vector in/out (host or device pointer, float[nparams]); copied. */
+srmc_status srmc_mlp_set_params(srmc_mlp *m, const float *params);
+srmc_status srmc_mlp_get_params(const srmc_mlp *m, float *params);
+/* u(a) and the input gradient du/da at n points: dev_a [n][n_in] float,
+ * dev_u [n], dev_grad [n][n_in] (may be NULL). */
+srmc_status srmc_mlp_eval(const srmc_mlp *m, const float *dev_a, long long n, float *dev_u,
+                          float *dev_grad, void *stream);
+/* Gradient of the loss (1/n) sum (u(a_s) - y_s)^2 with respect to the
+ * parameters into dev_grad [nparams] and the loss into dev_loss [1]. */
+srmc_status srmc_mlp_loss_grad(srmc_mlp *m, const float *dev_a, const float *dev_y, long long n,
+                               float *dev_grad, float *dev_loss, void *stream);
+/* Train on n_data points drawn from a finished (coarse) solve: steps i and
+ * strata k uniform, x ~ nu_k, a = (t_i, x), target y_i(x) from its FP64 table.
+ * iters Adam steps on consecutive batches (lr decays geometrically to lr/10).
+ * dev_loss_curve [iters] (may be NULL) receives the batch losses.
+ * n_data must be a multiple of batch. */
+srmc_status srmc_mlp_fit(srmc_mlp *m, const srmc_solver *coarse, long long n_data, int iters,
+                         int batch, float lr, unsigned long long seed, float *dev_loss_curve,
+                         void *stream);
+/* Tabulate zc = sigma^T grad_x u_theta(t_j, .) as the control rows of s for
+ * every (j, k): value at the stratum centre and central differences at
+ * +-h/4 along each axis (LP1 rows in the centred basis), then install them as
+ * by srmc_set_control.  LP1 solvers with d <= 7, n_in == d + 1. */
+srmc_status srmc_cv_tabulate(const srmc_mlp *m, srmc_solver *s, void *stream);
+
 /* Error of the fitted functions against the closed-form solution of the
  * model at the K stratum centres, for every step i = 0..N-1 (the metric of
  * the benchmark plan; Sec. 5.1 uses the same comparison at nu-distributed

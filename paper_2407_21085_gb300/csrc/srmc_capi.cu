@@ -13,23 +13,6 @@
 
 using srmc::Params;
 
-struct srmc_solver {
-    Params P;                   // device pointers inside point to the buffers below
-    int device;
-    bool fp64, lp1;
-    int mv;                     // model variant of the step kernel
-    int threads;
-    int done_from;              // every step >= done_from has been enqueued
-    double *cellF = nullptr;
-    float *cellF_f = nullptr;
-    double *stepc = nullptr;
-    float *stepc_f = nullptr;
-    float *Y32 = nullptr, *Z32 = nullptr;
-    double *Y64 = nullptr, *Z64 = nullptr;
-    unsigned long long *stats = nullptr;
-    cudaStream_t cap_stream = nullptr;   // private stream for graph capture
-    cudaGraphExec_t graph = nullptr;     // the N step launches of one solve
-};
 
 namespace {
 
@@ -68,11 +51,14 @@ void free_all(srmc_solver *s)
     if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
     cudaFree(s->cellF); cudaFree(s->cellF_f); cudaFree(s->stepc); cudaFree(s->stepc_f);
     cudaFree(s->Y32); cudaFree(s->Z32); cudaFree(s->Y64); cudaFree(s->Z64); cudaFree(s->stats);
+    cudaFree(s->C32); cudaFree(s->C64);
 }
 
 cudaError_t launch_step(const srmc_solver *s, int i, cudaStream_t st)
 {
-    const Params &P = s->P;
+    Params P = s->P;
+    P.C32 = s->cv ? s->C32 : nullptr;
+    P.C64 = s->cv ? s->C64 : nullptr;
     const int grid = (int)(P.K < 2147483647LL ? P.K : 2147483647LL);
     switch (P.d) {
     case 1: return srmc::launch_step_d1(P, i, s->fp64, s->lp1, s->mv, grid, s->threads, st);
@@ -572,6 +558,69 @@ srmc_status srmc_read_table(const srmc_solver *s, double *dst_y, double *dst_z, 
     if (dst_z)
         SRMC_CUDA(cudaMemcpyAsync(dst_z, s->Z64, sizeof(double) * rows * s->P.rz64, cudaMemcpyDefault,
                                   (cudaStream_t)stream), "srmc_read_table: copy z");
+    return SRMC_OK;
+}
+
+namespace {
+// [N][K][q][p] -> padded rows of the FP64 and FP32 control tables.
+__global__ void repack_control_kernel(const Params P, const double *src, double *c64, float *c32)
+{
+    const long long rows = (long long)P.N * P.K;
+    const int qp = P.q * P.p;
+    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < rows;
+         r += (long long)gridDim.x * blockDim.x) {
+        for (int a = 0; a < qp; ++a) {
+            const double v = src[r * qp + a];
+            c64[r * P.rz64 + a] = v;
+            c32[r * P.rz32 + a] = (float)v;
+        }
+    }
+}
+}  // namespace
+
+srmc_status srmc_set_control(srmc_solver *s, const double *rows)
+{
+    if (!s || !rows) return fail(SRMC_ERR_INVALID_ARG, "srmc_set_control: NULL argument");
+    if (!s->lp1) return fail(SRMC_ERR_UNSUPPORTED, "srmc_set_control: LP1 solvers only");
+    if (s->mv == srmc::MV_AFFINE) return fail(SRMC_ERR_UNSUPPORTED, "srmc_set_control: not for the affine model");
+    const size_t nrow = (size_t)s->P.N * (size_t)s->P.K;
+    const size_t n = nrow * (size_t)(s->P.q * s->P.p);
+    if (!s->C64) {
+        SRMC_CUDA(cudaMalloc(&s->C64, sizeof(double) * nrow * s->P.rz64), "cudaMalloc control");
+        SRMC_CUDA(cudaMalloc(&s->C32, sizeof(float) * nrow * s->P.rz32), "cudaMalloc control");
+        SRMC_CUDA(cudaMemset(s->C64, 0, sizeof(double) * nrow * s->P.rz64), "cudaMemset control");
+        SRMC_CUDA(cudaMemset(s->C32, 0, sizeof(float) * nrow * s->P.rz32), "cudaMemset control");
+    }
+    double *staging = nullptr;
+    SRMC_CUDA(cudaMalloc(&staging, sizeof(double) * n), "cudaMalloc control staging");
+    cudaError_t e = cudaMemcpy(staging, rows, sizeof(double) * n, cudaMemcpyDefault);
+    if (e == cudaSuccess) {
+        repack_control_kernel<<<grid_for((long long)nrow, 256), 256>>>(s->P, staging, s->C64, s->C32);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    cudaFree(staging);
+    if (e != cudaSuccess) return cuda_fail(e, "srmc_set_control");
+    s->cv = true;
+    if (s->graph) { cudaGraphExecDestroy(s->graph); s->graph = nullptr; }
+    return SRMC_OK;
+}
+
+srmc_status srmc_read_control(const srmc_solver *s, double *rows)
+{
+    if (!s || !rows) return fail(SRMC_ERR_INVALID_ARG, "srmc_read_control: NULL argument");
+    if (!s->cv || !s->C64) return fail(SRMC_ERR_STATE, "srmc_read_control: no control installed");
+    const size_t nrow = (size_t)s->P.N * (size_t)s->P.K, qp = (size_t)(s->P.q * s->P.p);
+    SRMC_CUDA(cudaMemcpy2D(rows, qp * sizeof(double), s->C64, (size_t)s->P.rz64 * sizeof(double),
+                           qp * sizeof(double), nrow, cudaMemcpyDefault), "srmc_read_control");
+    return SRMC_OK;
+}
+
+srmc_status srmc_clear_control(srmc_solver *s)
+{
+    if (!s) return fail(SRMC_ERR_INVALID_ARG, "srmc_clear_control: NULL solver");
+    s->cv = false;
+    if (s->graph) { cudaGraphExecDestroy(s->graph); s->graph = nullptr; }
     return SRMC_OK;
 }
 

@@ -46,6 +46,8 @@ struct Params {
     const float *stepc_f;
     float *Y32, *Z32;               // [N][K][ry32], [N][K][rz32]; N K r < 2^32
     double *Y64, *Z64;              // [N][K][ry64], [N][K][rz64]
+    const float *C32;               // control rows [N][K][rz32] (same layout as Z32)
+    const double *C64;              // control rows [N][K][rz64]
     unsigned long long *stats;      // [0] LP1->LP0 fallbacks, [1] non-finite rows
 };
 
@@ -245,6 +247,7 @@ template <> struct Form<double> {
     __device__ static const double *Ytab(const Params &P) { return P.Y64; }
     __device__ static const double *Ztab(const Params &P) { return P.Z64; }
     __device__ static int ry(const Params &P) { return P.ry64; }
+    __device__ static const double *Ctab(const Params &P) { return P.C64; }
     __device__ static int rz(const Params &P) { return P.rz64; }
 };
 template <> struct Form<float> {
@@ -264,6 +267,7 @@ template <> struct Form<float> {
     __device__ static const float *Ytab(const Params &P) { return P.Y32; }
     __device__ static const float *Ztab(const Params &P) { return P.Z32; }
     __device__ static int ry(const Params &P) { return P.ry32; }
+    __device__ static const float *Ctab(const Params &P) { return P.C32; }
     __device__ static int rz(const Params &P) { return P.rz32; }
 };
 

@@ -25,4 +25,48 @@ SRMC_DECLARE_STEP(7)
 SRMC_DECLARE_STEP(8)
 #undef SRMC_DECLARE_STEP
 
+// Table-row evaluation of y_i(x) in FP64 (truncated), x in double; the
+// kernel-side twin of srmc_eval used by the MLP data generator.
+__device__ __forceinline__ double eval_y64(const Params &P, int i, const double *x)
+{
+    double phi[DMAX + 1];
+    phi[0] = 1.0;
+    long long k = 0;
+    for (int l = 0; l < P.d; ++l) {
+        double t;
+        const int c = locate_dim(x[l], P.lo[l], P.h[l], P.cells[l], t);
+        k += (long long)c * P.stride[l];
+        phi[1 + l] = 2.0 * (t - (double)c) - 1.0;
+    }
+    const double *al = P.Y64 + ((long long)i * P.K + k) * P.ry64;
+    double v = al[0];
+    for (int c = 1; c < P.p; ++c) v += al[c] * phi[c];
+    return fmin(fmax(v, -P.Cy), P.Cy);
+}
+
 }  // namespace srmc
+
+using srmc::Params;
+
+// The solver object behind the opaque srmc_solver handle.
+struct srmc_solver {
+    Params P;                   // device pointers inside point to the buffers below
+    int device;
+    bool fp64, lp1;
+    int mv;                     // model variant of the step kernel
+    int threads;
+    int done_from;              // every step >= done_from has been enqueued
+    double *cellF = nullptr;
+    float *cellF_f = nullptr;
+    double *stepc = nullptr;
+    float *stepc_f = nullptr;
+    float *Y32 = nullptr, *Z32 = nullptr;
+    double *Y64 = nullptr, *Z64 = nullptr;
+    unsigned long long *stats = nullptr;
+    float *C32 = nullptr;                // control rows (FP32 copy, padded like Z32)
+    double *C64 = nullptr;               // control rows (FP64, padded like Z64)
+    bool cv = false;                     // control installed
+    cudaStream_t cap_stream = nullptr;   // private stream for graph capture
+    cudaGraphExec_t graph = nullptr;     // the N step launches of one solve
+};
+

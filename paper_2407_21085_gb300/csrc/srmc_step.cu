@@ -237,8 +237,11 @@ __device__ void chol_solve(const double *L, const double *Linv, const double *r,
 
 // y_{j}(x), z_{j}(x) from the row of the stratum holding x (truncated), or
 // g(x) when j == N.
-template <typename R, int D, bool LP1, int MODEL, bool ZIN>
-__device__ __forceinline__ void eval_at(const Params &P, int j, const R (&x)[D], R &y, R (&z)[D])
+// With CV, also hands back phi(x) and the row index of (j, stratum of x), from
+// which the control of the next increment is evaluated.
+template <typename R, int D, bool LP1, int MODEL, bool ZIN, bool CV>
+__device__ __forceinline__ void eval_at(const Params &P, int j, const R (&x)[D], R &y, R (&z)[D],
+                                        R (&phio)[LP1 ? D + 1 : 1], unsigned &rowo)
 {
     constexpr int p = LP1 ? D + 1 : 1;
     if (j == P.N) {
@@ -273,6 +276,29 @@ __device__ __forceinline__ void eval_at(const Params &P, int j, const R (&x)[D],
             z[l] = clamp_r(w, Form<R>::Cz(P));
         }
     }
+    if constexpr (CV) {
+#pragma unroll
+        for (int c = 0; c < p; ++c) phio[c] = phi[c];
+        rowo = row;
+    }
+}
+
+// zc(x) . dw for the control row `row` and the basis values phi of x:
+// sum_l T_Cz(beta_l . phi) dw_l (the martingale control of one increment).
+template <typename R, int D, int p>
+__device__ __forceinline__ R control_dot(const Params &P, unsigned row, const R (&phi)[p],
+                                         const R (&dw)[D])
+{
+    const R *b = Form<R>::Ctab(P) + row * (unsigned)Form<R>::rz(P);
+    R acc = (R)0;
+#pragma unroll
+    for (int l = 0; l < D; ++l) {
+        R w = __ldg(b + l * p);
+#pragma unroll
+        for (int c = 1; c < p; ++c) w += __ldg(b + l * p + c) * phi[c];
+        acc += clamp_r(w, Form<R>::Cz(P)) * dw[l];
+    }
+    return acc;
 }
 
 // Blocks per SM the compiler must fit (register budget): FP32 forms of
@@ -284,13 +310,14 @@ __device__ __forceinline__ void eval_at(const Params &P, int j, const R (&x)[D],
 #ifndef SRMC_MINB_HI
 #define SRMC_MINB_HI 4
 #endif
-template <typename R, int D>
+template <typename R, int D, bool CV>
 struct MinBlocks {
-    static constexpr int value = sizeof(R) == 8 ? 1 : (D <= 2 ? SRMC_MINB_LO : SRMC_MINB_HI);
+    static constexpr int value = sizeof(R) == 8 ? 1 : CV ? (D <= 2 ? 4 : 3)
+                                                        : (D <= 2 ? SRMC_MINB_LO : SRMC_MINB_HI);
 };
 
-template <typename R, int D, bool LP1, int MODEL, bool ZIN>
-__global__ void __launch_bounds__(MAX_THREADS, MinBlocks<R, D>::value)
+template <typename R, int D, bool LP1, int MODEL, bool ZIN, bool CV>
+__global__ void __launch_bounds__(MAX_THREADS, MinBlocks<R, D, CV>::value)
 step_kernel(const Params P, const int i)
 {
     constexpr int p = LP1 ? D + 1 : 1;
@@ -366,7 +393,13 @@ step_kernel(const Params P, const int i)
                     xj[l] = x[l] + Form<R>::b(P, l) * dt + Form<R>::sig(P, l) * dwi[l];
                 }
             }
-            eval_at<R, D, LP1, MODEL, ZIN>(P, i + 1, xj, yn, zj);
+            // Martingale control: CI = zc_i(x_i).dW_i (stratum k), CZ = sum_{j>i} zc_j(X_j).dW_j,
+            // zc_j evaluated at X_j from the control row of (j, stratum of X_j).
+            [[maybe_unused]] R CI = (R)0, CZ = (R)0;
+            [[maybe_unused]] R phij[p];
+            [[maybe_unused]] unsigned rowj = 0;
+            if constexpr (CV) CI = control_dot<R, D, p>(P, (unsigned)i * (unsigned)P.K + (unsigned)k, phi, dwi);
+            eval_at<R, D, LP1, MODEL, ZIN, CV>(P, i + 1, xj, yn, zj, phij, rowj);
             R S = (R)0;
             // Steps j = i+1 .. N-1 in groups of G, so that the word phase of
             // every step in a group is a compile-time constant.
@@ -378,22 +411,27 @@ step_kernel(const Params P, const int i)
                     if (j >= P.N) return;
                     unsigned wn[D];
                     W.template take<(D + D * (1 + g)) % 4, D, false>(P, wn);
-                    R xn[D], zn[D];
+                    R xn[D], zn[D], dw[D];
 #pragma unroll
                     for (int l = 0; l < D; ++l) {
-                        const R dw = sdt * normal_of(wn[l], (R)0);
-                        xn[l] = xj[l] + Form<R>::b(P, l) * dt + Form<R>::sig(P, l) * dw;
+                        dw[l] = sdt * normal_of(wn[l], (R)0);
+                        xn[l] = xj[l] + Form<R>::b(P, l) * dt + Form<R>::sig(P, l) * dw[l];
                     }
-                    eval_at<R, D, LP1, MODEL, ZIN>(P, j + 1, xn, yn, zn);
+                    if constexpr (CV) CZ += control_dot<R, D, p>(P, rowj, phij, dw);
+                    eval_at<R, D, LP1, MODEL, ZIN, CV>(P, j + 1, xn, yn, zn, phij, rowj);
                     S += dt * model_f<R, D, MODEL, ZIN>(P, j, xj, yn, zj);
 #pragma unroll
                     for (int l = 0; l < D; ++l) { xj[l] = xn[l]; zj[l] = zn[l]; }
                 });
             }
             S += model_g<R, D, MODEL>(P, xj);
+            // Z response uses S - CZ; the phase-A part of the Y response S - CZ - CI.
+            R SZ = S, SY = S;
+            if constexpr (CV) { SZ = S - CZ; SY = SZ - CI; }
             if constexpr (RS) {
                 // this path's products (zero for lanes past M)
-                const float Sv = valid ? (float)S : 0.0f;
+                const float Sv = valid ? (float)SZ : 0.0f;
+                const float Sy = valid ? (float)SY : 0.0f;
                 const float g1 = valid ? 1.0f : 0.0f;
                 float v[EA];
 #pragma unroll
@@ -405,7 +443,7 @@ step_kernel(const Params P, const int i)
                     for (int a = 0; a < p; ++a) v[EG + l * p + a] = (float)phi[a] * wz;
                 }
 #pragma unroll
-                for (int a = 0; a < p; ++a) v[EG + EZ + a] = (float)phi[a] * Sv;
+                for (int a = 0; a < p; ++a) v[EG + EZ + a] = (float)phi[a] * Sy;
                 mA.add_path(v, lane);
             } else {
                 if (valid) {
@@ -418,12 +456,12 @@ step_kernel(const Params P, const int i)
                     }
 #pragma unroll
                     for (int l = 0; l < q; ++l) {
-                        const R wz = S * dwi[l] * inv_dt;
+                        const R wz = SZ * dwi[l] * inv_dt;
 #pragma unroll
                         for (int a = 0; a < p; ++a) mA.add(EG + l * p + a, phi[a] * wz);
                     }
 #pragma unroll
-                    for (int a = 0; a < p; ++a) mA.add(EG + EZ + a, phi[a] * S);
+                    for (int a = 0; a < p; ++a) mA.add(EG + EZ + a, phi[a] * SY);
                 }
                 if (++since_flush == FLUSH) { mA.flush(lane); since_flush = 0; }
             }
@@ -490,7 +528,11 @@ step_kernel(const Params P, const int i)
                     x1[l] = x[l] + Form<R>::b(P, l) * dt + Form<R>::sig(P, l) * dw;
                 }
             }
-            eval_at<R, D, LP1, MODEL, ZIN>(P, i + 1, x1, y1, z1);
+            {
+                [[maybe_unused]] R phi1[p];
+                [[maybe_unused]] unsigned row1;
+                eval_at<R, D, LP1, MODEL, ZIN, false>(P, i + 1, x1, y1, z1, phi1, row1);
+            }
 #pragma unroll
             for (int l = 0; l < q; ++l) {
                 R w = beta_r[l * p];
@@ -542,10 +584,10 @@ step_kernel(const Params P, const int i)
     }
 }
 
-template <typename R, bool LP1, int MODEL, bool ZIN>
+template <typename R, bool LP1, int MODEL, bool ZIN, bool CV = false>
 cudaError_t launch_one(const Params &P, int i, int grid, int threads, cudaStream_t st)
 {
-    step_kernel<R, SRMC_STEP_D, LP1, MODEL, ZIN><<<grid, threads, 0, st>>>(P, i);
+    step_kernel<R, SRMC_STEP_D, LP1, MODEL, ZIN, CV><<<grid, threads, 0, st>>>(P, i);
     return cudaGetLastError();
 }
 
@@ -553,6 +595,15 @@ template <typename R>
 cudaError_t launch_prec(const Params &P, int i, bool lp1, int mv, int grid, int threads,
                         cudaStream_t st)
 {
+    if (P.C64 != nullptr) {             // control variate form (LP1 only)
+        if (!lp1) return cudaErrorInvalidValue;
+        switch (mv) {
+        case MV_COS:      return launch_one<R, true, MODEL_COS, false, true>(P, i, grid, threads, st);
+        case MV_COS_Z:    return launch_one<R, true, MODEL_COS, true, true>(P, i, grid, threads, st);
+        case MV_LOGISTIC: return launch_one<R, true, MODEL_LOGISTIC, true, true>(P, i, grid, threads, st);
+        }
+        return cudaErrorInvalidValue;
+    }
     switch (mv) {
     case MV_COS:      return lp1 ? launch_one<R, true, MODEL_COS, false>(P, i, grid, threads, st)
                                  : launch_one<R, false, MODEL_COS, false>(P, i, grid, threads, st);

@@ -74,6 +74,22 @@ def lib():
             L.srmc_stats.argtypes = [vp, C.POINTER(C.c_ulonglong)]
             L.srmc_read_table.argtypes = [vp, vp, vp, vp]
             L.srmc_closed_form_error.argtypes = [vp, vp, vp]
+            L.srmc_set_control.argtypes = [vp, vp]
+            L.srmc_clear_control.argtypes = [vp]
+            L.srmc_read_control.argtypes = [vp, vp]
+            L.srmc_mlp_create.argtypes = [i_, i_, C.c_ulonglong, C.POINTER(vp)]
+            L.srmc_mlp_destroy.argtypes = [vp]; L.srmc_mlp_destroy.restype = None
+            L.srmc_mlp_nparams.argtypes = [vp]; L.srmc_mlp_nparams.restype = i_
+            L.srmc_mlp_set_params.argtypes = [vp, vp]
+            L.srmc_mlp_get_params.argtypes = [vp, vp]
+            L.srmc_mlp_eval.argtypes = [vp, vp, ll, vp, vp, vp]
+            L.srmc_mlp_loss_grad.argtypes = [vp, vp, vp, ll, vp, vp, vp]
+            L.srmc_mlp_fit.argtypes = [vp, vp, ll, i_, i_, C.c_float, C.c_ulonglong, vp, vp]
+            L.srmc_cv_tabulate.argtypes = [vp, vp, vp]
+            for name in ("srmc_read_control", "srmc_mlp_create", "srmc_mlp_set_params",
+                         "srmc_mlp_get_params", "srmc_mlp_eval", "srmc_mlp_loss_grad", "srmc_mlp_fit",
+                         "srmc_cv_tabulate"):
+                getattr(L, name).restype = C.c_int
             L.srmc_philox.argtypes = [vp, C.POINTER(C.c_uint32), ll, vp, vp]
             L.srmc_normals.argtypes = [vp, ll, vp, vp, vp]
             L.srmc_locate.argtypes = [vp, vp, vp, ll, vp, vp]
@@ -82,7 +98,7 @@ def lib():
             L.srmc_version.restype = C.c_int
             for name in ("srmc_create", "srmc_solve", "srmc_solve_step", "srmc_eval", "srmc_centres",
                          "srmc_table", "srmc_read_table", "srmc_closed_form_error", "srmc_stats", "srmc_philox",
-                         "srmc_normals", "srmc_locate",
+                         "srmc_normals", "srmc_locate", "srmc_set_control", "srmc_clear_control",
                          "srmc_start_points"):
                 getattr(L, name).restype = C.c_int
             _lib = L
@@ -184,6 +200,24 @@ class Solver:
         """Copy the FP64 tables into caller tensors (host, pinned or device)."""
         _check(lib().srmc_read_table(self._h, _ptr(dst_y), _ptr(dst_z), _stream(stream)))
 
+    def srmc_set_control(self, rows):
+        """rows: numpy [N][K][q][p] float64 (host) or a CUDA float64 tensor."""
+        if isinstance(rows, np.ndarray):
+            self._ctl = np.ascontiguousarray(rows, dtype=np.float64)
+            ptr = C.c_void_p(self._ctl.ctypes.data)
+        else:
+            ptr = _ptr(rows)
+        _check(lib().srmc_set_control(self._h, ptr))
+
+    def srmc_clear_control(self):
+        _check(lib().srmc_clear_control(self._h))
+
+    def srmc_read_control(self):
+        p = 1 if self.w.basis == "lp0" else self.w.d + 1
+        out = np.zeros((self.w.N, self.K, self.w.q, p))
+        _check(lib().srmc_read_control(self._h, C.c_void_p(out.ctypes.data)))
+        return out
+
     def srmc_closed_form_error(self, out, stream=None):
         _check(lib().srmc_closed_form_error(self._h, _ptr(out), _stream(stream)))
 
@@ -240,3 +274,48 @@ def srmc_version() -> int:
 def build(force: bool = False) -> str:
     from . import build as _b
     return _b.build(force=force)
+
+
+class MLP:
+    """The control-variate network u_theta(t, x) (wraps srmc_mlp_create)."""
+
+    def __init__(self, n_in: int, hidden: int = 64, seed: int = 0):
+        h = C.c_void_p()
+        _check(lib().srmc_mlp_create(int(n_in), int(hidden), int(seed), C.byref(h)))
+        self._h = h
+        self.n_in = n_in
+        self.P = int(lib().srmc_mlp_nparams(h))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().srmc_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def srmc_mlp_set_params(self, params):
+        a = np.ascontiguousarray(params, dtype=np.float32)
+        _check(lib().srmc_mlp_set_params(self._h, C.c_void_p(a.ctypes.data)))
+
+    def srmc_mlp_get_params(self):
+        a = np.zeros(self.P, dtype=np.float32)
+        _check(lib().srmc_mlp_get_params(self._h, C.c_void_p(a.ctypes.data)))
+        return a
+
+    def srmc_mlp_eval(self, a, u, grad=None, stream=None):
+        _check(lib().srmc_mlp_eval(self._h, _ptr(a), a.shape[0], _ptr(u), _ptr(grad), _stream(stream)))
+
+    def srmc_mlp_loss_grad(self, a, y, grad, loss=None, stream=None):
+        _check(lib().srmc_mlp_loss_grad(self._h, _ptr(a), _ptr(y), a.shape[0], _ptr(grad), _ptr(loss),
+                                         _stream(stream)))
+
+    def srmc_mlp_fit(self, coarse: "Solver", n_data, iters, batch, lr, seed, loss_curve=None, stream=None):
+        _check(lib().srmc_mlp_fit(self._h, coarse.handle, int(n_data), int(iters), int(batch), float(lr),
+                                  int(seed), _ptr(loss_curve), _stream(stream)))
+
+    def srmc_cv_tabulate(self, solver: "Solver", stream=None):
+        _check(lib().srmc_cv_tabulate(self._h, solver.handle, _stream(stream)))

@@ -1,0 +1,115 @@
+"""GPU control-variate form through the C ABI against the FP64 oracle: both
+sides receive the same control rows (tabulated from a given function by the
+input generator) and the same Philox streams."""
+import numpy as np
+import pytest
+
+from paper_2407_21085_gb300 import workloads as W
+from tests.test_gpu_parity import _check
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dev():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2407_21085_gb300 import srmc
+    return torch, srmc
+
+
+def _cv_parity(dev, orc, w, fn):
+    torch, srmc = dev
+    rows = W.control_rows(w, fn)
+    s = srmc.Solver(w)
+    s.srmc_set_control(rows)
+    s.srmc_solve()
+    o = orc.Oracle(w)
+    o.set_control(rows)
+    o.solve_full(0)
+    x = s.centres()
+    xn = x.cpu().numpy()
+    for i in range(w.N):
+        gy, gz = s.evaluate(i, x)
+        ry, rz = o.eval(i, xn)
+        _check(w, gy.cpu().numpy(), gz.cpu().numpy(), ry, rz, where=f"step {i}")
+    return s
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_cv_cos_d2(dev, orc, prec):
+    w = W.cfg2(C=12, N=6, M=384, precision=prec)
+    _cv_parity(dev, orc, w, W.closed_form_z(w))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_cv_cos_d4_with_z_in_driver(dev, orc, prec):
+    w = W.cfg3(C=3, N=4, M=200, precision=prec)
+    _cv_parity(dev, orc, w, W.random_smooth_z(w, seed=3))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_cv_paper_logistic_d3(dev, orc, prec):
+    w = W.logistic_paper(d=3, N=4, C=3, M=160, precision=prec)
+    _cv_parity(dev, orc, w, W.random_smooth_z(w, seed=4, scale=0.1))
+
+
+def test_cv_d6(dev, orc):
+    w = W.cos_model("d6", d=6, N=3, C=2, a=2.0, M=96, s0=0.3, lam=0.2, kap=0.5, precision="fp32")
+    _cv_parity(dev, orc, w, W.closed_form_z(w))
+
+
+def test_clear_control_restores_the_plain_scheme(dev):
+    torch, srmc = dev
+    w = W.cfg2(C=8, N=5, M=256)
+    plain = srmc.Solver(w)
+    plain.srmc_solve()
+    s = srmc.Solver(w)
+    s.srmc_solve()
+    s.srmc_set_control(W.control_rows(w, W.closed_form_z(w)))
+    s.srmc_solve()                                 # graph re-captured with the control
+    x = s.centres()
+    yc, _ = s.evaluate(0, x)
+    yp, _ = plain.evaluate(0, x)
+    assert not torch.equal(yc, yp)
+    s.srmc_clear_control()
+    s.srmc_solve()
+    y2, _ = s.evaluate(0, x)
+    assert torch.equal(y2, yp)
+
+
+def test_control_needs_lp1(dev):
+    torch, srmc = dev
+    w = W.cfg2(C=4, N=3, M=64, basis="lp0")
+    s = srmc.Solver(w)
+    with pytest.raises(srmc.SrmcError) as e:
+        s.srmc_set_control(np.zeros((3, 16, 2, 1)))
+    assert e.value.status == 4
+
+
+def test_exact_control_cuts_the_spread_on_gpu(dev):
+    # Across seeds, the fitted y spreads less with the exact z as control
+    # (and the means agree): the variance reduction the control is for.
+    torch, srmc = dev
+    w0 = W.cfg2(C=16, N=10, M=1024)
+    rows = W.control_rows(w0, W.closed_form_z(w0))
+    ys = {"plain": [], "cv": []}
+    for seed in range(8):
+        w = w0.replace(seed=seed + 10)
+        for name in ("plain", "cv"):
+            s = srmc.Solver(w)
+            if name == "cv":
+                s.srmc_set_control(rows)
+            s.srmc_solve()
+            y, _ = s.evaluate(0, s.centres())
+            ys[name].append(y.cpu().numpy())
+    sp = np.std(np.array(ys["plain"]), axis=0, ddof=1)
+    sc = np.std(np.array(ys["cv"]), axis=0, ddof=1)
+    # inner strata: in the semi-infinite outer cells the tabulated control is
+    # extrapolated far from the centre and helps less
+    cells = np.stack(np.unravel_index(np.arange(w0.K), w0.cells[::-1]), 1)[:, ::-1]
+    inner = np.all((cells > 0) & (cells < np.array(w0.cells) - 1), axis=1)
+    assert np.mean(sc[inner]) < 0.4 * np.mean(sp[inner]), (np.mean(sc), np.mean(sp))
+    dm = np.abs(np.mean(ys["plain"], axis=0) - np.mean(ys["cv"], axis=0))[inner]
+    assert np.mean(dm) < 3 * np.mean(np.sqrt(sp ** 2 + sc ** 2)[inner]) / np.sqrt(8)

@@ -275,5 +275,11 @@ def test_closed_form_error_kernel(dev, model):
         want = [np.max(np.abs(y - u)), np.mean((y - u) ** 2), np.max(np.abs(z - zs)),
                 np.mean(np.sum((z - zs) ** 2, axis=1))]
         assert np.allclose(err[i], want, rtol=1e-9, atol=1e-14), (i, err[i], want)
-    # the fitted solution is close to the closed form (scheme + time-discretisation error)
-    assert err[:, 0].max() < 0.1
+    # at inner strata the fit is close to the closed form (scheme + time-discretisation
+    # error); the semi-infinite outer strata are evaluated at their nominal centre
+    cells = np.stack(np.unravel_index(np.arange(w.K), w.cells[::-1]), 1)[:, ::-1]
+    inner = np.all((cells > 0) & (cells < np.array(w.cells) - 1), axis=1)
+    y0, _ = s.evaluate(0, x)
+    u0 = (math.exp(w.params[0]) * np.cos(xn.sum(1) / math.sqrt(w.d)) if model == "cos"
+          else np.exp(xn.sum(1)) / (1 + np.exp(xn.sum(1))))
+    assert np.max(np.abs(y0.cpu().numpy() - u0)[inner]) < 0.1

@@ -160,9 +160,10 @@ def test_converges_to_population_scheme(orc, case):
 # be caught by the population pin or by the brute-force restatement.
 MUTANTS = {
     "driver_at_t_j_plus_1": ("S += orc_f(P, j, x, yn, zj) * dt;", "S += orc_f(P, j + 1, x, yn, zj) * dt;"),
-    "z_response_without_1_over_dt": ("B[m * q + l] = S1[m] * DW[m * q + l] / dt;",
-                                     "B[m * q + l] = S1[m] * DW[m * q + l];"),
-    "y_response_without_f_i": ("B[m] = S1[m] + orc_f(P, i, X0 + m * d, Y1[m], zi) * dt;", "B[m] = S1[m];"),
+    "z_response_without_1_over_dt": ("B[m * q + l] = (S1[m] - CZ[m]) * DW[m * q + l] / dt;",
+                                     "B[m * q + l] = (S1[m] - CZ[m]) * DW[m * q + l];"),
+    "y_response_without_f_i": ("B[m] = S1[m] + orc_f(P, i, X0 + m * d, Y1[m], zi) * dt - CZ[m] - CI[m];",
+                               "B[m] = S1[m] - CZ[m] - CI[m];"),
     "no_z_truncation_in_y_response": ("zi[l] = trunc_L(w, P->Cz);", "zi[l] = w;"),
     "euler_increment_dt_not_sqrt_dt": ("dw[l] = sdt * orc_normal_from_word", "dw[l] = dt * orc_normal_from_word"),
     "y_next_not_truncated": ("*y = trunc_L(v, C->P.Cy);", "*y = v;"),
