@@ -235,6 +235,103 @@ def run_gpu(args):
     return out, rank, w
 
 
+# ---- the second half of the metric: time to sup|y - u| <= eps, CV vs plain ------
+def cv_compare(args, stream):
+    """cfg5 (d = 6, 8^6 strata, N = 40): the plain scheme at M = 4096 against the
+    learned control variate (coarse plain run at M = 256 -> train u_theta ->
+    tabulate sigma grad u_theta -> CV run at M = 1024), with the plain scheme at
+    M = 1024 as an ablation.  eps = the sup error of the plain M = 4096 run
+    against the closed form at the centres of the inner strata, over all
+    steps.  Wall times are host-measured with the device synchronised, set-up
+    (allocation, graph capture) included.  The statistical error of a form is
+    estimated from two independent seeds: rms(y_A - y_B) / sqrt(2) over the
+    inner centres and all steps (the closed-form error also holds the
+    O(dt) and LP1 biases, which no control variate removes)."""
+    import torch
+    from paper_2407_21085_gb300 import srmc
+
+    w = W.cfg5()
+    wcv = w.replace(M=args.cv_M)
+    wco = w.replace(M=args.cv_coarse_M, seed=w.seed + 100)
+    # load the d = 6 kernels (plain and CV) on a tiny problem first
+    tiny = W.cos_model("warm", d=6, N=2, C=3, a=3.0, M=64, s0=0.3, lam=0.2, kap=0.5)
+    ws = srmc.Solver(tiny); ws.srmc_solve(stream)
+    wn = srmc.MLP(7, seed=0); wn.srmc_cv_tabulate(ws, stream); ws.srmc_solve(stream)
+    wn.srmc_mlp_fit(ws, n_data=4096, iters=2, batch=4096, lr=1e-3, seed=0, stream=stream)
+    torch.cuda.synchronize()
+    ws.close(); wn.close()
+
+    cells = torch.stack(torch.meshgrid(*[torch.arange(c) for c in w.cells[::-1]], indexing="ij"), -1)
+    cells = cells.reshape(-1, w.d).flip(-1).to("cuda")
+    inner = ((cells > 0) & (cells < w.cells[0] - 1)).all(-1)
+
+    def clock():
+        torch.cuda.synchronize()
+        return time.perf_counter()
+
+    def values(solver):
+        x = solver.centres()
+        return torch.stack([solver.evaluate(i, x)[0][inner] for i in range(w.N)])
+
+    def summary(solver, wall):
+        e_in, e_all = solver.closed_form_error(inner=True), solver.closed_form_error()
+        return {"M": solver.w.M, "wall_s": wall, "sup_err_inner": float(e_in[:, 0].max()),
+                "rms_err_inner": float(math.sqrt(e_in[:, 1].mean())), "sup_err_all": float(e_all[:, 0].max())}
+
+    out = {"workload": w.name,
+           "metric": "wall time to sup|y - u| <= eps at inner stratum centres (all steps)"}
+    t0 = clock()
+    sp = srmc.Solver(w)
+    sp.srmc_solve(stream)
+    plain = summary(sp, clock() - t0)
+    plain["path_steps_per_s"] = w.path_steps() / plain["wall_s"]
+    sp.close()
+
+    t0 = clock()
+    sa = srmc.Solver(wcv)
+    sa.srmc_solve(stream)
+    abl = summary(sa, clock() - t0)
+    ya = values(sa)
+    sa.close()
+    sb = srmc.Solver(wcv.replace(seed=w.seed + 1))
+    sb.srmc_solve(stream)
+    abl["stat_err_rms"] = float(((ya - values(sb)).pow(2).mean() / 2).sqrt())
+    sb.close()
+
+    stages = {}
+    t0 = clock()
+    co = srmc.Solver(wco)
+    co.srmc_solve(stream)
+    t1 = clock(); stages["coarse_solve"] = t1 - t0
+    net = srmc.MLP(w.d + 1, seed=args.seed)
+    net.srmc_mlp_fit(co, n_data=args.cv_data, iters=args.cv_iters, batch=8192, lr=3e-3, seed=args.seed + 1,
+                     stream=stream)
+    t2 = clock(); stages["train"] = t2 - t1
+    sc = srmc.Solver(wcv)
+    net.srmc_cv_tabulate(sc, stream)
+    t3 = clock(); stages["tabulate"] = t3 - t2
+    sc.srmc_solve(stream)
+    t4 = clock(); stages["cv_solve"] = t4 - t3
+    cv = summary(sc, t4 - t0)
+    cv.update({"coarse_M": wco.M, "train_points": args.cv_data, "train_iters": args.cv_iters, "stages_s": stages,
+               "cv_solve_path_steps_per_s": wcv.path_steps() / stages["cv_solve"]})
+    yc = values(sc)
+    sc.close()
+    sd = srmc.Solver(wcv.replace(seed=w.seed + 1))
+    net.srmc_cv_tabulate(sd, stream)
+    sd.srmc_solve(stream)
+    cv["stat_err_rms"] = float(((yc - values(sd)).pow(2).mean() / 2).sqrt())
+    sd.close(); co.close(); net.close()
+
+    eps = plain["sup_err_inner"]
+    out.update({"eps": eps, "plain": plain, "plain_same_M_as_cv": abl, "cv": cv,
+                "cv_reaches_eps": cv["sup_err_inner"] <= eps,
+                "plain_same_M_reaches_eps": abl["sup_err_inner"] <= eps,
+                "plain_over_cv_time": plain["wall_s"] / cv["wall_s"],
+                "variance_ratio_same_M": (abl["stat_err_rms"] / cv["stat_err_rms"]) ** 2})
+    return out
+
+
 # ---- the CPU oracle (cpu_baseline leg and the reference arm) -------------------
 def oracle_sample(w: W.Workload, M_sample: int, threads: int):
     """Time the FP64 oracle's full backward solve of the workload with M
@@ -296,6 +393,12 @@ def main():
     ap.add_argument("--ref-M", type=int, default=32, help="M of each reference-arm step")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--block-threads", type=int, default=0, help="threads per stratum block (0: library)")
+    ap.add_argument("--no-cv-compare", action="store_true", help="skip the CV-vs-plain comparison (cfg5)")
+    ap.add_argument("--cv-M", type=int, default=1024)
+    ap.add_argument("--cv-coarse-M", type=int, default=256)
+    ap.add_argument("--cv-data", type=int, default=1 << 20)
+    ap.add_argument("--cv-iters", type=int, default=2000)
+    ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per step-kernel launch from an ncu capture of this kernel")
     args = ap.parse_args()
@@ -309,6 +412,9 @@ def main():
         return
 
     out, rank, w = run_gpu(args)
+    if rank == 0 and out["n_gpus"] == 1 and not args.no_cv_compare:
+        import torch
+        out["cv_vs_plain"] = cv_compare(args, torch.cuda.current_stream())
     if rank == 0:
         if not args.no_cpu_baseline and out["n_gpus"] == 1:
             r, dt, sample = oracle_sample(w, args.cpu_M, cpu_cores())

@@ -228,6 +228,11 @@ srmc_status srmc_cv_tabulate(const srmc_mlp *m, srmc_solver *s, void *stream);
  * affine model.  Requires a finished solve. */
 srmc_status srmc_closed_form_error(const srmc_solver *s, double *dev_out, void *stream);
 
+/* The same restricted to the inner strata (no cell of the stratum is a
+ * semi-infinite outer cell), where the nominal centre lies in the stratum's
+ * bulk; K_inner = prod_l (cells[l] - 2) must be > 0. */
+srmc_status srmc_closed_form_error_inner(const srmc_solver *s, double *dev_out, void *stream);
+
 /* Counters since creation: [0] strata fits that fell back from LP1 to LP0
  * because the Gram matrix was numerically singular (Cholesky pivot below
  * 1e-12 of its trace); [1] non-finite coefficients written; [2] stratum-path

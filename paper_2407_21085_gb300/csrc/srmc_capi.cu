@@ -255,7 +255,7 @@ srmc_status srmc_create(const srmc_problem *pr, const srmc_strata *sa, const srm
     }
     {
         const int p_ = cf->basis == SRMC_LP1 ? d + 1 : 1;
-        const long long rmax = (long long)pad_to(q * p_, 4);
+        const long long rmax = (long long)q * pad_to(p_, 4);
         if ((long long)pr->N * K * rmax >= 4294967296LL)
             return fail(SRMC_ERR_UNSUPPORTED, "table too large: N K row-length must be < 2^32");
     }
@@ -286,6 +286,7 @@ srmc_status srmc_create(const srmc_problem *pr, const srmc_strata *sa, const srm
     P.zin = (s->mv == srmc::MV_COS_Z || s->mv == srmc::MV_LOGISTIC);
     P.ry32 = pad_to(p, 4); P.rz32 = pad_to(q * p, 4);
     P.ry64 = pad_to(p, 2); P.rz64 = pad_to(q * p, 2);
+    P.pp = pad_to(p, 4); P.rc32 = q * P.pp;
     int stride = 1;
     int off = 0;
     for (int l = 0; l < d; ++l) {
@@ -448,20 +449,25 @@ __device__ void closed_form(const Params &P, int i, const double *x, double &u, 
 }
 
 // One block per step: errors of y_i, z_i at every stratum centre.
-__global__ void closed_form_error_kernel(const Params P, double *out)
+__global__ void closed_form_error_kernel(const Params P, bool inner, double *out)
 {
     const int i = blockIdx.x;
     double ymax = 0.0, ysq = 0.0, zmax = 0.0, zsq = 0.0;
+    long long cnt = 0;
     for (long long k = threadIdx.x; k < P.K; k += blockDim.x) {
         double x[srmc::DMAX], phi[srmc::DMAX + 1], zs[srmc::DMAX], u;
         long long rem = k;
         phi[0] = 1.0;
+        bool outer = false;
         for (int l = 0; l < P.d; ++l) {
             const int c = (int)(rem % P.cells[l]);
             rem /= P.cells[l];
+            outer = outer || c == 0 || c == P.cells[l] - 1;
             x[l] = P.lo[l] + ((double)c + 0.5) * P.h[l];
             phi[1 + l] = 0.0;                    // centre of the nominal cell
         }
+        if (inner && outer) continue;
+        ++cnt;
         closed_form(P, i, x, u, zs);
         const long long row = (long long)i * P.K + k;
         const double *al = P.Y64 + row * P.ry64;
@@ -479,25 +485,30 @@ __global__ void closed_form_error_kernel(const Params P, double *out)
             zsq += dz * dz;
         }
     }
-    __shared__ double red[4][32];
+    __shared__ double red[5][32];
+    double cntd = (double)cnt;
     for (int o = 16; o > 0; o >>= 1) {
         ymax = fmax(ymax, __shfl_xor_sync(0xffffffffu, ymax, o));
         ysq += __shfl_xor_sync(0xffffffffu, ysq, o);
         zmax = fmax(zmax, __shfl_xor_sync(0xffffffffu, zmax, o));
         zsq += __shfl_xor_sync(0xffffffffu, zsq, o);
+        cntd += __shfl_xor_sync(0xffffffffu, cntd, o);
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (lane == 0) { red[0][warp] = ymax; red[1][warp] = ysq; red[2][warp] = zmax; red[3][warp] = zsq; }
+    if (lane == 0) {
+        red[0][warp] = ymax; red[1][warp] = ysq; red[2][warp] = zmax; red[3][warp] = zsq;
+        red[4][warp] = cntd;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double a = 0, b = 0, c = 0, e = 0;
+        double a = 0, b = 0, c = 0, e = 0, n = 0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
-            a = fmax(a, red[0][w]); b += red[1][w]; c = fmax(c, red[2][w]); e += red[3][w];
+            a = fmax(a, red[0][w]); b += red[1][w]; c = fmax(c, red[2][w]); e += red[3][w]; n += red[4][w];
         }
         out[4 * i + 0] = a;
-        out[4 * i + 1] = b / (double)P.K;
+        out[4 * i + 1] = b / n;
         out[4 * i + 2] = c;
-        out[4 * i + 3] = e / (double)P.K;
+        out[4 * i + 3] = e / n;
     }
 }
 }  // namespace
@@ -508,7 +519,20 @@ srmc_status srmc_closed_form_error(const srmc_solver *s, double *out, void *stre
     if (s->P.model == srmc::MODEL_AFFINE)
         return fail(SRMC_ERR_UNSUPPORTED, "srmc_closed_form_error: no closed form for the affine model");
     if (s->done_from > 0) return fail(SRMC_ERR_STATE, "srmc_closed_form_error: solve not finished");
-    closed_form_error_kernel<<<s->P.N, 256, 0, (cudaStream_t)stream>>>(s->P, out);
+    closed_form_error_kernel<<<s->P.N, 256, 0, (cudaStream_t)stream>>>(s->P, false, out);
+    SRMC_CUDA(cudaGetLastError(), "closed form error kernel launch");
+    return SRMC_OK;
+}
+
+srmc_status srmc_closed_form_error_inner(const srmc_solver *s, double *out, void *stream)
+{
+    if (!s || !out) return fail(SRMC_ERR_INVALID_ARG, "srmc_closed_form_error_inner: NULL argument");
+    if (s->P.model == srmc::MODEL_AFFINE)
+        return fail(SRMC_ERR_UNSUPPORTED, "srmc_closed_form_error_inner: no closed form for the affine model");
+    for (int l = 0; l < s->P.d; ++l)
+        if (s->P.cells[l] < 3) return fail(SRMC_ERR_INVALID_ARG, "srmc_closed_form_error_inner: no inner strata");
+    if (s->done_from > 0) return fail(SRMC_ERR_STATE, "srmc_closed_form_error_inner: solve not finished");
+    closed_form_error_kernel<<<s->P.N, 256, 0, (cudaStream_t)stream>>>(s->P, true, out);
     SRMC_CUDA(cudaGetLastError(), "closed form error kernel launch");
     return SRMC_OK;
 }
@@ -572,7 +596,7 @@ __global__ void repack_control_kernel(const Params P, const double *src, double 
         for (int a = 0; a < qp; ++a) {
             const double v = src[r * qp + a];
             c64[r * P.rz64 + a] = v;
-            c32[r * P.rz32 + a] = (float)v;
+            c32[r * P.rc32 + (a / P.p) * P.pp + a % P.p] = (float)v;
         }
     }
 }
@@ -587,9 +611,9 @@ srmc_status srmc_set_control(srmc_solver *s, const double *rows)
     const size_t n = nrow * (size_t)(s->P.q * s->P.p);
     if (!s->C64) {
         SRMC_CUDA(cudaMalloc(&s->C64, sizeof(double) * nrow * s->P.rz64), "cudaMalloc control");
-        SRMC_CUDA(cudaMalloc(&s->C32, sizeof(float) * nrow * s->P.rz32), "cudaMalloc control");
+        SRMC_CUDA(cudaMalloc(&s->C32, sizeof(float) * nrow * s->P.rc32), "cudaMalloc control");
         SRMC_CUDA(cudaMemset(s->C64, 0, sizeof(double) * nrow * s->P.rz64), "cudaMemset control");
-        SRMC_CUDA(cudaMemset(s->C32, 0, sizeof(float) * nrow * s->P.rz32), "cudaMemset control");
+        SRMC_CUDA(cudaMemset(s->C32, 0, sizeof(float) * nrow * s->P.rc32), "cudaMemset control");
     }
     double *staging = nullptr;
     SRMC_CUDA(cudaMalloc(&staging, sizeof(double) * n), "cudaMalloc control staging");

@@ -46,7 +46,8 @@ struct Params {
     const float *stepc_f;
     float *Y32, *Z32;               // [N][K][ry32], [N][K][rz32]; N K r < 2^32
     double *Y64, *Z64;              // [N][K][ry64], [N][K][rz64]
-    const float *C32;               // control rows [N][K][rz32] (same layout as Z32)
+    const float *C32;               // control rows [N][K][q][pp], pp = p padded to 4 floats
+    int pp, rc32;                   // per-component and per-row strides of C32
     const double *C64;              // control rows [N][K][rz64]
     unsigned long long *stats;      // [0] LP1->LP0 fallbacks, [1] non-finite rows
 };

@@ -527,7 +527,7 @@ __global__ void __launch_bounds__(WARPS * 32) mlp_tabulate_kernel(Net net, const
             else v = (double)GAs[warp][1 + 2 * (c - 1)][1 + l] - (double)GAs[warp][2 + 2 * (c - 1)][1 + l];
             v *= P.sig[l];
             c64[row * P.rz64 + a] = v;
-            c32[row * P.rz32 + a] = (float)v;
+            c32[row * P.rc32 + l * P.pp + c] = (float)v;
         }
         __syncwarp();
     }
@@ -741,9 +741,9 @@ srmc_status srmc_cv_tabulate(const srmc_mlp *m, srmc_solver *s, void *stream)
     const size_t nrow = (size_t)s->P.N * (size_t)s->P.K;
     if (!s->C64) {
         MLP_CUDA(cudaMalloc(&s->C64, sizeof(double) * nrow * s->P.rz64), "cudaMalloc control");
-        MLP_CUDA(cudaMalloc(&s->C32, sizeof(float) * nrow * s->P.rz32), "cudaMalloc control");
+        MLP_CUDA(cudaMalloc(&s->C32, sizeof(float) * nrow * s->P.rc32), "cudaMalloc control");
         MLP_CUDA(cudaMemset(s->C64, 0, sizeof(double) * nrow * s->P.rz64), "cudaMemset control");
-        MLP_CUDA(cudaMemset(s->C32, 0, sizeof(float) * nrow * s->P.rz32), "cudaMemset control");
+        MLP_CUDA(cudaMemset(s->C32, 0, sizeof(float) * nrow * s->P.rc32), "cudaMemset control");
     }
     const long long tiles = (long long)nrow;
     mlp_tabulate_kernel<<<grid_tiles(tiles), WARPS * 32, smem_tab(), (cudaStream_t)stream>>>(

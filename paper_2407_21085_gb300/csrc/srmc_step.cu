@@ -289,14 +289,34 @@ template <typename R, int D, int p>
 __device__ __forceinline__ R control_dot(const Params &P, unsigned row, const R (&phi)[p],
                                          const R (&dw)[D])
 {
-    const R *b = Form<R>::Ctab(P) + row * (unsigned)Form<R>::rz(P);
     R acc = (R)0;
+    if constexpr (sizeof(R) == 4) {
+        // FP32 rows: component l holds PP = p rounded up to 4 floats, read as
+        // PP/4 float4 (one or two 16-byte loads per component).
+        constexpr int PP = (p + 3) / 4 * 4;
+        const float4 *b = reinterpret_cast<const float4 *>(P.C32 + row * (unsigned)(D * PP));
 #pragma unroll
-    for (int l = 0; l < D; ++l) {
-        R w = __ldg(b + l * p);
+        for (int l = 0; l < D; ++l) {
+            float c[PP];
 #pragma unroll
-        for (int c = 1; c < p; ++c) w += __ldg(b + l * p + c) * phi[c];
-        acc += clamp_r(w, Form<R>::Cz(P)) * dw[l];
+            for (int v = 0; v < PP / 4; ++v) {
+                const float4 t = __ldg(b + l * (PP / 4) + v);
+                c[4 * v] = t.x; c[4 * v + 1] = t.y; c[4 * v + 2] = t.z; c[4 * v + 3] = t.w;
+            }
+            float w = c[0];
+#pragma unroll
+            for (int a = 1; a < p; ++a) w += c[a] * phi[a];
+            acc += clamp_r(w, Form<R>::Cz(P)) * dw[l];
+        }
+    } else {
+        const double *b = P.C64 + row * (unsigned)P.rz64;
+#pragma unroll
+        for (int l = 0; l < D; ++l) {
+            double w = __ldg(b + l * p);
+#pragma unroll
+            for (int a = 1; a < p; ++a) w += __ldg(b + l * p + a) * phi[a];
+            acc += clamp_r(w, Form<R>::Cz(P)) * dw[l];
+        }
     }
     return acc;
 }
@@ -310,9 +330,12 @@ __device__ __forceinline__ R control_dot(const Params &P, unsigned row, const R 
 #ifndef SRMC_MINB_HI
 #define SRMC_MINB_HI 4
 #endif
+#ifndef SRMC_CVMINB_HI
+#define SRMC_CVMINB_HI 3
+#endif
 template <typename R, int D, bool CV>
 struct MinBlocks {
-    static constexpr int value = sizeof(R) == 8 ? 1 : CV ? (D <= 2 ? 4 : 3)
+    static constexpr int value = sizeof(R) == 8 ? 1 : CV ? (D <= 2 ? 4 : SRMC_CVMINB_HI)
                                                         : (D <= 2 ? SRMC_MINB_LO : SRMC_MINB_HI);
 };
 
@@ -345,19 +368,21 @@ step_kernel(const Params P, const int i)
     const R dt = Form<R>::dt(P), sdt = Form<R>::sdt(P), inv_dt = (R)1 / dt;
 
     for (long long k = blockIdx.x; k < P.K; k += gridDim.x) {
-        // Cells of H_k and the sampler constants of each of its sides.
+        // Cells of H_k; the sampler constants of its sides are re-read (L1
+        // hits) at every path start rather than held in registers.
         int cell[D];
-        R Flo[D], Fchi[D], Wd[D];
         {
             long long rem = k;
 #pragma unroll
             for (int l = 0; l < D; ++l) {
                 cell[l] = (int)(rem % P.cells[l]);
                 rem /= P.cells[l];
-                const R *cf = Form<R>::cellF(P) + 3 * (P.cell_off[l] + cell[l]);
-                Flo[l] = __ldg(cf); Fchi[l] = __ldg(cf + 1); Wd[l] = __ldg(cf + 2);
             }
         }
+        auto sample_start = [&](unsigned w, int l) -> R {
+            const R *cf = Form<R>::cellF(P) + 3 * (P.cell_off[l] + cell[l]);
+            return sample_cell(w, __ldg(cf), __ldg(cf + 1), __ldg(cf + 2), Form<R>::mu_arg(P));
+        };
 
         // ---------------- phase A: responses of the Z and Y fits ---------------
         MA mA;
@@ -375,7 +400,7 @@ step_kernel(const Params P, const int i)
                 W.template take<0, D, true>(P, ws);
 #pragma unroll
                 for (int l = 0; l < D; ++l) {
-                    x[l] = sample_cell(ws[l], Flo[l], Fchi[l], Wd[l], Form<R>::mu_arg(P));
+                    x[l] = sample_start(ws[l], l);
                     if (LP1) {
                         R t;
                         if (sizeof(R) == 8) t = (x[l] - (R)P.lo[l]) / (R)P.h[l];
@@ -510,7 +535,7 @@ step_kernel(const Params P, const int i)
                 W.template take<0, D, true>(P, ws);
 #pragma unroll
                 for (int l = 0; l < D; ++l) {
-                    x[l] = sample_cell(ws[l], Flo[l], Fchi[l], Wd[l], Form<R>::mu_arg(P));
+                    x[l] = sample_start(ws[l], l);
                     if (LP1) {
                         R t;
                         if (sizeof(R) == 8) t = (x[l] - (R)P.lo[l]) / (R)P.h[l];

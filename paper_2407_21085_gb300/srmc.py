@@ -74,6 +74,8 @@ def lib():
             L.srmc_stats.argtypes = [vp, C.POINTER(C.c_ulonglong)]
             L.srmc_read_table.argtypes = [vp, vp, vp, vp]
             L.srmc_closed_form_error.argtypes = [vp, vp, vp]
+            L.srmc_closed_form_error_inner.argtypes = [vp, vp, vp]
+            L.srmc_closed_form_error_inner.restype = C.c_int
             L.srmc_set_control.argtypes = [vp, vp]
             L.srmc_clear_control.argtypes = [vp]
             L.srmc_read_control.argtypes = [vp, vp]
@@ -221,11 +223,15 @@ class Solver:
     def srmc_closed_form_error(self, out, stream=None):
         _check(lib().srmc_closed_form_error(self._h, _ptr(out), _stream(stream)))
 
-    def closed_form_error(self):
-        """[N][4] (max|dy|, mean dy^2, max|dz|, mean |dz|^2) at the centres, as numpy."""
+    def closed_form_error(self, inner=False):
+        """[N][4] (max|dy|, mean dy^2, max|dz|, mean |dz|^2) at the centres (of
+        the inner strata only if inner), as numpy."""
         import torch
         out = torch.empty((self.w.N, 4), dtype=torch.float64, device="cuda")
-        self.srmc_closed_form_error(out)
+        if inner:
+            _check(lib().srmc_closed_form_error_inner(self._h, _ptr(out), _stream(None)))
+        else:
+            self.srmc_closed_form_error(out)
         return out.cpu().numpy()
 
     def srmc_stats(self):
