@@ -23,6 +23,11 @@ srmc_status fail(srmc_status st, const std::string &msg)
     g_last_error = msg;
     return st;
 }
+}  // namespace
+
+void srmc::set_last_error(const std::string &msg) { g_last_error = msg; }
+
+namespace {
 
 srmc_status cuda_fail(cudaError_t e, const char *what)
 {

@@ -3,7 +3,13 @@
 
 #include "srmc_device.cuh"
 
+#include <string>
+
 namespace srmc {
+
+// Message returned by srmc_last_error() for the calling thread; every entry
+// point of the library reports through it.
+void set_last_error(const std::string &msg);
 
 // Model variants of the step kernel: the driver needs z only for the cos
 // model with kapz != 0 and for the logistic model.

@@ -25,11 +25,9 @@ constexpr int H = 64;       // hidden width
 constexpr int KIN = 16;     // padded input width (one k-tile)
 constexpr int WARPS = 4;    // warps per block
 
-thread_local std::string g_err;
-
 srmc_status mfail(srmc_status st, const std::string &m)
 {
-    g_err = m;
+    srmc::set_last_error(m);
     return st;
 }
 
