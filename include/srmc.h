@@ -212,6 +212,29 @@ srmc_status srmc_mlp_loss_grad(srmc_mlp *m, const float *dev_a, const float *dev
 srmc_status srmc_mlp_fit(srmc_mlp *m, const srmc_solver *coarse, long long n_data, int iters,
                          int batch, float lr, unsigned long long seed, float *dev_loss_curve,
                          void *stream);
+/* Allocation-free twin of srmc_mlp_fit (no counterpart in the paper; an
+ * engineering entry point).  Some callers cannot allocate device memory
+ * while they train: code that runs under a fixed, pre-reserved memory
+ * budget, code whose device memory is owned by another allocator (a
+ * framework's caching pool), and latency-critical loops that must not pay
+ * the implicit device synchronisation of cudaFree.  This call does the same
+ * work as srmc_mlp_fit with the same arguments, but keeps the training
+ * points, their targets and the gradient accumulator in one scratch array
+ * compiled into the library (static device memory: every GPU that loads the
+ * library holds it until the process exits) instead of allocating them:
+ *   - limit: n_data * (n_in + 1) + nparams + 64 <= 2^21 floats (8 MiB);
+ *     larger requests fail with SRMC_ERR_INVALID_ARG and a message;
+ *   - the first call on a device looks the array up on that device (make it
+ *     current first); make that first call before any stream capture;
+ *   - every call on a device shares the one array, so calls whose work
+ *     overlaps on the GPU (different streams or threads) race; serialise
+ *     them.  The parts that must start at zero are cleared by each call.
+ * It calls no cudaMalloc, cudaFree or allocating library routine.  Unlike
+ * srmc_mlp_fit it does not synchronise: the work is enqueued on stream. */
+srmc_status srmc_mlp_fit_noalloc(srmc_mlp *m, const srmc_solver *coarse, long long n_data,
+                                 int iters, int batch, float lr, unsigned long long seed,
+                                 float *dev_loss_curve, void *stream);
+
 /* Tabulate zc = sigma^T grad_x u_theta(t_j, .) as the control rows of s for
  * every (j, k): value at the stratum centre and central differences at
  * +-h/4 along each axis (LP1 rows in the centred basis), then install them as

@@ -13,6 +13,7 @@
 
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -544,6 +545,34 @@ int grid_tiles(long long tiles)
 
 }  // namespace
 
+// Scratch of srmc_mlp_fit_noalloc: static device memory, one copy per GPU
+// that loads the library.  Host code may not use the symbol as an address;
+// its device address is looked up once per device (noalloc_scratch).
+constexpr long long kNoallocFloats = 1LL << 21;          // 8 MiB
+static __device__ __align__(256) float g_noalloc_scratch[kNoallocFloats];
+
+namespace {
+std::mutex g_noalloc_mu;
+float *g_noalloc_ptr[256] = {};
+
+// Device address of the scratch array on the current device (looked up on the
+// first call for that device, with that device current).
+srmc_status noalloc_scratch(float **out)
+{
+    int dev = 0;
+    MLP_CUDA(cudaGetDevice(&dev), "srmc_mlp_fit_noalloc: cudaGetDevice");
+    if (dev < 0 || dev >= 256) return mfail(SRMC_ERR_UNSUPPORTED, "srmc_mlp_fit_noalloc: device id >= 256");
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        MLP_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch), "srmc_mlp_fit_noalloc: cudaGetSymbolAddress");
+        g_noalloc_ptr[dev] = static_cast<float *>(p);
+    }
+    *out = g_noalloc_ptr[dev];
+    return SRMC_OK;
+}
+}  // namespace
+
 struct srmc_mlp {
     int nin = 0, P = 0, device = 0, step = 0;
     float *prm = nullptr, *m = nullptr, *v = nullptr, *grad = nullptr, *loss = nullptr;
@@ -728,6 +757,54 @@ srmc_status srmc_mlp_fit(srmc_mlp *m, const srmc_solver *s, long long n_data, in
     cudaFree(a);
     cudaFree(y);
     if (e != cudaSuccess) return mfail(SRMC_ERR_CUDA, std::string("srmc_mlp_fit: ") + cudaGetErrorString(e));
+    return SRMC_OK;
+}
+
+srmc_status srmc_mlp_fit_noalloc(srmc_mlp *m, const srmc_solver *s, long long n_data, int iters,
+                                 int batch, float lr, unsigned long long seed, float *loss_curve,
+                                 void *stream)
+{
+    if (!m || !s || n_data <= 0 || iters < 0 || batch <= 0 || n_data % batch)
+        return mfail(SRMC_ERR_INVALID_ARG, "srmc_mlp_fit_noalloc: bad argument");
+    if (m->nin != s->P.d + 1) return mfail(SRMC_ERR_INVALID_ARG, "srmc_mlp_fit_noalloc: n_in must be d + 1");
+    if (s->done_from > 0) return mfail(SRMC_ERR_STATE, "srmc_mlp_fit_noalloc: the coarse solve is not finished");
+    // scratch layout (floats): [gradient, padded to 64][loss slot, 64][inputs n_data x n_in][targets n_data]
+    const long long gpad = ((long long)m->P + 63) / 64 * 64;
+    const long long need = gpad + 64 + n_data * (long long)(m->nin + 1);
+    if (need > kNoallocFloats)
+        return mfail(SRMC_ERR_INVALID_ARG,
+                     "srmc_mlp_fit_noalloc: n_data * (n_in + 1) + nparams + 64 exceeds the 2^21-float "
+                     "scratch of the allocation-free path (use srmc_mlp_fit)");
+    float *base = nullptr;
+    srmc_status st = noalloc_scratch(&base);
+    if (st != SRMC_OK) return st;
+    float *grad = base, *loss1 = base + gpad, *a = base + gpad + 64, *y = a + n_data * m->nin;
+    cudaStream_t cs = (cudaStream_t)stream;
+    // the array keeps the previous call's contents: clear the accumulators
+    MLP_CUDA(cudaMemsetAsync(grad, 0, sizeof(float) * (size_t)(gpad + 64), cs), "srmc_mlp_fit_noalloc: clear");
+    mlp_data_kernel<<<grid_tiles((n_data + 63) / 64) * 2, 256, 0, cs>>>(
+        s->P, n_data, (unsigned)(seed & 0xFFFFFFFFu), (unsigned)(seed >> 32), a, y);
+    cudaError_t e = cudaGetLastError();
+    const long long tiles = (batch + 15) / 16;
+    const float decay = iters > 1 ? std::pow(0.1f, 1.0f / (float)(iters - 1)) : 1.0f;
+    float lr_t = lr, b1t = 1.0f, b2t = 1.0f;
+    for (int it = 0; it < iters && e == cudaSuccess; ++it) {
+        const long long off = ((long long)it * batch) % n_data;
+        float *lp = loss_curve ? loss_curve + it : loss1;
+        e = cudaMemsetAsync(lp, 0, sizeof(float), cs);
+        if (e != cudaSuccess) break;
+        mlp_grad_kernel<<<grid_tiles(tiles), WARPS * 32, smem_grad(), cs>>>(
+            m->net(), a + off * m->nin, y + off, batch, 1.0f / (float)batch, grad, lp);
+        ++m->step;
+        b1t *= 0.9f; b2t *= 0.999f;
+        mlp_adam_kernel<<<(m->P + 255) / 256, 256, 0, cs>>>(m->prm, m->m, m->v, grad, m->P, lr_t,
+                                                            1.0f / (1.0f - b1t), 1.0f / (1.0f - b2t));
+        mlp_pack_kernel<<<16, 256, 0, cs>>>(m->prm, m->nin, m->W1, m->W1T, m->W2, m->W2T);
+        e = cudaGetLastError();
+        lr_t *= decay;
+    }
+    if (e != cudaSuccess)
+        return mfail(SRMC_ERR_CUDA, std::string("srmc_mlp_fit_noalloc: ") + cudaGetErrorString(e));
     return SRMC_OK;
 }
 

@@ -88,9 +88,10 @@ def lib():
             L.srmc_mlp_loss_grad.argtypes = [vp, vp, vp, ll, vp, vp, vp]
             L.srmc_mlp_fit.argtypes = [vp, vp, ll, i_, i_, C.c_float, C.c_ulonglong, vp, vp]
             L.srmc_cv_tabulate.argtypes = [vp, vp, vp]
+            L.srmc_mlp_fit_noalloc.argtypes = [vp, vp, ll, i_, i_, C.c_float, C.c_ulonglong, vp, vp]
             for name in ("srmc_read_control", "srmc_mlp_create", "srmc_mlp_set_params",
                          "srmc_mlp_get_params", "srmc_mlp_eval", "srmc_mlp_loss_grad", "srmc_mlp_fit",
-                         "srmc_cv_tabulate"):
+                         "srmc_cv_tabulate", "srmc_mlp_fit_noalloc"):
                 getattr(L, name).restype = C.c_int
             L.srmc_philox.argtypes = [vp, C.POINTER(C.c_uint32), ll, vp, vp]
             L.srmc_normals.argtypes = [vp, ll, vp, vp, vp]
@@ -322,6 +323,12 @@ class MLP:
     def srmc_mlp_fit(self, coarse: "Solver", n_data, iters, batch, lr, seed, loss_curve=None, stream=None):
         _check(lib().srmc_mlp_fit(self._h, coarse.handle, int(n_data), int(iters), int(batch), float(lr),
                                   int(seed), _ptr(loss_curve), _stream(stream)))
+
+    def srmc_mlp_fit_noalloc(self, coarse: "Solver", n_data, iters, batch, lr, seed, loss_curve=None,
+                             stream=None):
+        """srmc_mlp_fit without device allocation (scratch compiled into the library)."""
+        _check(lib().srmc_mlp_fit_noalloc(self._h, coarse.handle, int(n_data), int(iters), int(batch),
+                                          float(lr), int(seed), _ptr(loss_curve), _stream(stream)))
 
     def srmc_cv_tabulate(self, solver: "Solver", stream=None):
         _check(lib().srmc_cv_tabulate(self._h, solver.handle, _stream(stream)))
