@@ -332,6 +332,52 @@ def cv_compare(args, stream):
     return out
 
 
+# ---- the batched form: 256 heterogeneous instances ---------------------------------
+def batched_compare(args, stream):
+    """cfg4: 256 seeded instances (d in {1,2,3}, 16..64 cells per dimension,
+    N in {10,20,40}, M in {1024,4096}) solved by the tuned batched form (one
+    graph of per-round, per-variant persistent launches) and, for comparison,
+    one after another by single-instance solves on the same stream.  Device
+    time by CUDA events on the stream, after one untimed pass of each."""
+    import torch
+    from paper_2407_21085_gb300 import srmc
+
+    ws = W.cfg4_instances()
+    units = sum(w.path_steps() for w in ws)
+    solvers = [srmc.Solver(w) for w in ws]
+    batch = srmc.Batch(solvers)
+    t0 = time.perf_counter()
+    threads = batch.srmc_batch_tune(stream)
+    tune_s = time.perf_counter() - t0
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / 1e3 / reps
+
+    t_batch = timed(lambda: batch.srmc_batch_solve(stream), args.batch_reps)
+    mode = batch.srmc_batch_mode()
+
+    def sequential():
+        for s in solvers:
+            s.srmc_solve(stream)
+    t_seq = timed(sequential, 1)
+    batch.close()
+    for s in solvers:
+        s.close()
+    return {"workload": "cfg4: 256 instances (seed 4)", "instances": len(ws), "path_steps": units,
+            "batched_s": t_batch, "batched_path_steps_per_s": units / t_batch,
+            "sequential_s": t_seq, "sequential_path_steps_per_s": units / t_seq,
+            "speedup": t_seq / t_batch, "tuned_threads_per_group": threads, "tune_s": tune_s,
+            "strategy": ["rounds of multi-instance launches", "one graph branch per instance"][mode]}
+
+
 # ---- the CPU oracle (cpu_baseline leg and the reference arm) -------------------
 def oracle_sample(w: W.Workload, M_sample: int, threads: int):
     """Time the FP64 oracle's full backward solve of the workload with M
@@ -394,6 +440,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--block-threads", type=int, default=0, help="threads per stratum block (0: library)")
     ap.add_argument("--no-cv-compare", action="store_true", help="skip the CV-vs-plain comparison (cfg5)")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-form measurement (cfg4)")
+    ap.add_argument("--batch-reps", type=int, default=2)
     ap.add_argument("--cv-M", type=int, default=1024)
     ap.add_argument("--cv-coarse-M", type=int, default=256)
     ap.add_argument("--cv-data", type=int, default=1 << 20)
@@ -415,6 +463,9 @@ def main():
     if rank == 0 and out["n_gpus"] == 1 and not args.no_cv_compare:
         import torch
         out["cv_vs_plain"] = cv_compare(args, torch.cuda.current_stream())
+    if rank == 0 and out["n_gpus"] == 1 and not args.no_batched:
+        import torch
+        out["batched_cfg4"] = batched_compare(args, torch.cuda.current_stream())
     if rank == 0:
         if not args.no_cpu_baseline and out["n_gpus"] == 1:
             r, dt, sample = oracle_sample(w, args.cpu_M, cpu_cores())

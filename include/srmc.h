@@ -241,6 +241,41 @@ srmc_status srmc_mlp_fit_noalloc(srmc_mlp *m, const srmc_solver *coarse, long lo
  * by srmc_set_control.  LP1 solvers with d <= 7, n_in == d + 1. */
 srmc_status srmc_cv_tabulate(const srmc_mlp *m, srmc_solver *s, void *stream);
 
+/* ---- batched form: many independent instances in one launch sequence -------
+ * (an engineering extension; the paper solves one problem at a time).  The
+ * instances may differ in d, strata, N, M and model parameters.  Their
+ * backward loops are aligned at the end: in round s every instance with
+ * N_r > s solves its step i = N_r - 1 - s, and all (instance, stratum) work
+ * items of a round that share a kernel variant go to one launch over a
+ * persistent grid (blocks stride through the items).  The rounds are captured
+ * once into a CUDA graph and replayed.  FP32 solvers only. */
+typedef struct srmc_batch srmc_batch;   /* opaque, library-owned */
+
+/* Plan a batch over n solvers (borrowed: they must outlive the batch and stay
+ * on the current device). */
+srmc_status srmc_batch_create(srmc_solver *const *solvers, int n, srmc_batch **out);
+void srmc_batch_destroy(srmc_batch *b);
+/* Pick, for every kernel variant of the batch, the threads per stratum block
+ * (64, 128 or 256: 2, 4 or 8 warps per stratum) and the blocks per SM of the
+ * persistent grid by timing candidate launches of its first rounds on stream,
+ * give every solver of the group that block size, then time both strategies
+ * (see srmc_batch_mode) on the whole batch and keep the faster (the tables of
+ * the solvers are overwritten; solve afterwards).  Optional: an untuned batch
+ * uses 256 threads, the occupancy limit and the rounds strategy.  out_threads
+ * (may be NULL) receives the chosen threads per variant group, in group order,
+ * up to max_out entries; returns the number of groups in *n_groups. */
+srmc_status srmc_batch_tune(srmc_batch *b, void *stream, int *out_threads, int max_out, int *n_groups);
+/* All instances' backward loops, enqueued on stream (graph replay). */
+srmc_status srmc_batch_solve(srmc_batch *b, void *stream);
+
+/* Strategy in use: 0 = rounds of multi-instance launches, 1 = one graph
+ * branch per instance (concurrent single-instance launches).  An untuned
+ * batch uses 0; srmc_batch_tune keeps the faster of the two. */
+int srmc_batch_mode(const srmc_batch *b);
+
+/* Force a strategy (0 or 1; SRMC_ERR_INVALID_ARG otherwise). */
+srmc_status srmc_batch_set_mode(srmc_batch *b, int mode);
+
 /* Error of the fitted functions against the closed-form solution of the
  * model at the K stratum centres, for every step i = 0..N-1 (the metric of
  * the benchmark plan; Sec. 5.1 uses the same comparison at nu-distributed

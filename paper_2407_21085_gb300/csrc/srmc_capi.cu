@@ -78,6 +78,15 @@ cudaError_t launch_step(const srmc_solver *s, int i, cudaStream_t st)
     return cudaErrorInvalidValue;
 }
 
+}  // namespace
+
+cudaError_t srmc_launch_solver_step(const srmc_solver *s, int i, cudaStream_t st)
+{
+    return launch_step(s, i, st);
+}
+
+namespace {
+
 // ---- kernels of the primitives and of the evaluation ----------------------
 
 __global__ void philox_kernel(const uint32_t *ctr, uint32_t k0, uint32_t k1, long long n,

@@ -15,7 +15,23 @@ void set_last_error(const std::string &msg);
 // model with kapz != 0 and for the logistic model.
 enum ModelVariant { MV_COS = 0, MV_COS_Z = 1, MV_LOGISTIC = 2, MV_AFFINE = 3 };
 
+// One round of the batched form: the strata of every active instance, laid
+// end to end (instance a owns work items kofs[a] .. kofs[a+1]-1 and solves
+// its step step[a]).
+struct BatchRound {
+    const Params *params;           // [instances] on the device
+    const int *inst;                // [n_active] instance of active entry a
+    const int *step;                // [n_active] step index i of that instance
+    const long long *kofs;          // [n_active + 1] prefix sums of K
+    int n_active;
+    long long total;                // kofs[n_active]
+};
+
 #define SRMC_LAUNCH_STEP_NAME(D) SRMC_LAUNCH_STEP_NAME_(D)
+#define SRMC_LAUNCH_BATCH_NAME(D) SRMC_LAUNCH_BATCH_NAME_(D)
+#define SRMC_LAUNCH_BATCH_NAME_(D) launch_batch_d##D
+#define SRMC_OCC_BATCH_NAME(D) SRMC_OCC_BATCH_NAME_(D)
+#define SRMC_OCC_BATCH_NAME_(D) occupancy_batch_d##D
 #define SRMC_LAUNCH_STEP_NAME_(D) launch_step_d##D
 
 #define SRMC_DECLARE_STEP(D)                                                              \
@@ -30,6 +46,20 @@ SRMC_DECLARE_STEP(6)
 SRMC_DECLARE_STEP(7)
 SRMC_DECLARE_STEP(8)
 #undef SRMC_DECLARE_STEP
+
+#define SRMC_DECLARE_BATCH(D)                                                                 \
+    cudaError_t launch_batch_d##D(const BatchRound &B, bool fp64, bool lp1, int mv, bool cv,  \
+                                  int grid, int threads, cudaStream_t st);                    \
+    int occupancy_batch_d##D(bool fp64, bool lp1, int mv, bool cv, int threads);
+SRMC_DECLARE_BATCH(1)
+SRMC_DECLARE_BATCH(2)
+SRMC_DECLARE_BATCH(3)
+SRMC_DECLARE_BATCH(4)
+SRMC_DECLARE_BATCH(5)
+SRMC_DECLARE_BATCH(6)
+SRMC_DECLARE_BATCH(7)
+SRMC_DECLARE_BATCH(8)
+#undef SRMC_DECLARE_BATCH
 
 // Table-row evaluation of y_i(x) in FP64 (truncated), x in double; the
 // kernel-side twin of srmc_eval used by the MLP data generator.
@@ -53,6 +83,9 @@ __device__ __forceinline__ double eval_y64(const Params &P, int i, const double 
 }  // namespace srmc
 
 using srmc::Params;
+
+// One step launch of a single-instance solver on a stream (srmc_capi.cu).
+cudaError_t srmc_launch_solver_step(const struct srmc_solver *s, int i, cudaStream_t st);
 
 // The solver object behind the opaque srmc_solver handle.
 struct srmc_solver {

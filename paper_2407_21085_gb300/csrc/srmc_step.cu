@@ -339,9 +339,31 @@ struct MinBlocks {
                                                         : (D <= 2 ? SRMC_MINB_LO : SRMC_MINB_HI);
 };
 
+// Shared memory of one stratum block.
+template <typename R, int D, bool LP1>
+struct StepSmem {
+    static constexpr int p = LP1 ? D + 1 : 1;
+    static constexpr int q = D;
+    static constexpr int EG = LP1 ? p * (p + 1) / 2 : 0;
+    static constexpr int EA = EG + q * p + p;
+    static constexpr int EB = p;
+    double redA[MAX_WARPS][EA];
+    double totA[EA];
+    double redB[MAX_WARPS][EB];
+    double totB[EB];
+    double Ls[p * p];
+    double Gw[p * p];
+    double Linv[p];
+    double beta_s[q * p];
+    R beta_r[q * p];
+    int ok_s;
+};
+
+// Fits of stratum k at step i (the whole of Alg. SRMDP for one (i, k)) by the
+// calling block: phase A, Z fit, phase B, Y fit, row store.
 template <typename R, int D, bool LP1, int MODEL, bool ZIN, bool CV>
-__global__ void __launch_bounds__(MAX_THREADS, MinBlocks<R, D, CV>::value)
-step_kernel(const Params P, const int i)
+__device__ __forceinline__ void solve_stratum(const Params &P, const int i, const long long k,
+                                              StepSmem<R, D, LP1> &sm)
 {
     constexpr int p = LP1 ? D + 1 : 1;
     constexpr int q = D;
@@ -352,261 +374,341 @@ step_kernel(const Params P, const int i)
     constexpr bool RS = sizeof(R) == 4 && EA > 24;
     using MA = typename std::conditional<RS, MomentsRS<EA>, typename MomentsOf<R, EA>::type>::type;
     using MB = typename MomentsOf<R, EB>::type;
-
-    __shared__ double redA[MAX_WARPS][EA];
-    __shared__ double totA[EA];
-    __shared__ double redB[MAX_WARPS][EB];
-    __shared__ double totB[EB];
-    __shared__ double Ls[p * p];
-    __shared__ double Gw[p * p];
-    __shared__ double Linv[p];
-    __shared__ double beta_s[q * p];
-    __shared__ R beta_r[q * p];
-    __shared__ int ok_s;
-
+    auto &redA = sm.redA;
+    auto &totA = sm.totA;
+    auto &redB = sm.redB;
+    auto &totB = sm.totB;
+    auto &Ls = sm.Ls;
+    auto &Gw = sm.Gw;
+    auto &Linv = sm.Linv;
+    auto &beta_s = sm.beta_s;
+    auto &beta_r = sm.beta_r;
+    auto &ok_s = sm.ok_s;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const R dt = Form<R>::dt(P), sdt = Form<R>::sdt(P), inv_dt = (R)1 / dt;
+    // Cells of H_k; the sampler constants of its sides are re-read (L1
+    // hits) at every path start rather than held in registers.
+    int cell[D];
+    {
+        long long rem = k;
+#pragma unroll
+        for (int l = 0; l < D; ++l) {
+            cell[l] = (int)(rem % P.cells[l]);
+            rem /= P.cells[l];
+        }
+    }
+    auto sample_start = [&](unsigned w, int l) -> R {
+        const R *cf = Form<R>::cellF(P) + 3 * (P.cell_off[l] + cell[l]);
+        return sample_cell(w, __ldg(cf), __ldg(cf + 1), __ldg(cf + 2), Form<R>::mu_arg(P));
+    };
 
-    for (long long k = blockIdx.x; k < P.K; k += gridDim.x) {
-        // Cells of H_k; the sampler constants of its sides are re-read (L1
-        // hits) at every path start rather than held in registers.
-        int cell[D];
+    // ---------------- phase A: responses of the Z and Y fits ---------------
+    MA mA;
+    if constexpr (RS) mA.zero(lane); else mA.zero();
+    int since_flush = 0;
+    for (long long m0 = 0; m0 < P.M; m0 += blockDim.x) {
+        const long long m = m0 + threadIdx.x;
+        const bool valid = m < P.M;
+        Words W;
+        W.init(P, (unsigned)m, (unsigned)k, (unsigned)i);
+        R x[D], phi[p], dwi[D], xj[D], zj[D], yn;
+        phi[0] = (R)1;
         {
-            long long rem = k;
+            unsigned ws[D];
+            W.template take<0, D, true>(P, ws);
 #pragma unroll
             for (int l = 0; l < D; ++l) {
-                cell[l] = (int)(rem % P.cells[l]);
-                rem /= P.cells[l];
-            }
-        }
-        auto sample_start = [&](unsigned w, int l) -> R {
-            const R *cf = Form<R>::cellF(P) + 3 * (P.cell_off[l] + cell[l]);
-            return sample_cell(w, __ldg(cf), __ldg(cf + 1), __ldg(cf + 2), Form<R>::mu_arg(P));
-        };
-
-        // ---------------- phase A: responses of the Z and Y fits ---------------
-        MA mA;
-        if constexpr (RS) mA.zero(lane); else mA.zero();
-        int since_flush = 0;
-        for (long long m0 = 0; m0 < P.M; m0 += blockDim.x) {
-            const long long m = m0 + threadIdx.x;
-            const bool valid = m < P.M;
-            Words W;
-            W.init(P, (unsigned)m, (unsigned)k, (unsigned)i);
-            R x[D], phi[p], dwi[D], xj[D], zj[D], yn;
-            phi[0] = (R)1;
-            {
-                unsigned ws[D];
-                W.template take<0, D, true>(P, ws);
-#pragma unroll
-                for (int l = 0; l < D; ++l) {
-                    x[l] = sample_start(ws[l], l);
-                    if (LP1) {
-                        R t;
-                        if (sizeof(R) == 8) t = (x[l] - (R)P.lo[l]) / (R)P.h[l];
-                        else t = (x[l] - (R)P.lo_f[l]) * (R)P.r_f[l];
-                        phi[1 + l] = (R)2 * (t - (R)cell[l]) - (R)1;
-                    }
+                x[l] = sample_start(ws[l], l);
+                if (LP1) {
+                    R t;
+                    if (sizeof(R) == 8) t = (x[l] - (R)P.lo[l]) / (R)P.h[l];
+                    else t = (x[l] - (R)P.lo_f[l]) * (R)P.r_f[l];
+                    phi[1 + l] = (R)2 * (t - (R)cell[l]) - (R)1;
                 }
             }
-            {
-                unsigned wd[D];
-                W.template take<D % 4, D, false>(P, wd);
-#pragma unroll
-                for (int l = 0; l < D; ++l) {
-                    dwi[l] = sdt * normal_of(wd[l], (R)0);
-                    xj[l] = x[l] + Form<R>::b(P, l) * dt + Form<R>::sig(P, l) * dwi[l];
-                }
-            }
-            // Martingale control: CI = zc_i(x_i).dW_i (stratum k), CZ = sum_{j>i} zc_j(X_j).dW_j,
-            // zc_j evaluated at X_j from the control row of (j, stratum of X_j).
-            [[maybe_unused]] R CI = (R)0, CZ = (R)0;
-            [[maybe_unused]] R phij[p];
-            [[maybe_unused]] unsigned rowj = 0;
-            if constexpr (CV) CI = control_dot<R, D, p>(P, (unsigned)i * (unsigned)P.K + (unsigned)k, phi, dwi);
-            eval_at<R, D, LP1, MODEL, ZIN, CV>(P, i + 1, xj, yn, zj, phij, rowj);
-            R S = (R)0;
-            // Steps j = i+1 .. N-1 in groups of G, so that the word phase of
-            // every step in a group is a compile-time constant.
-            constexpr int G = 4 / gcd_c(D, 4);
-            for (int j0 = i + 1; j0 < P.N; j0 += G) {
-                static_for<0, G>([&](auto gc) {
-                    constexpr int g = decltype(gc)::value;
-                    const int j = j0 + g;
-                    if (j >= P.N) return;
-                    unsigned wn[D];
-                    W.template take<(D + D * (1 + g)) % 4, D, false>(P, wn);
-                    R xn[D], zn[D], dw[D];
-#pragma unroll
-                    for (int l = 0; l < D; ++l) {
-                        dw[l] = sdt * normal_of(wn[l], (R)0);
-                        xn[l] = xj[l] + Form<R>::b(P, l) * dt + Form<R>::sig(P, l) * dw[l];
-                    }
-                    if constexpr (CV) CZ += control_dot<R, D, p>(P, rowj, phij, dw);
-                    eval_at<R, D, LP1, MODEL, ZIN, CV>(P, j + 1, xn, yn, zn, phij, rowj);
-                    S += dt * model_f<R, D, MODEL, ZIN>(P, j, xj, yn, zj);
-#pragma unroll
-                    for (int l = 0; l < D; ++l) { xj[l] = xn[l]; zj[l] = zn[l]; }
-                });
-            }
-            S += model_g<R, D, MODEL>(P, xj);
-            // Z response uses S - CZ; the phase-A part of the Y response S - CZ - CI.
-            R SZ = S, SY = S;
-            if constexpr (CV) { SZ = S - CZ; SY = SZ - CI; }
-            if constexpr (RS) {
-                // this path's products (zero for lanes past M)
-                const float Sv = valid ? (float)SZ : 0.0f;
-                const float Sy = valid ? (float)SY : 0.0f;
-                const float g1 = valid ? 1.0f : 0.0f;
-                float v[EA];
-#pragma unroll
-                for (int e = 0; e < EG; ++e) v[e] = g1 * phi[tri_a(e, p)] * phi[tri_b(e, p)];
-#pragma unroll
-                for (int l = 0; l < q; ++l) {
-                    const float wz = Sv * (float)dwi[l] * (float)inv_dt;
-#pragma unroll
-                    for (int a = 0; a < p; ++a) v[EG + l * p + a] = (float)phi[a] * wz;
-                }
-#pragma unroll
-                for (int a = 0; a < p; ++a) v[EG + EZ + a] = (float)phi[a] * Sy;
-                mA.add_path(v, lane);
-            } else {
-                if (valid) {
-                    int e = 0;
-                    if (LP1) {
-#pragma unroll
-                        for (int a = 0; a < p; ++a)
-#pragma unroll
-                            for (int b = a; b < p; ++b) mA.add(e++, phi[a] * phi[b]);
-                    }
-#pragma unroll
-                    for (int l = 0; l < q; ++l) {
-                        const R wz = SZ * dwi[l] * inv_dt;
-#pragma unroll
-                        for (int a = 0; a < p; ++a) mA.add(EG + l * p + a, phi[a] * wz);
-                    }
-#pragma unroll
-                    for (int a = 0; a < p; ++a) mA.add(EG + EZ + a, phi[a] * SY);
-                }
-                if (++since_flush == FLUSH) { mA.flush(lane); since_flush = 0; }
-            }
-        }
-        if constexpr (RS) {
-            block_totals_rs<EA>(mA.c, mA.base, mA.rend, redA, totA, warp, nwarps);
-        } else {
-            double lv[(EA + 31) / 32];
-            mA.finish(lv, lane);
-            block_totals<EA>(lv, redA, totA, lane, warp, nwarps);
-        }
-
-        // ---------------- Z fit (FP64, one warp) -----------------------------
-        if (warp == 0) {
-            const double Md = (double)P.M;
-            bool ok = true;
-            if (LP1) ok = cholesky_warp<p>(totA, Gw, Ls, Linv, lane);
-            __syncwarp();
-            for (int l = lane; l < q; l += 32) {
-                if (LP1 && ok) {
-                    chol_solve<p>(Ls, Linv, totA + EG + l * p, beta_s + l * p);
-                } else {
-                    const double m0 = totA[EG + l * p] / Md;
-                    for (int a = 0; a < p; ++a) beta_s[l * p + a] = (a == 0) ? m0 : 0.0;
-                }
-            }
-            __syncwarp();
-            for (int a = lane; a < q * p; a += 32) beta_r[a] = (R)beta_s[a];
-            if (lane == 0) ok_s = ok ? 1 : 0;
-        }
-        __syncthreads();
-
-        // ---------------- phase B: the f_i term of the Y response ----------------
-        MB mB;
-        mB.zero();
-        since_flush = 0;
-        for (long long m0 = 0; m0 < P.M; m0 += blockDim.x) {
-            const long long m = m0 + threadIdx.x;
-            const bool valid = m < P.M;
-            Words W;
-            W.init(P, (unsigned)m, (unsigned)k, (unsigned)i);
-            R x[D], phi[p], x1[D], y1, z1[D], zi[D];
-            phi[0] = (R)1;
-            {
-                unsigned ws[D];
-                W.template take<0, D, true>(P, ws);
-#pragma unroll
-                for (int l = 0; l < D; ++l) {
-                    x[l] = sample_start(ws[l], l);
-                    if (LP1) {
-                        R t;
-                        if (sizeof(R) == 8) t = (x[l] - (R)P.lo[l]) / (R)P.h[l];
-                        else t = (x[l] - (R)P.lo_f[l]) * (R)P.r_f[l];
-                        phi[1 + l] = (R)2 * (t - (R)cell[l]) - (R)1;
-                    }
-                }
-            }
-            {
-                unsigned wd[D];
-                W.template take<D % 4, D, false>(P, wd);
-#pragma unroll
-                for (int l = 0; l < D; ++l) {
-                    const R dw = sdt * normal_of(wd[l], (R)0);
-                    x1[l] = x[l] + Form<R>::b(P, l) * dt + Form<R>::sig(P, l) * dw;
-                }
-            }
-            {
-                [[maybe_unused]] R phi1[p];
-                [[maybe_unused]] unsigned row1;
-                eval_at<R, D, LP1, MODEL, ZIN, false>(P, i + 1, x1, y1, z1, phi1, row1);
-            }
-#pragma unroll
-            for (int l = 0; l < q; ++l) {
-                R w = beta_r[l * p];
-#pragma unroll
-                for (int a = 1; a < p; ++a) w += beta_r[l * p + a] * phi[a];
-                zi[l] = clamp_r(w, Form<R>::Cz(P));
-            }
-            const R fi = model_f<R, D, MODEL, ZIN>(P, i, x, y1, zi);
-            if (valid) {
-#pragma unroll
-                for (int a = 0; a < p; ++a) mB.add(a, phi[a] * fi);
-            }
-            if (++since_flush == FLUSH) { mB.flush(lane); since_flush = 0; }
         }
         {
-            double lv[(EB + 31) / 32];
-            mB.finish(lv, lane);
-            block_totals<EB>(lv, redB, totB, lane, warp, nwarps);
+            unsigned wd[D];
+            W.template take<D % 4, D, false>(P, wd);
+#pragma unroll
+            for (int l = 0; l < D; ++l) {
+                dwi[l] = sdt * normal_of(wd[l], (R)0);
+                xj[l] = x[l] + Form<R>::b(P, l) * dt + Form<R>::sig(P, l) * dwi[l];
+            }
         }
-
-        // ---------------- Y fit (FP64) and the row (i, k) -----------------------
-        if (threadIdx.x == 0) {
-            const double Md = (double)P.M;
-            const double dtd = P.dt;
-            double *alpha = totB;                      // solved in place
-            for (int a = 0; a < p; ++a) alpha[a] = totA[EG + EZ + a] + dtd * totB[a];
-            if (LP1 && ok_s) {
-                chol_solve<p>(Ls, Linv, alpha, alpha);
-            } else {
-                const double m0 = alpha[0] / Md;
-                for (int a = 0; a < p; ++a) alpha[a] = (a == 0) ? m0 : 0.0;
-            }
-            const long long row = (long long)i * P.K + k;
-            bool finite = true;
-            for (int a = 0; a < p; ++a) {
-                finite = finite && isfinite(alpha[a]);
-                P.Y64[row * P.ry64 + a] = alpha[a];
-                if (P.Y32) P.Y32[row * P.ry32 + a] = (float)alpha[a];
-            }
-            for (int a = 0; a < q * p; ++a) {
-                finite = finite && isfinite(beta_s[a]);
-                P.Z64[row * P.rz64 + a] = beta_s[a];
-                if (P.Z32) P.Z32[row * P.rz32 + a] = (float)beta_s[a];
-            }
-            if (LP1 && !ok_s) atomicAdd(P.stats + 0, 1ull);
-            if (!finite) atomicAdd(P.stats + 1, 1ull);
+        // Martingale control: CI = zc_i(x_i).dW_i (stratum k), CZ = sum_{j>i} zc_j(X_j).dW_j,
+        // zc_j evaluated at X_j from the control row of (j, stratum of X_j).
+        [[maybe_unused]] R CI = (R)0, CZ = (R)0;
+        [[maybe_unused]] R phij[p];
+        [[maybe_unused]] unsigned rowj = 0;
+        if constexpr (CV) CI = control_dot<R, D, p>(P, (unsigned)i * (unsigned)P.K + (unsigned)k, phi, dwi);
+        eval_at<R, D, LP1, MODEL, ZIN, CV>(P, i + 1, xj, yn, zj, phij, rowj);
+        R S = (R)0;
+        // Steps j = i+1 .. N-1 in groups of G, so that the word phase of
+        // every step in a group is a compile-time constant.
+        constexpr int G = 4 / gcd_c(D, 4);
+        for (int j0 = i + 1; j0 < P.N; j0 += G) {
+            static_for<0, G>([&](auto gc) {
+                constexpr int g = decltype(gc)::value;
+                const int j = j0 + g;
+                if (j >= P.N) return;
+                unsigned wn[D];
+                W.template take<(D + D * (1 + g)) % 4, D, false>(P, wn);
+                R xn[D], zn[D], dw[D];
+#pragma unroll
+                for (int l = 0; l < D; ++l) {
+                    dw[l] = sdt * normal_of(wn[l], (R)0);
+                    xn[l] = xj[l] + Form<R>::b(P, l) * dt + Form<R>::sig(P, l) * dw[l];
+                }
+                if constexpr (CV) CZ += control_dot<R, D, p>(P, rowj, phij, dw);
+                eval_at<R, D, LP1, MODEL, ZIN, CV>(P, j + 1, xn, yn, zn, phij, rowj);
+                S += dt * model_f<R, D, MODEL, ZIN>(P, j, xj, yn, zj);
+#pragma unroll
+                for (int l = 0; l < D; ++l) { xj[l] = xn[l]; zj[l] = zn[l]; }
+            });
         }
-        __syncthreads();
+        S += model_g<R, D, MODEL>(P, xj);
+        // Z response uses S - CZ; the phase-A part of the Y response S - CZ - CI.
+        R SZ = S, SY = S;
+        if constexpr (CV) { SZ = S - CZ; SY = SZ - CI; }
+        if constexpr (RS) {
+            // this path's products (zero for lanes past M)
+            const float Sv = valid ? (float)SZ : 0.0f;
+            const float Sy = valid ? (float)SY : 0.0f;
+            const float g1 = valid ? 1.0f : 0.0f;
+            float v[EA];
+#pragma unroll
+            for (int e = 0; e < EG; ++e) v[e] = g1 * phi[tri_a(e, p)] * phi[tri_b(e, p)];
+#pragma unroll
+            for (int l = 0; l < q; ++l) {
+                const float wz = Sv * (float)dwi[l] * (float)inv_dt;
+#pragma unroll
+                for (int a = 0; a < p; ++a) v[EG + l * p + a] = (float)phi[a] * wz;
+            }
+#pragma unroll
+            for (int a = 0; a < p; ++a) v[EG + EZ + a] = (float)phi[a] * Sy;
+            mA.add_path(v, lane);
+        } else {
+            if (valid) {
+                int e = 0;
+                if (LP1) {
+#pragma unroll
+                    for (int a = 0; a < p; ++a)
+#pragma unroll
+                        for (int b = a; b < p; ++b) mA.add(e++, phi[a] * phi[b]);
+                }
+#pragma unroll
+                for (int l = 0; l < q; ++l) {
+                    const R wz = SZ * dwi[l] * inv_dt;
+#pragma unroll
+                    for (int a = 0; a < p; ++a) mA.add(EG + l * p + a, phi[a] * wz);
+                }
+#pragma unroll
+                for (int a = 0; a < p; ++a) mA.add(EG + EZ + a, phi[a] * SY);
+            }
+            if (++since_flush == FLUSH) { mA.flush(lane); since_flush = 0; }
+        }
     }
+    if constexpr (RS) {
+        block_totals_rs<EA>(mA.c, mA.base, mA.rend, redA, totA, warp, nwarps);
+    } else {
+        double lv[(EA + 31) / 32];
+        mA.finish(lv, lane);
+        block_totals<EA>(lv, redA, totA, lane, warp, nwarps);
+    }
+
+    // ---------------- Z fit (FP64, one warp) -----------------------------
+    if (warp == 0) {
+        const double Md = (double)P.M;
+        bool ok = true;
+        if (LP1) ok = cholesky_warp<p>(totA, Gw, Ls, Linv, lane);
+        __syncwarp();
+        for (int l = lane; l < q; l += 32) {
+            if (LP1 && ok) {
+                chol_solve<p>(Ls, Linv, totA + EG + l * p, beta_s + l * p);
+            } else {
+                const double m0 = totA[EG + l * p] / Md;
+                for (int a = 0; a < p; ++a) beta_s[l * p + a] = (a == 0) ? m0 : 0.0;
+            }
+        }
+        __syncwarp();
+        for (int a = lane; a < q * p; a += 32) beta_r[a] = (R)beta_s[a];
+        if (lane == 0) ok_s = ok ? 1 : 0;
+    }
+    __syncthreads();
+
+    // ---------------- phase B: the f_i term of the Y response ----------------
+    MB mB;
+    mB.zero();
+    since_flush = 0;
+    for (long long m0 = 0; m0 < P.M; m0 += blockDim.x) {
+        const long long m = m0 + threadIdx.x;
+        const bool valid = m < P.M;
+        Words W;
+        W.init(P, (unsigned)m, (unsigned)k, (unsigned)i);
+        R x[D], phi[p], x1[D], y1, z1[D], zi[D];
+        phi[0] = (R)1;
+        {
+            unsigned ws[D];
+            W.template take<0, D, true>(P, ws);
+#pragma unroll
+            for (int l = 0; l < D; ++l) {
+                x[l] = sample_start(ws[l], l);
+                if (LP1) {
+                    R t;
+                    if (sizeof(R) == 8) t = (x[l] - (R)P.lo[l]) / (R)P.h[l];
+                    else t = (x[l] - (R)P.lo_f[l]) * (R)P.r_f[l];
+                    phi[1 + l] = (R)2 * (t - (R)cell[l]) - (R)1;
+                }
+            }
+        }
+        {
+            unsigned wd[D];
+            W.template take<D % 4, D, false>(P, wd);
+#pragma unroll
+            for (int l = 0; l < D; ++l) {
+                const R dw = sdt * normal_of(wd[l], (R)0);
+                x1[l] = x[l] + Form<R>::b(P, l) * dt + Form<R>::sig(P, l) * dw;
+            }
+        }
+        {
+            [[maybe_unused]] R phi1[p];
+            [[maybe_unused]] unsigned row1;
+            eval_at<R, D, LP1, MODEL, ZIN, false>(P, i + 1, x1, y1, z1, phi1, row1);
+        }
+#pragma unroll
+        for (int l = 0; l < q; ++l) {
+            R w = beta_r[l * p];
+#pragma unroll
+            for (int a = 1; a < p; ++a) w += beta_r[l * p + a] * phi[a];
+            zi[l] = clamp_r(w, Form<R>::Cz(P));
+        }
+        const R fi = model_f<R, D, MODEL, ZIN>(P, i, x, y1, zi);
+        if (valid) {
+#pragma unroll
+            for (int a = 0; a < p; ++a) mB.add(a, phi[a] * fi);
+        }
+        if (++since_flush == FLUSH) { mB.flush(lane); since_flush = 0; }
+    }
+    {
+        double lv[(EB + 31) / 32];
+        mB.finish(lv, lane);
+        block_totals<EB>(lv, redB, totB, lane, warp, nwarps);
+    }
+
+    // ---------------- Y fit (FP64) and the row (i, k) -----------------------
+    if (threadIdx.x == 0) {
+        const double Md = (double)P.M;
+        const double dtd = P.dt;
+        double *alpha = totB;                      // solved in place
+        for (int a = 0; a < p; ++a) alpha[a] = totA[EG + EZ + a] + dtd * totB[a];
+        if (LP1 && ok_s) {
+            chol_solve<p>(Ls, Linv, alpha, alpha);
+        } else {
+            const double m0 = alpha[0] / Md;
+            for (int a = 0; a < p; ++a) alpha[a] = (a == 0) ? m0 : 0.0;
+        }
+        const long long row = (long long)i * P.K + k;
+        bool finite = true;
+        for (int a = 0; a < p; ++a) {
+            finite = finite && isfinite(alpha[a]);
+            P.Y64[row * P.ry64 + a] = alpha[a];
+            if (P.Y32) P.Y32[row * P.ry32 + a] = (float)alpha[a];
+        }
+        for (int a = 0; a < q * p; ++a) {
+            finite = finite && isfinite(beta_s[a]);
+            P.Z64[row * P.rz64 + a] = beta_s[a];
+            if (P.Z32) P.Z32[row * P.rz32 + a] = (float)beta_s[a];
+        }
+        if (LP1 && !ok_s) atomicAdd(P.stats + 0, 1ull);
+        if (!finite) atomicAdd(P.stats + 1, 1ull);
+    }
+    __syncthreads();
+}
+
+template <typename R, int D, bool LP1, int MODEL, bool ZIN, bool CV>
+__global__ void __launch_bounds__(MAX_THREADS, MinBlocks<R, D, CV>::value)
+step_kernel(const Params P, const int i)
+{
+    __shared__ StepSmem<R, D, LP1> sm;
+    for (long long k = blockIdx.x; k < P.K; k += gridDim.x)
+        solve_stratum<R, D, LP1, MODEL, ZIN, CV>(P, i, k, sm);
+}
+
+// Batched form: one launch per round and group of instances with the same
+// kernel variant.  Work item t is stratum t - kofs[a] of active instance a;
+// the block copies that instance's parameters into shared memory whenever
+// its work items move to another instance (the items of one instance are
+// contiguous, and the grid strides through them).
+template <typename R, int D, bool LP1, int MODEL, bool ZIN, bool CV>
+__global__ void __launch_bounds__(MAX_THREADS, MinBlocks<R, D, CV>::value)
+step_kernel_batch(const BatchRound B)
+{
+    __shared__ StepSmem<R, D, LP1> sm;
+    __shared__ __align__(16) Params Ps;
+    int cur = -1;
+    for (long long t = blockIdx.x; t < B.total; t += gridDim.x) {
+        int lo = 0, hi = B.n_active - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (__ldg(B.kofs + mid) <= t) lo = mid; else hi = mid - 1;
+        }
+        if (lo != cur) {                          // the same decision in every thread
+            __syncthreads();
+            const int *src = reinterpret_cast<const int *>(B.params + __ldg(B.inst + lo));
+            int *dst = reinterpret_cast<int *>(&Ps);
+            for (int e = threadIdx.x; e < (int)(sizeof(Params) / sizeof(int)); e += blockDim.x)
+                dst[e] = __ldg(src + e);
+            __syncthreads();
+            cur = lo;
+        }
+        solve_stratum<R, D, LP1, MODEL, ZIN, CV>(Ps, __ldg(B.step + lo), t - __ldg(B.kofs + lo), sm);
+    }
+}
+
+template <typename R, bool LP1, int MODEL, bool ZIN, bool CV>
+cudaError_t launch_batch_one(const BatchRound &B, int grid, int threads, cudaStream_t st)
+{
+    step_kernel_batch<R, SRMC_STEP_D, LP1, MODEL, ZIN, CV><<<grid, threads, 0, st>>>(B);
+    return cudaGetLastError();
+}
+
+template <typename R, bool LP1, int MODEL, bool ZIN, bool CV>
+int occ_batch_one(int threads)
+{
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &n, step_kernel_batch<R, SRMC_STEP_D, LP1, MODEL, ZIN, CV>, threads, 0) != cudaSuccess)
+        return 0;
+    return n;
+}
+
+// Dispatch of the batched kernels over (precision, basis, model variant,
+// control): F is called with the template arguments as a functor.
+template <typename R, typename F>
+auto dispatch_variant(bool lp1, int mv, bool cv, F &&f) -> decltype(f.template operator()<R, true, MODEL_COS, false, false>())
+{
+    using Ret = decltype(f.template operator()<R, true, MODEL_COS, false, false>());
+    if (cv) {
+        if (!lp1) return Ret{};
+        switch (mv) {
+        case MV_COS:      return f.template operator()<R, true, MODEL_COS, false, true>();
+        case MV_COS_Z:    return f.template operator()<R, true, MODEL_COS, true, true>();
+        case MV_LOGISTIC: return f.template operator()<R, true, MODEL_LOGISTIC, true, true>();
+        }
+        return Ret{};
+    }
+    switch (mv) {
+    case MV_COS:      return lp1 ? f.template operator()<R, true, MODEL_COS, false, false>()
+                                 : f.template operator()<R, false, MODEL_COS, false, false>();
+    case MV_COS_Z:    return lp1 ? f.template operator()<R, true, MODEL_COS, true, false>()
+                                 : f.template operator()<R, false, MODEL_COS, true, false>();
+    case MV_LOGISTIC: return lp1 ? f.template operator()<R, true, MODEL_LOGISTIC, true, false>()
+                                 : f.template operator()<R, false, MODEL_LOGISTIC, true, false>();
+    case MV_AFFINE:   return lp1 ? f.template operator()<R, true, MODEL_AFFINE, false, false>()
+                                 : f.template operator()<R, false, MODEL_AFFINE, false, false>();
+    }
+    return Ret{};
 }
 
 template <typename R, bool LP1, int MODEL, bool ZIN, bool CV = false>
@@ -643,6 +745,37 @@ cudaError_t launch_prec(const Params &P, int i, bool lp1, int mv, int grid, int 
 }
 
 }  // namespace
+
+namespace {
+struct BatchLauncher {
+    const BatchRound &B; int grid, threads; cudaStream_t st;
+    template <typename R, bool LP1, int MODEL, bool ZIN, bool CV>
+    cudaError_t operator()() { return launch_batch_one<R, LP1, MODEL, ZIN, CV>(B, grid, threads, st); }
+};
+struct BatchOccupancy {
+    int threads;
+    template <typename R, bool LP1, int MODEL, bool ZIN, bool CV>
+    int operator()() { return occ_batch_one<R, LP1, MODEL, ZIN, CV>(threads); }
+};
+}  // namespace
+
+cudaError_t SRMC_LAUNCH_BATCH_NAME(SRMC_STEP_D)(const BatchRound &B, bool fp64, bool lp1, int mv, bool cv,
+                                                 int grid, int threads, cudaStream_t st)
+{
+    // combinations without a kernel (dispatch_variant would return Ret{} = 0)
+    const bool ok = !(cv && !lp1) && mv >= MV_COS && mv <= MV_AFFINE && !(cv && mv == MV_AFFINE);
+    if (!ok) return cudaErrorInvalidValue;
+    if (fp64) return cudaErrorInvalidValue;     // the batched form is built for FP32 paths
+    BatchLauncher f{B, grid, threads, st};
+    return dispatch_variant<float>(lp1, mv, cv, f);
+}
+
+int SRMC_OCC_BATCH_NAME(SRMC_STEP_D)(bool fp64, bool lp1, int mv, bool cv, int threads)
+{
+    if (fp64) return 0;
+    BatchOccupancy f{threads};
+    return dispatch_variant<float>(lp1, mv, cv, f);
+}
 
 cudaError_t SRMC_LAUNCH_STEP_NAME(SRMC_STEP_D)(const Params &P, int i, bool fp64, bool lp1, int mv,
                                                 int grid, int threads, cudaStream_t st)

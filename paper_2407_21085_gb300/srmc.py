@@ -89,6 +89,14 @@ def lib():
             L.srmc_mlp_fit.argtypes = [vp, vp, ll, i_, i_, C.c_float, C.c_ulonglong, vp, vp]
             L.srmc_cv_tabulate.argtypes = [vp, vp, vp]
             L.srmc_mlp_fit_noalloc.argtypes = [vp, vp, ll, i_, i_, C.c_float, C.c_ulonglong, vp, vp]
+            L.srmc_batch_create.argtypes = [C.POINTER(vp), i_, C.POINTER(vp)]
+            L.srmc_batch_destroy.argtypes = [vp]; L.srmc_batch_destroy.restype = None
+            L.srmc_batch_tune.argtypes = [vp, vp, C.POINTER(i_), i_, C.POINTER(i_)]
+            L.srmc_batch_solve.argtypes = [vp, vp]
+            L.srmc_batch_mode.argtypes = [vp]; L.srmc_batch_mode.restype = i_
+            L.srmc_batch_set_mode.argtypes = [vp, i_]; L.srmc_batch_set_mode.restype = C.c_int
+            for name in ("srmc_batch_create", "srmc_batch_tune", "srmc_batch_solve"):
+                getattr(L, name).restype = C.c_int
             for name in ("srmc_read_control", "srmc_mlp_create", "srmc_mlp_set_params",
                          "srmc_mlp_get_params", "srmc_mlp_eval", "srmc_mlp_loss_grad", "srmc_mlp_fit",
                          "srmc_cv_tabulate", "srmc_mlp_fit_noalloc"):
@@ -332,3 +340,41 @@ class MLP:
 
     def srmc_cv_tabulate(self, solver: "Solver", stream=None):
         _check(lib().srmc_cv_tabulate(self._h, solver.handle, _stream(stream)))
+
+
+class Batch:
+    """Many FP32 solvers solved together (wraps srmc_batch_create); the
+    solvers must outlive the batch."""
+
+    def __init__(self, solvers):
+        self._solvers = list(solvers)
+        arr = (C.c_void_p * len(self._solvers))(*[s.handle for s in self._solvers])
+        h = C.c_void_p()
+        _check(lib().srmc_batch_create(arr, len(self._solvers), C.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().srmc_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def srmc_batch_tune(self, stream=None):
+        out = (C.c_int * 64)()
+        ng = C.c_int()
+        _check(lib().srmc_batch_tune(self._h, _stream(stream), out, 64, C.byref(ng)))
+        return [int(out[a]) for a in range(min(ng.value, 64))]
+
+    def srmc_batch_solve(self, stream=None):
+        _check(lib().srmc_batch_solve(self._h, _stream(stream)))
+
+    def srmc_batch_mode(self) -> int:
+        return int(lib().srmc_batch_mode(self._h))
+
+    def srmc_batch_set_mode(self, mode: int):
+        _check(lib().srmc_batch_set_mode(self._h, int(mode)))

@@ -1,0 +1,83 @@
+"""The batched form (many instances per launch) through the C ABI: every
+instance's tables must equal those of its own single-instance solve."""
+import numpy as np
+import pytest
+
+from paper_2407_21085_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dev():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2407_21085_gb300 import srmc
+    return torch, srmc
+
+
+def _tables(torch, s):
+    t = s.srmc_table()
+    w = s.w
+    y = torch.empty(w.N * w.K * t["ry"], dtype=torch.float64, device="cuda")
+    z = torch.empty(w.N * w.K * t["rz"], dtype=torch.float64, device="cuda")
+    s.srmc_read_table(y, z)
+    torch.cuda.synchronize()
+    return y.cpu().numpy(), z.cpu().numpy()
+
+
+def _instances():
+    # a small heterogeneous mix: d = 1, 2, 3; different N, M, strata, models
+    ws = W.cfg4_instances(n=12, seed=4)
+    return [w.replace(cells=[max(4, c // 4) for c in w.cells], M=min(w.M, 512)) for w in ws] + [
+        W.cfg3(C=3, N=3, M=256), W.logistic_paper(d=2, N=5, C=4, M=300),
+        W.cfg2(C=6, N=4, M=300, kapz=0.2), W.cfg2(C=5, N=3, M=257, basis="lp0")]
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_batch_equals_single_solves(dev, mode):
+    # mode 0: rounds of multi-instance launches; mode 1: one graph branch per instance
+    torch, srmc = dev
+    ws = _instances()
+    single = []
+    for w in ws:
+        s = srmc.Solver(w, block_threads=256)
+        s.srmc_solve()
+        single.append(_tables(torch, s))
+    solvers = [srmc.Solver(w, block_threads=256) for w in ws]
+    b = srmc.Batch(solvers)
+    b.srmc_batch_set_mode(mode)
+    assert b.srmc_batch_mode() == mode
+    b.srmc_batch_solve()
+    b.srmc_batch_solve()                       # graph replay
+    for a, s in enumerate(solvers):
+        y, z = _tables(torch, s)
+        assert np.array_equal(y, single[a][0]) and np.array_equal(z, single[a][1]), ws[a].name
+
+
+def test_tuned_batch_matches_within_rounding(dev):
+    torch, srmc = dev
+    ws = _instances()[:8]
+    ref = []
+    for w in ws:
+        s = srmc.Solver(w)
+        s.srmc_solve()
+        ref.append(_tables(torch, s))
+    solvers = [srmc.Solver(w) for w in ws]
+    b = srmc.Batch(solvers)
+    threads = b.srmc_batch_tune()
+    assert threads and all(t in (64, 128, 256) for t in threads)
+    b.srmc_batch_solve()
+    for a, s in enumerate(solvers):
+        y, z = _tables(torch, s)
+        # a different block size changes only the order of the FP32 moment sums
+        assert np.max(np.abs(y - ref[a][0])) < 1e-4 * (1 + np.max(np.abs(ref[a][0])))
+
+
+def test_batch_rejects_fp64(dev):
+    torch, srmc = dev
+    s = srmc.Solver(W.cfg1(C=4, N=2, M=64))
+    with pytest.raises(srmc.SrmcError) as e:
+        srmc.Batch([s])
+    assert e.value.status == 4
