@@ -47,13 +47,46 @@ def fp32_peak_tflops(sms: int, mhz: float) -> float:
     return sms * 128 * 2 * mhz * 1e6 / 1e12
 
 
+def kernel_source_hash() -> str:
+    """sha256 of the CUDA sources and headers of the library (a traffic record
+    taken from an ncu capture is used only while this hash matches)."""
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2407_21085_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, name), "rb") as fh:
+                h.update(name.encode() + b"\0" + fh.read())
+    with open(os.path.join(ROOT, "include", "srmc.h"), "rb") as fh:
+        h.update(fh.read())
+    return h.hexdigest()
+
+
+def recorded_traffic(workload_name: str, control: bool):
+    """DRAM bytes per step-kernel launch from profiles/step_kernel_traffic.json
+    (written from an ncu capture of the same build and workload), else None."""
+    path = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
+    try:
+        with open(path) as fh:
+            rec = json.load(fh)
+    except (OSError, ValueError):
+        return None
+    for e in rec.get("records", []):
+        if (e.get("workload") == workload_name and bool(e.get("control")) == control
+                and e.get("kernel_source_sha256") == kernel_source_hash()):
+            return e.get("dram_bytes_per_launch")
+    return None
+
+
 def workload(name: str) -> W.Workload:
     makers = {"cfg1": W.cfg1, "cfg2": W.cfg2, "cfg2_fp64": lambda: W.cfg2(precision="fp64"),
               "cfg2_lp0": lambda: W.cfg2(basis="lp0"), "cfg3": W.cfg3, "cfg5": W.cfg5,
               "cfg5_M1024": lambda: W.cfg5(M=1024, name="cfg5_d6_K262144_N40_M1024"),
               # reduced-M cases of the same kernels, for profiler captures
               "cfg3_M2048": lambda: W.cfg3(M=2048, name="cfg3_d4_K20736_N50_M2048"),
-              "cfg5_M512": lambda: W.cfg5(M=512, name="cfg5_d6_K262144_N40_M512")}
+              "cfg5_M512": lambda: W.cfg5(M=512, name="cfg5_d6_K262144_N40_M512"),
+              # same cell width as cfg5 (0.75) on a smaller box, for profiler captures
+              "cfg5_small_M512": lambda: W.cfg5(M=512, C=5, a=1.875, name="cfg5small_d6_K15625_N40_M512")}
     return makers[name]()
 
 
@@ -145,6 +178,12 @@ def run_gpu(args):
     units = w.path_steps()
     stream = torch.cuda.current_stream()
     solver = srmc.Solver(w, block_threads=args.block_threads)
+    if args.control_random:
+        # the timed kernel becomes the control-variate step kernel (control rows
+        # tabulated from an untrained network: the cost does not depend on them)
+        net = srmc.MLP(w.d + 1, seed=args.seed)
+        net.srmc_cv_tabulate(solver, stream)
+        net.close()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
     def one_step(events=None):
@@ -197,6 +236,10 @@ def run_gpu(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         s2 = srmc.Solver(w, block_threads=args.block_threads)
+        if args.control_random:
+            net = srmc.MLP(w.d + 1, seed=args.seed)
+            net.srmc_cv_tabulate(s2, stream)
+            net.close()
         s2.srmc_solve(stream)
         s2.srmc_read_table(host_y, host_z, stream)
         stream.synchronize()
@@ -219,12 +262,15 @@ def run_gpu(args):
         "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32" if w.precision == "fp32" else "f64",
         "data": "synthetic",
-        "config": {"workload": w.name, "d": w.d, "strata": w.K, "N": w.N, "M": w.M, "basis": w.basis,
+        "config": {"workload": w.name + (" + control variate" if args.control_random else ""),
+                   "d": w.d, "strata": w.K, "N": w.N, "M": w.M, "basis": w.basis,
                    "precision": w.precision, "model": "cos (u = e^{lam(T-t)} cos(sum x/sqrt d))",
                    "path_steps_per_solve": units, "l2": "flushed between steps (512 MiB write)",
                    "parallelism": f"replicas x{ws}", "block_threads": args.block_threads or "library"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": args.traffic,
+                     "frac": achieved / peak,
+                     "traffic": args.traffic if args.traffic is not None
+                     else recorded_traffic(w.name, args.control_random),
                      "kernel": "step_kernel", "flops_per_unit": flops_per_path_step(w.d),
                      "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x {peak_mhz:.0f} MHz"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": tab_bytes},
@@ -250,7 +296,7 @@ def cv_compare(args, stream):
     import torch
     from paper_2407_21085_gb300 import srmc
 
-    w = W.cfg5()
+    w = W.cfg5() if not args.cv_small else W.cfg5(C=5, a=1.875, name="cfg5small_d6_K15625_N40_M4096")
     wcv = w.replace(M=args.cv_M)
     wco = w.replace(M=args.cv_coarse_M, seed=w.seed + 100)
     # load the d = 6 kernels (plain and CV) on a tiny problem first
@@ -442,6 +488,10 @@ def main():
     ap.add_argument("--no-cv-compare", action="store_true", help="skip the CV-vs-plain comparison (cfg5)")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-form measurement (cfg4)")
     ap.add_argument("--batch-reps", type=int, default=2)
+    ap.add_argument("--cv-small", action="store_true",
+                    help="CV comparison on 5^6 strata of the same width (for profiler captures)")
+    ap.add_argument("--control-random", action="store_true",
+                    help="time the control-variate step kernel (rows from an untrained network)")
     ap.add_argument("--cv-M", type=int, default=1024)
     ap.add_argument("--cv-coarse-M", type=int, default=256)
     ap.add_argument("--cv-data", type=int, default=1 << 20)
