@@ -62,7 +62,7 @@ def kernel_source_hash() -> str:
     return h.hexdigest()
 
 
-def recorded_traffic(workload_name: str, control: bool):
+def recorded_traffic(workload_name: str, control):
     """DRAM bytes per step-kernel launch from profiles/step_kernel_traffic.json
     (written from an ncu capture of the same build and workload), else None."""
     path = os.path.join(ROOT, "profiles", "step_kernel_traffic.json")
@@ -72,10 +72,28 @@ def recorded_traffic(workload_name: str, control: bool):
     except (OSError, ValueError):
         return None
     for e in rec.get("records", []):
-        if (e.get("workload") == workload_name and bool(e.get("control")) == control
+        if (e.get("workload") == workload_name and e.get("control", False) == control
                 and e.get("kernel_source_sha256") == kernel_source_hash()):
             return e.get("dram_bytes_per_launch")
     return None
+
+
+def control_kind(args):
+    """False (plain), True (tabulated control rows) or "own" (the run's own z)."""
+    return "own" if args.control_own else bool(args.control_random)
+
+
+def install_control(args, solver, stream):
+    """--control-random: the timed kernel becomes the control-variate step
+    kernel with rows tabulated from an untrained network (its cost does not
+    depend on them); --control-own: the kernel with the run's own z control."""
+    from paper_2407_21085_gb300 import srmc
+    if args.control_own:
+        solver.srmc_set_own_control()
+    elif args.control_random:
+        net = srmc.MLP(solver.w.d + 1, seed=args.seed)
+        net.srmc_cv_tabulate(solver, stream)
+        net.close()
 
 
 def workload(name: str) -> W.Workload:
@@ -178,12 +196,7 @@ def run_gpu(args):
     units = w.path_steps()
     stream = torch.cuda.current_stream()
     solver = srmc.Solver(w, block_threads=args.block_threads)
-    if args.control_random:
-        # the timed kernel becomes the control-variate step kernel (control rows
-        # tabulated from an untrained network: the cost does not depend on them)
-        net = srmc.MLP(w.d + 1, seed=args.seed)
-        net.srmc_cv_tabulate(solver, stream)
-        net.close()
+    install_control(args, solver, stream)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
 
     def one_step(events=None):
@@ -236,10 +249,7 @@ def run_gpu(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         s2 = srmc.Solver(w, block_threads=args.block_threads)
-        if args.control_random:
-            net = srmc.MLP(w.d + 1, seed=args.seed)
-            net.srmc_cv_tabulate(s2, stream)
-            net.close()
+        install_control(args, s2, stream)
         s2.srmc_solve(stream)
         s2.srmc_read_table(host_y, host_z, stream)
         stream.synchronize()
@@ -262,7 +272,8 @@ def run_gpu(args):
         "warmup": args.warmup, "ms_per_step": total_ms_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32" if w.precision == "fp32" else "f64",
         "data": "synthetic",
-        "config": {"workload": w.name + (" + control variate" if args.control_random else ""),
+        "config": {"workload": w.name + {False: "", True: " + control variate",
+                                          "own": " + own-z control"}[control_kind(args)],
                    "d": w.d, "strata": w.K, "N": w.N, "M": w.M, "basis": w.basis,
                    "precision": w.precision, "model": "cos (u = e^{lam(T-t)} cos(sum x/sqrt d))",
                    "path_steps_per_solve": units, "l2": "flushed between steps (512 MiB write)",
@@ -270,7 +281,7 @@ def run_gpu(args):
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak,
                      "traffic": args.traffic if args.traffic is not None
-                     else recorded_traffic(w.name, args.control_random),
+                     else recorded_traffic(w.name, control_kind(args)),
                      "kernel": "step_kernel", "flops_per_unit": flops_per_path_step(w.d),
                      "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x {peak_mhz:.0f} MHz"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": tab_bytes},
@@ -286,7 +297,9 @@ def cv_compare(args, stream):
     """cfg5 (d = 6, 8^6 strata, N = 40): the plain scheme at M = 4096 against the
     learned control variate (coarse plain run at M = 256 -> train u_theta ->
     tabulate sigma grad u_theta -> CV run at M = 1024), with the plain scheme at
-    M = 1024 as an ablation.  eps = the sup error of the plain M = 4096 run
+    M = 1024 as an ablation, and the run's own control (the fitted z of the
+    later steps, no network) at M = 1024 as the zero-cost baseline of a
+    control.  eps = the sup error of the plain M = 4096 run
     against the closed form at the centres of the inner strata, over all
     steps.  Wall times are host-measured with the device synchronised, set-up
     (allocation, graph capture) included.  The statistical error of a form is
@@ -303,6 +316,7 @@ def cv_compare(args, stream):
     tiny = W.cos_model("warm", d=6, N=2, C=3, a=3.0, M=64, s0=0.3, lam=0.2, kap=0.5)
     ws = srmc.Solver(tiny); ws.srmc_solve(stream)
     wn = srmc.MLP(7, seed=0); wn.srmc_cv_tabulate(ws, stream); ws.srmc_solve(stream)
+    ws.srmc_set_own_control(); ws.srmc_solve(stream)
     wn.srmc_mlp_fit(ws, n_data=4096, iters=2, batch=4096, lr=1e-3, seed=0, stream=stream)
     torch.cuda.synchronize()
     ws.close(); wn.close()
@@ -344,6 +358,20 @@ def cv_compare(args, stream):
     abl["stat_err_rms"] = float(((ya - values(sb)).pow(2).mean() / 2).sqrt())
     sb.close()
 
+    t0 = clock()
+    so = srmc.Solver(wcv)
+    so.srmc_set_own_control()
+    so.srmc_solve(stream)
+    own = summary(so, clock() - t0)
+    own["path_steps_per_s"] = wcv.path_steps() / own["wall_s"]
+    yo = values(so)
+    so.close()
+    so = srmc.Solver(wcv.replace(seed=w.seed + 1))
+    so.srmc_set_own_control()
+    so.srmc_solve(stream)
+    own["stat_err_rms"] = float(((yo - values(so)).pow(2).mean() / 2).sqrt())
+    so.close()
+
     stages = {}
     t0 = clock()
     co = srmc.Solver(wco)
@@ -370,9 +398,11 @@ def cv_compare(args, stream):
     sd.close(); co.close(); net.close()
 
     eps = plain["sup_err_inner"]
-    out.update({"eps": eps, "plain": plain, "plain_same_M_as_cv": abl, "cv": cv,
+    out.update({"eps": eps, "plain": plain, "plain_same_M_as_cv": abl, "own_z_control_same_M": own, "cv": cv,
                 "cv_reaches_eps": cv["sup_err_inner"] <= eps,
                 "plain_same_M_reaches_eps": abl["sup_err_inner"] <= eps,
+                "own_z_control_reaches_eps": own["sup_err_inner"] <= eps,
+                "variance_ratio_own_z_same_M": (abl["stat_err_rms"] / own["stat_err_rms"]) ** 2,
                 "plain_over_cv_time": plain["wall_s"] / cv["wall_s"],
                 "variance_ratio_same_M": (abl["stat_err_rms"] / cv["stat_err_rms"]) ** 2})
     return out
@@ -492,6 +522,8 @@ def main():
                     help="CV comparison on 5^6 strata of the same width (for profiler captures)")
     ap.add_argument("--control-random", action="store_true",
                     help="time the control-variate step kernel (rows from an untrained network)")
+    ap.add_argument("--control-own", action="store_true",
+                    help="time the step kernel with the run's own z control")
     ap.add_argument("--cv-M", type=int, default=1024)
     ap.add_argument("--cv-coarse-M", type=int, default=256)
     ap.add_argument("--cv-data", type=int, default=1 << 20)

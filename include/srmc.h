@@ -168,8 +168,29 @@ srmc_status srmc_read_table(const srmc_solver *s, double *dst_y, double *dst_z, 
  * functions keep their expectation while the response variance drops when
  * zc approximates the true z = sigma^T grad u.  rows: [N][K][q][p] doubles,
  * host or device memory, centred basis phi = [1, (x - c_k)/(h/2)]; copied
- * (synchronously).  LP1 solvers only (SRMC_ERR_UNSUPPORTED otherwise). */
+ * (synchronously).  LP1 solvers only (SRMC_ERR_UNSUPPORTED otherwise).
+ * The FP64 form uses the rows as given.  The FP32 form keeps them in
+ * binary16 (round to nearest even, magnitudes above 65504 saturated, below
+ * 2^-14 with reduced relative precision) and evaluates zc in FP32: its
+ * control is the function of the rounded rows, still free of dW_j, so the
+ * expectation argument above holds unchanged; only the variance reduction
+ * depends on the rounding (relative 2^-11 in the coefficients).
+ * srmc_read_control returns the rows as given (FP64). */
 srmc_status srmc_set_control(srmc_solver *s, const double *rows);
+
+/* The run's own martingale control (an extension of Alg. SRMDP, not in the
+ * paper): both responses of cloud C_{i,k} lose sum_{j>i} z_j(X_j).dW_j, z_j
+ * the truncated z fit of step j in the stratum holding X_j -- the function
+ * the path already looks up when the driver depends on z.  Each z_j is fitted
+ * from clouds drawn independently of C_{i,k} before step i is solved, so the
+ * term has zero conditional mean given x_i (independence of the clouds, the
+ * definition of the simulations in Sec. 4) and the fitted functions keep their
+ * expectation.  There is no step-i term (z_i is fitted from the same cloud).
+ * No rows are stored: the control costs one z-row gather per path-step where
+ * the driver does not already need it.  Replaces any installed rows;
+ * srmc_read_control then fails with SRMC_ERR_STATE.  LP1 solvers, not the
+ * affine model (SRMC_ERR_UNSUPPORTED otherwise). */
+srmc_status srmc_set_own_control(srmc_solver *s);
 
 /* Remove the control variate (the plain scheme again). */
 srmc_status srmc_clear_control(srmc_solver *s);
@@ -290,6 +311,7 @@ srmc_status srmc_closed_form_error(const srmc_solver *s, double *dev_out, void *
  * semi-infinite outer cell), where the nominal centre lies in the stratum's
  * bulk; K_inner = prod_l (cells[l] - 2) must be > 0. */
 srmc_status srmc_closed_form_error_inner(const srmc_solver *s, double *dev_out, void *stream);
+
 
 /* Counters since creation: [0] strata fits that fell back from LP1 to LP0
  * because the Gram matrix was numerically singular (Cholesky pivot below

@@ -115,6 +115,7 @@ def _bind(L):
     L.orc_fallbacks.argtypes = [C.c_void_p]; L.orc_fallbacks.restype = C.c_int64
     L.orc_path_steps.argtypes = [C.c_void_p]; L.orc_path_steps.restype = C.c_int64
     L.orc_set_control.argtypes = [C.c_void_p, dp]; L.orc_set_control.restype = C.c_int
+    L.orc_set_own_control.argtypes = [C.c_void_p, C.c_int]; L.orc_set_own_control.restype = None
     fp = C.POINTER(C.c_float)
     L.orc_mlp_nparams.argtypes = [C.c_int, C.c_int]; L.orc_mlp_nparams.restype = C.c_int
     L.orc_bf16.argtypes = [C.c_double]; L.orc_bf16.restype = C.c_float
@@ -305,6 +306,11 @@ class Oracle:
         self._control = np.ascontiguousarray(rows, dtype=np.float64)
         if self._L.orc_set_control(self._ctx, _dptr(self._control)) != 0:
             raise MemoryError("oracle: control rows")
+
+    def set_own_control(self, on: bool = True):
+        """Control from the run's own fitted z of the later steps."""
+        self._control = None
+        self._L.orc_set_own_control(self._ctx, 1 if on else 0)
 
     @property
     def fallbacks(self) -> int:

@@ -347,6 +347,7 @@ int orc_lstsq_householder(int n, int p, int r, double *A, double *B, double *X)
 struct orc_ctx {
     orc_problem P;
     double *control;    /* [N][K][q][dimb] centred-basis control rows, or NULL */
+    int own_control;    /* control from the fitted z of later steps        */
     int64_t K;          /* number of strata                                 */
     int dimb;           /* basis dimension: 1 (LP0) or d+1 (LP1)            */
     int R;              /* row length (1+q)*dimb                            */
@@ -387,12 +388,20 @@ int orc_set_control(orc_ctx *C, const double *rows)
 {
     free(C->control);
     C->control = NULL;
+    C->own_control = 0;
     if (!rows) return 0;
     size_t n = (size_t)C->P.N * (size_t)C->K * (size_t)C->P.q * (size_t)C->dimb;
     C->control = (double *)malloc(sizeof(double) * n);
     if (!C->control) return 1;
     memcpy(C->control, rows, sizeof(double) * n);
     return 0;
+}
+
+void orc_set_own_control(orc_ctx *C, int on)
+{
+    free(C->control);
+    C->control = NULL;
+    C->own_control = on != 0;
 }
 
 /* zc_j(x) . dw for a point x of stratum k (control rows in the centred basis
@@ -507,6 +516,9 @@ static int64_t fit_impl(orc_ctx *C, int i, int64_t k, int lazy)
             if (C->control) {
                 const double cd = control_dot(C, j, j == i ? k : orc_locate(P, x), x, dw);
                 if (j == i) CI[m] = cd; else CZ[m] += cd;
+            } else if (C->own_control && j > i) {
+                /* z_j(x_j) of the fitted row, as looked up for the driver */
+                for (int l = 0; l < q; ++l) CZ[m] += zj[l] * dw[l];
             }
             if (j + 1 == N) {
                 yn = orc_g(P, xn);

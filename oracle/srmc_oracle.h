@@ -102,6 +102,12 @@ int64_t  orc_eval(orc_ctx *C, int i, int64_t n, const double *x, double *y, doub
  * Both have zero conditional mean given x_i, so the fitted functions keep
  * their expectation.  The rows are copied; NULL removes the control. */
 int      orc_set_control(orc_ctx *C, const double *rows);
+/* The run's own control: with on != 0 both responses of cloud C_{i,k} lose
+ * sum_{j>i} z_j(X_j).dW_j, z_j the truncated fit of the stratum holding X_j
+ * at step j (fitted from other, independent clouds before step i, so
+ * E[z_j(X_j).dW_j | X_j] = 0; no step-i term).  Replaces any control rows;
+ * orc_set_control(C, NULL) or on = 0 removes it. */
+void     orc_set_own_control(orc_ctx *C, int on);
 
 /* Number of (i,k) fits that fell back to LP0 because R was singular. */
 int64_t  orc_fallbacks(const orc_ctx *C);

@@ -219,11 +219,11 @@ srmc_status srmc_batch_create(srmc_solver *const *solvers, int n, srmc_batch **o
     for (int r = 0; r < n; ++r) {
         const srmc_solver *s = solvers[r];
         auto it = std::find_if(b->groups.begin(), b->groups.end(), [&](const Group &g) {
-            return g.d == s->P.d && g.mv == s->mv && g.lp1 == s->lp1 && g.cv == s->cv;
+            return g.d == s->P.d && g.mv == srmc::kernel_mv(s) && g.lp1 == s->lp1 && g.cv == s->cv;
         });
         if (it == b->groups.end()) {
             Group g;
-            g.d = s->P.d; g.mv = s->mv; g.lp1 = s->lp1; g.cv = s->cv;
+            g.d = s->P.d; g.mv = srmc::kernel_mv(s); g.lp1 = s->lp1; g.cv = s->cv;
             b->groups.push_back(g);
             it = b->groups.end() - 1;
         }
@@ -262,8 +262,10 @@ srmc_status srmc_batch_create(srmc_solver *const *solvers, int n, srmc_batch **o
     std::vector<Params> params(n);
     for (int r = 0; r < n; ++r) {
         params[r] = solvers[r]->P;
-        params[r].C32 = solvers[r]->cv ? solvers[r]->C32 : nullptr;
-        params[r].C64 = solvers[r]->cv ? solvers[r]->C64 : nullptr;
+        const bool rows = solvers[r]->cv && !solvers[r]->cv_own;
+        params[r].C16 = rows ? solvers[r]->C16 : nullptr;
+        params[r].C64 = rows ? solvers[r]->C64 : nullptr;
+        params[r].cv_own = solvers[r]->cv && solvers[r]->cv_own ? 1 : 0;
     }
     cudaError_t e = cudaMalloc(&b->d_params, sizeof(Params) * n);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_ints, sizeof(int) * std::max<size_t>(ints.size(), 1));

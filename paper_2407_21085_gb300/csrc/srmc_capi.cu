@@ -1,11 +1,13 @@
 // srmc_capi.cu -- the C ABI of libsrmc (include/srmc.h): solver set-up, the
 // backward time loop, evaluation of the fitted functions, and kernels for the
 // method's primitives.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <limits>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/srmc.h"
@@ -50,30 +52,70 @@ double logistic_cdf(double x, double mu)
 
 int pad_to(int v, int m) { return (v + m - 1) / m * m; }
 
+// Halves per component of a binary16 control row: 4 (one 8-byte load) for
+// p <= 4, else p rounded up to 8 (16-byte loads).
+int half_pad(int p) { return p <= 4 ? 4 : pad_to(p, 8); }
+
+// Stratum locality order: the strata sorted by the Morton code of their
+// cell coordinates (coordinate bits interleaved from the most significant
+// level down; a dimension of 2^b cells contributes b bits, at most 39 bits in
+// all since K < 2^31).  Work item t of a step launch solves stratum order[t],
+// so the blocks resident at one time cover a compact box of cells and the
+// rows their paths gather at later steps overlap in L1/L2.  The order only
+// assigns strata to blocks: every stratum is solved by exactly one block and
+// its result does not depend on the order.
+std::vector<unsigned> morton_order(const int *cells, int d, long long K)
+{
+    int bits[SRMC_DMAX], maxb = 0;
+    for (int l = 0; l < d; ++l) {
+        bits[l] = 0;
+        while ((1LL << bits[l]) < cells[l]) ++bits[l];
+        maxb = std::max(maxb, bits[l]);
+    }
+    std::vector<std::pair<unsigned long long, unsigned>> key((size_t)K);
+    for (long long k = 0; k < K; ++k) {
+        long long rem = k;
+        int c[SRMC_DMAX];
+        for (int l = 0; l < d; ++l) { c[l] = (int)(rem % cells[l]); rem /= cells[l]; }
+        unsigned long long m = 0;
+        for (int t = maxb - 1; t >= 0; --t)
+            for (int l = d - 1; l >= 0; --l)
+                if (t < bits[l]) m = (m << 1) | (unsigned long long)((c[l] >> t) & 1);
+        key[(size_t)k] = {m, (unsigned)k};
+    }
+    std::sort(key.begin(), key.end());
+    std::vector<unsigned> order((size_t)K);
+    for (size_t t = 0; t < order.size(); ++t) order[t] = key[t].second;
+    return order;
+}
+
 void free_all(srmc_solver *s)
 {
     if (s->graph) cudaGraphExecDestroy(s->graph);
     if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
     cudaFree(s->cellF); cudaFree(s->cellF_f); cudaFree(s->stepc); cudaFree(s->stepc_f);
     cudaFree(s->Y32); cudaFree(s->Z32); cudaFree(s->Y64); cudaFree(s->Z64); cudaFree(s->stats);
-    cudaFree(s->C32); cudaFree(s->C64);
+    cudaFree(s->C16); cudaFree(s->C64); cudaFree(s->order);
 }
 
 cudaError_t launch_step(const srmc_solver *s, int i, cudaStream_t st)
 {
     Params P = s->P;
-    P.C32 = s->cv ? s->C32 : nullptr;
-    P.C64 = s->cv ? s->C64 : nullptr;
+    const bool rows = s->cv && !s->cv_own;
+    P.C16 = rows ? s->C16 : nullptr;
+    P.C64 = rows ? s->C64 : nullptr;
+    P.cv_own = s->cv && s->cv_own ? 1 : 0;
+    const int mv = srmc::kernel_mv(s);
     const int grid = (int)(P.K < 2147483647LL ? P.K : 2147483647LL);
     switch (P.d) {
-    case 1: return srmc::launch_step_d1(P, i, s->fp64, s->lp1, s->mv, grid, s->threads, st);
-    case 2: return srmc::launch_step_d2(P, i, s->fp64, s->lp1, s->mv, grid, s->threads, st);
-    case 3: return srmc::launch_step_d3(P, i, s->fp64, s->lp1, s->mv, grid, s->threads, st);
-    case 4: return srmc::launch_step_d4(P, i, s->fp64, s->lp1, s->mv, grid, s->threads, st);
-    case 5: return srmc::launch_step_d5(P, i, s->fp64, s->lp1, s->mv, grid, s->threads, st);
-    case 6: return srmc::launch_step_d6(P, i, s->fp64, s->lp1, s->mv, grid, s->threads, st);
-    case 7: return srmc::launch_step_d7(P, i, s->fp64, s->lp1, s->mv, grid, s->threads, st);
-    case 8: return srmc::launch_step_d8(P, i, s->fp64, s->lp1, s->mv, grid, s->threads, st);
+    case 1: return srmc::launch_step_d1(P, i, s->fp64, s->lp1, mv, grid, s->threads, st);
+    case 2: return srmc::launch_step_d2(P, i, s->fp64, s->lp1, mv, grid, s->threads, st);
+    case 3: return srmc::launch_step_d3(P, i, s->fp64, s->lp1, mv, grid, s->threads, st);
+    case 4: return srmc::launch_step_d4(P, i, s->fp64, s->lp1, mv, grid, s->threads, st);
+    case 5: return srmc::launch_step_d5(P, i, s->fp64, s->lp1, mv, grid, s->threads, st);
+    case 6: return srmc::launch_step_d6(P, i, s->fp64, s->lp1, mv, grid, s->threads, st);
+    case 7: return srmc::launch_step_d7(P, i, s->fp64, s->lp1, mv, grid, s->threads, st);
+    case 8: return srmc::launch_step_d8(P, i, s->fp64, s->lp1, mv, grid, s->threads, st);
     }
     return cudaErrorInvalidValue;
 }
@@ -269,7 +311,7 @@ srmc_status srmc_create(const srmc_problem *pr, const srmc_strata *sa, const srm
     }
     {
         const int p_ = cf->basis == SRMC_LP1 ? d + 1 : 1;
-        const long long rmax = (long long)q * pad_to(p_, 4);
+        const long long rmax = (long long)q * std::max(pad_to(p_, 4), half_pad(p_));
         if ((long long)pr->N * K * rmax >= 4294967296LL)
             return fail(SRMC_ERR_UNSUPPORTED, "table too large: N K row-length must be < 2^32");
     }
@@ -300,7 +342,7 @@ srmc_status srmc_create(const srmc_problem *pr, const srmc_strata *sa, const srm
     P.zin = (s->mv == srmc::MV_COS_Z || s->mv == srmc::MV_LOGISTIC);
     P.ry32 = pad_to(p, 4); P.rz32 = pad_to(q * p, 4);
     P.ry64 = pad_to(p, 2); P.rz64 = pad_to(q * p, 2);
-    P.pp = pad_to(p, 4); P.rc32 = q * P.pp;
+    P.ph = half_pad(p); P.rc16 = q * P.ph;
     int stride = 1;
     int off = 0;
     for (int l = 0; l < d; ++l) {
@@ -400,6 +442,13 @@ srmc_status srmc_create(const srmc_problem *pr, const srmc_strata *sa, const srm
     if ((e = cudaMemset(s->stats, 0, sizeof(unsigned long long) * 4)) != cudaSuccess) return bail(e, "cudaMemset");
     P.cellF = s->cellF; P.cellF_f = s->cellF_f; P.stepc = s->stepc; P.stepc_f = s->stepc_f;
     P.Y32 = s->Y32; P.Z32 = s->Z32; P.Y64 = s->Y64; P.Z64 = s->Z64; P.stats = s->stats;
+    if (d >= SRMC_ORDER_MIN_D && K > 1 && K <= SRMC_ORDER_MAX_K) {
+        const std::vector<unsigned> order = morton_order(sa->cells, d, K);
+        if ((e = cudaMalloc(&s->order, sizeof(unsigned) * order.size())) != cudaSuccess) return bail(e, "cudaMalloc order");
+        if ((e = cudaMemcpy(s->order, order.data(), sizeof(unsigned) * order.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
+            return bail(e, "cudaMemcpy order");
+        P.order = s->order;
+    }
     *out = s;
     g_last_error.clear();
     return SRMC_OK;
@@ -600,8 +649,9 @@ srmc_status srmc_read_table(const srmc_solver *s, double *dst_y, double *dst_z, 
 }
 
 namespace {
-// [N][K][q][p] -> padded rows of the FP64 and FP32 control tables.
-__global__ void repack_control_kernel(const Params P, const double *src, double *c64, float *c32)
+// [N][K][q][p] -> padded rows of the FP64 table and of the binary16 table of
+// the FP32 form (round to nearest even, saturated at +-65504).
+__global__ void repack_control_kernel(const Params P, const double *src, double *c64, __half *c16)
 {
     const long long rows = (long long)P.N * P.K;
     const int qp = P.q * P.p;
@@ -610,7 +660,7 @@ __global__ void repack_control_kernel(const Params P, const double *src, double 
         for (int a = 0; a < qp; ++a) {
             const double v = src[r * qp + a];
             c64[r * P.rz64 + a] = v;
-            c32[r * P.rc32 + (a / P.p) * P.pp + a % P.p] = (float)v;
+            c16[r * P.rc16 + (a / P.p) * P.ph + a % P.p] = __double2half(fmin(fmax(v, -65504.0), 65504.0));
         }
     }
 }
@@ -625,21 +675,22 @@ srmc_status srmc_set_control(srmc_solver *s, const double *rows)
     const size_t n = nrow * (size_t)(s->P.q * s->P.p);
     if (!s->C64) {
         SRMC_CUDA(cudaMalloc(&s->C64, sizeof(double) * nrow * s->P.rz64), "cudaMalloc control");
-        SRMC_CUDA(cudaMalloc(&s->C32, sizeof(float) * nrow * s->P.rc32), "cudaMalloc control");
+        SRMC_CUDA(cudaMalloc(&s->C16, sizeof(__half) * nrow * s->P.rc16), "cudaMalloc control");
         SRMC_CUDA(cudaMemset(s->C64, 0, sizeof(double) * nrow * s->P.rz64), "cudaMemset control");
-        SRMC_CUDA(cudaMemset(s->C32, 0, sizeof(float) * nrow * s->P.rc32), "cudaMemset control");
+        SRMC_CUDA(cudaMemset(s->C16, 0, sizeof(__half) * nrow * s->P.rc16), "cudaMemset control");
     }
     double *staging = nullptr;
     SRMC_CUDA(cudaMalloc(&staging, sizeof(double) * n), "cudaMalloc control staging");
     cudaError_t e = cudaMemcpy(staging, rows, sizeof(double) * n, cudaMemcpyDefault);
     if (e == cudaSuccess) {
-        repack_control_kernel<<<grid_for((long long)nrow, 256), 256>>>(s->P, staging, s->C64, s->C32);
+        repack_control_kernel<<<grid_for((long long)nrow, 256), 256>>>(s->P, staging, s->C64, s->C16);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     cudaFree(staging);
     if (e != cudaSuccess) return cuda_fail(e, "srmc_set_control");
     s->cv = true;
+    s->cv_own = false;
     if (s->graph) { cudaGraphExecDestroy(s->graph); s->graph = nullptr; }
     return SRMC_OK;
 }
@@ -647,10 +698,23 @@ srmc_status srmc_set_control(srmc_solver *s, const double *rows)
 srmc_status srmc_read_control(const srmc_solver *s, double *rows)
 {
     if (!s || !rows) return fail(SRMC_ERR_INVALID_ARG, "srmc_read_control: NULL argument");
-    if (!s->cv || !s->C64) return fail(SRMC_ERR_STATE, "srmc_read_control: no control installed");
+    if (!s->cv || s->cv_own || !s->C64)
+        return fail(SRMC_ERR_STATE, "srmc_read_control: no control rows installed");
     const size_t nrow = (size_t)s->P.N * (size_t)s->P.K, qp = (size_t)(s->P.q * s->P.p);
     SRMC_CUDA(cudaMemcpy2D(rows, qp * sizeof(double), s->C64, (size_t)s->P.rz64 * sizeof(double),
                            qp * sizeof(double), nrow, cudaMemcpyDefault), "srmc_read_control");
+    return SRMC_OK;
+}
+
+srmc_status srmc_set_own_control(srmc_solver *s)
+{
+    if (!s) return fail(SRMC_ERR_INVALID_ARG, "srmc_set_own_control: NULL solver");
+    if (!s->lp1) return fail(SRMC_ERR_UNSUPPORTED, "srmc_set_own_control: LP1 solvers only");
+    if (s->mv == srmc::MV_AFFINE)
+        return fail(SRMC_ERR_UNSUPPORTED, "srmc_set_own_control: not for the affine model");
+    s->cv = true;
+    s->cv_own = true;
+    if (s->graph) { cudaGraphExecDestroy(s->graph); s->graph = nullptr; }
     return SRMC_OK;
 }
 
@@ -658,6 +722,7 @@ srmc_status srmc_clear_control(srmc_solver *s)
 {
     if (!s) return fail(SRMC_ERR_INVALID_ARG, "srmc_clear_control: NULL solver");
     s->cv = false;
+    s->cv_own = false;
     if (s->graph) { cudaGraphExecDestroy(s->graph); s->graph = nullptr; }
     return SRMC_OK;
 }

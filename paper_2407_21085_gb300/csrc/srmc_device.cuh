@@ -8,6 +8,7 @@
 #include <cstdint>
 #include <type_traits>
 #include <cuda_runtime.h>
+#include <cuda_fp16.h>
 #include <math_constants.h>
 
 namespace srmc {
@@ -46,10 +47,12 @@ struct Params {
     const float *stepc_f;
     float *Y32, *Z32;               // [N][K][ry32], [N][K][rz32]; N K r < 2^32
     double *Y64, *Z64;              // [N][K][ry64], [N][K][rz64]
-    const float *C32;               // control rows [N][K][q][pp], pp = p padded to 4 floats
-    int pp, rc32;                   // per-component and per-row strides of C32
+    const __half *C16;              // control rows of the FP32 form in binary16: [N][K][q][ph],
+    int ph, rc16;                   // ph = 4 (p <= 4) or p padded to 8; rc16 = q ph
     const double *C64;              // control rows [N][K][rz64]
     unsigned long long *stats;      // [0] LP1->LP0 fallbacks, [1] non-finite rows
+    const unsigned *order;          // [K] stratum solved by work item t (NULL: t itself)
+    int cv_own;                     // control from the fitted z of later steps (ZIN kernels)
 };
 
 // ---- Philox-4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) --------------------
@@ -248,7 +251,6 @@ template <> struct Form<double> {
     __device__ static const double *Ytab(const Params &P) { return P.Y64; }
     __device__ static const double *Ztab(const Params &P) { return P.Z64; }
     __device__ static int ry(const Params &P) { return P.ry64; }
-    __device__ static const double *Ctab(const Params &P) { return P.C64; }
     __device__ static int rz(const Params &P) { return P.rz64; }
 };
 template <> struct Form<float> {
@@ -268,7 +270,6 @@ template <> struct Form<float> {
     __device__ static const float *Ytab(const Params &P) { return P.Y32; }
     __device__ static const float *Ztab(const Params &P) { return P.Z32; }
     __device__ static int ry(const Params &P) { return P.ry32; }
-    __device__ static const float *Ctab(const Params &P) { return P.C32; }
     __device__ static int rz(const Params &P) { return P.rz32; }
 };
 

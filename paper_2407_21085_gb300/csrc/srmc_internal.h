@@ -5,6 +5,16 @@
 
 #include <string>
 
+// A step launch solves the strata in Morton order of their cells (host-built
+// table, 4 bytes per stratum) for d >= SRMC_ORDER_MIN_D and K up to
+// SRMC_ORDER_MAX_K; below, index order already keeps neighbours together.
+#ifndef SRMC_ORDER_MIN_D
+#define SRMC_ORDER_MIN_D 3
+#endif
+#ifndef SRMC_ORDER_MAX_K
+#define SRMC_ORDER_MAX_K (1LL << 25)
+#endif
+
 namespace srmc {
 
 // Message returned by srmc_last_error() for the calling thread; every entry
@@ -102,10 +112,23 @@ struct srmc_solver {
     float *Y32 = nullptr, *Z32 = nullptr;
     double *Y64 = nullptr, *Z64 = nullptr;
     unsigned long long *stats = nullptr;
-    float *C32 = nullptr;                // control rows (FP32 copy, padded like Z32)
+    __half *C16 = nullptr;               // control rows of the FP32 form (binary16, [q][ph] per row)
     double *C64 = nullptr;               // control rows (FP64, padded like Z64)
+    unsigned *order = nullptr;           // locality order of the strata (NULL: index order)
     bool cv = false;                     // control installed
+    bool cv_own = false;                 // ... and it is the run's own fitted z
     cudaStream_t cap_stream = nullptr;   // private stream for graph capture
     cudaGraphExec_t graph = nullptr;     // the N step launches of one solve
 };
+
+namespace srmc {
+// Step-kernel model variant of a solver: the run's own control needs z_j at
+// every path point, so the cos model without z in its driver runs the
+// variant that evaluates z (whose z term then has coefficient kapz = 0).
+inline int kernel_mv(const srmc_solver *s)
+{
+    return (s->cv && s->cv_own && s->mv == MV_COS) ? (int)MV_COS_Z : s->mv;
+}
+}  // namespace srmc
+
 

@@ -476,7 +476,7 @@ __global__ void mlp_data_kernel(const Params P, long long n, unsigned k0, unsign
 // Control rows from the network: one warp per (j, k) tile; tile rows are the
 // stratum centre (row 0) and c +- (h_m/4) e_m (rows 1 + 2m, 2 + 2m).
 __global__ void __launch_bounds__(WARPS * 32) mlp_tabulate_kernel(Net net, const Params P, double *c64,
-                                                                  float *c32)
+                                                                  __half *c16)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     SmemW &w = *reinterpret_cast<SmemW *>(smem);
@@ -526,7 +526,7 @@ __global__ void __launch_bounds__(WARPS * 32) mlp_tabulate_kernel(Net net, const
             else v = (double)GAs[warp][1 + 2 * (c - 1)][1 + l] - (double)GAs[warp][2 + 2 * (c - 1)][1 + l];
             v *= P.sig[l];
             c64[row * P.rz64 + a] = v;
-            c32[row * P.rc32 + l * P.pp + c] = (float)v;
+            c16[row * P.rc16 + l * P.ph + c] = __double2half(fmin(fmax(v, -65504.0), 65504.0));
         }
         __syncwarp();
     }
@@ -816,15 +816,16 @@ srmc_status srmc_cv_tabulate(const srmc_mlp *m, srmc_solver *s, void *stream)
     const size_t nrow = (size_t)s->P.N * (size_t)s->P.K;
     if (!s->C64) {
         MLP_CUDA(cudaMalloc(&s->C64, sizeof(double) * nrow * s->P.rz64), "cudaMalloc control");
-        MLP_CUDA(cudaMalloc(&s->C32, sizeof(float) * nrow * s->P.rc32), "cudaMalloc control");
+        MLP_CUDA(cudaMalloc(&s->C16, sizeof(__half) * nrow * s->P.rc16), "cudaMalloc control");
         MLP_CUDA(cudaMemset(s->C64, 0, sizeof(double) * nrow * s->P.rz64), "cudaMemset control");
-        MLP_CUDA(cudaMemset(s->C32, 0, sizeof(float) * nrow * s->P.rc32), "cudaMemset control");
+        MLP_CUDA(cudaMemset(s->C16, 0, sizeof(__half) * nrow * s->P.rc16), "cudaMemset control");
     }
     const long long tiles = (long long)nrow;
     mlp_tabulate_kernel<<<grid_tiles(tiles), WARPS * 32, smem_tab(), (cudaStream_t)stream>>>(
-        m->net(), s->P, s->C64, s->C32);
+        m->net(), s->P, s->C64, s->C16);
     MLP_CUDA(cudaGetLastError(), "mlp tabulate launch");
     s->cv = true;
+    s->cv_own = false;
     if (s->graph) { cudaGraphExecDestroy(s->graph); s->graph = nullptr; }
     return SRMC_OK;
 }

@@ -283,6 +283,13 @@ __device__ __forceinline__ void eval_at(const Params &P, int j, const R (&x)[D],
     }
 }
 
+// The two binary16 values packed in u (low half first), widened to FP32.
+__device__ __forceinline__ void widen_h2(unsigned u, float &lo, float &hi)
+{
+    lo = __half2float(__ushort_as_half((unsigned short)(u & 0xFFFFu)));
+    hi = __half2float(__ushort_as_half((unsigned short)(u >> 16)));
+}
+
 // zc(x) . dw for the control row `row` and the basis values phi of x:
 // sum_l T_Cz(beta_l . phi) dw_l (the martingale control of one increment).
 template <typename R, int D, int p>
@@ -291,17 +298,24 @@ __device__ __forceinline__ R control_dot(const Params &P, unsigned row, const R 
 {
     R acc = (R)0;
     if constexpr (sizeof(R) == 4) {
-        // FP32 rows: component l holds PP = p rounded up to 4 floats, read as
-        // PP/4 float4 (one or two 16-byte loads per component).
-        constexpr int PP = (p + 3) / 4 * 4;
-        const float4 *b = reinterpret_cast<const float4 *>(P.C32 + row * (unsigned)(D * PP));
+        // FP32 form: binary16 rows, component l holding PH halves (4 for
+        // p <= 4: one 8-byte load; else p rounded up to 8: 16-byte loads),
+        // widened to FP32 for the arithmetic.
+        constexpr int PH = p <= 4 ? 4 : (p + 7) / 8 * 8;
+        const unsigned *b = reinterpret_cast<const unsigned *>(P.C16) + row * (unsigned)(D * PH / 2);
 #pragma unroll
         for (int l = 0; l < D; ++l) {
-            float c[PP];
+            float c[PH];
+            if constexpr (PH == 4) {
+                const uint2 t = __ldg(reinterpret_cast<const uint2 *>(b + l * 2));
+                widen_h2(t.x, c[0], c[1]); widen_h2(t.y, c[2], c[3]);
+            } else {
 #pragma unroll
-            for (int v = 0; v < PP / 4; ++v) {
-                const float4 t = __ldg(b + l * (PP / 4) + v);
-                c[4 * v] = t.x; c[4 * v + 1] = t.y; c[4 * v + 2] = t.z; c[4 * v + 3] = t.w;
+                for (int v = 0; v < PH / 8; ++v) {
+                    const uint4 t = __ldg(reinterpret_cast<const uint4 *>(b + l * (PH / 2)) + v);
+                    widen_h2(t.x, c[8 * v], c[8 * v + 1]); widen_h2(t.y, c[8 * v + 2], c[8 * v + 3]);
+                    widen_h2(t.z, c[8 * v + 4], c[8 * v + 5]); widen_h2(t.w, c[8 * v + 6], c[8 * v + 7]);
+                }
             }
             float w = c[0];
 #pragma unroll
@@ -323,7 +337,9 @@ __device__ __forceinline__ R control_dot(const Params &P, unsigned row, const R 
 
 // Blocks per SM the compiler must fit (register budget): FP32 forms of
 // higher dimension would otherwise take > 100 registers and run 2 blocks/SM.
-// (Measured on GB300: 5 blocks for d <= 2 and 4 for d >= 3 are best.)
+// (Measured on GB300: 5 blocks for d <= 2 and 4 for d >= 3 are best; the
+// control-variate kernel at d = 6 runs 6 % faster with 4 blocks and a
+// 96-byte spill than with 3 blocks and none.)
 #ifndef SRMC_MINB_LO
 #define SRMC_MINB_LO 5
 #endif
@@ -331,12 +347,16 @@ __device__ __forceinline__ R control_dot(const Params &P, unsigned row, const R 
 #define SRMC_MINB_HI 4
 #endif
 #ifndef SRMC_CVMINB_HI
-#define SRMC_CVMINB_HI 3
+#define SRMC_CVMINB_HI 4
 #endif
-template <typename R, int D, bool CV>
+#ifndef SRMC_CVZMINB_HI
+#define SRMC_CVZMINB_HI 3
+#endif
+template <typename R, int D, bool CV, bool ZIN>
 struct MinBlocks {
-    static constexpr int value = sizeof(R) == 8 ? 1 : CV ? (D <= 2 ? 4 : SRMC_CVMINB_HI)
-                                                        : (D <= 2 ? SRMC_MINB_LO : SRMC_MINB_HI);
+    static constexpr int value = sizeof(R) == 8 ? 1
+                               : CV ? (D <= 2 ? 4 : ZIN ? SRMC_CVZMINB_HI : SRMC_CVMINB_HI)
+                                    : (D <= 2 ? SRMC_MINB_LO : SRMC_MINB_HI);
 };
 
 // Shared memory of one stratum block.
@@ -437,11 +457,14 @@ __device__ __forceinline__ void solve_stratum(const Params &P, const int i, cons
             }
         }
         // Martingale control: CI = zc_i(x_i).dW_i (stratum k), CZ = sum_{j>i} zc_j(X_j).dW_j,
-        // zc_j evaluated at X_j from the control row of (j, stratum of X_j).
+        // zc_j evaluated at X_j from the control row of (j, stratum of X_j); with the
+        // run's own control zc_j = z_j, the fitted z of step j, and CI = 0.
         [[maybe_unused]] R CI = (R)0, CZ = (R)0;
         [[maybe_unused]] R phij[p];
         [[maybe_unused]] unsigned rowj = 0;
-        if constexpr (CV) CI = control_dot<R, D, p>(P, (unsigned)i * (unsigned)P.K + (unsigned)k, phi, dwi);
+        if constexpr (CV) {
+            if (!P.cv_own) CI = control_dot<R, D, p>(P, (unsigned)i * (unsigned)P.K + (unsigned)k, phi, dwi);
+        }
         eval_at<R, D, LP1, MODEL, ZIN, CV>(P, i + 1, xj, yn, zj, phij, rowj);
         R S = (R)0;
         // Steps j = i+1 .. N-1 in groups of G, so that the word phase of
@@ -460,7 +483,18 @@ __device__ __forceinline__ void solve_stratum(const Params &P, const int i, cons
                     dw[l] = sdt * normal_of(wn[l], (R)0);
                     xn[l] = xj[l] + Form<R>::b(P, l) * dt + Form<R>::sig(P, l) * dw[l];
                 }
-                if constexpr (CV) CZ += control_dot<R, D, p>(P, rowj, phij, dw);
+                if constexpr (CV) {
+                    // own control: z_j(X_j), already evaluated for the driver
+                    bool own = false;
+                    if constexpr (ZIN) {
+                        if (P.cv_own) {
+                            own = true;
+#pragma unroll
+                            for (int l = 0; l < D; ++l) CZ += zj[l] * dw[l];
+                        }
+                    }
+                    if (!own) CZ += control_dot<R, D, p>(P, rowj, phij, dw);
+                }
                 eval_at<R, D, LP1, MODEL, ZIN, CV>(P, j + 1, xn, yn, zn, phij, rowj);
                 S += dt * model_f<R, D, MODEL, ZIN>(P, j, xj, yn, zj);
 #pragma unroll
@@ -627,12 +661,14 @@ __device__ __forceinline__ void solve_stratum(const Params &P, const int i, cons
 }
 
 template <typename R, int D, bool LP1, int MODEL, bool ZIN, bool CV>
-__global__ void __launch_bounds__(MAX_THREADS, MinBlocks<R, D, CV>::value)
+__global__ void __launch_bounds__(MAX_THREADS, MinBlocks<R, D, CV, ZIN>::value)
 step_kernel(const Params P, const int i)
 {
     __shared__ StepSmem<R, D, LP1> sm;
-    for (long long k = blockIdx.x; k < P.K; k += gridDim.x)
+    for (long long t = blockIdx.x; t < P.K; t += gridDim.x) {
+        const long long k = P.order ? (long long)__ldg(P.order + t) : t;
         solve_stratum<R, D, LP1, MODEL, ZIN, CV>(P, i, k, sm);
+    }
 }
 
 // Batched form: one launch per round and group of instances with the same
@@ -641,7 +677,7 @@ step_kernel(const Params P, const int i)
 // its work items move to another instance (the items of one instance are
 // contiguous, and the grid strides through them).
 template <typename R, int D, bool LP1, int MODEL, bool ZIN, bool CV>
-__global__ void __launch_bounds__(MAX_THREADS, MinBlocks<R, D, CV>::value)
+__global__ void __launch_bounds__(MAX_THREADS, MinBlocks<R, D, CV, ZIN>::value)
 step_kernel_batch(const BatchRound B)
 {
     __shared__ StepSmem<R, D, LP1> sm;
@@ -722,7 +758,7 @@ template <typename R>
 cudaError_t launch_prec(const Params &P, int i, bool lp1, int mv, int grid, int threads,
                         cudaStream_t st)
 {
-    if (P.C64 != nullptr) {             // control variate form (LP1 only)
+    if (P.C64 != nullptr || P.cv_own) { // control variate form (LP1 only)
         if (!lp1) return cudaErrorInvalidValue;
         switch (mv) {
         case MV_COS:      return launch_one<R, true, MODEL_COS, false, true>(P, i, grid, threads, st);

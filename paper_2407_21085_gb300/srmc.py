@@ -78,6 +78,7 @@ def lib():
             L.srmc_closed_form_error_inner.restype = C.c_int
             L.srmc_set_control.argtypes = [vp, vp]
             L.srmc_clear_control.argtypes = [vp]
+            L.srmc_set_own_control.argtypes = [vp]
             L.srmc_read_control.argtypes = [vp, vp]
             L.srmc_mlp_create.argtypes = [i_, i_, C.c_ulonglong, C.POINTER(vp)]
             L.srmc_mlp_destroy.argtypes = [vp]; L.srmc_mlp_destroy.restype = None
@@ -110,7 +111,7 @@ def lib():
             for name in ("srmc_create", "srmc_solve", "srmc_solve_step", "srmc_eval", "srmc_centres",
                          "srmc_table", "srmc_read_table", "srmc_closed_form_error", "srmc_stats", "srmc_philox",
                          "srmc_normals", "srmc_locate", "srmc_set_control", "srmc_clear_control",
-                         "srmc_start_points"):
+                         "srmc_set_own_control", "srmc_start_points"):
                 getattr(L, name).restype = C.c_int
             _lib = L
     return _lib
@@ -219,6 +220,10 @@ class Solver:
         else:
             ptr = _ptr(rows)
         _check(lib().srmc_set_control(self._h, ptr))
+
+    def srmc_set_own_control(self):
+        """Control from the solver's own fitted z of the later steps."""
+        _check(lib().srmc_set_own_control(self._h))
 
     def srmc_clear_control(self):
         _check(lib().srmc_clear_control(self._h))

@@ -109,8 +109,28 @@ def clamp(v, L):
     return v if L <= 0 else float(np.clip(v, -L, L))
 
 
-def solve(w):
-    """All rows: rows[i][k] = (alpha[p], beta[q, p]) in the raw basis."""
+def control_value(w, rows, j, k, x, dw):
+    """zc_j(x).dw with zc_j(x) = T_Cz(beta_{j,k} . [1, (x - c_k)/(h/2)]), c_k the
+    centre of the nominal cell of stratum k (rows [N][K][q][p], centred)."""
+    cs = cells_of(w, k)
+    v = [1.0]
+    if rows.shape[-1] > 1:
+        for l in range(w.d):
+            h = (w.hi[l] - w.lo[l]) / w.cells[l]
+            c = w.lo[l] + (cs[l] + 0.5) * h
+            v.append((x[l] - c) / (h / 2))
+    v = np.array(v)
+    return sum(clamp(float(rows[j, k, l] @ v), w.Cz) * dw[l] for l in range(w.q))
+
+
+def solve(w, control=None):
+    """All rows: rows[i][k] = (alpha[p], beta[q, p]) in the raw basis.
+
+    control: None; an array of control rows [N][K][q][p] (centred basis),
+    whose step-i term zc_i(x_i).dW_i (stratum k) leaves the Y response and
+    whose later terms sum_{j>i} zc_j(X_j).dW_j (stratum of X_j) leave both
+    responses; or "own": the later terms with z_j the fitted z of the run
+    itself, no step-i term."""
     N, d, q, M = w.N, w.d, w.q, w.M
     dt = w.T / N
     p = 1 if w.basis == "lp0" else d + 1
@@ -130,7 +150,7 @@ def solve(w):
 
     for i in range(N - 1, -1, -1):
         for k in range(w.K):
-            X0, DW, S1, Y1 = [], [], [], []
+            X0, DW, S1, Y1, CZ, CI = [], [], [], [], [], []
             for m in range(M):
                 x = start(w, i, k, m)
                 X0.append(x.copy())
@@ -141,6 +161,20 @@ def solve(w):
                                    for l in range(q)])
                     incs.append(dw)
                     path.append(path[-1] + b * dt + sig @ dw)
+                cz = ci = 0.0
+                for j in range(i, N):
+                    xj, dw = path[j - i], incs[j - i]
+                    if isinstance(control, str) and control == "own":
+                        if j > i:
+                            cz += float(y_and_z(j, xj)[1] @ dw)
+                    elif control is not None:
+                        v = control_value(w, control, j, k if j == i else locate(w, xj), xj, dw)
+                        if j == i:
+                            ci = v
+                        else:
+                            cz += v
+                CZ.append(cz)
+                CI.append(ci)
                 S = g(w, path[-1])
                 for j in range(i + 1, N):
                     xj, xj1 = path[j - i], path[j - i + 1]
@@ -151,11 +185,12 @@ def solve(w):
                 DW.append(incs[0])
                 Y1.append(y_and_z(i + 1, path[1])[0])
             A = np.array([phi(x) for x in X0])
-            Bz = np.array([S1[m] * DW[m] / dt for m in range(M)])
+            Bz = np.array([(S1[m] - CZ[m]) * DW[m] / dt for m in range(M)])
             beta = np.linalg.lstsq(A, Bz, rcond=None)[0].T          # q x p
             zi = [np.array([clamp(float(beta[l] @ phi(X0[m])), w.Cz) for l in range(q)])
                   for m in range(M)]
-            By = np.array([S1[m] + f(w, i, X0[m], Y1[m], zi[m]) * dt for m in range(M)])
+            By = np.array([S1[m] + f(w, i, X0[m], Y1[m], zi[m]) * dt - CZ[m] - CI[m]
+                           for m in range(M)])
             alpha = np.linalg.lstsq(A, By, rcond=None)[0]
             rows[i][k] = (alpha, beta)
     return rows, y_and_z

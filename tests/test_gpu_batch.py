@@ -81,3 +81,34 @@ def test_batch_rejects_fp64(dev):
     with pytest.raises(srmc.SrmcError) as e:
         srmc.Batch([s])
     assert e.value.status == 4
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_batch_with_controls_equals_single_solves(dev, mode):
+    # instances with tabulated control rows, with the run's own control (the
+    # cos model without z in its driver then runs the z-evaluating variant)
+    # and without control, in one batch
+    torch, srmc = dev
+    ws = [W.cfg2(C=6, N=4, M=300), W.cfg2(C=5, N=5, M=200), W.cfg3(C=3, N=3, M=256),
+          W.logistic_paper(d=2, N=4, C=4, M=300), W.cfg2(C=4, N=3, M=128)]
+    how = ["rows", "own", "own", "own", "none"]
+
+    def make(w, h):
+        s = srmc.Solver(w, block_threads=256)
+        if h == "rows":
+            s.srmc_set_control(W.control_rows(w, W.closed_form_z(w)))
+        elif h == "own":
+            s.srmc_set_own_control()
+        return s
+    single = []
+    for w, h in zip(ws, how):
+        s = make(w, h)
+        s.srmc_solve()
+        single.append(_tables(torch, s))
+    solvers = [make(w, h) for w, h in zip(ws, how)]
+    b = srmc.Batch(solvers)
+    b.srmc_batch_set_mode(mode)
+    b.srmc_batch_solve()
+    for a, s in enumerate(solvers):
+        y, z = _tables(torch, s)
+        assert np.array_equal(y, single[a][0]) and np.array_equal(z, single[a][1]), (ws[a].name, how[a])

@@ -19,9 +19,18 @@ def dev():
     return torch, srmc
 
 
+def _rows(w, fn):
+    """Control rows for w; for the FP32 form rounded to binary16, the form in
+    which that solver keeps them, so that both sides use the same control."""
+    rows = W.control_rows(w, fn)
+    if w.precision == "fp32":
+        rows = rows.astype(np.float16).astype(np.float64)
+    return rows
+
+
 def _cv_parity(dev, orc, w, fn):
     torch, srmc = dev
-    rows = W.control_rows(w, fn)
+    rows = _rows(w, fn)
     s = srmc.Solver(w)
     s.srmc_set_control(rows)
     s.srmc_solve()
@@ -58,6 +67,27 @@ def test_cv_paper_logistic_d3(dev, orc, prec):
 def test_cv_d6(dev, orc):
     w = W.cos_model("d6", d=6, N=3, C=2, a=2.0, M=96, s0=0.3, lam=0.2, kap=0.5, precision="fp32")
     _cv_parity(dev, orc, w, W.closed_form_z(w))
+
+
+def test_fp32_form_rounds_rows_to_binary16(dev):
+    # The FP32 form stores the rows in binary16 (round to nearest even,
+    # saturating at +-65504): rows given in FP64 and the same rows rounded
+    # beforehand give bit-identical solves; read_control returns the rows
+    # as given.
+    torch, srmc = dev
+    w = W.cfg3(C=3, N=3, M=128)
+    rows = W.control_rows(w, W.random_smooth_z(w, seed=5))
+    rows[0, 0, 0, 0] = 1e6                         # saturates to 65504
+    r16 = np.clip(rows, -65504, 65504).astype(np.float16).astype(np.float64)
+    assert not np.array_equal(rows, r16)
+    out = []
+    for r in (rows, r16):
+        s = srmc.Solver(w)
+        s.srmc_set_control(r)
+        assert np.array_equal(s.srmc_read_control(), r)
+        s.srmc_solve()
+        out.append([t.cpu().numpy() for t in s.evaluate(0, s.centres())])
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
 
 
 def test_clear_control_restores_the_plain_scheme(dev):
@@ -113,3 +143,79 @@ def test_exact_control_cuts_the_spread_on_gpu(dev):
     assert np.mean(sc[inner]) < 0.4 * np.mean(sp[inner]), (np.mean(sc), np.mean(sp))
     dm = np.abs(np.mean(ys["plain"], axis=0) - np.mean(ys["cv"], axis=0))[inner]
     assert np.mean(dm) < 3 * np.mean(np.sqrt(sp ** 2 + sc ** 2)[inner]) / np.sqrt(8)
+
+
+# ---- the run's own control: z_j of the later steps ----------------------------
+
+def _own_parity(dev, orc, w):
+    torch, srmc = dev
+    s = srmc.Solver(w)
+    s.srmc_set_own_control()
+    s.srmc_solve()
+    o = orc.Oracle(w)
+    o.set_own_control()
+    o.solve_full(0)
+    x = s.centres()
+    xn = x.cpu().numpy()
+    for i in range(w.N):
+        gy, gz = s.evaluate(i, x)
+        ry, rz = o.eval(i, xn)
+        _check(w, gy.cpu().numpy(), gz.cpu().numpy(), ry, rz, where=f"step {i}")
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_own_control_cos_without_z_in_driver(dev, orc, prec):
+    _own_parity(dev, orc, W.cfg2(C=12, N=6, M=384, precision=prec))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_own_control_with_z_in_driver(dev, orc, prec):
+    _own_parity(dev, orc, W.cfg3(C=3, N=4, M=200, precision=prec))
+    _own_parity(dev, orc, W.logistic_paper(d=3, N=4, C=3, M=160, precision=prec))
+
+
+def test_own_control_state(dev):
+    torch, srmc = dev
+    w = W.cfg2(C=6, N=4, M=128)
+    plain = srmc.Solver(w)
+    plain.srmc_solve()
+    s = srmc.Solver(w)
+    s.srmc_set_control(W.control_rows(w, W.closed_form_z(w)))
+    s.srmc_set_own_control()                       # replaces the rows
+    with pytest.raises(srmc.SrmcError) as e:
+        s.srmc_read_control()
+    assert e.value.status == 5
+    s.srmc_solve()
+    y_own = s.evaluate(0, s.centres())[0]
+    assert not torch.equal(y_own, plain.evaluate(0, plain.centres())[0])
+    s.srmc_clear_control()
+    s.srmc_solve()
+    assert torch.equal(s.evaluate(0, s.centres())[0], plain.evaluate(0, plain.centres())[0])
+    lp0 = srmc.Solver(W.cfg2(C=4, N=3, M=64, basis="lp0"))
+    with pytest.raises(srmc.SrmcError) as e:
+        lp0.srmc_set_own_control()
+    assert e.value.status == 4
+
+
+def test_own_control_cuts_the_spread_on_gpu(dev):
+    # d = 1 (the case pinned on the oracle): the fitted z are accurate enough
+    # there for the own control to remove much of the later steps' noise
+    torch, srmc = dev
+    w0 = W.cos_model("v", d=1, N=10, C=8, a=2.0, M=2000, s0=0.5, lam=0.5, kap=0.5, kapz=0.0)
+    ys = {"plain": [], "own": []}
+    for seed in range(8):
+        w = w0.replace(seed=seed + 40)
+        for name in ("plain", "own"):
+            s = srmc.Solver(w)
+            if name == "own":
+                s.srmc_set_own_control()
+            s.srmc_solve()
+            y, _ = s.evaluate(0, s.centres())
+            ys[name].append(y.cpu().numpy())
+    sp = np.std(np.array(ys["plain"]), axis=0, ddof=1)
+    so = np.std(np.array(ys["own"]), axis=0, ddof=1)
+    cells = np.stack(np.unravel_index(np.arange(w0.K), w0.cells[::-1]), 1)[:, ::-1]
+    inner = np.all((cells > 0) & (cells < np.array(w0.cells) - 1), axis=1)
+    assert np.mean(so[inner]) < 0.6 * np.mean(sp[inner]), (np.mean(so[inner]), np.mean(sp[inner]))
+    dm = np.abs(np.mean(ys["plain"], axis=0) - np.mean(ys["own"], axis=0))[inner]
+    assert np.mean(dm) < 3 * np.mean(np.sqrt(sp ** 2 + so ** 2)[inner]) / np.sqrt(8)

@@ -101,6 +101,19 @@ def test_other_dimensions(dev, orc, d, C, N, M, prec):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_uneven_cells_in_morton_order(dev, orc, prec):
+    # d = 3 and 4 with different cell counts per dimension (3, 7, 5 and
+    # 2, 9, 3, 4 cells on boxes of different widths): the step launches solve
+    # the strata in Morton order of cells with 2, 3, 3 and 1, 4, 2, 2 bits,
+    # so every stratum must still be solved once and land in its own row.
+    for cells, a in (([3, 7, 5], [2.0, 3.0, 2.5]), ([2, 9, 3, 4], [1.5, 3.0, 2.0, 2.0])):
+        w = W.cos_model("uneven", d=len(cells), N=3, C=2, a=2.0, M=64, s0=0.3, lam=0.2, kap=0.5,
+                        kapz=0.1, precision=prec)
+        w = w.replace(cells=cells, lo=[-v for v in a], hi=list(a), name=f"uneven_{len(cells)}")
+        _full_parity(dev, orc, w)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_paper_logistic_model(dev, orc, prec):
     # The test BSDE of Sec. 5.1 (driver uses sum z), d=3, strata on [-6.5,6.5]^3
     _full_parity(dev, orc, W.logistic_paper(d=3, N=4, C=3, M=200, precision=prec))
@@ -283,3 +296,4 @@ def test_closed_form_error_kernel(dev, model):
     u0 = (math.exp(w.params[0]) * np.cos(xn.sum(1) / math.sqrt(w.d)) if model == "cos"
           else np.exp(xn.sum(1)) / (1 + np.exp(xn.sum(1))))
     assert np.max(np.abs(y0.cpu().numpy() - u0)[inner]) < 0.1
+

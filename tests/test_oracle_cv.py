@@ -8,7 +8,8 @@ import numpy as np
 import pytest
 
 from paper_2407_21085_gb300 import workloads as W
-from tests.test_oracle_scheme import POP_CASES, _population, _population_case, POP_XS
+from tests import brute_force as bf
+from tests.test_oracle_scheme import BF_CASES, POP_CASES, POP_XS, _bf_workload, _population, _population_case
 
 
 def _params(nin, H, seed=0, scale=0.6):
@@ -156,3 +157,125 @@ def test_population_pin_catches_control_mistakes(orc, tmp_path, name):
     lib = orc.compile_variant(src.replace(old, new), str(tmp_path / f"cmut_{name}.so"))
     worst, _ = _pop_disc_with_control(orc, POP_CASES[0], W.closed_form_z, library=lib, R=4)
     assert worst > 1.5, (name, worst)
+
+
+# ---- both controls against the straight-line restatement ----------------------
+
+def _control_mismatch(orc, n, mode):
+    w = _bf_workload(BF_CASES[n])
+    if mode == "own":
+        control = "own"
+    else:
+        control = W.control_rows(w, W.random_smooth_z(w, seed=n + 1, scale=0.8))
+    y_and_z = bf.solve(w, control)[1]
+    o = orc.Oracle(w)
+    if mode == "own":
+        o.set_own_control()
+    else:
+        o.set_control(control)
+    o.solve_full(1)
+    x = np.random.default_rng(3).uniform(-2, 2, size=(30, w.d))
+    worst = 0.0
+    for i in range(w.N):
+        y, z = o.eval(i, x)
+        for a in range(len(x)):
+            yb, zb = y_and_z(i, x[a])
+            worst = max(worst, abs(y[a] - yb), float(np.max(np.abs(z[a] - zb))))
+    return worst
+
+
+@pytest.mark.parametrize("n", range(len(BF_CASES)))
+@pytest.mark.parametrize("mode", ["rows", "own"])
+def test_control_brute_force_tiny(orc, n, mode):
+    # Tabulated rows (step-i term in the Y response, later terms in both) and
+    # the run's own z (later terms only) on the same Philox draws as a
+    # separately written restatement; with N = 2 or 3 every term is exercised.
+    assert _control_mismatch(orc, n, mode) < 1e-10
+
+
+def test_own_control_changes_the_fits(orc):
+    # guard: the own control is not a no-op (N = 3: steps 0 and 1 see it)
+    w = _bf_workload(BF_CASES[0])
+    o1, o2 = orc.Oracle(w), orc.Oracle(w)
+    o2.set_own_control()
+    o1.solve_full(1); o2.solve_full(1)
+    x = np.linspace(-1, 1, 7)[:, None]
+    assert np.array_equal(o1.eval(w.N - 1, x)[0], o2.eval(w.N - 1, x)[0])   # no later step
+    assert np.max(np.abs(o1.eval(0, x)[0] - o2.eval(0, x)[0])) > 1e-6
+
+
+def test_own_control_leaves_the_population_limit_unchanged(orc):
+    # The fitted z_j of later steps come from clouds independent of C_{i,k}, so
+    # the control has zero conditional mean: the average over seeds still
+    # converges to the M -> infinity limit of the plain scheme.
+    w = _population_case(*POP_CASES[0])
+    pop = _population(POP_CASES[0])
+    R = 6
+    ys, zs = [], []
+    for r in range(R):
+        o = orc.Oracle(w.replace(seed=200 + r))
+        o.set_own_control()
+        o.solve_full(0)
+        ys.append([o.eval(i, POP_XS)[0] for i in range(w.N)])
+        zs.append([o.eval(i, POP_XS)[1][:, 0] for i in range(w.N)])
+    ys, zs = np.array(ys), np.array(zs)
+    worst = 0.0
+    for i in range(w.N):
+        yp, zp = pop(i, POP_XS[:, 0])
+        for arr, ref in ((ys[:, i], yp), (zs[:, i], zp)):
+            se = arr.std(0, ddof=1) / math.sqrt(R)
+            worst = max(worst, float(np.max(np.abs(arr.mean(0) - ref) / (5 * se + 2e-4))))
+    assert worst <= 1.0
+
+
+def test_own_control_reduces_the_spread(orc):
+    # The run's fitted z approximates s0 du/dx, so subtracting its martingale
+    # removes most of the response noise of the later steps: the seed-to-seed
+    # spread of y_0 drops (less than with the exact z), the mean stays.
+    w = W.cos_model("v", d=1, N=10, C=8, a=2.0, M=2000, s0=0.5, lam=0.5, kap=0.5, kapz=0.0)
+    xs = W.centres(w)[2:6]
+    out = {}
+    for name in ("plain", "own"):
+        ys = []
+        for r in range(6):
+            o = orc.Oracle(w.replace(seed=300 + r))
+            if name == "own":
+                o.set_own_control()
+            o.solve_full(0)
+            ys.append(o.eval(0, xs)[0])
+        out[name] = np.array(ys)
+    sp, so = out["plain"].std(0, ddof=1), out["own"].std(0, ddof=1)
+    assert so.mean() < 0.6 * sp.mean(), (so.mean(), sp.mean())
+    diff = np.abs(out["plain"].mean(0) - out["own"].mean(0))
+    assert np.all(diff < 5 * np.sqrt(sp ** 2 + so ** 2) / math.sqrt(6) + 1e-4)
+
+
+OWN_MUTANTS = {
+    # sign of the own control (still zero-mean: only the restatement sees it)
+    "own_sign": ("for (int l = 0; l < q; ++l) CZ[m] += zj[l] * dw[l];",
+                 "for (int l = 0; l < q; ++l) CZ[m] -= zj[l] * dw[l];"),
+    # the control must leave the Z response too
+    "z_response_without_control": ("for (int l = 0; l < q; ++l) B[m * q + l] = (S1[m] - CZ[m]) * DW[m * q + l] / dt;",
+                                   "for (int l = 0; l < q; ++l) B[m * q + l] = S1[m] * DW[m * q + l] / dt;"),
+}
+
+
+@pytest.mark.parametrize("name", sorted(OWN_MUTANTS))
+def test_brute_force_catches_own_control_mistakes(orc, tmp_path, name):
+    old, new = OWN_MUTANTS[name]
+    src = orc.source_text()
+    assert src.count(old) == 1
+    lib = orc.compile_variant(src.replace(old, new), str(tmp_path / f"own_{name}.so"))
+    w = _bf_workload(BF_CASES[0])
+    y_and_z = bf.solve(w, "own")[1]
+    o = orc.Oracle(w, library=lib)
+    o.set_own_control()
+    o.solve_full(1)
+    x = np.random.default_rng(3).uniform(-2, 2, size=(30, w.d))
+    worst = 0.0
+    for i in range(w.N):
+        y, z = o.eval(i, x)
+        for a in range(len(x)):
+            yb, zb = y_and_z(i, x[a])
+            worst = max(worst, abs(y[a] - yb), float(np.max(np.abs(z[a] - zb))))
+    assert worst > 1e-6, (name, worst)
