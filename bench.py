@@ -47,18 +47,18 @@ def fp32_peak_tflops(sms: int, mhz: float) -> float:
     return sms * 128 * 2 * mhz * 1e6 / 1e12
 
 
+STEP_KERNEL_SOURCES = ("srmc_step.cu", "srmc_device.cuh", "srmc_internal.h")
+
+
 def kernel_source_hash() -> str:
-    """sha256 of the CUDA sources and headers of the library (a traffic record
+    """sha256 of the sources the step kernel is compiled from (a traffic record
     taken from an ncu capture is used only while this hash matches)."""
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2407_21085_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh", ".h")):
-            with open(os.path.join(csrc, name), "rb") as fh:
-                h.update(name.encode() + b"\0" + fh.read())
-    with open(os.path.join(ROOT, "include", "srmc.h"), "rb") as fh:
-        h.update(fh.read())
+    for name in STEP_KERNEL_SOURCES:
+        with open(os.path.join(csrc, name), "rb") as fh:
+            h.update(name.encode() + b"\0" + fh.read())
     return h.hexdigest()
 
 
@@ -408,6 +408,74 @@ def cv_compare(args, stream):
     return out
 
 
+# ---- the paper's own experiment (Sec. 5.1): error indicators over many runs ----------
+def paper_table_rows(table: str):
+    """Rows (N, cells per dimension, M, runs) of the d = 4 tables of Sec. 5.2:
+    LP1 with #C = floor(3 sqrt(d sqrt(N)) - 5), M = (d+1) N^2; LP0 with
+    #C = floor(4 sqrt(N)), M = N^2.  The run counts are ours (10^3 in the
+    paper), fewer where one run takes seconds."""
+    d = 4
+    if table == "lp1_d4":
+        rows = [(5, 1000), (10, 1000), (20, 1000), (50, 10)]
+        return d, "lp1", [(N, int(math.floor(3 * math.sqrt(d * math.sqrt(N)) - 5)), (d + 1) * N * N, R)
+                          for N, R in rows]
+    if table == "lp0_d4":
+        rows = [(5, 1000), (10, 1000), (20, 200)]
+        return d, "lp0", [(N, int(math.floor(4 * math.sqrt(N))), N * N, R) for N, R in rows]
+    raise ValueError(table)
+
+
+def paper_table(args, stream):
+    """The error indicators of Sec. 5.1 (eq. mse) for the paper's test BSDE
+    (X = W, logistic model, mu = 1, T = 1, strata on [-6.5, 6.5]^4, FP32 paths):
+    R independent runs (Philox seeds 1..R), each evaluated against the closed
+    form at n points per step drawn i.i.d. from nu independently of the
+    clouds; MSE_Y,max = ln(max_i S_i^y / (R n)), MSE_Y,av = ln(sum_i S_i^y /
+    (R n N)), MSE_Z,av likewise with |z_i - z*|^2, S_i the sums over runs and
+    points.  (The paper pairs run m with one point R_{i,m}; n points per run
+    estimate the same expectation with less noise.)  GPU time per run = CUDA
+    events around srmc_solve on the stream."""
+    import torch
+    from paper_2407_21085_gb300 import srmc
+
+    d, basis, rows = paper_table_rows(args.paper_table)
+    n = args.paper_points
+    out = []
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(12345)
+    for N, C, M, R in rows:
+        w0 = W.logistic_paper(d=d, N=N, C=C, M=M, basis=basis)
+        sums = torch.zeros((N, 2), dtype=torch.float64, device="cuda")
+        part = torch.empty((N, 2), dtype=torch.float64, device="cuda")
+        ms = []
+        t0 = time.perf_counter()
+        for r in range(R):
+            s = srmc.Solver(w0.replace(seed=r + 1))
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            s.srmc_solve(stream)
+            b.record(stream)
+            U = torch.rand((N, n, d), dtype=torch.float64, device="cuda", generator=gen)
+            U = U.clamp_(1e-300, 1.0 - 2.0 ** -53)
+            X = torch.log(U) - torch.log1p(-U)              # logistic, mu = 1
+            s.srmc_point_error(X, part, stream)
+            sums += part
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+            s.close()
+        wall = time.perf_counter() - t0
+        S = sums.cpu().numpy()
+        out.append({"dt": 1.0 / N, "N": N, "cells_per_dim": C, "K": C ** d, "M": M, "runs": R,
+                    "points_per_step_per_run": n,
+                    "MSE_Y_max": float(math.log(S[:, 0].max() / (R * n))),
+                    "MSE_Y_av": float(math.log(S[:, 0].sum() / (R * n * N))),
+                    "MSE_Z_av": float(math.log(S[:, 1].sum() / (R * n * N))),
+                    "gpu_ms_per_run": statistics.median(ms), "wall_s_all_runs": wall,
+                    "path_steps_per_run": w0.path_steps()})
+    return {"paper_table": args.paper_table, "model": "logistic (Sec. 5.1)", "precision": "fp32",
+            "basis": basis, "d": d, "rows": out}
+
+
 # ---- the batched form: 256 heterogeneous instances ---------------------------------
 def batched_compare(args, stream):
     """cfg4: 256 seeded instances (d in {1,2,3}, 16..64 cells per dimension,
@@ -524,6 +592,9 @@ def main():
                     help="time the control-variate step kernel (rows from an untrained network)")
     ap.add_argument("--control-own", action="store_true",
                     help="time the step kernel with the run's own z control")
+    ap.add_argument("--paper-table", choices=["lp1_d4", "lp0_d4"], default=None,
+                    help="instead of the benchmark: the error indicators of Sec. 5.1 over many runs")
+    ap.add_argument("--paper-points", type=int, default=1000, help="nu points per step per run")
     ap.add_argument("--cv-M", type=int, default=1024)
     ap.add_argument("--cv-coarse-M", type=int, default=256)
     ap.add_argument("--cv-data", type=int, default=1 << 20)
@@ -534,6 +605,12 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+
+    if args.paper_table:
+        import torch
+        torch.cuda.set_device(0)
+        print(json.dumps(paper_table(args, torch.cuda.current_stream())), flush=True)
+        return
 
     if args.impl == "reference":
         out = run_reference(args)

@@ -312,6 +312,18 @@ srmc_status srmc_closed_form_error(const srmc_solver *s, double *dev_out, void *
  * bulk; K_inner = prod_l (cells[l] - 2) must be > 0. */
 srmc_status srmc_closed_form_error_inner(const srmc_solver *s, double *dev_out, void *stream);
 
+/* Squared errors against the closed form at caller-given points, the
+ * ingredients of the error indicators of Sec. 5.1 (eq. mse): dev_x
+ * [N][n][d] doubles (device), n points per step i = 0..N-1 (in Sec. 5.1
+ * drawn i.i.d. from nu, independently of the clouds); dev_out [N][2]
+ * doubles (device): sum_a (y_i(x) - u(t_i, x))^2 and sum_a |z_i(x) - z*(t_i, x)|^2
+ * over the n points of step i, with y_i, z_i the truncated fitted functions
+ * of the stratum holding x and the closed forms of srmc_closed_form_error.
+ * dev_out is overwritten (cleared on stream first).  Summation order across
+ * blocks is not fixed (double atomics).  SRMC_ERR_UNSUPPORTED for the affine
+ * model; requires a finished solve.  Asynchronous on stream. */
+srmc_status srmc_point_error(const srmc_solver *s, const double *dev_x, long long n, double *dev_out,
+                             void *stream);
 
 /* Counters since creation: [0] strata fits that fell back from LP1 to LP0
  * because the Gram matrix was numerically singular (Cholesky pivot below

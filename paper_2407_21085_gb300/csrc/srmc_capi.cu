@@ -505,9 +505,64 @@ __device__ void closed_form(const Params &P, int i, const double *x, double &u, 
         u = e * cos(s);
         for (int l = 0; l < P.q; ++l) zs[l] = -P.prm[3] * e * sin(s) / P.sqrt_d;
     } else {
-        const double w = exp(t + sx);
-        u = w / (1.0 + w);
-        for (int l = 0; l < P.q; ++l) zs[l] = w / ((1.0 + w) * (1.0 + w));
+        // w = exp(a), a = t + sum x: u = w/(1+w), z_l = w/(1+w)^2, written with
+        // e = exp(-|a|) <= 1 so that no intermediate overflows
+        const double a = t + sx;
+        const double e = exp(-fabs(a));
+        u = a >= 0.0 ? 1.0 / (1.0 + e) : e / (1.0 + e);
+        for (int l = 0; l < P.q; ++l) zs[l] = e / ((1.0 + e) * (1.0 + e));
+    }
+}
+
+// Squared errors of y_i, z_i against the closed form at the points
+// x[i][a][d], a < n, summed per step into out[2 i] (y) and out[2 i + 1]
+// (|z|^2 over the q components); grid (blocks per step, steps), out cleared.
+__global__ void point_error_kernel(const Params P, const double *x, long long n, double *out)
+{
+    __shared__ double red[2][32];
+    for (int i = blockIdx.y; i < P.N; i += gridDim.y) {
+        double ysq = 0.0, zsq = 0.0;
+        for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < n;
+             a += (long long)gridDim.x * blockDim.x) {
+            const double *xa = x + ((long long)i * n + a) * P.d;
+            double phi[srmc::DMAX + 1], zs[srmc::DMAX], u;
+            phi[0] = 1.0;
+            long long k = 0;
+            for (int l = 0; l < P.d; ++l) {
+                double t;
+                const int c = srmc::locate_dim(xa[l], P.lo[l], P.h[l], P.cells[l], t);
+                k += (long long)c * P.stride[l];
+                phi[1 + l] = 2.0 * (t - (double)c) - 1.0;
+            }
+            closed_form(P, i, xa, u, zs);
+            const long long row = (long long)i * P.K + k;
+            const double *al = P.Y64 + row * P.ry64;
+            double v = al[0];
+            for (int c = 1; c < P.p; ++c) v += al[c] * phi[c];
+            const double dy = fmin(fmax(v, -P.Cy), P.Cy) - u;
+            ysq += dy * dy;
+            const double *be = P.Z64 + row * P.rz64;
+            for (int l = 0; l < P.q; ++l) {
+                double w = be[l * P.p];
+                for (int c = 1; c < P.p; ++c) w += be[l * P.p + c] * phi[c];
+                const double dz = fmin(fmax(w, -P.Cz), P.Cz) - zs[l];
+                zsq += dz * dz;
+            }
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+            ysq += __shfl_xor_sync(0xffffffffu, ysq, o);
+            zsq += __shfl_xor_sync(0xffffffffu, zsq, o);
+        }
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+        if (lane == 0) { red[0][warp] = ysq; red[1][warp] = zsq; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double a = 0.0, b = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { a += red[0][w]; b += red[1][w]; }
+            atomicAdd(out + 2 * i, a);
+            atomicAdd(out + 2 * i + 1, b);
+        }
+        __syncthreads();                               // red is reused for the next step
     }
 }
 
@@ -584,6 +639,25 @@ srmc_status srmc_closed_form_error(const srmc_solver *s, double *out, void *stre
     if (s->done_from > 0) return fail(SRMC_ERR_STATE, "srmc_closed_form_error: solve not finished");
     closed_form_error_kernel<<<s->P.N, 256, 0, (cudaStream_t)stream>>>(s->P, false, out);
     SRMC_CUDA(cudaGetLastError(), "closed form error kernel launch");
+    return SRMC_OK;
+}
+
+srmc_status srmc_point_error(const srmc_solver *s, const double *x, long long n, double *out, void *stream)
+{
+    if (!s || !out) return fail(SRMC_ERR_INVALID_ARG, "srmc_point_error: NULL argument");
+    if (n < 0) return fail(SRMC_ERR_INVALID_ARG, "srmc_point_error: n < 0");
+    if (n > 0 && !x) return fail(SRMC_ERR_INVALID_ARG, "srmc_point_error: NULL points");
+    if (s->P.model == srmc::MODEL_AFFINE)
+        return fail(SRMC_ERR_UNSUPPORTED, "srmc_point_error: no closed form for the affine model");
+    if (s->done_from > 0) return fail(SRMC_ERR_STATE, "srmc_point_error: solve not finished");
+    SRMC_CUDA(cudaMemsetAsync(out, 0, sizeof(double) * 2 * (size_t)s->P.N, (cudaStream_t)stream),
+              "srmc_point_error: clear");
+    if (n == 0) return SRMC_OK;
+    long long bx = (n + 255) / 256;
+    if (bx > 64) bx = 64;
+    const unsigned by = (unsigned)(s->P.N < 65535 ? s->P.N : 65535);
+    point_error_kernel<<<dim3((unsigned)bx, by), 256, 0, (cudaStream_t)stream>>>(s->P, x, n, out);
+    SRMC_CUDA(cudaGetLastError(), "point error kernel launch");
     return SRMC_OK;
 }
 

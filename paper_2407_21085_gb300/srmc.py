@@ -76,6 +76,8 @@ def lib():
             L.srmc_closed_form_error.argtypes = [vp, vp, vp]
             L.srmc_closed_form_error_inner.argtypes = [vp, vp, vp]
             L.srmc_closed_form_error_inner.restype = C.c_int
+            L.srmc_point_error.argtypes = [vp, vp, ll, vp, vp]
+            L.srmc_point_error.restype = C.c_int
             L.srmc_set_control.argtypes = [vp, vp]
             L.srmc_clear_control.argtypes = [vp]
             L.srmc_set_own_control.argtypes = [vp]
@@ -233,6 +235,11 @@ class Solver:
         out = np.zeros((self.w.N, self.K, self.w.q, p))
         _check(lib().srmc_read_control(self._h, C.c_void_p(out.ctypes.data)))
         return out
+
+    def srmc_point_error(self, x, out, stream=None):
+        """x: CUDA float64 [N][n][d]; out: CUDA float64 [N][2] (sums of squared
+        y and z errors against the closed form per step)."""
+        _check(lib().srmc_point_error(self._h, _ptr(x), int(x.shape[1]), _ptr(out), _stream(stream)))
 
     def srmc_closed_form_error(self, out, stream=None):
         _check(lib().srmc_closed_form_error(self._h, _ptr(out), _stream(stream)))

@@ -297,3 +297,45 @@ def test_closed_form_error_kernel(dev, model):
           else np.exp(xn.sum(1)) / (1 + np.exp(xn.sum(1))))
     assert np.max(np.abs(y0.cpu().numpy() - u0)[inner]) < 0.1
 
+
+@pytest.mark.parametrize("model", ["cos", "logistic"])
+def test_point_error_kernel(dev, model):
+    # Sums of squared errors against the closed form at given points per step
+    # (the ingredients of the indicators of Sec. 5.1, eq. mse) equal the same
+    # sums on the host from srmc_eval and the closed forms; the points are
+    # drawn from nu (logistic, mu = 1) like the paper's R_{i,m}, plus exact
+    # cell edges and far-out points of the semi-infinite cells.
+    torch, srmc = dev
+    if model == "cos":
+        w = W.cfg2(C=16, N=6, M=512, kapz=0.1)
+    else:
+        w = W.logistic_paper(d=2, N=5, C=8, M=400)
+    s = srmc.Solver(w)
+    s.srmc_solve()
+    rng = np.random.default_rng(5)
+    n = 1000
+    U = rng.uniform(size=(w.N, n, w.d))
+    X = np.log(U / (1 - U))
+    X[:, :3] = np.array(w.lo) + (np.array(w.hi) - np.array(w.lo)) / np.array(w.cells)   # an exact edge
+    X[:, 3:6] = 1e3
+    xt = torch.from_numpy(X).cuda()
+    out = torch.empty((w.N, 2), dtype=torch.float64, device="cuda")
+    s.srmc_point_error(xt, out)
+    got = out.cpu().numpy()
+    for i in range(w.N):
+        y, z = s.evaluate(i, xt[i].contiguous())
+        y, z = y.cpu().numpy(), z.cpu().numpy()
+        t, xi = i * w.dt, X[i]
+        if model == "cos":
+            lam, s0 = w.params[0], w.params[3]
+            sv = xi.sum(1) / math.sqrt(w.d)
+            u = math.exp(lam * (1 - t)) * np.cos(sv)
+            zs = np.repeat((-s0 * math.exp(lam * (1 - t)) * np.sin(sv) / math.sqrt(w.d))[:, None], w.d, 1)
+        else:
+            om = np.exp(np.minimum(t + xi.sum(1), 700.0))
+            u = om / (1 + om)
+            zs = np.repeat((om / (1 + om) ** 2)[:, None], w.d, 1)
+        want = [np.sum((y - u) ** 2), np.sum((z - zs) ** 2)]
+        assert np.allclose(got[i], want, rtol=1e-9, atol=1e-12), (i, got[i], want)
+    with pytest.raises(srmc.SrmcError):
+        srmc.Solver(W.affine(d=1, N=2, C=2, M=8, g0=0, gv=[1], f0=0, fv=[0], a=0)).srmc_point_error(xt, out)
