@@ -37,9 +37,10 @@ L2_FLUSH_BYTES = 512 << 20
 
 
 def flops_per_path_step(d: int) -> float:
-    """Algorithmic FP32 FLOPs of one stratum-path-step (Euler, locate, centre,
-    y and z evaluation, clamps, driver, response update): 2 d^2 + 13 d + 20."""
-    return 2.0 * d * d + 13.0 * d + 20.0
+    """Algorithmic FP32 FLOPs of one stratum-path-step: Euler, locate, centre,
+    y and z evaluation, clamps, driver and response update (2 d^2 + 13 d + 20)
+    plus the q = d normals by inversion (a degree-9 polynomial: 18 each)."""
+    return 2.0 * d * d + 13.0 * d + 20.0 + 18.0 * d
 
 
 def fp32_peak_tflops(sms: int, mhz: float) -> float:
@@ -126,6 +127,20 @@ def max_over_ranks(value: float, backend_device=None) -> float:
     return float(t.item())
 
 
+def rank_workload(name: str, rank: int) -> W.Workload:
+    """The replica solved by rank r: the named workload with its own Philox
+    instance (instance + 1000 r), so that ranks draw independent clouds."""
+    w = workload(name)
+    return w.replace(instance=w.instance + 1000 * rank)
+
+
+def whole_job_rate(units_per_rank: int, world: int, steps: int, local_ms: float, device=None):
+    """Units of all ranks / the slowest rank's elapsed time (weak scaling:
+    every rank solves its own instance of the same size); returns (rate, max ms)."""
+    max_ms = max_over_ranks(local_ms, device)
+    return units_per_rank * world * steps / (max_ms / 1e3), max_ms
+
+
 def barrier():
     import torch.distributed as dist
     if dist.is_available() and dist.is_initialized():
@@ -192,7 +207,7 @@ def run_gpu(args):
     props = torch.cuda.get_device_properties(dev)
     sms = props.multi_processor_count
 
-    w = workload(args.workload).replace(instance=workload(args.workload).instance + 1000 * rank)
+    w = rank_workload(args.workload, rank)
     units = w.path_steps()
     stream = torch.cuda.current_stream()
     solver = srmc.Solver(w, block_threads=args.block_threads)
@@ -233,8 +248,7 @@ def run_gpu(args):
     barrier()
     clocks = sampler.stop()
     total_ms = sum(step_ms)
-    total_ms_max = max_over_ranks(total_ms, dev)
-    value = units * ws * args.steps / (total_ms_max / 1e3)
+    value, total_ms_max = whole_job_rate(units, ws, args.steps, total_ms, dev)
 
     # End to end through the public API with host buffers: create (host
     # parameters -> device), solve, copy the FP64 coefficient tables to pinned
@@ -256,8 +270,7 @@ def run_gpu(args):
         s2.close()
         if r > 0:
             e2e_ms.append((time.perf_counter() - t0) * 1e3)
-    e2e_max = max_over_ranks(sum(e2e_ms), dev)
-    e2e_value = units * ws * len(e2e_ms) / (e2e_max / 1e3) if e2e_ms else None
+    e2e_value = whole_job_rate(units, ws, len(e2e_ms), sum(e2e_ms), dev)[0] if e2e_ms else None
     tab_bytes = (ny + nz) * 8
 
     # Roofline of the dominant kernel (the step kernel: every launch is one).
