@@ -82,25 +82,41 @@ typedef struct {
     int n_params;
 } srmc_problem;
 
-/* Strata (assumption A_Strat): the box [lo_l, hi_l) cut into cells[l] equal
- * cells per dimension, the first and last cell of every dimension extended
- * to -inf / +inf.  Stratum index k = sum_l c_l prod_{l'<l} cells[l']
- * (dimension 0 fastest); a point x is in cell c_l = clamp(floor((x_l - lo_l) /
- * h_l), 0, cells[l]-1), h_l = (hi_l - lo_l)/cells[l], in FP64 (single-precision
- * paths take the same decision as floor((x_l - lo_l) * r_l), r_l = cells[l] /
- * (hi_l - lo_l) rounded to float).  mu: scale of the logistic law nu (eq.
- * logistic).  All arrays host, [d]. */
+/* Strata (assumption HS): cells[l] half-open cells per dimension, stratum
+ * index k = sum_l c_l prod_{l'<l} cells[l'] (dimension 0 fastest).
+ *   kind SRMC_STRATA_EQUAL_SIZE (HS, example i): the box [lo_l, hi_l) cut
+ *     into equal cells, the first and last cell of every dimension extended
+ *     to -inf / +inf; x is in cell c_l = clamp(floor((x_l - lo_l) / h_l), 0,
+ *     cells[l]-1), h_l = (hi_l - lo_l)/cells[l], in FP64 (single-precision
+ *     paths take the same decision as floor((x_l - lo_l) * r_l), r_l =
+ *     cells[l] / (hi_l - lo_l) rounded to float).  Basis centre: the centre of
+ *     the nominal cell; basis unit h_l / 2.
+ *   kind SRMC_STRATA_EQUAL_PROB (HS, example ii): nu(H_k) = 1/K; the axis is
+ *     cut at the logistic quantiles e_c = log(c / (C - c)) / mu, c = 1..C-1
+ *     (C = cells[l]), x is in the cell c with e_c <= x < e_{c+1} (the edges
+ *     held in double, or rounded to float for single-precision paths).  Basis
+ *     centre: the median of nu restricted to the cell, F^{-1}((c + 1/2)/C);
+ *     basis unit: F^{-1}((c + 3/4)/C) - F^{-1}((c + 1/4)/C).  lo, hi unused
+ *     (may be NULL).
+ * The centred LP1 basis of a stratum is phi = [1, (x_l - centre_l) / unit_l].
+ * mu: scale of the logistic law nu (eq. logistic).  Arrays host, [d]. */
+typedef enum { SRMC_STRATA_EQUAL_SIZE = 0, SRMC_STRATA_EQUAL_PROB = 1 } srmc_strata_kind;
 typedef struct {
     const int *cells;
     const double *lo, *hi;
     double mu;
+    int kind;                  /* srmc_strata_kind */
 } srmc_strata;
 
 /* Scheme configuration.  M: paths per stratum and step, M >= dim of the basis
- * (Def. of the clouds).  Cy, Cz: truncation levels of y and of each component
- * of z (eq. TL, Prop. a.s. bounds); a value <= 0 disables that truncation.
- * block_threads: threads per stratum block, a multiple of 32 in [32, 256],
- * or 0 for the library's choice. */
+ * (Def. of the clouds).  M_strata: NULL, or a host array [K] of per-stratum
+ * path counts M_k (each >= dim of the basis and < 2^32; copied) that
+ * replaces M -- the paper fixes M for all strata to balance the work and
+ * notes that the analysis adapts to M_k (Sec. 3, after Alg. SRMDP).  Cy, Cz:
+ * truncation levels of y and of each component of z (eq. TL, Prop. a.s.
+ * bounds); a value <= 0 disables that truncation.  block_threads: threads per
+ * stratum block, a multiple of 32 in [32, 256], or 0 for the library's
+ * choice. */
 typedef struct {
     srmc_basis basis;
     srmc_precision prec;
@@ -109,6 +125,7 @@ typedef struct {
     unsigned instance;
     double Cy, Cz;
     int block_threads;
+    const long long *M_strata;
 } srmc_config;
 
 typedef struct srmc_solver srmc_solver;   /* opaque, library-owned */
@@ -141,13 +158,16 @@ srmc_status srmc_solve_step(srmc_solver *s, int i, void *stream);
 srmc_status srmc_eval(const srmc_solver *s, int i, const double *dev_x, long long n,
                       double *dev_y, double *dev_z, void *stream);
 
-/* The K stratum centres (centre of the nominal finite cell in every
- * dimension), written to dev_x: [K][d] double. */
+/* The K stratum basis centres (the centre of the nominal finite cell, or
+ * the median of nu restricted to the cell, in every dimension), written to
+ * dev_x: [K][d] double. */
 srmc_status srmc_centres(const srmc_solver *s, double *dev_x, void *stream);
 
 /* Layout of the FP64 coefficient table: row (i,k) holds alpha[p] then
- * beta[q][p] in the centred basis phi(x) = [1, (x - c_k)/(h/2)], p = 1 (LP0)
- * or d+1 (LP1), c_k the nominal centre; y_i(x) = T_Cy(alpha . phi(x)).
+ * beta[q][p] in the centred basis phi(x) = [1, (x - c_k)/s_k], p = 1 (LP0)
+ * or d+1 (LP1), c_k and s_k the basis centre and unit of the stratum (see
+ * srmc_strata: h/2 and the nominal cell centre for equal-size cells);
+ * y_i(x) = T_Cy(alpha . phi(x)).
  * *dev_y64 / *dev_z64 are borrowed pointers to [N][K][ry] and [N][K][rz]
  * doubles, valid until srmc_destroy. */
 srmc_status srmc_table(const srmc_solver *s, const double **dev_y64, const double **dev_z64,
@@ -167,7 +187,7 @@ srmc_status srmc_read_table(const srmc_solver *s, double *dst_y, double *dst_z, 
  * x_i (dW_j is independent of everything known at t_j), so the fitted
  * functions keep their expectation while the response variance drops when
  * zc approximates the true z = sigma^T grad u.  rows: [N][K][q][p] doubles,
- * host or device memory, centred basis phi = [1, (x - c_k)/(h/2)]; copied
+ * host or device memory, centred basis phi = [1, (x - c_k)/s_k]; copied
  * (synchronously).  LP1 solvers only (SRMC_ERR_UNSUPPORTED otherwise).
  * The FP64 form uses the rows as given.  The FP32 form keeps them in
  * binary16 (round to nearest even, magnitudes above 65504 saturated, below
@@ -257,9 +277,10 @@ srmc_status srmc_mlp_fit_noalloc(srmc_mlp *m, const srmc_solver *coarse, long lo
                                  float *dev_loss_curve, void *stream);
 
 /* Tabulate zc = sigma^T grad_x u_theta(t_j, .) as the control rows of s for
- * every (j, k): value at the stratum centre and central differences at
- * +-h/4 along each axis (LP1 rows in the centred basis), then install them as
- * by srmc_set_control.  LP1 solvers with d <= 7, n_in == d + 1. */
+ * every (j, k): value at the stratum's basis centre and central differences
+ * at +- half a basis unit along each axis (h/4 for equal-size cells; LP1 rows
+ * in the centred basis), then install them as by srmc_set_control.  LP1
+ * solvers with d <= 7, n_in == d + 1. */
 srmc_status srmc_cv_tabulate(const srmc_mlp *m, srmc_solver *s, void *stream);
 
 /* ---- batched form: many independent instances in one launch sequence -------
@@ -269,7 +290,8 @@ srmc_status srmc_cv_tabulate(const srmc_mlp *m, srmc_solver *s, void *stream);
  * N_r > s solves its step i = N_r - 1 - s, and all (instance, stratum) work
  * items of a round that share a kernel variant go to one launch over a
  * persistent grid (blocks stride through the items).  The rounds are captured
- * once into a CUDA graph and replayed.  FP32 solvers only. */
+ * once into a CUDA graph and replayed.  FP32 solvers with equal-size strata
+ * only (SRMC_ERR_UNSUPPORTED otherwise). */
 typedef struct srmc_batch srmc_batch;   /* opaque, library-owned */
 
 /* Plan a batch over n solvers (borrowed: they must outlive the batch and stay

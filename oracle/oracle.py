@@ -25,6 +25,7 @@ DMAX = 8
 PMAX = 24
 MODELS = {"cos": 0, "logistic": 1, "affine": 2}
 BASES = {"lp0": 0, "lp1": 1}
+STRATA = {"size": 0, "prob": 1}
 
 _lock = threading.Lock()
 _lib = None
@@ -52,6 +53,7 @@ class _Problem(C.Structure):
         ("cells", C.c_int * DMAX), ("lo", C.c_double * DMAX), ("hi", C.c_double * DMAX),
         ("mu", C.c_double), ("basis", C.c_int), ("M", C.c_int64),
         ("seed", C.c_uint64), ("instance", C.c_uint32), ("Cy", C.c_double), ("Cz", C.c_double),
+        ("strata", C.c_int), ("M_strata", C.POINTER(C.c_int64)),
     ]
 
 
@@ -98,6 +100,7 @@ def _bind(L):
     L.orc_locate_dim_f32.restype = C.c_int
     L.orc_cell_edges.argtypes = [P, C.c_int, C.c_int, dp, dp]
     L.orc_stratum_centre.argtypes = [P, C.c_int64, dp]
+    L.orc_cell_scale.argtypes = [P, C.c_int, C.c_int]; L.orc_cell_scale.restype = C.c_double
     L.orc_start_point.argtypes = [P, C.c_int, C.c_int64, C.c_int64, dp]
     L.orc_g.argtypes = [P, dp]; L.orc_g.restype = C.c_double
     L.orc_f.argtypes = [P, C.c_int, dp, C.c_double, dp]; L.orc_f.restype = C.c_double
@@ -149,6 +152,12 @@ def to_struct(w) -> _Problem:
     p.seed = int(w.seed)
     p.instance = int(w.instance)
     p.Cy, p.Cz = float(w.Cy), float(w.Cz)
+    p.strata = STRATA[getattr(w, "strata", "size")]
+    ms = getattr(w, "M_strata", None)
+    if ms is not None:
+        arr = np.ascontiguousarray(ms, dtype=np.int64)
+        p._keep = arr                      # owned by the struct object
+        p.M_strata = arr.ctypes.data_as(C.POINTER(C.c_int64))
     return p
 
 
@@ -210,6 +219,11 @@ def stratum_centre(w, k):
     x = np.zeros(w.d)
     lib().orc_stratum_centre(C.byref(to_struct(w)), int(k), _dptr(x))
     return x
+
+
+def cell_scale(w, l, c):
+    """Unit of the centred basis coordinate of cell c of dimension l."""
+    return float(lib().orc_cell_scale(C.byref(to_struct(w)), int(l), int(c)))
 
 
 def start_point(w, i, k, m):

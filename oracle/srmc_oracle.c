@@ -122,6 +122,13 @@ double orc_logistic_cdf(double x, double mu)
  * qc = 1 - F(xhi) + (1-U) w, w = F(xhi) - F(xlo): p + qc = 1, so
  * F(x) = p/(p+qc) = p, the same map as Alg. 3 without the cancellation of
  * 1/p - 1 in the upper tail.  U and 1-U are both exact lattice values. */
+static double sample_from_masses(double U, double Uc, double Flo, double Fchi, double w, double mu)
+{
+    double p = Flo + U * w;
+    double qc = Fchi + Uc * w;
+    return log(p / qc) / mu;
+}
+
 static double sample_restricted_uc(double U, double Uc, double xlo, double xhi, double mu)
 {
     double Flo = orc_logistic_cdf(xlo, mu);
@@ -129,9 +136,7 @@ static double sample_restricted_uc(double U, double Uc, double xlo, double xhi, 
     double w;
     if (xlo > 0.0) w = orc_logistic_cdf(-xlo, mu) - Fchi;  /* both in the upper tail */
     else w = orc_logistic_cdf(xhi, mu) - Flo;
-    double p = Flo + U * w;
-    double qc = Fchi + Uc * w;
-    return log(p / qc) / mu;
+    return sample_from_masses(U, Uc, Flo, Fchi, w, mu);
 }
 
 double orc_sample_restricted(double U, double xlo, double xhi, double mu)
@@ -150,8 +155,31 @@ static double cell_width(const orc_problem *P, int l)
     return (P->hi[l] - P->lo[l]) / (double)P->cells[l];
 }
 
+/* Equal-probability cells (assumption HS, example ii): nu is the product of
+ * one-dimensional logistic laws, so cutting every axis at the quantiles
+ * F^{-1}(c/C) = log(c/(C-c))/mu, c = 1..C-1, gives nu(H_k) = 1/K. */
+static double prob_quantile(double num, double den, double mu)    /* F^{-1}(num/(num+den)) */
+{
+    return log(num / den) / mu;
+}
+
+static double prob_edge(const orc_problem *P, int l, int c)
+{
+    int C = P->cells[l];
+    if (c <= 0) return -INFINITY;
+    if (c >= C) return INFINITY;
+    return prob_quantile((double)c, (double)(C - c), P->mu);
+}
+
 int orc_locate_dim(const orc_problem *P, int l, double x)
 {
+    if (P->strata == ORC_STRATA_PROB) {
+        /* the cell [e_c, e_{c+1}) holding x, by scanning the edges upwards
+         * (NaN compares false everywhere and lands in cell 0) */
+        int c = 0;
+        while (c < P->cells[l] - 1 && x >= prob_edge(P, l, c + 1)) ++c;
+        return c;
+    }
     double t = (x - P->lo[l]) / cell_width(P, l);
     int C = P->cells[l];
     if (!(t >= 0.0)) return 0;                 /* below the box, or NaN */
@@ -192,6 +220,11 @@ void orc_stratum_cells(const orc_problem *P, int64_t k, int *cells)
 
 void orc_cell_edges(const orc_problem *P, int l, int c, double *xlo, double *xhi)
 {
+    if (P->strata == ORC_STRATA_PROB) {
+        *xlo = prob_edge(P, l, c);
+        *xhi = prob_edge(P, l, c + 1);
+        return;
+    }
     double h = cell_width(P, l);
     *xlo = (c == 0) ? -INFINITY : P->lo[l] + (double)c * h;
     *xhi = (c == P->cells[l] - 1) ? INFINITY : P->lo[l] + (double)(c + 1) * h;
@@ -201,8 +234,24 @@ void orc_stratum_centre(const orc_problem *P, int64_t k, double *x)
 {
     int cells[ORC_DMAX];
     orc_stratum_cells(P, k, cells);
-    for (int l = 0; l < P->d; ++l)
-        x[l] = P->lo[l] + ((double)cells[l] + 0.5) * cell_width(P, l);
+    for (int l = 0; l < P->d; ++l) {
+        if (P->strata == ORC_STRATA_PROB) {
+            /* the median of nu restricted to the cell: F^{-1}((c + 1/2)/C) */
+            const int C = P->cells[l], c = cells[l];
+            x[l] = prob_quantile(c + 0.5, C - c - 0.5, P->mu);
+        } else {
+            x[l] = P->lo[l] + ((double)cells[l] + 0.5) * cell_width(P, l);
+        }
+    }
+}
+
+double orc_cell_scale(const orc_problem *P, int l, int c)
+{
+    if (P->strata == ORC_STRATA_PROB) {
+        const int C = P->cells[l];
+        return prob_quantile(c + 0.75, C - c - 0.75, P->mu) - prob_quantile(c + 0.25, C - c - 0.25, P->mu);
+    }
+    return 0.5 * cell_width(P, l);
 }
 
 /* Start point of path m of cloud C_{i,k}: draws 0..d-1, one per coordinate
@@ -213,6 +262,13 @@ void orc_start_point(const orc_problem *P, int i, int64_t k, int64_t m, double *
     orc_stratum_cells(P, k, cells);
     for (int l = 0; l < P->d; ++l) {
         uint32_t w = orc_draw_word(P, i, k, m, l);
+        if (P->strata == ORC_STRATA_PROB) {
+            /* F(e_c) = c/C and 1 - F(e_{c+1}) = (C-c-1)/C by the choice of the edges */
+            const double C = (double)P->cells[l], c = (double)cells[l];
+            x[l] = sample_from_masses(orc_uniform(w), orc_uniform(0xFFFFFFFFu - w),
+                                      c / C, (C - c - 1.0) / C, 1.0 / C, P->mu);
+            continue;
+        }
         double xlo, xhi;
         orc_cell_edges(P, l, cells[l], &xlo, &xhi);
         x[l] = sample_restricted_uc(orc_uniform(w), orc_uniform(0xFFFFFFFFu - w),
@@ -411,10 +467,12 @@ static double control_dot(const orc_ctx *C, int j, int64_t k, const double *x, c
     const orc_problem *P = &C->P;
     const int p = C->dimb;
     double phi[ORC_DMAX + 1], ctr[ORC_DMAX];
+    int cells[ORC_DMAX];
     orc_stratum_centre(P, k, ctr);
+    orc_stratum_cells(P, k, cells);
     phi[0] = 1.0;
     if (p > 1)
-        for (int l = 0; l < P->d; ++l) phi[1 + l] = (x[l] - ctr[l]) / (0.5 * cell_width(P, l));
+        for (int l = 0; l < P->d; ++l) phi[1 + l] = (x[l] - ctr[l]) / orc_cell_scale(P, l, cells[l]);
     const double *row = C->control + ((size_t)j * (size_t)C->K + (size_t)k) * (size_t)(P->q * p);
     double s = 0.0;
     for (int l = 0; l < P->q; ++l) {
@@ -480,7 +538,8 @@ static int64_t fit_impl(orc_ctx *C, int i, int64_t k, int lazy)
 {
     const orc_problem *P = &C->P;
     const int d = P->d, q = P->q, N = P->N, p = C->dimb;
-    const int64_t M = P->M;
+    /* M may vary with the stratum (Sec. 3: the analysis adapts to M_k) */
+    const int64_t M = P->M_strata ? P->M_strata[k] : P->M;
     const double dt = P->T / (double)N, sdt = sqrt(dt);
     int64_t missing = 0;
 

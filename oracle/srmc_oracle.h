@@ -34,6 +34,9 @@ extern "C" {
 
 enum { ORC_MODEL_COS = 0, ORC_MODEL_LOGISTIC = 1, ORC_MODEL_AFFINE = 2 };
 enum { ORC_LP0 = 0, ORC_LP1 = 1 };
+/* Strata (assumption HS): equal size on the box [lo, hi) (example i), or equal
+ * probability under nu, nu(H_k) = 1/K (example ii; lo and hi unused). */
+enum { ORC_STRATA_SIZE = 0, ORC_STRATA_PROB = 1 };
 
 /* One SRMC problem: forward SDE, driver/terminal model, grid, strata, basis. */
 typedef struct {
@@ -52,6 +55,8 @@ typedef struct {
     uint64_t seed;                  /* Philox seed                           */
     uint32_t instance;              /* instance id folded into the key       */
     double Cy, Cz;                  /* truncation levels; <= 0 disables      */
+    int strata;                     /* ORC_STRATA_SIZE / ORC_STRATA_PROB     */
+    const int64_t *M_strata;        /* [K] paths of each stratum, or NULL: M */
 } orc_problem;
 
 /* ---- primitives ---------------------------------------------------------- */
@@ -68,6 +73,10 @@ int      orc_locate_dim_f32(float x, float lo, float r, int C);
 void     orc_cell_edges(const orc_problem *P, int l, int c, double *xlo, double *xhi);
 void     orc_stratum_cells(const orc_problem *P, int64_t k, int *cells);
 void     orc_stratum_centre(const orc_problem *P, int64_t k, double *x);
+/* Unit of the centred basis coordinate of cell c in dimension l: h/2 for
+ * equal-size cells; for equal-probability cells the width between the
+ * quantiles (c + 1/4)/C and (c + 3/4)/C of nu (finite for the outer cells). */
+double   orc_cell_scale(const orc_problem *P, int l, int c);
 void     orc_start_point(const orc_problem *P, int i, int64_t k, int64_t m, double *x);
 double   orc_g(const orc_problem *P, const double *x);
 double   orc_f(const orc_problem *P, int j, const double *x, double y, const double *z);
@@ -96,9 +105,10 @@ const double *orc_row(const orc_ctx *C, int i, int64_t k);
  * Returns the number of points whose row is missing. */
 int64_t  orc_eval(orc_ctx *C, int i, int64_t n, const double *x, double *y, double *z);
 /* Control variate (a martingale control subtracted from the responses):
- * rows [N][K][q][p] in the centred basis phi = [1, (x - c_k)/(h/2)] give
- * zc_j(x) = T_Cz(beta . phi(x)) for x in stratum k; the Y response loses
- * sum_{j>=i} zc_j(X_j).dW_j and the Z response sum_{j>i} zc_j(X_j).dW_j.
+ * rows [N][K][q][p] in the centred basis phi = [1, (x - c_k)/s] (c_k and s
+ * from orc_stratum_centre and orc_cell_scale) give zc_j(x) = T_Cz(beta . phi(x))
+ * for x in stratum k; the Y response loses sum_{j>=i} zc_j(X_j).dW_j and the
+ * Z response sum_{j>i} zc_j(X_j).dW_j.
  * Both have zero conditional mean given x_i, so the fitted functions keep
  * their expectation.  The rows are copied; NULL removes the control. */
 int      orc_set_control(orc_ctx *C, const double *rows);

@@ -156,7 +156,7 @@ cudaError_t enqueue_branches(srmc_batch *b, cudaStream_t st)
     for (size_t r = 0; r < order.size(); ++r) order[r] = (int)r;
     auto work = [&](int r) {
         const Params &P = b->solvers[r]->P;
-        return (double)P.K * (double)P.M * (double)P.N * (double)(P.N + 1);
+        return (double)b->solvers[r]->M_sum * (double)P.N * (double)(P.N + 1);
     };
     std::sort(order.begin(), order.end(), [&](int x, int y) { return work(x) > work(y); });
     const int ns = (int)std::min<size_t>(b->branch.size(), order.size());
@@ -210,6 +210,8 @@ srmc_status srmc_batch_create(srmc_solver *const *solvers, int n, srmc_batch **o
     for (int r = 0; r < n; ++r) {
         if (!solvers[r]) return bfail(SRMC_ERR_INVALID_ARG, "srmc_batch_create: NULL solver");
         if (solvers[r]->fp64) return bfail(SRMC_ERR_UNSUPPORTED, "srmc_batch_create: FP32 solvers only");
+        if (solvers[r]->P.kind != 0)
+            return bfail(SRMC_ERR_UNSUPPORTED, "srmc_batch_create: equal-size strata only");
         if (solvers[r]->device != dev) return bfail(SRMC_ERR_INVALID_ARG, "srmc_batch_create: solver on another device");
     }
     srmc_batch *b = new srmc_batch();

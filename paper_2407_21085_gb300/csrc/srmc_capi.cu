@@ -52,6 +52,9 @@ double logistic_cdf(double x, double mu)
 
 int pad_to(int v, int m) { return (v + m - 1) / m * m; }
 
+// F^{-1}(num / (num + den)) of the logistic law with scale mu.
+double logistic_quantile(double num, double den, double mu) { return std::log(num / den) / mu; }
+
 // Halves per component of a binary16 control row: 4 (one 8-byte load) for
 // p <= 4, else p rounded up to 8 (16-byte loads).
 int half_pad(int p) { return p <= 4 ? 4 : pad_to(p, 8); }
@@ -93,9 +96,10 @@ void free_all(srmc_solver *s)
 {
     if (s->graph) cudaGraphExecDestroy(s->graph);
     if (s->cap_stream) cudaStreamDestroy(s->cap_stream);
-    cudaFree(s->cellF); cudaFree(s->cellF_f); cudaFree(s->stepc); cudaFree(s->stepc_f);
+    cudaFree(s->cellF); cudaFree(s->cellF_f); cudaFree(s->cellB); cudaFree(s->cellB_f);
+    cudaFree(s->stepc); cudaFree(s->stepc_f);
     cudaFree(s->Y32); cudaFree(s->Z32); cudaFree(s->Y64); cudaFree(s->Z64); cudaFree(s->stats);
-    cudaFree(s->C16); cudaFree(s->C64); cudaFree(s->order);
+    cudaFree(s->C16); cudaFree(s->C64); cudaFree(s->order); cudaFree(s->Mk);
 }
 
 cudaError_t launch_step(const srmc_solver *s, int i, cudaStream_t st)
@@ -107,6 +111,19 @@ cudaError_t launch_step(const srmc_solver *s, int i, cudaStream_t st)
     P.cv_own = s->cv && s->cv_own ? 1 : 0;
     const int mv = srmc::kernel_mv(s);
     const int grid = (int)(P.K < 2147483647LL ? P.K : 2147483647LL);
+    if (P.kind != 0) {
+        switch (P.d) {
+        case 1: return srmc::launch_step_prob_d1(P, i, s->fp64, s->lp1, mv, grid, s->threads, st);
+        case 2: return srmc::launch_step_prob_d2(P, i, s->fp64, s->lp1, mv, grid, s->threads, st);
+        case 3: return srmc::launch_step_prob_d3(P, i, s->fp64, s->lp1, mv, grid, s->threads, st);
+        case 4: return srmc::launch_step_prob_d4(P, i, s->fp64, s->lp1, mv, grid, s->threads, st);
+        case 5: return srmc::launch_step_prob_d5(P, i, s->fp64, s->lp1, mv, grid, s->threads, st);
+        case 6: return srmc::launch_step_prob_d6(P, i, s->fp64, s->lp1, mv, grid, s->threads, st);
+        case 7: return srmc::launch_step_prob_d7(P, i, s->fp64, s->lp1, mv, grid, s->threads, st);
+        case 8: return srmc::launch_step_prob_d8(P, i, s->fp64, s->lp1, mv, grid, s->threads, st);
+        }
+        return cudaErrorInvalidValue;
+    }
     switch (P.d) {
     case 1: return srmc::launch_step_d1(P, i, s->fp64, s->lp1, mv, grid, s->threads, st);
     case 2: return srmc::launch_step_d2(P, i, s->fp64, s->lp1, mv, grid, s->threads, st);
@@ -160,11 +177,11 @@ __global__ void locate_kernel(const Params P, const double *x64, const float *x3
         for (int l = 0; l < P.d; ++l) {
             int c;
             if (x64) {
-                double t;
-                c = srmc::locate_dim(x64[a * P.d + l], P.lo[l], P.h[l], P.cells[l], t);
+                double u;
+                c = srmc::cell_of(P, l, x64[a * P.d + l], u);
             } else {
-                float t;
-                c = srmc::locate_dim(x32[a * P.d + l], P.lo_f[l], P.r_f[l], P.cells[l], t);
+                float u;
+                c = srmc::cell_of(P, l, x32[a * P.d + l], u);
             }
             k += (long long)c * P.stride[l];
         }
@@ -203,7 +220,7 @@ __global__ void centres_kernel(const Params P, double *x)
         for (int l = 0; l < P.d; ++l) {
             const int c = (int)(rem % P.cells[l]);
             rem /= P.cells[l];
-            x[k * P.d + l] = P.lo[l] + ((double)c + 0.5) * P.h[l];
+            x[k * P.d + l] = srmc::cell_centre(P, l, c);
         }
     }
 }
@@ -239,10 +256,8 @@ __global__ void eval_kernel(const Params P, int i, const double *x, long long n,
         phi[0] = 1.0;
         long long k = 0;
         for (int l = 0; l < P.d; ++l) {
-            double t;
-            const int c = srmc::locate_dim(xa[l], P.lo[l], P.h[l], P.cells[l], t);
+            const int c = srmc::cell_of(P, l, xa[l], phi[1 + l]);
             k += (long long)c * P.stride[l];
-            phi[1 + l] = 2.0 * (t - (double)c) - 1.0;
         }
         const long long row = (long long)i * P.K + k;
         const double *al = P.Y64 + row * P.ry64;
@@ -298,12 +313,16 @@ srmc_status srmc_create(const srmc_problem *pr, const srmc_strata *sa, const srm
         return fail(SRMC_ERR_INVALID_ARG, "params: n_params must be in [0, 24]");
     const int need = pr->model == SRMC_MODEL_COS ? 4 : pr->model == SRMC_MODEL_AFFINE ? 3 + 2 * d : 0;
     if (pr->n_params < need) return fail(SRMC_ERR_INVALID_ARG, "too few model parameters");
-    if (!sa->cells || !sa->lo || !sa->hi) return fail(SRMC_ERR_INVALID_ARG, "strata arrays are required");
+    if (sa->kind != SRMC_STRATA_EQUAL_SIZE && sa->kind != SRMC_STRATA_EQUAL_PROB)
+        return fail(SRMC_ERR_INVALID_ARG, "unknown strata kind");
+    const bool prob = sa->kind == SRMC_STRATA_EQUAL_PROB;
+    if (!sa->cells || (!prob && (!sa->lo || !sa->hi)))
+        return fail(SRMC_ERR_INVALID_ARG, "strata arrays are required");
     if (!(sa->mu > 0.0) || !std::isfinite(sa->mu)) return fail(SRMC_ERR_INVALID_ARG, "mu must be > 0");
     long long K = 1, cells_total = 0;
     for (int l = 0; l < d; ++l) {
         if (sa->cells[l] < 1) return fail(SRMC_ERR_INVALID_ARG, "cells must be >= 1");
-        if (!(sa->lo[l] < sa->hi[l]) || !std::isfinite(sa->lo[l]) || !std::isfinite(sa->hi[l]))
+        if (!prob && (!(sa->lo[l] < sa->hi[l]) || !std::isfinite(sa->lo[l]) || !std::isfinite(sa->hi[l])))
             return fail(SRMC_ERR_INVALID_ARG, "need finite lo < hi");
         K *= sa->cells[l];
         cells_total += sa->cells[l];
@@ -320,8 +339,19 @@ srmc_status srmc_create(const srmc_problem *pr, const srmc_strata *sa, const srm
     if (cf->prec != SRMC_FP32 && cf->prec != SRMC_FP64) return fail(SRMC_ERR_INVALID_ARG, "precision");
     if (cf->M < p) return fail(SRMC_ERR_INVALID_ARG, "M must be >= the basis dimension");
     if (cf->M > 4294967295LL) return fail(SRMC_ERR_INVALID_ARG, "M must be < 2^32");
+    long long M_max = cf->M, M_sum = cf->M * K;
+    if (cf->M_strata) {
+        M_max = 0; M_sum = 0;
+        for (long long k = 0; k < K; ++k) {
+            const long long mk = cf->M_strata[k];
+            if (mk < p) return fail(SRMC_ERR_INVALID_ARG, "M_strata: every M_k must be >= the basis dimension");
+            if (mk > 4294967295LL) return fail(SRMC_ERR_INVALID_ARG, "M_strata: every M_k must be < 2^32");
+            M_max = std::max(M_max, mk);
+            M_sum += mk;
+        }
+    }
     int threads = cf->block_threads;
-    if (threads == 0) threads = cf->M >= 256 ? 256 : (int)((cf->M + 31) / 32 * 32);
+    if (threads == 0) threads = M_max >= 256 ? 256 : (int)((M_max + 31) / 32 * 32);
     if (threads < 32 || threads > srmc::MAX_THREADS || threads % 32)
         return fail(SRMC_ERR_INVALID_ARG, "block_threads must be a multiple of 32 in [32, 256]");
 
@@ -335,6 +365,7 @@ srmc_status srmc_create(const srmc_problem *pr, const srmc_strata *sa, const srm
     s->done_from = pr->N;
     P.d = d; P.q = q; P.N = pr->N; P.p = p;
     P.K = K; P.M = cf->M;
+    s->M_sum = M_sum;
     P.model = pr->model;
     const double kapz = pr->model == SRMC_MODEL_COS ? pr->params[2] : 0.0;
     s->mv = pr->model == SRMC_MODEL_COS ? (kapz != 0.0 ? srmc::MV_COS_Z : srmc::MV_COS)
@@ -345,16 +376,19 @@ srmc_status srmc_create(const srmc_problem *pr, const srmc_strata *sa, const srm
     P.ph = half_pad(p); P.rc16 = q * P.ph;
     int stride = 1;
     int off = 0;
+    P.kind = prob ? 1 : 0;
     for (int l = 0; l < d; ++l) {
         P.cells[l] = sa->cells[l];
         P.stride[l] = stride; stride *= sa->cells[l];
         P.cell_off[l] = off; off += sa->cells[l];
-        P.lo[l] = sa->lo[l];
-        P.h[l] = (sa->hi[l] - sa->lo[l]) / (double)sa->cells[l];
+        // (equal-probability strata use the per-cell table; lo = 0, h = 1 unused)
+        const double lo = prob ? 0.0 : sa->lo[l], hi = prob ? (double)sa->cells[l] : sa->hi[l];
+        P.lo[l] = lo;
+        P.h[l] = (hi - lo) / (double)sa->cells[l];
         P.b[l] = pr->b[l];
         P.sig[l] = pr->sigma[l * q + l];
-        P.lo_f[l] = (float)sa->lo[l];
-        P.r_f[l] = (float)((double)sa->cells[l] / (sa->hi[l] - sa->lo[l]));
+        P.lo_f[l] = (float)lo;
+        P.r_f[l] = (float)((double)sa->cells[l] / (hi - lo));
         P.b_f[l] = (float)pr->b[l];
         P.sig_f[l] = (float)P.sig[l];
     }
@@ -365,6 +399,7 @@ srmc_status srmc_create(const srmc_problem *pr, const srmc_strata *sa, const srm
     P.sqrt_d = std::sqrt((double)d);
     P.dt_f = (float)P.dt; P.sdt_f = (float)P.sdt;
     P.inv_mu_f = (float)(1.0 / sa->mu);
+    P.mu_f = (float)sa->mu;
     P.inv_sqrt_d_f = (float)(1.0 / std::sqrt((double)d));
     const double inf = std::numeric_limits<double>::infinity();
     P.Cy = cf->Cy > 0.0 ? cf->Cy : inf;
@@ -382,22 +417,43 @@ srmc_status srmc_create(const srmc_problem *pr, const srmc_strata *sa, const srm
         P.lin_f = (float)P.lin;
     }
 
-    // Sampler constants of every cell side (Alg. 3): F(x-), 1 - F(x+), F(x+) - F(x-).
-    std::vector<double> cellF(3 * cells_total);
-    std::vector<float> cellF_f(3 * cells_total);
-    for (int l = 0; l < d; ++l)
-        for (int c = 0; c < sa->cells[l]; ++c) {
-            const double h = P.h[l];
-            const double xlo = c == 0 ? -inf : sa->lo[l] + (double)c * h;
-            const double xhi = c == sa->cells[l] - 1 ? inf : sa->lo[l] + (double)(c + 1) * h;
-            const double Flo = logistic_cdf(xlo, sa->mu);
-            const double Fchi = logistic_cdf(-xhi, sa->mu);
-            const double w = xlo > 0.0 ? logistic_cdf(-xlo, sa->mu) - Fchi
-                                       : logistic_cdf(xhi, sa->mu) - Flo;
+    // Sampler constants of every cell side (Alg. 3): F(x-), 1 - F(x+), F(x+) - F(x-);
+    // per-cell edges, basis centre and 1/unit (the centred LP1 coordinate).
+    std::vector<double> cellF(3 * cells_total), cellB(4 * cells_total);
+    std::vector<float> cellF_f(3 * cells_total), cellB_f(4 * cells_total);
+    for (int l = 0; l < d; ++l) {
+        const int C = sa->cells[l];
+        for (int c = 0; c < C; ++c) {
+            double xlo, xhi, Flo, Fchi, w, ctr, unit;
+            if (prob) {
+                // equal nu-probability cells: edges at the logistic quantiles c/C,
+                // so F(x-) = c/C and 1 - F(x+) = (C-c-1)/C exactly
+                xlo = c == 0 ? -inf : logistic_quantile((double)c, (double)(C - c), sa->mu);
+                xhi = c == C - 1 ? inf : logistic_quantile((double)(c + 1), (double)(C - c - 1), sa->mu);
+                Flo = (double)c / (double)C;
+                Fchi = (double)(C - c - 1) / (double)C;
+                w = 1.0 / (double)C;
+                ctr = logistic_quantile(c + 0.5, C - c - 0.5, sa->mu);
+                unit = logistic_quantile(c + 0.75, C - c - 0.75, sa->mu) -
+                       logistic_quantile(c + 0.25, C - c - 0.25, sa->mu);
+            } else {
+                const double h = P.h[l];
+                xlo = c == 0 ? -inf : sa->lo[l] + (double)c * h;
+                xhi = c == C - 1 ? inf : sa->lo[l] + (double)(c + 1) * h;
+                Flo = logistic_cdf(xlo, sa->mu);
+                Fchi = logistic_cdf(-xhi, sa->mu);
+                w = xlo > 0.0 ? logistic_cdf(-xlo, sa->mu) - Fchi : logistic_cdf(xhi, sa->mu) - Flo;
+                ctr = sa->lo[l] + ((double)c + 0.5) * h;
+                unit = 0.5 * h;
+            }
             const int o = 3 * (P.cell_off[l] + c);
             cellF[o] = Flo; cellF[o + 1] = Fchi; cellF[o + 2] = w;
             cellF_f[o] = (float)Flo; cellF_f[o + 1] = (float)Fchi; cellF_f[o + 2] = (float)w;
+            const int b = 4 * (P.cell_off[l] + c);
+            cellB[b] = xlo; cellB[b + 1] = xhi; cellB[b + 2] = ctr; cellB[b + 3] = 1.0 / unit;
+            for (int a = 0; a < 4; ++a) cellB_f[b + a] = (float)cellB[b + a];
         }
+    }
     // Per-step driver constants of the cos model: kap e_j^2, kapz s0^2 e_j^2.
     std::vector<double> stepc(2 * (pr->N + 1), 0.0);
     std::vector<float> stepc_f(2 * (pr->N + 1), 0.0f);
@@ -422,6 +478,8 @@ srmc_status srmc_create(const srmc_problem *pr, const srmc_strata *sa, const srm
     const size_t rows = (size_t)pr->N * (size_t)K;
     if ((e = cudaMalloc(&s->cellF, sizeof(double) * cellF.size())) != cudaSuccess) return bail(e, "cudaMalloc");
     if ((e = cudaMalloc(&s->cellF_f, sizeof(float) * cellF_f.size())) != cudaSuccess) return bail(e, "cudaMalloc");
+    if ((e = cudaMalloc(&s->cellB, sizeof(double) * cellB.size())) != cudaSuccess) return bail(e, "cudaMalloc");
+    if ((e = cudaMalloc(&s->cellB_f, sizeof(float) * cellB_f.size())) != cudaSuccess) return bail(e, "cudaMalloc");
     if ((e = cudaMalloc(&s->stepc, sizeof(double) * stepc.size())) != cudaSuccess) return bail(e, "cudaMalloc");
     if ((e = cudaMalloc(&s->stepc_f, sizeof(float) * stepc_f.size())) != cudaSuccess) return bail(e, "cudaMalloc");
     if ((e = cudaMalloc(&s->Y64, sizeof(double) * rows * P.ry64)) != cudaSuccess) return bail(e, "cudaMalloc Y64");
@@ -433,6 +491,8 @@ srmc_status srmc_create(const srmc_problem *pr, const srmc_strata *sa, const srm
     if ((e = cudaMalloc(&s->stats, sizeof(unsigned long long) * 4)) != cudaSuccess) return bail(e, "cudaMalloc");
     if ((e = cudaMemcpy(s->cellF, cellF.data(), sizeof(double) * cellF.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return bail(e, "cudaMemcpy");
     if ((e = cudaMemcpy(s->cellF_f, cellF_f.data(), sizeof(float) * cellF_f.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return bail(e, "cudaMemcpy");
+    if ((e = cudaMemcpy(s->cellB, cellB.data(), sizeof(double) * cellB.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return bail(e, "cudaMemcpy");
+    if ((e = cudaMemcpy(s->cellB_f, cellB_f.data(), sizeof(float) * cellB_f.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return bail(e, "cudaMemcpy");
     if ((e = cudaMemcpy(s->stepc, stepc.data(), sizeof(double) * stepc.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return bail(e, "cudaMemcpy");
     if ((e = cudaMemcpy(s->stepc_f, stepc_f.data(), sizeof(float) * stepc_f.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return bail(e, "cudaMemcpy");
     if ((e = cudaMemset(s->Y64, 0, sizeof(double) * rows * P.ry64)) != cudaSuccess) return bail(e, "cudaMemset");
@@ -441,7 +501,16 @@ srmc_status srmc_create(const srmc_problem *pr, const srmc_strata *sa, const srm
     if (s->Z32 && (e = cudaMemset(s->Z32, 0, sizeof(float) * rows * P.rz32)) != cudaSuccess) return bail(e, "cudaMemset");
     if ((e = cudaMemset(s->stats, 0, sizeof(unsigned long long) * 4)) != cudaSuccess) return bail(e, "cudaMemset");
     P.cellF = s->cellF; P.cellF_f = s->cellF_f; P.stepc = s->stepc; P.stepc_f = s->stepc_f;
+    P.cellB = s->cellB; P.cellB_f = s->cellB_f;
     P.Y32 = s->Y32; P.Z32 = s->Z32; P.Y64 = s->Y64; P.Z64 = s->Z64; P.stats = s->stats;
+    if (cf->M_strata) {
+        std::vector<unsigned> mk((size_t)K);
+        for (long long k = 0; k < K; ++k) mk[(size_t)k] = (unsigned)cf->M_strata[k];
+        if ((e = cudaMalloc(&s->Mk, sizeof(unsigned) * mk.size())) != cudaSuccess) return bail(e, "cudaMalloc M_strata");
+        if ((e = cudaMemcpy(s->Mk, mk.data(), sizeof(unsigned) * mk.size(), cudaMemcpyHostToDevice)) != cudaSuccess)
+            return bail(e, "cudaMemcpy M_strata");
+        P.Mk = s->Mk;
+    }
     if (d >= SRMC_ORDER_MIN_D && K > 1 && K <= SRMC_ORDER_MAX_K) {
         const std::vector<unsigned> order = morton_order(sa->cells, d, K);
         if ((e = cudaMalloc(&s->order, sizeof(unsigned) * order.size())) != cudaSuccess) return bail(e, "cudaMalloc order");
@@ -529,10 +598,8 @@ __global__ void point_error_kernel(const Params P, const double *x, long long n,
             phi[0] = 1.0;
             long long k = 0;
             for (int l = 0; l < P.d; ++l) {
-                double t;
-                const int c = srmc::locate_dim(xa[l], P.lo[l], P.h[l], P.cells[l], t);
+                const int c = srmc::cell_of(P, l, xa[l], phi[1 + l]);
                 k += (long long)c * P.stride[l];
-                phi[1 + l] = 2.0 * (t - (double)c) - 1.0;
             }
             closed_form(P, i, xa, u, zs);
             const long long row = (long long)i * P.K + k;
@@ -581,8 +648,8 @@ __global__ void closed_form_error_kernel(const Params P, bool inner, double *out
             const int c = (int)(rem % P.cells[l]);
             rem /= P.cells[l];
             outer = outer || c == 0 || c == P.cells[l] - 1;
-            x[l] = P.lo[l] + ((double)c + 0.5) * P.h[l];
-            phi[1 + l] = 0.0;                    // centre of the nominal cell
+            x[l] = srmc::cell_centre(P, l, c);
+            phi[1 + l] = 0.0;                    // the basis centre of the cell
         }
         if (inner && outer) continue;
         ++cnt;
@@ -811,7 +878,7 @@ srmc_status srmc_stats(const srmc_solver *s, unsigned long long out[3])
     out[1] = h[1];
     long long steps = 0;
     for (int i = s->done_from; i < s->P.N; ++i) steps += (long long)(s->P.N - i);
-    out[2] = (unsigned long long)(steps * s->P.K * s->P.M);
+    out[2] = (unsigned long long)(steps * s->M_sum);
     return SRMC_OK;
 }
 

@@ -32,7 +32,8 @@ struct Params {
     double lo[DMAX], h[DMAX], b[DMAX], sig[DMAX];
     float lo_f[DMAX], r_f[DMAX], b_f[DMAX], sig_f[DMAX];
     double T, dt, sdt, mu, sqrt_d;
-    float dt_f, sdt_f, inv_mu_f, inv_sqrt_d_f;
+    float dt_f, sdt_f, inv_mu_f, inv_sqrt_d_f, mu_f;
+    int kind;                       // 0: equal-size cells on the box, 1: equal nu-probability
     double Cy, Cz;                  // +inf when disabled
     float Cy_f, Cz_f;
     unsigned key0, key1;
@@ -43,6 +44,8 @@ struct Params {
     float lin_f;
     const double *cellF;            // [sum cells][3]: F(x-), 1 - F(x+), F(x+) - F(x-)
     const float *cellF_f;
+    const double *cellB;            // [sum cells][4]: x-, x+, basis centre, 1 / basis unit
+    const float *cellB_f;
     const double *stepc;            // [N+1][2] per-step driver constants
     const float *stepc_f;
     float *Y32, *Z32;               // [N][K][ry32], [N][K][rz32]; N K r < 2^32
@@ -52,6 +55,7 @@ struct Params {
     const double *C64;              // control rows [N][K][rz64]
     unsigned long long *stats;      // [0] LP1->LP0 fallbacks, [1] non-finite rows
     const unsigned *order;          // [K] stratum solved by work item t (NULL: t itself)
+    const unsigned *Mk;             // [K] paths of each stratum (NULL: M for all)
     int cv_own;                     // control from the fitted z of later steps (ZIN kernels)
 };
 
@@ -232,6 +236,40 @@ __device__ __forceinline__ int locate_dim(float x, float lo, float r, int C, flo
     return (int)fminf(fmaxf(floorf(t), 0.0f), (float)(C - 1));
 }
 
+// Equal-probability cells (assumption HS, example ii): the cell of x along
+// an axis of C cells whose rows B[4c..4c+3] = (x-, x+, centre, 1/unit) are
+// given, and the centred basis coordinate (x - centre)/unit.  The guess
+// floor(C F(x)) from the logistic CDF is off by at most one cell (F is
+// accurate to a few ulps, far below 1/C), and one comparison with the
+// stored edges settles it; NaN lands in cell 0 like the equal-size form.
+__device__ __forceinline__ int locate_prob(double x, const double *B, int C, double mu, double &phi)
+{
+    const double F = 1.0 / (1.0 + exp(-mu * x));
+    int c = (int)fmin(fmax(floor(F * (double)C), 0.0), (double)(C - 1));
+    if (c > 0 && x < __ldg(B + 4 * c)) --c;
+    else if (c < C - 1 && x >= __ldg(B + 4 * c + 1)) ++c;
+    phi = (x - __ldg(B + 4 * c + 2)) * __ldg(B + 4 * c + 3);
+    return c;
+}
+__device__ __forceinline__ int locate_prob(float x, const float *B, int C, float mu, float &phi)
+{
+    const float F = __fdividef(1.0f, 1.0f + __expf(-mu * x));
+    int c = (int)fminf(fmaxf(floorf(F * (float)C), 0.0f), (float)(C - 1));
+    const float4 b = __ldg(reinterpret_cast<const float4 *>(B) + c);
+    float ctr = b.z, inv = b.w;
+    if (c > 0 && x < b.x) {
+        --c;
+        const float2 v = __ldg(reinterpret_cast<const float2 *>(B + 4 * c + 2));
+        ctr = v.x; inv = v.y;
+    } else if (c < C - 1 && x >= b.y) {
+        ++c;
+        const float2 v = __ldg(reinterpret_cast<const float2 *>(B + 4 * c + 2));
+        ctr = v.x; inv = v.y;
+    }
+    phi = (x - ctr) * inv;
+    return c;
+}
+
 // Precision traits: which parameter copies a form reads.
 template <typename R> struct Form;
 template <> struct Form<double> {
@@ -247,6 +285,8 @@ template <> struct Form<double> {
     __device__ static double lin(const Params &P) { return P.lin; }
     __device__ static double mu_arg(const Params &P) { return P.mu; }
     __device__ static const double *cellF(const Params &P) { return P.cellF; }
+    __device__ static const double *cellB(const Params &P) { return P.cellB; }
+    __device__ static double mu(const Params &P) { return P.mu; }
     __device__ static const double *stepc(const Params &P) { return P.stepc; }
     __device__ static const double *Ytab(const Params &P) { return P.Y64; }
     __device__ static const double *Ztab(const Params &P) { return P.Z64; }
@@ -266,6 +306,8 @@ template <> struct Form<float> {
     __device__ static float lin(const Params &P) { return P.lin_f; }
     __device__ static float mu_arg(const Params &P) { return P.inv_mu_f; }
     __device__ static const float *cellF(const Params &P) { return P.cellF_f; }
+    __device__ static const float *cellB(const Params &P) { return P.cellB_f; }
+    __device__ static float mu(const Params &P) { return P.mu_f; }
     __device__ static const float *stepc(const Params &P) { return P.stepc_f; }
     __device__ static const float *Ytab(const Params &P) { return P.Y32; }
     __device__ static const float *Ztab(const Params &P) { return P.Z32; }

@@ -43,10 +43,14 @@ struct BatchRound {
 #define SRMC_OCC_BATCH_NAME(D) SRMC_OCC_BATCH_NAME_(D)
 #define SRMC_OCC_BATCH_NAME_(D) occupancy_batch_d##D
 #define SRMC_LAUNCH_STEP_NAME_(D) launch_step_d##D
+#define SRMC_LAUNCH_STEP_PROB_NAME(D) SRMC_LAUNCH_STEP_PROB_NAME_(D)
+#define SRMC_LAUNCH_STEP_PROB_NAME_(D) launch_step_prob_d##D
 
 #define SRMC_DECLARE_STEP(D)                                                              \
     cudaError_t launch_step_d##D(const Params &P, int i, bool fp64, bool lp1, int mv, int grid, \
-                                 int threads, cudaStream_t st);
+                                 int threads, cudaStream_t st);                               \
+    cudaError_t launch_step_prob_d##D(const Params &P, int i, bool fp64, bool lp1, int mv,    \
+                                      int grid, int threads, cudaStream_t st);
 SRMC_DECLARE_STEP(1)
 SRMC_DECLARE_STEP(2)
 SRMC_DECLARE_STEP(3)
@@ -71,6 +75,35 @@ SRMC_DECLARE_BATCH(7)
 SRMC_DECLARE_BATCH(8)
 #undef SRMC_DECLARE_BATCH
 
+// Cell of x along axis l for either kind of strata, and the centred basis
+// coordinate (x - centre)/unit of that cell, in FP64 and in FP32.
+__device__ __forceinline__ int cell_of(const Params &P, int l, double x, double &phi)
+{
+    if (P.kind != 0) return locate_prob(x, P.cellB + 4 * P.cell_off[l], P.cells[l], P.mu, phi);
+    double t;
+    const int c = locate_dim(x, P.lo[l], P.h[l], P.cells[l], t);
+    phi = 2.0 * (t - (double)c) - 1.0;
+    return c;
+}
+__device__ __forceinline__ int cell_of(const Params &P, int l, float x, float &phi)
+{
+    if (P.kind != 0) return locate_prob(x, P.cellB_f + 4 * P.cell_off[l], P.cells[l], P.mu_f, phi);
+    float t;
+    const int c = locate_dim(x, P.lo_f[l], P.r_f[l], P.cells[l], t);
+    phi = 2.0f * (t - (float)c) - 1.0f;
+    return c;
+}
+
+// Basis centre and unit of cell c along axis l (FP64 table).
+__device__ __forceinline__ double cell_centre(const Params &P, int l, int c)
+{
+    return P.cellB[4 * (P.cell_off[l] + c) + 2];
+}
+__device__ __forceinline__ double cell_unit(const Params &P, int l, int c)
+{
+    return 1.0 / P.cellB[4 * (P.cell_off[l] + c) + 3];
+}
+
 // Table-row evaluation of y_i(x) in FP64 (truncated), x in double; the
 // kernel-side twin of srmc_eval used by the MLP data generator.
 __device__ __forceinline__ double eval_y64(const Params &P, int i, const double *x)
@@ -79,10 +112,8 @@ __device__ __forceinline__ double eval_y64(const Params &P, int i, const double 
     phi[0] = 1.0;
     long long k = 0;
     for (int l = 0; l < P.d; ++l) {
-        double t;
-        const int c = locate_dim(x[l], P.lo[l], P.h[l], P.cells[l], t);
+        const int c = cell_of(P, l, x[l], phi[1 + l]);
         k += (long long)c * P.stride[l];
-        phi[1 + l] = 2.0 * (t - (double)c) - 1.0;
     }
     const double *al = P.Y64 + ((long long)i * P.K + k) * P.ry64;
     double v = al[0];
@@ -107,6 +138,8 @@ struct srmc_solver {
     int done_from;              // every step >= done_from has been enqueued
     double *cellF = nullptr;
     float *cellF_f = nullptr;
+    double *cellB = nullptr;             // per cell: edges, basis centre, 1/unit
+    float *cellB_f = nullptr;
     double *stepc = nullptr;
     float *stepc_f = nullptr;
     float *Y32 = nullptr, *Z32 = nullptr;
@@ -115,6 +148,8 @@ struct srmc_solver {
     __half *C16 = nullptr;               // control rows of the FP32 form (binary16, [q][ph] per row)
     double *C64 = nullptr;               // control rows (FP64, padded like Z64)
     unsigned *order = nullptr;           // locality order of the strata (NULL: index order)
+    unsigned *Mk = nullptr;              // paths of each stratum (NULL: M for all)
+    long long M_sum = 0;                 // sum of the paths over the strata
     bool cv = false;                     // control installed
     bool cv_own = false;                 // ... and it is the run's own fitted z
     cudaStream_t cap_stream = nullptr;   // private stream for graph capture

@@ -474,7 +474,9 @@ __global__ void mlp_data_kernel(const Params P, long long n, unsigned k0, unsign
 }
 
 // Control rows from the network: one warp per (j, k) tile; tile rows are the
-// stratum centre (row 0) and c +- (h_m/4) e_m (rows 1 + 2m, 2 + 2m).
+// stratum's basis centre (row 0) and c +- (unit_m/2) e_m (rows 1 + 2m, 2 + 2m),
+// unit_m the basis unit of the stratum's cell along axis m (h_m/2 for
+// equal-size cells).
 __global__ void __launch_bounds__(WARPS * 32) mlp_tabulate_kernel(Net net, const Params P, double *c64,
                                                                   __half *c16)
 {
@@ -488,13 +490,14 @@ __global__ void __launch_bounds__(WARPS * 32) mlp_tabulate_kernel(Net net, const
     for (long long t = (long long)blockIdx.x * WARPS + warp; t < tiles; t += (long long)gridDim.x * WARPS) {
         const int j = (int)(t / P.K);
         const long long k = t % P.K;
-        double ctr[srmc::DMAX];
+        double ctr[srmc::DMAX], half[srmc::DMAX];      // basis centre, half a basis unit
         {
             long long rem = k;
             for (int l = 0; l < d; ++l) {
                 const int c = (int)(rem % P.cells[l]);
                 rem /= P.cells[l];
-                ctr[l] = P.lo[l] + ((double)c + 0.5) * P.h[l];
+                ctr[l] = srmc::cell_centre(P, l, c);
+                half[l] = 0.5 * srmc::cell_unit(P, l, c);
             }
         }
         const float tj = (float)((double)j * P.dt);
@@ -506,7 +509,7 @@ __global__ void __launch_bounds__(WARPS * 32) mlp_tabulate_kernel(Net net, const
             double x = ctr[l];
             if (r >= 1 && r <= 2 * d) {
                 const int m = (r - 1) >> 1;
-                if (m == l) x += ((r & 1) ? 0.25 : -0.25) * P.h[l];
+                if (m == l) x += (r & 1) ? half[l] : -half[l];
             }
             return (float)x;
         });

@@ -24,6 +24,12 @@
 #ifndef SRMC_STEP_D
 #error "compile with -DSRMC_STEP_D=<dimension>"
 #endif
+// Kind of strata the unit is compiled for: 0 equal size (the launchers
+// launch_step_dD, launch_batch_dD), 1 equal nu-probability (launch_step_prob_dD;
+// the batched form is built for equal-size strata only).
+#ifndef SRMC_STEP_KIND
+#define SRMC_STEP_KIND 0
+#endif
 
 namespace srmc {
 namespace {
@@ -251,12 +257,23 @@ __device__ __forceinline__ void eval_at(const Params &P, int j, const R (&x)[D],
     unsigned kk = 0;
     R phi[p];
     phi[0] = (R)1;
+    if constexpr (SRMC_STEP_KIND == 0) {
 #pragma unroll
-    for (int l = 0; l < D; ++l) {
-        R t;
-        const int c = locate_dim(x[l], Form<R>::lo(P, l), Form<R>::scale(P, l), P.cells[l], t);
-        kk += (unsigned)c * (unsigned)P.stride[l];
-        if (LP1) phi[1 + l] = (R)2 * (t - (R)c) - (R)1;
+        for (int l = 0; l < D; ++l) {
+            R t;
+            const int c = locate_dim(x[l], Form<R>::lo(P, l), Form<R>::scale(P, l), P.cells[l], t);
+            kk += (unsigned)c * (unsigned)P.stride[l];
+            if (LP1) phi[1 + l] = (R)2 * (t - (R)c) - (R)1;
+        }
+    } else {
+#pragma unroll
+        for (int l = 0; l < D; ++l) {
+            R u;
+            const int c = locate_prob(x[l], Form<R>::cellB(P) + 4 * P.cell_off[l], P.cells[l],
+                                      Form<R>::mu(P), u);
+            kk += (unsigned)c * (unsigned)P.stride[l];
+            if (LP1) phi[1 + l] = u;
+        }
     }
     const unsigned row = (unsigned)j * (unsigned)P.K + kk;     // N K < 2^32 (checked at create)
     R a[p];
@@ -406,6 +423,7 @@ __device__ __forceinline__ void solve_stratum(const Params &P, const int i, cons
     auto &ok_s = sm.ok_s;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     const R dt = Form<R>::dt(P), sdt = Form<R>::sdt(P), inv_dt = (R)1 / dt;
+    const long long Mk = P.Mk ? (long long)__ldg(P.Mk + k) : P.M;     // paths of this cloud
     // Cells of H_k; the sampler constants of its sides are re-read (L1
     // hits) at every path start rather than held in registers.
     int cell[D];
@@ -417,6 +435,19 @@ __device__ __forceinline__ void solve_stratum(const Params &P, const int i, cons
             rem /= P.cells[l];
         }
     }
+    // Centred basis coordinate of a start point x of cell cell[l] (the cell is
+    // known: a start point is never located).
+    auto start_phi = [&](R x, int l) -> R {
+        if constexpr (SRMC_STEP_KIND != 0) {
+            const R *b = Form<R>::cellB(P) + 4 * (P.cell_off[l] + cell[l]);
+            return (x - __ldg(b + 2)) * __ldg(b + 3);
+        } else {
+            R t;
+            if (sizeof(R) == 8) t = (x - (R)P.lo[l]) / (R)P.h[l];
+            else t = (x - (R)P.lo_f[l]) * (R)P.r_f[l];
+            return (R)2 * (t - (R)cell[l]) - (R)1;
+        }
+    };
     auto sample_start = [&](unsigned w, int l) -> R {
         const R *cf = Form<R>::cellF(P) + 3 * (P.cell_off[l] + cell[l]);
         return sample_cell(w, __ldg(cf), __ldg(cf + 1), __ldg(cf + 2), Form<R>::mu_arg(P));
@@ -426,9 +457,9 @@ __device__ __forceinline__ void solve_stratum(const Params &P, const int i, cons
     MA mA;
     if constexpr (RS) mA.zero(lane); else mA.zero();
     int since_flush = 0;
-    for (long long m0 = 0; m0 < P.M; m0 += blockDim.x) {
+    for (long long m0 = 0; m0 < Mk; m0 += blockDim.x) {
         const long long m = m0 + threadIdx.x;
-        const bool valid = m < P.M;
+        const bool valid = m < Mk;
         Words W;
         W.init(P, (unsigned)m, (unsigned)k, (unsigned)i);
         R x[D], phi[p], dwi[D], xj[D], zj[D], yn;
@@ -439,12 +470,7 @@ __device__ __forceinline__ void solve_stratum(const Params &P, const int i, cons
 #pragma unroll
             for (int l = 0; l < D; ++l) {
                 x[l] = sample_start(ws[l], l);
-                if (LP1) {
-                    R t;
-                    if (sizeof(R) == 8) t = (x[l] - (R)P.lo[l]) / (R)P.h[l];
-                    else t = (x[l] - (R)P.lo_f[l]) * (R)P.r_f[l];
-                    phi[1 + l] = (R)2 * (t - (R)cell[l]) - (R)1;
-                }
+                if (LP1) phi[1 + l] = start_phi(x[l], l);
             }
         }
         {
@@ -553,7 +579,7 @@ __device__ __forceinline__ void solve_stratum(const Params &P, const int i, cons
 
     // ---------------- Z fit (FP64, one warp) -----------------------------
     if (warp == 0) {
-        const double Md = (double)P.M;
+        const double Md = (double)Mk;
         bool ok = true;
         if (LP1) ok = cholesky_warp<p>(totA, Gw, Ls, Linv, lane);
         __syncwarp();
@@ -575,9 +601,9 @@ __device__ __forceinline__ void solve_stratum(const Params &P, const int i, cons
     MB mB;
     mB.zero();
     since_flush = 0;
-    for (long long m0 = 0; m0 < P.M; m0 += blockDim.x) {
+    for (long long m0 = 0; m0 < Mk; m0 += blockDim.x) {
         const long long m = m0 + threadIdx.x;
-        const bool valid = m < P.M;
+        const bool valid = m < Mk;
         Words W;
         W.init(P, (unsigned)m, (unsigned)k, (unsigned)i);
         R x[D], phi[p], x1[D], y1, z1[D], zi[D];
@@ -588,12 +614,7 @@ __device__ __forceinline__ void solve_stratum(const Params &P, const int i, cons
 #pragma unroll
             for (int l = 0; l < D; ++l) {
                 x[l] = sample_start(ws[l], l);
-                if (LP1) {
-                    R t;
-                    if (sizeof(R) == 8) t = (x[l] - (R)P.lo[l]) / (R)P.h[l];
-                    else t = (x[l] - (R)P.lo_f[l]) * (R)P.r_f[l];
-                    phi[1 + l] = (R)2 * (t - (R)cell[l]) - (R)1;
-                }
+                if (LP1) phi[1 + l] = start_phi(x[l], l);
             }
         }
         {
@@ -632,7 +653,7 @@ __device__ __forceinline__ void solve_stratum(const Params &P, const int i, cons
 
     // ---------------- Y fit (FP64) and the row (i, k) -----------------------
     if (threadIdx.x == 0) {
-        const double Md = (double)P.M;
+        const double Md = (double)Mk;
         const double dtd = P.dt;
         double *alpha = totB;                      // solved in place
         for (int a = 0; a < p; ++a) alpha[a] = totA[EG + EZ + a] + dtd * totB[a];
@@ -782,6 +803,7 @@ cudaError_t launch_prec(const Params &P, int i, bool lp1, int mv, int grid, int 
 
 }  // namespace
 
+#if SRMC_STEP_KIND == 0
 namespace {
 struct BatchLauncher {
     const BatchRound &B; int grid, threads; cudaStream_t st;
@@ -813,8 +835,15 @@ int SRMC_OCC_BATCH_NAME(SRMC_STEP_D)(bool fp64, bool lp1, int mv, bool cv, int t
     return dispatch_variant<float>(lp1, mv, cv, f);
 }
 
+#endif  // SRMC_STEP_KIND == 0
+
+#if SRMC_STEP_KIND == 0
 cudaError_t SRMC_LAUNCH_STEP_NAME(SRMC_STEP_D)(const Params &P, int i, bool fp64, bool lp1, int mv,
                                                 int grid, int threads, cudaStream_t st)
+#else
+cudaError_t SRMC_LAUNCH_STEP_PROB_NAME(SRMC_STEP_D)(const Params &P, int i, bool fp64, bool lp1, int mv,
+                                                     int grid, int threads, cudaStream_t st)
+#endif
 {
     return fp64 ? launch_prec<double>(P, i, lp1, mv, grid, threads, st)
                 : launch_prec<float>(P, i, lp1, mv, grid, threads, st);

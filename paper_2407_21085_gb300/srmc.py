@@ -23,6 +23,7 @@ STATUS = {0: "SRMC_OK", 1: "SRMC_ERR_INVALID_ARG", 2: "SRMC_ERR_CUDA", 3: "SRMC_
 MODELS = {"cos": 0, "logistic": 1, "affine": 2}
 BASES = {"lp0": 0, "lp1": 1}
 PRECISIONS = {"fp32": 0, "fp64": 1}
+STRATA = {"size": 0, "prob": 1}
 
 
 class SrmcError(RuntimeError):
@@ -39,13 +40,14 @@ class srmc_problem(C.Structure):
 
 class srmc_strata(C.Structure):
     _fields_ = [("cells", C.POINTER(C.c_int)), ("lo", C.POINTER(C.c_double)),
-                ("hi", C.POINTER(C.c_double)), ("mu", C.c_double)]
+                ("hi", C.POINTER(C.c_double)), ("mu", C.c_double), ("kind", C.c_int)]
 
 
 class srmc_config(C.Structure):
     _fields_ = [("basis", C.c_int), ("prec", C.c_int), ("M", C.c_longlong),
                 ("seed", C.c_ulonglong), ("instance", C.c_uint), ("Cy", C.c_double),
-                ("Cz", C.c_double), ("block_threads", C.c_int)]
+                ("Cz", C.c_double), ("block_threads", C.c_int),
+                ("M_strata", C.POINTER(C.c_longlong))]
 
 
 _lock = threading.Lock()
@@ -168,9 +170,13 @@ class Solver:
         self._hi = _darr(w.hi)
         pr = srmc_problem(d, q, int(w.N), float(w.T), self._b, self._sig, MODELS[w.model],
                           self._prm, len(w.params))
-        sa = srmc_strata(self._cells, self._lo, self._hi, float(w.mu))
+        sa = srmc_strata(self._cells, self._lo, self._hi, float(w.mu),
+                         STRATA.get(getattr(w, "strata", "size"), -1))
+        ms = getattr(w, "M_strata", None)
+        self._ms = None if ms is None else (C.c_longlong * len(ms))(*[int(v) for v in ms])
         cf = srmc_config(BASES[w.basis], PRECISIONS[w.precision], int(w.M), int(w.seed),
-                         int(w.instance), float(w.Cy), float(w.Cz), int(block_threads))
+                         int(w.instance), float(w.Cy), float(w.Cz), int(block_threads),
+                         self._ms)
         h = C.c_void_p()
         _check(L.srmc_create(C.byref(pr), C.byref(sa), C.byref(cf), C.byref(h)))
         self._h = h

@@ -21,7 +21,7 @@ import dataclasses
 import math
 import random
 from dataclasses import dataclass, field
-from typing import List
+from typing import List, Optional
 
 
 @dataclass
@@ -46,6 +46,8 @@ class Workload:
     instance: int = 0
     Cy: float = 0.0                # <= 0: no truncation of y
     Cz: float = 0.0                # <= 0: no truncation of z
+    strata: str = "size"           # "size": equal cells on [lo, hi); "prob": nu(H_k) = 1/K
+    M_strata: Optional[List[int]] = None   # paths of each stratum (overrides M), [K]
 
     def __post_init__(self):
         if self.q == 0:
@@ -64,8 +66,9 @@ class Workload:
         return self.T / self.N
 
     def path_steps(self) -> int:
-        """Stratum-path-steps of one full backward solve: K M N (N+1) / 2."""
-        return self.K * self.M * self.N * (self.N + 1) // 2
+        """Stratum-path-steps of one full backward solve: (sum_k M_k) N (N+1) / 2."""
+        paths = sum(self.M_strata) if self.M_strata is not None else self.K * self.M
+        return paths * self.N * (self.N + 1) // 2
 
     def replace(self, **kw) -> "Workload":
         w = dataclasses.replace(self, **kw)
@@ -174,37 +177,76 @@ ALL = {"cfg1": cfg1, "cfg2": cfg2, "cfg3": cfg3, "cfg5": cfg5}
 
 
 # ---- inputs of the control-variate form ---------------------------------------
-def centres(w: Workload):
-    """Stratum centres [K][d] (centre of the nominal finite cell), k with
-    dimension 0 fastest."""
+def _cell_index(w: Workload):
     import numpy as np
     idx = np.arange(w.K)
+    out = np.zeros((w.K, w.d), dtype=np.int64)
+    for l in range(w.d):
+        out[:, l] = idx % w.cells[l]
+        idx = idx // w.cells[l]
+    return out
+
+
+def _logistic_quantile(num, den, mu):
+    """F^{-1}(num / (num + den)) of the logistic law with scale mu."""
+    import numpy as np
+    return np.log(np.asarray(num, dtype=float) / np.asarray(den, dtype=float)) / mu
+
+
+def centres(w: Workload):
+    """Stratum centres [K][d], k with dimension 0 fastest: the centre of the
+    nominal finite cell (equal-size strata) or the median of nu restricted to
+    the cell (equal-probability strata)."""
+    import numpy as np
+    cells = _cell_index(w)
     out = np.zeros((w.K, w.d))
     for l in range(w.d):
-        c = idx % w.cells[l]
-        idx = idx // w.cells[l]
-        h = (w.hi[l] - w.lo[l]) / w.cells[l]
-        out[:, l] = w.lo[l] + (c + 0.5) * h
+        c = cells[:, l]
+        if w.strata == "prob":
+            C = w.cells[l]
+            out[:, l] = _logistic_quantile(c + 0.5, C - c - 0.5, w.mu)
+        else:
+            h = (w.hi[l] - w.lo[l]) / w.cells[l]
+            out[:, l] = w.lo[l] + (c + 0.5) * h
+    return out
+
+
+def cell_units(w: Workload):
+    """[K][d]: the unit of the centred basis coordinate of each stratum, h/2
+    (equal size) or the width between the quantiles (c + 1/4)/C and
+    (c + 3/4)/C of nu (equal probability)."""
+    import numpy as np
+    cells = _cell_index(w)
+    out = np.zeros((w.K, w.d))
+    for l in range(w.d):
+        c = cells[:, l]
+        if w.strata == "prob":
+            C = w.cells[l]
+            out[:, l] = (_logistic_quantile(c + 0.75, C - c - 0.75, w.mu)
+                         - _logistic_quantile(c + 0.25, C - c - 0.25, w.mu))
+        else:
+            out[:, l] = 0.5 * (w.hi[l] - w.lo[l]) / w.cells[l]
     return out
 
 
 def control_rows(w: Workload, fn):
     """Tabulate a control function fn(t, X[n][d]) -> [n][q] on the strata as
-    rows [N][K][q][p] in the centred basis [1, (x - c_k)/(h/2)]: the value at
-    the centre and, for LP1, central differences at c +- (h/4) e_m (a step of
-    one unit of the centred coordinate)."""
+    rows [N][K][q][p] in the centred basis [1, (x - c_k)/s_k] (centres and
+    units s_k as above): the value at the centre and, for LP1, central
+    differences at c +- (s_k/2) e_m (a step of one unit of the centred
+    coordinate)."""
     import numpy as np
     p = 1 if w.basis == "lp0" else w.d + 1
     ctr = centres(w)
-    h = (np.array(w.hi) - np.array(w.lo)) / np.array(w.cells)
+    unit = cell_units(w)
     rows = np.zeros((w.N, w.K, w.q, p))
     for j in range(w.N):
         t = j * w.T / w.N
         rows[j, :, :, 0] = fn(t, ctr)
         if p > 1:
             for m in range(w.d):
-                e = np.zeros(w.d)
-                e[m] = h[m] / 4
+                e = np.zeros((w.K, w.d))
+                e[:, m] = unit[:, m] / 2
                 rows[j, :, :, 1 + m] = fn(t, ctr + e) - fn(t, ctr - e)
     return rows
 

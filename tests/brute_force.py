@@ -51,10 +51,26 @@ def cells_of(w, k):
 
 
 def edges(w, l, c):
-    h = (w.hi[l] - w.lo[l]) / w.cells[l]
+    C = w.cells[l]
+    if getattr(w, "strata", "size") == "prob":
+        # equal nu-probability: cut at the logistic quantiles c/C
+        a = -math.inf if c == 0 else float(special.logit(c / C)) / w.mu
+        b = math.inf if c == C - 1 else float(special.logit((c + 1) / C)) / w.mu
+        return a, b
+    h = (w.hi[l] - w.lo[l]) / C
     a = -math.inf if c == 0 else w.lo[l] + c * h
-    b = math.inf if c == w.cells[l] - 1 else w.lo[l] + (c + 1) * h
+    b = math.inf if c == C - 1 else w.lo[l] + (c + 1) * h
     return a, b
+
+
+def centre_and_unit(w, l, c):
+    """Centre of cell c and the unit of the centred basis coordinate."""
+    C = w.cells[l]
+    if getattr(w, "strata", "size") == "prob":
+        q = lambda u: float(special.logit(u / C)) / w.mu
+        return q(c + 0.5), q(c + 0.75) - q(c + 0.25)
+    h = (w.hi[l] - w.lo[l]) / C
+    return w.lo[l] + (c + 0.5) * h, h / 2
 
 
 def start(w, i, k, m):
@@ -62,8 +78,11 @@ def start(w, i, k, m):
     cs = cells_of(w, k)
     for l in range(w.d):
         a, b = edges(w, l, cs[l])
-        Fa = 0.0 if a == -math.inf else special.expit(w.mu * a)
-        Fb = 1.0 if b == math.inf else special.expit(w.mu * b)
+        if getattr(w, "strata", "size") == "prob":
+            Fa, Fb = cs[l] / w.cells[l], (cs[l] + 1) / w.cells[l]
+        else:
+            Fa = 0.0 if a == -math.inf else special.expit(w.mu * a)
+            Fb = 1.0 if b == math.inf else special.expit(w.mu * b)
         U = unif(word(w, i, k, m, l))
         x[l] = special.logit(Fa + U * (Fb - Fa)) / w.mu
     return x
@@ -72,8 +91,13 @@ def start(w, i, k, m):
 def locate(w, x):
     k, stride = 0, 1
     for l in range(w.d):
-        h = (w.hi[l] - w.lo[l]) / w.cells[l]
-        c = int(min(max(math.floor((x[l] - w.lo[l]) / h), 0), w.cells[l] - 1))
+        if getattr(w, "strata", "size") == "prob":
+            c = 0
+            while c < w.cells[l] - 1 and x[l] >= edges(w, l, c + 1)[0]:
+                c += 1
+        else:
+            h = (w.hi[l] - w.lo[l]) / w.cells[l]
+            c = int(min(max(math.floor((x[l] - w.lo[l]) / h), 0), w.cells[l] - 1))
         k += c * stride
         stride *= w.cells[l]
     return k
@@ -116,9 +140,8 @@ def control_value(w, rows, j, k, x, dw):
     v = [1.0]
     if rows.shape[-1] > 1:
         for l in range(w.d):
-            h = (w.hi[l] - w.lo[l]) / w.cells[l]
-            c = w.lo[l] + (cs[l] + 0.5) * h
-            v.append((x[l] - c) / (h / 2))
+            c, unit = centre_and_unit(w, l, cs[l])
+            v.append((x[l] - c) / unit)
     v = np.array(v)
     return sum(clamp(float(rows[j, k, l] @ v), w.Cz) * dw[l] for l in range(w.q))
 
@@ -150,8 +173,9 @@ def solve(w, control=None):
 
     for i in range(N - 1, -1, -1):
         for k in range(w.K):
+            Mk = M if getattr(w, "M_strata", None) is None else int(w.M_strata[k])
             X0, DW, S1, Y1, CZ, CI = [], [], [], [], [], []
-            for m in range(M):
+            for m in range(Mk):
                 x = start(w, i, k, m)
                 X0.append(x.copy())
                 path = [x]
@@ -185,12 +209,12 @@ def solve(w, control=None):
                 DW.append(incs[0])
                 Y1.append(y_and_z(i + 1, path[1])[0])
             A = np.array([phi(x) for x in X0])
-            Bz = np.array([(S1[m] - CZ[m]) * DW[m] / dt for m in range(M)])
+            Bz = np.array([(S1[m] - CZ[m]) * DW[m] / dt for m in range(Mk)])
             beta = np.linalg.lstsq(A, Bz, rcond=None)[0].T          # q x p
             zi = [np.array([clamp(float(beta[l] @ phi(X0[m])), w.Cz) for l in range(q)])
-                  for m in range(M)]
+                  for m in range(Mk)]
             By = np.array([S1[m] + f(w, i, X0[m], Y1[m], zi[m]) * dt - CZ[m] - CI[m]
-                           for m in range(M)])
+                           for m in range(Mk)])
             alpha = np.linalg.lstsq(A, By, rcond=None)[0]
             rows[i][k] = (alpha, beta)
     return rows, y_and_z

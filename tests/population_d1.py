@@ -50,12 +50,19 @@ def population_solve(w, grid_step=0.02):
     sd = w.sigma[0][0] * math.sqrt(dt)
     shift = w.b[0] * dt
     C = w.cells[0]
-    h = (w.hi[0] - w.lo[0]) / C
-    inner = [w.lo[0] + c * h for c in range(1, C)]
-    p = 1 if w.basis == "lp0" else 2
+    if getattr(w, "strata", "size") == "prob":
+        # equal nu-probability cells: edges at the logistic quantiles c/C
+        inner = [math.log(c / (C - c)) / mu for c in range(1, C)]
 
-    def cell(x):
-        return np.clip(np.floor((x - w.lo[0]) / h), 0, C - 1).astype(int)
+        def cell(x):
+            return np.searchsorted(np.array(inner), x, side="right").astype(int)
+    else:
+        h = (w.hi[0] - w.lo[0]) / C
+        inner = [w.lo[0] + c * h for c in range(1, C)]
+
+        def cell(x):
+            return np.clip(np.floor((x - w.lo[0]) / h), 0, C - 1).astype(int)
+    p = 1 if w.basis == "lp0" else 2
 
     def phi(x):
         return np.ones((len(x), 1)) if p == 1 else np.stack([np.ones_like(x), x], axis=1)
@@ -76,8 +83,8 @@ def population_solve(w, grid_step=0.02):
     # Cell quadrature of nu_k (logistic density restricted to the cell).
     cellq = []
     for c in range(C):
-        a = -XMAX if c == 0 else w.lo[0] + c * h
-        b = XMAX if c == C - 1 else w.lo[0] + (c + 1) * h
+        a = -XMAX if c == 0 else inner[c - 1]
+        b = XMAX if c == C - 1 else inner[c]
         xs, ws = _nodes(a, b)
         dens = mu * np.exp(-mu * xs) / (1 + np.exp(-mu * xs)) ** 2
         wk = ws * dens

@@ -112,3 +112,11 @@ def test_batch_with_controls_equals_single_solves(dev, mode):
     for a, s in enumerate(solvers):
         y, z = _tables(torch, s)
         assert np.array_equal(y, single[a][0]) and np.array_equal(z, single[a][1]), (ws[a].name, how[a])
+
+
+def test_batch_rejects_equal_probability_strata(dev):
+    torch, srmc = dev
+    s = srmc.Solver(W.cfg2(C=4, N=2, M=64).replace(strata="prob"))
+    with pytest.raises(srmc.SrmcError) as e:
+        srmc.Batch([s])
+    assert e.value.status == 4

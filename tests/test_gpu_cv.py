@@ -219,3 +219,12 @@ def test_own_control_cuts_the_spread_on_gpu(dev):
     assert np.mean(so[inner]) < 0.6 * np.mean(sp[inner]), (np.mean(so[inner]), np.mean(sp[inner]))
     dm = np.abs(np.mean(ys["plain"], axis=0) - np.mean(ys["own"], axis=0))[inner]
     assert np.mean(dm) < 3 * np.mean(np.sqrt(sp ** 2 + so ** 2)[inner]) / np.sqrt(8)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_controls_on_equal_probability_strata(dev, orc, prec):
+    # control rows in the centred basis of equal-probability cells (median
+    # centre, quantile unit) and the run's own control
+    w = W.cfg2(C=7, N=5, M=256, precision=prec).replace(strata="prob")
+    _cv_parity(dev, orc, w, W.closed_form_z(w))
+    _own_parity(dev, orc, w)

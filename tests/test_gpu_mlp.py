@@ -71,11 +71,13 @@ def test_mlp_loss_gradient_vs_oracle(dev, orc, nin):
         assert _rel(g[s:e], gr[s:e]) < 2e-2, (name, _rel(g[s:e], gr[s:e]))
 
 
-def test_tabulated_control_rows_vs_oracle(dev, orc):
+@pytest.mark.parametrize("strata", ["size", "prob"])
+def test_tabulated_control_rows_vs_oracle(dev, orc, strata):
     # Control rows from the network on the GPU vs the same rows computed from
-    # the oracle's network at the same points (centre, +-h/4 per axis).
+    # the oracle's network at the same points (basis centre, +- half a basis
+    # unit per axis: h/4 for equal-size cells).
     torch, srmc = dev
-    w = W.cos_model("tab", d=3, N=4, C=3, a=2.0, M=64, s0=0.35, lam=0.2, kap=0.5)
+    w = W.cos_model("tab", d=3, N=4, C=3, a=2.0, M=64, s0=0.35, lam=0.2, kap=0.5).replace(strata=strata)
     prm = _params(4, 64, seed=21)
     net = srmc.MLP(4)
     net.srmc_mlp_set_params(prm)

@@ -114,6 +114,35 @@ def test_uneven_cells_in_morton_order(dev, orc, prec):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_equal_probability_strata(dev, orc, prec):
+    # nu(H_k) = 1/K (assumption HS, example ii): cos model in d = 1, 2, 3 (with
+    # z in the driver, LP0 too) and the paper's logistic model in d = 2.
+    cases = [W.cfg1(C=9, N=5, M=300).replace(strata="prob"),
+             W.cfg2(C=7, N=5, M=384, kapz=0.2).replace(strata="prob"),
+             W.cos_model("p3", d=3, N=3, C=4, a=1.0, M=200, s0=0.3, lam=0.2, kap=0.5,
+                         kapz=0.1).replace(strata="prob", cells=[3, 5, 4]),
+             W.logistic_paper(d=2, N=4, C=5, M=300).replace(strata="prob")]
+    if prec == "fp64":
+        cases.append(W.cfg2(C=6, N=4, M=256, basis="lp0").replace(strata="prob"))
+    for w in cases:
+        _full_parity(dev, orc, w.replace(precision=prec))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_per_stratum_path_counts(dev, orc, prec):
+    # M_k varying with the stratum (the minimum p = 3, a ragged 257, and
+    # random counts up to 600), with and without z in the driver; the path-step
+    # count of the solve is sum_k M_k N (N+1) / 2.
+    rng = np.random.default_rng(9)
+    for w in (W.cfg2(C=6, N=4, M=300, precision=prec), W.cfg3(C=2, N=3, M=64, precision=prec)):
+        Ms = rng.integers(w.d + 1, 600, size=w.K).tolist()
+        Ms[0], Ms[1] = w.d + 1, 257
+        w = w.replace(M_strata=Ms)
+        s, _ = _full_parity(dev, orc, w)
+        assert s.srmc_stats()["path_steps"] == w.path_steps()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_paper_logistic_model(dev, orc, prec):
     # The test BSDE of Sec. 5.1 (driver uses sum z), d=3, strata on [-6.5,6.5]^3
     _full_parity(dev, orc, W.logistic_paper(d=3, N=4, C=3, M=200, precision=prec))
@@ -189,6 +218,13 @@ def test_invalid_arguments(dev):
     assert e.value.status == 4
     with pytest.raises(srmc.SrmcError) as e:
         srmc.Solver(W.cfg2(M=64), block_threads=48)
+    assert e.value.status == 1
+    w4 = W.cfg2(C=2, N=2, M=64)
+    with pytest.raises(srmc.SrmcError) as e:
+        srmc.Solver(w4.replace(M_strata=[64, 2, 64, 64]))   # one M_k below d + 1
+    assert e.value.status == 1
+    with pytest.raises(srmc.SrmcError) as e:
+        srmc.Solver(w4.replace(strata="bogus"))               # unknown strata kind
     assert e.value.status == 1
     s = srmc.Solver(W.cfg2(C=4, N=5, M=64))
     with pytest.raises(srmc.SrmcError) as e:

@@ -128,3 +128,61 @@ def test_start_points(dev, orc, prec):
         inside = np.mean(kk.cpu().numpy() == k)
         # single-precision draws may round onto an edge with probability ~1e-6
         assert inside == 1.0 if prec == "fp64" else inside >= 0.99
+
+
+# ---- equal-probability strata (assumption HS, example ii) --------------------
+
+def _prob_workloads():
+    return [W.cfg1().replace(strata="prob", cells=[9]),
+            W.cfg3(C=5, N=4).replace(strata="prob", cells=[3, 7, 5, 4])]
+
+
+@pytest.mark.parametrize("n", [0, 1])
+def test_prob_locate_bit_exact_fp64_and_fp32(dev, orc, n):
+    # FP64: the oracle's edge scan and the kernel's CDF guess + one edge
+    # comparison take the same decision everywhere, exact edges and their
+    # neighbouring doubles included.  FP32: the kernel's decision equals the
+    # cell of x among the edges rounded to float.
+    torch, srmc = dev
+    w = _prob_workloads()[n]
+    s = srmc.Solver(w.replace(M=max(w.d + 1, 8)))
+    rng = np.random.default_rng(7)
+    pts = [rng.logistic(size=(3000, w.d)) * 1.5]
+    for l in range(w.d):
+        for c in range(1, w.cells[l]):
+            e = orc.cell_edges(w, l, c)[0]
+            for v in (e, np.nextafter(e, -np.inf), np.nextafter(e, np.inf)):
+                p = rng.logistic(size=(1, w.d))
+                p[0, l] = v
+                pts.append(p)
+    big = np.zeros((4, w.d)); big[0] = 1e300; big[1] = -1e300; big[2] = np.inf; big[3] = -np.inf
+    pts.append(big)
+    x = np.concatenate(pts)
+    k = torch.empty(len(x), dtype=torch.int64, device="cuda")
+    s.srmc_locate(torch.from_numpy(x).cuda(), k)
+    assert np.array_equal(k.cpu().numpy(), np.array([orc.locate(w, p) for p in x]))
+    xf = x.astype(np.float32)
+    s.srmc_locate(torch.from_numpy(xf).cuda(), k)
+    stride = np.cumprod([1] + list(w.cells[:-1]))
+    want = np.zeros(len(xf), dtype=np.int64)
+    for l in range(w.d):
+        ef = np.array([np.float32(orc.cell_edges(w, l, c)[0]) for c in range(1, w.cells[l])])
+        want += np.searchsorted(ef, xf[:, l], side="right") * stride[l]
+    assert np.array_equal(k.cpu().numpy(), want)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_prob_start_points_and_centres(dev, orc, prec):
+    torch, srmc = dev
+    w = _prob_workloads()[1].replace(precision=prec)
+    s = srmc.Solver(w)
+    c = s.centres().cpu().numpy()
+    assert np.allclose(c, W.centres(w), rtol=1e-15, atol=1e-15)
+    assert np.allclose(c, np.array([orc.stratum_centre(w, k) for k in range(w.K)]), rtol=1e-15, atol=1e-15)
+    rng = np.random.default_rng(8)
+    for (i, k) in [(0, 0), (3, w.K - 1), (2, int(rng.integers(0, w.K)))]:
+        x = torch.empty((257, w.d), dtype=torch.float64, device="cuda")
+        s.srmc_start_points(i, k, 5, x)
+        want = np.array([orc.start_point(w, i, k, 5 + a) for a in range(257)])
+        tol = 1e-13 if prec == "fp64" else 2e-6
+        assert np.allclose(x.cpu().numpy(), want, rtol=tol, atol=tol)

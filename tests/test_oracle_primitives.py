@@ -185,6 +185,72 @@ def test_start_points_lie_in_their_stratum(orc):
         assert orc.locate(w, orc.start_point(w, i, k, m)) == k
 
 
+# ---- equal-probability strata (assumption HS, example ii) --------------------
+
+def _prob(w, C=None):
+    return w.replace(strata="prob", cells=[C or c for c in w.cells])
+
+
+@pytest.mark.parametrize("C", [1, 2, 3, 7, 16])
+def test_prob_strata_have_equal_nu_mass(orc, C):
+    # nu(H_k) = 1/K: every cell of every axis has logistic mass 1/C (scipy's
+    # logistic CDF at the oracle's edges); the edges increase; centre = the
+    # median of the restricted law; the basis unit is positive and finite.
+    for mu in (1.0, 0.6):
+        w = _prob(W.cfg1(), C).replace(mu=mu)
+        prev = -math.inf
+        for c in range(C):
+            a, b = orc.cell_edges(w, 0, c)
+            assert a == prev and a < b
+            prev = b
+            mass = stats.logistic.cdf(mu * b) - stats.logistic.cdf(mu * a)
+            assert abs(mass - 1.0 / C) < 1e-14
+            ctr = orc.stratum_centre(w, c)[0]
+            assert abs(stats.logistic.cdf(mu * ctr) - (c + 0.5) / C) < 1e-14
+            q = lambda u: stats.logistic.ppf(u) / mu
+            assert math.isclose(orc.cell_scale(w, 0, c), q((c + 0.75) / C) - q((c + 0.25) / C), rel_tol=1e-12)
+        assert prev == math.inf
+
+
+def test_prob_locate_edges_and_scan(orc):
+    # Half-open cells at the oracle's own edges: the edge value belongs to the
+    # upper cell, the next double below to the lower one; random points agree
+    # with scipy's logistic CDF (floor(C F(x))) away from the edges.
+    w = _prob(W.cfg1(), 9)
+    for c in range(1, 9):
+        e = orc.cell_edges(w, 0, c)[0]
+        assert orc.locate_dim(w, 0, e) == c
+        assert orc.locate_dim(w, 0, np.nextafter(e, -np.inf)) == c - 1
+    assert orc.locate_dim(w, 0, -1e300) == 0 and orc.locate_dim(w, 0, 1e300) == 8
+    assert orc.locate_dim(w, 0, float("nan")) == 0
+    rng = np.random.default_rng(4)
+    for x in rng.logistic(size=3000) * 1.5:
+        t = 9 * stats.logistic.cdf(x)
+        if abs(t - round(t)) < 1e-9:
+            continue
+        assert orc.locate_dim(w, 0, x) == min(int(math.floor(t)), 8)
+
+
+def test_prob_start_points_follow_the_restricted_law(orc):
+    # Start points of an outer and an inner cell lie in the cell and follow nu
+    # restricted to it (KS against scipy's logistic law); they also match the
+    # second restatement.
+    w = _prob(W.cfg1(), 6)
+    for c in (0, 2, 5):
+        a, b = orc.cell_edges(w, 0, c)
+        xs = np.array([orc.start_point(w, 3, c, m)[0] for m in range(4000)])
+        assert np.all((xs >= a) & (xs < b))
+        Fa, Fb = c / 6, (c + 1) / 6
+        assert stats.kstest(xs, lambda x: (stats.logistic.cdf(x) - Fa) / (Fb - Fa)).pvalue > 1e-3
+    w2 = _prob(W.cfg3(), 5)
+    rng = np.random.default_rng(5)
+    for _ in range(200):
+        k = int(rng.integers(0, w2.K)); m = int(rng.integers(0, 999)); i = int(rng.integers(0, w2.N))
+        x = orc.start_point(w2, i, k, m)
+        assert orc.locate(w2, x) == k
+        assert np.allclose(x, bf.start(w2, i, k, m), rtol=1e-12, atol=1e-13)
+
+
 def test_householder_lstsq_vs_lapack(orc):
     rng = np.random.default_rng(4)
     for (n, p, r) in [(50, 3, 2), (7, 7, 1), (1000, 5, 4), (3, 1, 1)]:

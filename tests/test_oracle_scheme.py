@@ -69,6 +69,9 @@ BF_CASES = [
     dict(d=1, N=2, C=4, M=8, kapz=0.4, basis="lp1"),
     dict(d=2, N=2, C=2, M=6, kapz=0.3, basis="lp1"),
     dict(d=2, N=3, C=2, M=4, kapz=0.0, basis="lp0"),
+    dict(d=1, N=3, C=4, M=6, kapz=0.2, basis="lp1", strata="prob"),
+    dict(d=2, N=2, C=3, M=6, kapz=0.0, basis="lp1", strata="prob"),
+    dict(d=2, N=3, C=2, M=9, kapz=0.1, basis="lp1", M_strata=[3, 9, 5, 7]),
 ]
 _BF = {}
 
@@ -76,7 +79,8 @@ _BF = {}
 def _bf_workload(case):
     w = W.cos_model("bf", d=case["d"], N=case["N"], C=case["C"], a=1.0, M=case["M"], s0=0.5,
                     lam=0.5, kap=0.4, kapz=case["kapz"], basis=case["basis"], seed=11, instance=3)
-    return w.replace(Cy=1.5, Cz=1.2)       # active truncation somewhere
+    return w.replace(Cy=1.5, Cz=1.2, strata=case.get("strata", "size"),   # active truncation somewhere
+                     M_strata=case.get("M_strata"))
 
 
 def _brute_force_mismatch(orc, n, library=None):
@@ -104,10 +108,10 @@ def test_brute_force_tiny(orc, n):
     assert _brute_force_mismatch(orc, n) < 1e-10
 
 
-def _population_case(Cy, Cz, basis):
+def _population_case(Cy, Cz, basis, strata="size"):
     w = W.cos_model("pop", d=1, N=3, C=4, a=1.0, M=20000, s0=0.5, lam=0.5, kap=0.5,
                     kapz=0.3, basis=basis, seed=5)
-    return w.replace(Cy=Cy, Cz=Cz)
+    return w.replace(Cy=Cy, Cz=Cz, strata=strata)
 
 
 _POP = {}
@@ -144,7 +148,7 @@ def _population_discrepancy(orc, case, library=None, R=6):
     return worst
 
 
-POP_CASES = [(3.3, 5.7, "lp1"), (0.9, 0.35, "lp1"), (3.3, 5.7, "lp0")]
+POP_CASES = [(3.3, 5.7, "lp1"), (0.9, 0.35, "lp1"), (3.3, 5.7, "lp0"), (3.3, 5.7, "lp1", "prob")]
 
 
 @pytest.mark.parametrize("case", POP_CASES)
