@@ -60,7 +60,10 @@ typedef enum { SRMC_FP32 = 0, SRMC_FP64 = 1 } srmc_precision;
  *   SRMC_MODEL_COS:      {lam, kap, kapz, s0};  g(x) = cos(s), s = sum_l x_l / sqrt(d),
  *                        f_j(x,y,z) = (lam + s0^2/2) y + kap (y^2 - u(t_j,x)^2)
  *                                     + kapz (|z|^2 - s0^2 e^{2 lam (T-t_j)} sin^2 s),
- *                        u(t,x) = e^{lam (T-t)} cos(s) solves the PDE when sigma = s0 I.
+ *                                     - (1/s0) sum_l b_l(x) z_l,
+ *                        u(t,x) = e^{lam (T-t)} cos(s) solves the PDE when sigma = s0 I
+ *                        (the last term cancels the drift b(x).grad u; it vanishes
+ *                        without drift).
  *   SRMC_MODEL_LOGISTIC: {} ; the test BSDE of Sec. 5.1: w = exp(t + sum x),
  *                        g = w(T,x)/(1+w(T,x)), f = (sum_l z_l)(y - (2+q)/(2q)).
  *   SRMC_MODEL_AFFINE:   {g0, g_1..g_d, f0, f_1..f_d, a}; g = g0 + g.x,
@@ -68,9 +71,21 @@ typedef enum { SRMC_FP32 = 0, SRMC_FP64 = 1 } srmc_precision;
 typedef enum { SRMC_MODEL_COS = 0, SRMC_MODEL_LOGISTIC = 1, SRMC_MODEL_AFFINE = 2 } srmc_model;
 
 /* Forward SDE, driver, terminal condition and time grid (Sec. 1-2).
- * b: [d] constant drift (host).  sigma: [d*q] row-major constant diffusion
+ * Drift b_l(x) = b_l - theta_l x_l (theta = 0: constant drift; theta > 0:
+ * Ornstein-Uhlenbeck, mean reverting to b_l/theta_l).  b: [d] (host).
+ * theta: [d] (host) or NULL for 0.  sigma: [d*q] row-major constant diffusion
  * (host); this build requires q == d and a diagonal sigma, else
- * SRMC_ERR_UNSUPPORTED.  params: [n_params <= SRMC_PMAX] (host). */
+ * SRMC_ERR_UNSUPPORTED.  params: [n_params <= SRMC_PMAX] (host).
+ * dynamics: how X moves between grid times (assumption HX):
+ *   SRMC_DYN_EULER (Alg. 2): X_{j+1} = X_j + b(X_j) dt + sigma dW_j;
+ *   SRMC_DYN_EXACT (Alg. 1): the SDE itself, X_{j+1,l} = X_{j,l} e^{-theta_l dt}
+ *     + b_l B_l + sigma_l I_l with B_l = (1 - e^{-theta_l dt})/theta_l and
+ *     I_l = int e^{-theta_l (t_{j+1} - s)} dW_s, drawn jointly with dW_j: given
+ *     dW_j, I_l = (B_l/dt) dW_{j,l} + r_l xi_l with r_l^2 = Var I_l - B_l^2/dt,
+ *     xi a second standard normal per coordinate and step (draws d + 2(j-i)q + q
+ *     + l; dW_j takes d + 2(j-i)q + l).  Equal-size strata only; identical to
+ *     Euler when theta = 0 up to the draw layout. */
+typedef enum { SRMC_DYN_EULER = 0, SRMC_DYN_EXACT = 1 } srmc_dynamics;
 typedef struct {
     int d, q;
     int N;
@@ -80,6 +95,8 @@ typedef struct {
     srmc_model model;
     const double *params;
     int n_params;
+    const double *theta;
+    int dynamics;              /* srmc_dynamics */
 } srmc_problem;
 
 /* Strata (assumption HS): cells[l] half-open cells per dimension, stratum

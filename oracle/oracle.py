@@ -26,6 +26,7 @@ PMAX = 24
 MODELS = {"cos": 0, "logistic": 1, "affine": 2}
 BASES = {"lp0": 0, "lp1": 1}
 STRATA = {"size": 0, "prob": 1}
+DYNAMICS = {"euler": 0, "exact": 1}
 
 _lock = threading.Lock()
 _lib = None
@@ -54,6 +55,7 @@ class _Problem(C.Structure):
         ("mu", C.c_double), ("basis", C.c_int), ("M", C.c_int64),
         ("seed", C.c_uint64), ("instance", C.c_uint32), ("Cy", C.c_double), ("Cz", C.c_double),
         ("strata", C.c_int), ("M_strata", C.POINTER(C.c_int64)),
+        ("theta", C.c_double * DMAX), ("dynamics", C.c_int),
     ]
 
 
@@ -153,6 +155,9 @@ def to_struct(w) -> _Problem:
     p.instance = int(w.instance)
     p.Cy, p.Cz = float(w.Cy), float(w.Cz)
     p.strata = STRATA[getattr(w, "strata", "size")]
+    for l, v in enumerate(getattr(w, "theta", None) or []):
+        p.theta[l] = float(v)
+    p.dynamics = DYNAMICS[getattr(w, "dynamics", "euler")]
     ms = getattr(w, "M_strata", None)
     if ms is not None:
         arr = np.ascontiguousarray(ms, dtype=np.int64)

@@ -254,6 +254,24 @@ double orc_cell_scale(const orc_problem *P, int l, int c)
     return 0.5 * cell_width(P, l);
 }
 
+/* Exact transition of one coordinate of dX = (b - theta X) dt + s dW over dt
+ * (Alg. 1): X' = X A + b B + s I with A = e^{-theta dt}, where the Ito integral
+ * I = int_0^dt e^{-theta (dt - u)} dW_u is Gaussian with Var I =
+ * (1 - e^{-2 theta dt})/(2 theta) and Cov(I, dW) = B = (1 - e^{-theta dt})/theta.
+ * Given dW, I = (B/dt) dW + r xi2 with r^2 = Var I - B^2/dt and xi2 ~ N(0,1)
+ * independent of dW.  theta = 0 gives A = 1, B = dt, I = dW (Brownian). */
+static void ou_coeffs(double theta, double dt, double *A, double *B, double *r)
+{
+    if (theta == 0.0) { *A = 1.0; *B = dt; *r = 0.0; return; }
+    const double a = theta * dt;
+    *A = exp(-a);
+    *B = -expm1(-a) / theta;
+    double r2;
+    if (fabs(a) < 1e-4) r2 = dt * a * a / 12.0 * (1.0 - a);   /* series; the difference cancels */
+    else r2 = -expm1(-2.0 * a) / (2.0 * theta) - (*B) * (*B) / dt;
+    *r = sqrt(r2 > 0.0 ? r2 : 0.0);
+}
+
 /* Start point of path m of cloud C_{i,k}: draws 0..d-1, one per coordinate
  * (Alg. 3). */
 void orc_start_point(const orc_problem *P, int i, int64_t k, int64_t m, double *x)
@@ -317,6 +335,15 @@ double orc_f(const orc_problem *P, int j, const double *x, double y, const doubl
         double e = exp(lam * (P->T - tj));
         double u = e * cos(s);
         double v = (lam + 0.5 * s0 * s0) * y + kap * (y * y - u * u);
+        /* with a drift b(x) = b - theta x the generator adds b(x).grad u =
+         * b(x).z / s0 (z = s0 grad u), which the driver cancels */
+        double bz = 0.0;
+        int drift = 0;
+        for (int l = 0; l < P->d; ++l) {
+            if (P->b[l] != 0.0 || P->theta[l] != 0.0) drift = 1;
+            bz += (P->b[l] - P->theta[l] * x[l]) * z[l];
+        }
+        if (drift) v -= bz / s0;
         if (kapz != 0.0) {
             double zz = 0.0;
             for (int l = 0; l < P->q; ++l) zz += z[l] * z[l];
@@ -554,6 +581,7 @@ static int64_t fit_impl(orc_ctx *C, int i, int64_t k, int lazy)
     double *coef = (double *)malloc(sizeof(double) * (size_t)(p * (q > 1 ? q : 1)));
     double row[(1 + ORC_DMAX) * (1 + ORC_DMAX)];
     int64_t steps = 0;
+    const int nw = P->dynamics == ORC_EXACT ? 2 : 1;   /* normal blocks per step */
 
     for (int64_t m = 0; m < M; ++m) {
         double x[ORC_DMAX], xn[ORC_DMAX], dw[ORC_DMAX], zj[ORC_DMAX], zn[ORC_DMAX];
@@ -562,14 +590,27 @@ static int64_t fit_impl(orc_ctx *C, int i, int64_t k, int lazy)
         for (int l = 0; l < d; ++l) X0[m * d + l] = x[l];
         double S = 0.0;
         for (int j = i; j < N; ++j) {
-            /* Delta W_j = sqrt(dt) xi, xi ~ N(0, I_q), draws d + (j-i) q + l. */
+            /* Delta W_j = sqrt(dt) xi, xi ~ N(0, I_q): draws d + (j-i) nw q + l;
+             * the exact dynamics takes q more normals per step (xi2, next q draws). */
+            const int64_t base = d + (int64_t)(j - i) * nw * q;
             for (int l = 0; l < q; ++l)
-                dw[l] = sdt * orc_normal_from_word(orc_draw_word(P, i, k, m, d + (int64_t)(j - i) * q + l));
-            /* Euler step, Alg. 2, read with the coefficients at (t_j, X_j). */
-            for (int l = 0; l < d; ++l) {
-                double v = x[l] + P->b[l] * dt;
-                for (int r = 0; r < q; ++r) v += P->sigma[l * q + r] * dw[r];
-                xn[l] = v;
+                dw[l] = sdt * orc_normal_from_word(orc_draw_word(P, i, k, m, base + l));
+            if (P->dynamics == ORC_EXACT) {
+                /* Alg. 1, per coordinate (diagonal sigma) */
+                for (int l = 0; l < d; ++l) {
+                    const double xi2 = orc_normal_from_word(orc_draw_word(P, i, k, m, base + q + l));
+                    double A, B, r;
+                    ou_coeffs(P->theta[l], dt, &A, &B, &r);
+                    const double I = (B / dt) * dw[l] + r * xi2;
+                    xn[l] = x[l] * A + P->b[l] * B + P->sigma[l * q + l] * I;
+                }
+            } else {
+                /* Euler step, Alg. 2, read with the coefficients at (t_j, X_j). */
+                for (int l = 0; l < d; ++l) {
+                    double v = x[l] + (P->b[l] - P->theta[l] * x[l]) * dt;
+                    for (int r = 0; r < q; ++r) v += P->sigma[l * q + r] * dw[r];
+                    xn[l] = v;
+                }
             }
             steps++;
             if (C->control) {

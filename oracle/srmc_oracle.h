@@ -10,14 +10,20 @@
  *
  * What it computes, with the passage it follows:
  *   - time grid t_i = i*dt, dt = T/N                               (Sec. 2, eq. MDP)
- *   - Euler Markov chain X_{j+1} = X_j + b dt + sigma dW_j          (Alg. 2, "Euler dynamics")
- *   - equal-size hypercube strata, exterior cells infinite          (assumption A_Strat)
+ *   - Euler Markov chain X_{j+1} = X_j + b(X_j) dt + sigma dW_j     (Alg. 2, "Euler dynamics")
+ *     with the affine drift b(x) = b - theta x, or the exact
+ *     transition of that SDE (Ornstein-Uhlenbeck)                   (Alg. 1, "SDE dynamics")
+ *   - equal-size hypercube strata, exterior cells infinite, or
+ *     strata of equal nu-probability                                (assumption HS, i and ii)
  *   - logistic law nu, restricted law nu_k, inverse-CDF sampler     (assumption A_nu, Alg. 3)
  *   - fresh, independent clouds C_{i,k} of M paths                  (Def. "Simulations and empirical measures")
  *   - backward SRMDP recursion: Z-OLS then Y-OLS, truncation T_L    (Alg. SRMDP, eq. PsiM; eq. TL)
  *   - LP0 as the mean, LP1 by Householder QR of A=[1, x_i]          (Sec. 4.1, eqs. lp0/lp1 explicit)
  *   - Philox-4x32-10 counter RNG from its published definition      (Salmon, Moraes, Dror, Shaw, SC'11)
  *   - standard normal by inversion, Phi^{-1}(U), one uniform each
+ *   - martingale controls subtracted from the responses (tabulated rows or
+ *     the run's own fitted z) and a small MLP with bf16 emulation: extensions
+ *     of the method, not in the paper
  *
  * Parity pins of every function live in tests/test_oracle_*.py.
  */
@@ -37,13 +43,16 @@ enum { ORC_LP0 = 0, ORC_LP1 = 1 };
 /* Strata (assumption HS): equal size on the box [lo, hi) (example i), or equal
  * probability under nu, nu(H_k) = 1/K (example ii; lo and hi unused). */
 enum { ORC_STRATA_SIZE = 0, ORC_STRATA_PROB = 1 };
+/* Markov chain between grid times (Sec. 2, assumption HX): the Euler scheme
+ * (Alg. 2) or the SDE itself (Alg. 1, exact for the affine drift below). */
+enum { ORC_EULER = 0, ORC_EXACT = 1 };
 
 /* One SRMC problem: forward SDE, driver/terminal model, grid, strata, basis. */
 typedef struct {
     int d, q;                       /* dim of X and of W                     */
     int N;                          /* number of time steps                  */
     double T;                       /* horizon                               */
-    double b[ORC_DMAX];             /* constant drift                        */
+    double b[ORC_DMAX];             /* drift b_l - theta_l x_l (constant part) */
     double sigma[ORC_DMAX * ORC_DMAX]; /* constant diffusion, row-major d x q */
     int model;                      /* ORC_MODEL_*                           */
     double params[ORC_PMAX];        /* model parameters (see srmc_oracle.c)  */
@@ -57,6 +66,8 @@ typedef struct {
     double Cy, Cz;                  /* truncation levels; <= 0 disables      */
     int strata;                     /* ORC_STRATA_SIZE / ORC_STRATA_PROB     */
     const int64_t *M_strata;        /* [K] paths of each stratum, or NULL: M */
+    double theta[ORC_DMAX];         /* mean reversion of the drift (0: constant) */
+    int dynamics;                   /* ORC_EULER / ORC_EXACT (diagonal sigma)  */
 } orc_problem;
 
 /* ---- primitives ---------------------------------------------------------- */

@@ -212,6 +212,8 @@ srmc_status srmc_batch_create(srmc_solver *const *solvers, int n, srmc_batch **o
         if (solvers[r]->fp64) return bfail(SRMC_ERR_UNSUPPORTED, "srmc_batch_create: FP32 solvers only");
         if (solvers[r]->P.kind != 0)
             return bfail(SRMC_ERR_UNSUPPORTED, "srmc_batch_create: equal-size strata only");
+        if (solvers[r]->exact)
+            return bfail(SRMC_ERR_UNSUPPORTED, "srmc_batch_create: Euler dynamics only");
         if (solvers[r]->device != dev) return bfail(SRMC_ERR_INVALID_ARG, "srmc_batch_create: solver on another device");
     }
     srmc_batch *b = new srmc_batch();

@@ -52,6 +52,22 @@ double logistic_cdf(double x, double mu)
 
 int pad_to(int v, int m) { return (v + m - 1) / m * m; }
 
+// Exact step over dt of dX = (b - theta X) dt + s dW (Alg. 1): X' = A X + b B
+// + s I, where the stochastic integral I = int_0^dt e^{-theta (dt - u)} dW_u has
+// Var I = (1 - e^{-2 theta dt}) / (2 theta) and Cov(I, dW) = B =
+// (1 - e^{-theta dt}) / theta; given dW, I = (B/dt) dW + r xi with
+// r^2 = Var I - B^2/dt (a second-order series where the two nearly cancel).
+void ou_transition(double theta, double dt, double &A, double &B, double &r)
+{
+    if (theta == 0.0) { A = 1.0; B = dt; r = 0.0; return; }
+    const double a = theta * dt;
+    A = std::exp(-a);
+    B = -std::expm1(-a) / theta;
+    const double r2 = std::fabs(a) < 1e-4 ? dt * a * a / 12.0 * (1.0 - a)
+                                          : -std::expm1(-2.0 * a) / (2.0 * theta) - B * B / dt;
+    r = std::sqrt(r2 > 0.0 ? r2 : 0.0);
+}
+
 // F^{-1}(num / (num + den)) of the logistic law with scale mu.
 double logistic_quantile(double num, double den, double mu) { return std::log(num / den) / mu; }
 
@@ -111,6 +127,19 @@ cudaError_t launch_step(const srmc_solver *s, int i, cudaStream_t st)
     P.cv_own = s->cv && s->cv_own ? 1 : 0;
     const int mv = srmc::kernel_mv(s);
     const int grid = (int)(P.K < 2147483647LL ? P.K : 2147483647LL);
+    if (s->exact) {
+        switch (P.d) {
+        case 1: return srmc::launch_step_exact_d1(P, i, s->fp64, s->lp1, mv, grid, s->threads, st);
+        case 2: return srmc::launch_step_exact_d2(P, i, s->fp64, s->lp1, mv, grid, s->threads, st);
+        case 3: return srmc::launch_step_exact_d3(P, i, s->fp64, s->lp1, mv, grid, s->threads, st);
+        case 4: return srmc::launch_step_exact_d4(P, i, s->fp64, s->lp1, mv, grid, s->threads, st);
+        case 5: return srmc::launch_step_exact_d5(P, i, s->fp64, s->lp1, mv, grid, s->threads, st);
+        case 6: return srmc::launch_step_exact_d6(P, i, s->fp64, s->lp1, mv, grid, s->threads, st);
+        case 7: return srmc::launch_step_exact_d7(P, i, s->fp64, s->lp1, mv, grid, s->threads, st);
+        case 8: return srmc::launch_step_exact_d8(P, i, s->fp64, s->lp1, mv, grid, s->threads, st);
+        }
+        return cudaErrorInvalidValue;
+    }
     if (P.kind != 0) {
         switch (P.d) {
         case 1: return srmc::launch_step_prob_d1(P, i, s->fp64, s->lp1, mv, grid, s->threads, st);
@@ -309,6 +338,14 @@ srmc_status srmc_create(const srmc_problem *pr, const srmc_strata *sa, const srm
                 return fail(SRMC_ERR_UNSUPPORTED, "this build requires a diagonal sigma");
     if (pr->model < SRMC_MODEL_COS || pr->model > SRMC_MODEL_AFFINE)
         return fail(SRMC_ERR_INVALID_ARG, "unknown model");
+    if (pr->dynamics != SRMC_DYN_EULER && pr->dynamics != SRMC_DYN_EXACT)
+        return fail(SRMC_ERR_INVALID_ARG, "unknown dynamics");
+    bool has_drift = false;
+    for (int l = 0; l < d; ++l) {
+        const double th = pr->theta ? pr->theta[l] : 0.0;
+        if (!std::isfinite(th) || !std::isfinite(pr->b[l])) return fail(SRMC_ERR_INVALID_ARG, "b and theta must be finite");
+        has_drift = has_drift || th != 0.0 || pr->b[l] != 0.0;
+    }
     if (pr->n_params < 0 || pr->n_params > SRMC_PMAX || (pr->n_params > 0 && !pr->params))
         return fail(SRMC_ERR_INVALID_ARG, "params: n_params must be in [0, 24]");
     const int need = pr->model == SRMC_MODEL_COS ? 4 : pr->model == SRMC_MODEL_AFFINE ? 3 + 2 * d : 0;
@@ -316,6 +353,8 @@ srmc_status srmc_create(const srmc_problem *pr, const srmc_strata *sa, const srm
     if (sa->kind != SRMC_STRATA_EQUAL_SIZE && sa->kind != SRMC_STRATA_EQUAL_PROB)
         return fail(SRMC_ERR_INVALID_ARG, "unknown strata kind");
     const bool prob = sa->kind == SRMC_STRATA_EQUAL_PROB;
+    if (prob && pr->dynamics == SRMC_DYN_EXACT)
+        return fail(SRMC_ERR_UNSUPPORTED, "exact dynamics are built for equal-size strata only");
     if (!sa->cells || (!prob && (!sa->lo || !sa->hi)))
         return fail(SRMC_ERR_INVALID_ARG, "strata arrays are required");
     if (!(sa->mu > 0.0) || !std::isfinite(sa->mu)) return fail(SRMC_ERR_INVALID_ARG, "mu must be > 0");
@@ -368,8 +407,11 @@ srmc_status srmc_create(const srmc_problem *pr, const srmc_strata *sa, const srm
     s->M_sum = M_sum;
     P.model = pr->model;
     const double kapz = pr->model == SRMC_MODEL_COS ? pr->params[2] : 0.0;
-    s->mv = pr->model == SRMC_MODEL_COS ? (kapz != 0.0 ? srmc::MV_COS_Z : srmc::MV_COS)
+    // the cos model's driver reads z when kapz != 0 or when it cancels a drift
+    s->mv = pr->model == SRMC_MODEL_COS ? (kapz != 0.0 || has_drift ? srmc::MV_COS_Z : srmc::MV_COS)
           : pr->model == SRMC_MODEL_LOGISTIC ? srmc::MV_LOGISTIC : srmc::MV_AFFINE;
+    s->exact = pr->dynamics == SRMC_DYN_EXACT;
+    P.drift = pr->model == SRMC_MODEL_COS && has_drift ? 1 : 0;
     P.zin = (s->mv == srmc::MV_COS_Z || s->mv == srmc::MV_LOGISTIC);
     P.ry32 = pad_to(p, 4); P.rz32 = pad_to(q * p, 4);
     P.ry64 = pad_to(p, 2); P.rz64 = pad_to(q * p, 2);
@@ -394,6 +436,27 @@ srmc_status srmc_create(const srmc_problem *pr, const srmc_strata *sa, const srm
     }
     P.T = pr->T;
     P.dt = pr->T / (double)pr->N;
+    for (int l = 0; l < d; ++l) {
+        const double th = pr->theta ? pr->theta[l] : 0.0;
+        P.theta[l] = th;
+        if (s->exact) {
+            double A, B, r;
+            ou_transition(th, P.dt, A, B, r);
+            P.A[l] = A; P.c[l] = pr->b[l] * B; P.s1[l] = P.sig[l] * B / P.dt; P.s2[l] = P.sig[l] * r;
+        } else {
+            P.A[l] = 1.0 - th * P.dt; P.c[l] = pr->b[l] * P.dt; P.s1[l] = P.sig[l]; P.s2[l] = 0.0;
+        }
+        P.A_f[l] = (float)P.A[l]; P.c_f[l] = (float)P.c[l];
+        P.s1_f[l] = (float)P.s1[l]; P.s2_f[l] = (float)P.s2[l]; P.theta_f[l] = (float)th;
+    }
+    if (P.drift) {
+        if (!(pr->params[3] != 0.0)) {
+            delete s;
+            return fail(SRMC_ERR_INVALID_ARG, "the cos model with a drift needs s0 != 0");
+        }
+        P.inv_s0 = 1.0 / pr->params[3];
+        P.inv_s0_f = (float)P.inv_s0;
+    }
     P.sdt = std::sqrt(P.dt);
     P.mu = sa->mu;
     P.sqrt_d = std::sqrt((double)d);

@@ -31,6 +31,14 @@ struct Params {
     int cell_off[DMAX];             // offset of dimension l in cellF
     double lo[DMAX], h[DMAX], b[DMAX], sig[DMAX];
     float lo_f[DMAX], r_f[DMAX], b_f[DMAX], sig_f[DMAX];
+    // One step of the chain, per coordinate: X' = A X + c + s1 dW + s2 xi2
+    // (Euler: A = 1 - theta dt, c = b dt, s1 = sigma, s2 = 0; exact OU: see
+    // srmc_create), and the drift's mean reversion for the driver.
+    double A[DMAX], c[DMAX], s1[DMAX], s2[DMAX], theta[DMAX];
+    float A_f[DMAX], c_f[DMAX], s1_f[DMAX], s2_f[DMAX], theta_f[DMAX];
+    int drift;                      // cos model: driver carries -(1/s0) b(x).z
+    double inv_s0;
+    float inv_s0_f;
     double T, dt, sdt, mu, sqrt_d;
     float dt_f, sdt_f, inv_mu_f, inv_sqrt_d_f, mu_f;
     int kind;                       // 0: equal-size cells on the box, 1: equal nu-probability
@@ -276,6 +284,12 @@ template <> struct Form<double> {
     __device__ static double lo(const Params &P, int l) { return P.lo[l]; }
     __device__ static double scale(const Params &P, int l) { return P.h[l]; }   // divide by h
     __device__ static double b(const Params &P, int l) { return P.b[l]; }
+    __device__ static double A(const Params &P, int l) { return P.A[l]; }
+    __device__ static double c(const Params &P, int l) { return P.c[l]; }
+    __device__ static double s1(const Params &P, int l) { return P.s1[l]; }
+    __device__ static double s2(const Params &P, int l) { return P.s2[l]; }
+    __device__ static double theta(const Params &P, int l) { return P.theta[l]; }
+    __device__ static double inv_s0(const Params &P) { return P.inv_s0; }
     __device__ static double sig(const Params &P, int l) { return P.sig[l]; }
     __device__ static double dt(const Params &P) { return P.dt; }
     __device__ static double sdt(const Params &P) { return P.sdt; }
@@ -297,6 +311,12 @@ template <> struct Form<float> {
     __device__ static float lo(const Params &P, int l) { return P.lo_f[l]; }
     __device__ static float scale(const Params &P, int l) { return P.r_f[l]; }  // multiply by r
     __device__ static float b(const Params &P, int l) { return P.b_f[l]; }
+    __device__ static float A(const Params &P, int l) { return P.A_f[l]; }
+    __device__ static float c(const Params &P, int l) { return P.c_f[l]; }
+    __device__ static float s1(const Params &P, int l) { return P.s1_f[l]; }
+    __device__ static float s2(const Params &P, int l) { return P.s2_f[l]; }
+    __device__ static float theta(const Params &P, int l) { return P.theta_f[l]; }
+    __device__ static float inv_s0(const Params &P) { return P.inv_s0_f; }
     __device__ static float sig(const Params &P, int l) { return P.sig_f[l]; }
     __device__ static float dt(const Params &P) { return P.dt_f; }
     __device__ static float sdt(const Params &P) { return P.sdt_f; }
@@ -368,6 +388,12 @@ __device__ __forceinline__ R model_f(const Params &P, int j, const R (&x)[D], R 
 #pragma unroll
             for (int l = 0; l < D; ++l) zz += z[l] * z[l];
             v += Form<R>::prm(P, 2) * zz - c1 * cs * cs - c2 * sn * sn;
+            if (P.drift) {          // uniform: cancels the drift b(x).grad u = b(x).z / s0
+                R bz = (R)0;
+#pragma unroll
+                for (int l = 0; l < D; ++l) bz += (Form<R>::b(P, l) - Form<R>::theta(P, l) * x[l]) * z[l];
+                v -= bz * Form<R>::inv_s0(P);
+            }
         } else {
             const R cs = cos_r(s);
             v -= c1 * cs * cs;

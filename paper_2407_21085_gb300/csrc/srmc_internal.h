@@ -45,12 +45,16 @@ struct BatchRound {
 #define SRMC_LAUNCH_STEP_NAME_(D) launch_step_d##D
 #define SRMC_LAUNCH_STEP_PROB_NAME(D) SRMC_LAUNCH_STEP_PROB_NAME_(D)
 #define SRMC_LAUNCH_STEP_PROB_NAME_(D) launch_step_prob_d##D
+#define SRMC_LAUNCH_STEP_EXACT_NAME(D) SRMC_LAUNCH_STEP_EXACT_NAME_(D)
+#define SRMC_LAUNCH_STEP_EXACT_NAME_(D) launch_step_exact_d##D
 
 #define SRMC_DECLARE_STEP(D)                                                              \
     cudaError_t launch_step_d##D(const Params &P, int i, bool fp64, bool lp1, int mv, int grid, \
                                  int threads, cudaStream_t st);                               \
     cudaError_t launch_step_prob_d##D(const Params &P, int i, bool fp64, bool lp1, int mv,    \
-                                      int grid, int threads, cudaStream_t st);
+                                      int grid, int threads, cudaStream_t st);                \
+    cudaError_t launch_step_exact_d##D(const Params &P, int i, bool fp64, bool lp1, int mv,   \
+                                       int grid, int threads, cudaStream_t st);
 SRMC_DECLARE_STEP(1)
 SRMC_DECLARE_STEP(2)
 SRMC_DECLARE_STEP(3)
@@ -152,6 +156,7 @@ struct srmc_solver {
     long long M_sum = 0;                 // sum of the paths over the strata
     bool cv = false;                     // control installed
     bool cv_own = false;                 // ... and it is the run's own fitted z
+    bool exact = false;                  // exact dynamics (Alg. 1)
     cudaStream_t cap_stream = nullptr;   // private stream for graph capture
     cudaGraphExec_t graph = nullptr;     // the N step launches of one solve
 };

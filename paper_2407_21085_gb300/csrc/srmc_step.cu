@@ -30,11 +30,28 @@
 #ifndef SRMC_STEP_KIND
 #define SRMC_STEP_KIND 0
 #endif
+// Dynamics of the unit: 0 the Euler scheme (Alg. 2), 1 the exact affine-drift
+// SDE (Alg. 1; launch_step_exact_dD), which draws a second block of q normals
+// per step.  Exact dynamics are built for equal-size strata only.
+#ifndef SRMC_STEP_DYN
+#define SRMC_STEP_DYN 0
+#endif
 
 namespace srmc {
 namespace {
 
 constexpr int FLUSH = 16;
+constexpr int NW = SRMC_STEP_DYN == 1 ? 2 : 1;     // blocks of q normals per step
+
+// One step of the chain for coordinate l: X' = A X + c + s1 dW (+ s2 xi2 for
+// the exact dynamics).
+template <typename R>
+__device__ __forceinline__ R chain_step(const Params &P, int l, R x, R dw, R xi2)
+{
+    R v = fma(Form<R>::A(P, l), x, Form<R>::c(P, l)) + Form<R>::s1(P, l) * dw;
+    if constexpr (NW == 2) v += Form<R>::s2(P, l) * xi2;
+    return v;
+}
 
 template <int E>
 struct Moments64 {
@@ -474,12 +491,13 @@ __device__ __forceinline__ void solve_stratum(const Params &P, const int i, cons
             }
         }
         {
-            unsigned wd[D];
+            unsigned wd[D], we[D];
             W.template take<D % 4, D, false>(P, wd);
+            if constexpr (NW == 2) W.template take<(2 * D) % 4, D, false>(P, we);
 #pragma unroll
             for (int l = 0; l < D; ++l) {
                 dwi[l] = sdt * normal_of(wd[l], (R)0);
-                xj[l] = x[l] + Form<R>::b(P, l) * dt + Form<R>::sig(P, l) * dwi[l];
+                xj[l] = chain_step<R>(P, l, x[l], dwi[l], NW == 2 ? normal_of(we[l], (R)0) : (R)0);
             }
         }
         // Martingale control: CI = zc_i(x_i).dW_i (stratum k), CZ = sum_{j>i} zc_j(X_j).dW_j,
@@ -495,19 +513,20 @@ __device__ __forceinline__ void solve_stratum(const Params &P, const int i, cons
         R S = (R)0;
         // Steps j = i+1 .. N-1 in groups of G, so that the word phase of
         // every step in a group is a compile-time constant.
-        constexpr int G = 4 / gcd_c(D, 4);
+        constexpr int G = 4 / gcd_c(NW * D, 4);
         for (int j0 = i + 1; j0 < P.N; j0 += G) {
             static_for<0, G>([&](auto gc) {
                 constexpr int g = decltype(gc)::value;
                 const int j = j0 + g;
                 if (j >= P.N) return;
-                unsigned wn[D];
-                W.template take<(D + D * (1 + g)) % 4, D, false>(P, wn);
+                unsigned wn[D], we[D];
+                W.template take<(D + NW * D * (1 + g)) % 4, D, false>(P, wn);
+                if constexpr (NW == 2) W.template take<(2 * D + NW * D * (1 + g)) % 4, D, false>(P, we);
                 R xn[D], zn[D], dw[D];
 #pragma unroll
                 for (int l = 0; l < D; ++l) {
                     dw[l] = sdt * normal_of(wn[l], (R)0);
-                    xn[l] = xj[l] + Form<R>::b(P, l) * dt + Form<R>::sig(P, l) * dw[l];
+                    xn[l] = chain_step<R>(P, l, xj[l], dw[l], NW == 2 ? normal_of(we[l], (R)0) : (R)0);
                 }
                 if constexpr (CV) {
                     // own control: z_j(X_j), already evaluated for the driver
@@ -618,12 +637,13 @@ __device__ __forceinline__ void solve_stratum(const Params &P, const int i, cons
             }
         }
         {
-            unsigned wd[D];
+            unsigned wd[D], we[D];
             W.template take<D % 4, D, false>(P, wd);
+            if constexpr (NW == 2) W.template take<(2 * D) % 4, D, false>(P, we);
 #pragma unroll
             for (int l = 0; l < D; ++l) {
                 const R dw = sdt * normal_of(wd[l], (R)0);
-                x1[l] = x[l] + Form<R>::b(P, l) * dt + Form<R>::sig(P, l) * dw;
+                x1[l] = chain_step<R>(P, l, x[l], dw, NW == 2 ? normal_of(we[l], (R)0) : (R)0);
             }
         }
         {
@@ -803,7 +823,7 @@ cudaError_t launch_prec(const Params &P, int i, bool lp1, int mv, int grid, int 
 
 }  // namespace
 
-#if SRMC_STEP_KIND == 0
+#if SRMC_STEP_KIND == 0 && SRMC_STEP_DYN == 0
 namespace {
 struct BatchLauncher {
     const BatchRound &B; int grid, threads; cudaStream_t st;
@@ -835,9 +855,12 @@ int SRMC_OCC_BATCH_NAME(SRMC_STEP_D)(bool fp64, bool lp1, int mv, bool cv, int t
     return dispatch_variant<float>(lp1, mv, cv, f);
 }
 
-#endif  // SRMC_STEP_KIND == 0
+#endif  // batched form
 
-#if SRMC_STEP_KIND == 0
+#if SRMC_STEP_DYN == 1
+cudaError_t SRMC_LAUNCH_STEP_EXACT_NAME(SRMC_STEP_D)(const Params &P, int i, bool fp64, bool lp1, int mv,
+                                                      int grid, int threads, cudaStream_t st)
+#elif SRMC_STEP_KIND == 0
 cudaError_t SRMC_LAUNCH_STEP_NAME(SRMC_STEP_D)(const Params &P, int i, bool fp64, bool lp1, int mv,
                                                 int grid, int threads, cudaStream_t st)
 #else

@@ -24,6 +24,7 @@ MODELS = {"cos": 0, "logistic": 1, "affine": 2}
 BASES = {"lp0": 0, "lp1": 1}
 PRECISIONS = {"fp32": 0, "fp64": 1}
 STRATA = {"size": 0, "prob": 1}
+DYNAMICS = {"euler": 0, "exact": 1}
 
 
 class SrmcError(RuntimeError):
@@ -35,7 +36,8 @@ class SrmcError(RuntimeError):
 class srmc_problem(C.Structure):
     _fields_ = [("d", C.c_int), ("q", C.c_int), ("N", C.c_int), ("T", C.c_double),
                 ("b", C.POINTER(C.c_double)), ("sigma", C.POINTER(C.c_double)),
-                ("model", C.c_int), ("params", C.POINTER(C.c_double)), ("n_params", C.c_int)]
+                ("model", C.c_int), ("params", C.POINTER(C.c_double)), ("n_params", C.c_int),
+                ("theta", C.POINTER(C.c_double)), ("dynamics", C.c_int)]
 
 
 class srmc_strata(C.Structure):
@@ -168,8 +170,11 @@ class Solver:
         self._cells = (C.c_int * d)(*[int(c) for c in w.cells])
         self._lo = _darr(w.lo)
         self._hi = _darr(w.hi)
+        th = getattr(w, "theta", None)
+        self._theta = _darr(th) if th else None
         pr = srmc_problem(d, q, int(w.N), float(w.T), self._b, self._sig, MODELS[w.model],
-                          self._prm, len(w.params))
+                          self._prm, len(w.params), self._theta,
+                          DYNAMICS.get(getattr(w, "dynamics", "euler"), -1))
         sa = srmc_strata(self._cells, self._lo, self._hi, float(w.mu),
                          STRATA.get(getattr(w, "strata", "size"), -1))
         ms = getattr(w, "M_strata", None)

@@ -48,6 +48,8 @@ class Workload:
     Cz: float = 0.0                # <= 0: no truncation of z
     strata: str = "size"           # "size": equal cells on [lo, hi); "prob": nu(H_k) = 1/K
     M_strata: Optional[List[int]] = None   # paths of each stratum (overrides M), [K]
+    theta: List[float] = field(default_factory=list)   # drift b_l - theta_l x_l (empty: 0)
+    dynamics: str = "euler"        # "euler" (Alg. 2) | "exact" (Alg. 1)
 
     def __post_init__(self):
         if self.q == 0:

@@ -120,6 +120,11 @@ def f(w, j, x, y, z):
         s = x.sum() / math.sqrt(w.d)
         e = math.exp(lam * (w.T - t))
         out = (lam + s0 * s0 / 2) * y + kap * (y * y - (e * math.cos(s)) ** 2)
+        drift = _drift(w, x)
+        if np.any(drift != 0.0):
+            # u solves the PDE whose generator has drift b(x): the driver
+            # cancels b(x).grad u = b(x).z / s0
+            out -= float(np.dot(drift, z)) / s0
         if kapz:
             out += kapz * (float(np.dot(z, z)) - (s0 * e * math.sin(s)) ** 2)
         return out
@@ -127,6 +132,34 @@ def f(w, j, x, y, z):
         return float(np.sum(z)) * (y - (2 + w.q) / (2 * w.q))
     p, d = w.params, w.d
     return p[1 + d] + float(np.dot(p[2 + d:2 + 2 * d], x)) + p[2 + 2 * d] * y
+
+
+def _drift(w, x):
+    th = np.array(w.theta if getattr(w, "theta", None) else [0.0] * w.d, dtype=float)
+    return np.array(w.b, dtype=float) - th * x
+
+
+def ou_step(w, x, dw, xi2):
+    """One exact step (Alg. 1) of dX_l = (b_l - theta_l X_l) dt + s_l dW_l:
+    X' = X e^{-theta dt} + (b/theta)(1 - e^{-theta dt}) + s I, I the Ito integral
+    of e^{-theta(dt-u)}, which given dW is normal with mean (Cov/dt) dW and
+    variance Var I - Cov^2/dt (Cov = (1 - e^{-theta dt})/theta,
+    Var I = (1 - e^{-2 theta dt})/(2 theta)); theta = 0 gives X + b dt + s dW."""
+    dt = w.T / w.N
+    th = w.theta if getattr(w, "theta", None) else [0.0] * w.d
+    out = np.empty(w.d)
+    for l in range(w.d):
+        t, s = th[l], w.sigma[l][l]
+        if t == 0.0:
+            out[l] = x[l] + w.b[l] * dt + s * dw[l]
+            continue
+        A = math.exp(-t * dt)
+        cov = (1.0 - A) / t
+        var = (1.0 - A * A) / (2.0 * t)
+        cond_var = max(var - cov * cov / dt, 0.0)
+        I = cov / dt * dw[l] + math.sqrt(cond_var) * xi2[l]
+        out[l] = x[l] * A + w.b[l] * cov + s * I
+    return out
 
 
 def clamp(v, L):
@@ -180,11 +213,17 @@ def solve(w, control=None):
                 X0.append(x.copy())
                 path = [x]
                 incs = []
+                exact = getattr(w, "dynamics", "euler") == "exact"
+                nw = 2 if exact else 1
                 for j in range(i, N):
-                    dw = np.array([math.sqrt(dt) * normal(word(w, i, k, m, d + (j - i) * q + l))
-                                   for l in range(q)])
+                    base = d + (j - i) * nw * q
+                    dw = np.array([math.sqrt(dt) * normal(word(w, i, k, m, base + l)) for l in range(q)])
                     incs.append(dw)
-                    path.append(path[-1] + b * dt + sig @ dw)
+                    if exact:
+                        xi2 = [normal(word(w, i, k, m, base + q + l)) for l in range(q)]
+                        path.append(ou_step(w, path[-1], dw, xi2))
+                    else:
+                        path.append(path[-1] + _drift(w, path[-1]) * dt + sig @ dw)
                 cz = ci = 0.0
                 for j in range(i, N):
                     xj, dw = path[j - i], incs[j - i]

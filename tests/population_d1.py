@@ -47,8 +47,26 @@ def population_solve(w, grid_step=0.02):
     lam, kap, kapz, s0 = w.params[:4]
     N, T, mu = w.N, w.T, w.mu
     dt = T / N
-    sd = w.sigma[0][0] * math.sqrt(dt)
-    shift = w.b[0] * dt
+    # Transition X' = A x + c + sd xi (xi ~ N(0,1)), and E[dW | X'] = zfac xi.
+    # Euler (Alg. 2) with drift b - theta x: A = 1 - theta dt, c = b dt,
+    # sd = s sqrt(dt), zfac = sqrt(dt).  Exact (Alg. 1): A = e^{-theta dt},
+    # c = b B, sd = s sqrt(Var I), zfac = Cov(dW, I)/sqrt(Var I) = B/sqrt(Var I)
+    # with B = (1 - A)/theta, Var I = (1 - A^2)/(2 theta).
+    b0 = w.b[0]
+    th = w.theta[0] if getattr(w, "theta", None) else 0.0
+    if getattr(w, "dynamics", "euler") == "exact" and th != 0.0:
+        A = math.exp(-th * dt)
+        B = (1.0 - A) / th
+        var_i = (1.0 - A * A) / (2.0 * th)
+        c_shift, sd, zfac = b0 * B, w.sigma[0][0] * math.sqrt(var_i), B / math.sqrt(var_i)
+    else:
+        A = 1.0 - th * dt
+        c_shift, sd, zfac = b0 * dt, w.sigma[0][0] * math.sqrt(dt), math.sqrt(dt)
+    has_drift = b0 != 0.0 or th != 0.0
+
+    def drift_z(xs, zs):
+        # the driver's b(x).z / s0 term (cancels the drift in the PDE of u)
+        return -(b0 - th * xs) * zs / s0 if has_drift else 0.0
     C = w.cells[0]
     if getattr(w, "strata", "size") == "prob":
         # equal nu-probability cells: edges at the logistic quantiles c/C
@@ -98,20 +116,20 @@ def population_solve(w, grid_step=0.02):
         return np.linalg.solve(G, r)
 
     def gauss_mean(values_at_nodes, x):
-        """E[h(x + shift + sd xi)] for every x in the array x."""
+        """E[h(A x + c + sd xi)] for every x in the array x."""
         out = np.empty((len(x),) + values_at_nodes.shape[1:])
         for s in range(0, len(x), 256):
             xx = x[s:s + 256]
-            ker = np.exp(-0.5 * ((XN[None, :] - xx[:, None] - shift) / sd) ** 2) / (sd * math.sqrt(2 * math.pi))
+            ker = np.exp(-0.5 * ((XN[None, :] - A * xx[:, None] - c_shift) / sd) ** 2) / (sd * math.sqrt(2 * math.pi))
             out[s:s + 256] = (ker * WN[None, :]) @ values_at_nodes
         return out
 
     def moment1(values_at_nodes, x):
-        """E[h(X') xi] with xi = (X' - x - shift)/sd."""
+        """E[h(X') xi] with xi = (X' - A x - c)/sd."""
         out = np.empty(len(x))
         for s in range(0, len(x), 256):
             xx = x[s:s + 256]
-            xi = (XN[None, :] - xx[:, None] - shift) / sd
+            xi = (XN[None, :] - A * xx[:, None] - c_shift) / sd
             ker = np.exp(-0.5 * xi ** 2) / (sd * math.sqrt(2 * math.pi))
             out[s:s + 256] = (ker * xi * WN[None, :]) @ values_at_nodes
         return out
@@ -126,9 +144,9 @@ def population_solve(w, grid_step=0.02):
         if j == N:
             return np.cos(xs)
         val = smooth(xs)
-        if kapz:
+        if kapz or has_drift:
             zj = clamp(np.sum(phi(xs) * zb[cell(xs)], axis=1), w.Cz)
-            val = val + dt * kapz * (zj ** 2 - sin2e2(j, xs))
+            val = val + dt * (kapz * (zj ** 2 - sin2e2(j, xs)) + drift_z(xs, zj))
         return val
 
     def y_at(xs, j):
@@ -139,11 +157,11 @@ def population_solve(w, grid_step=0.02):
     for i in range(N - 1, -1, -1):
         vN = v_at(XN, i + 1, v_next_smooth, z_next)
         yN = y_at(XN, i + 1)
-        # Z fit: W_i(x) = E[v_{i+1}(X') xi] sqrt(dt) / dt.
+        # Z fit: W_i(x) = E[v_{i+1}(X') dW] / dt = E[v_{i+1}(X') xi] zfac / dt.
         bz = np.zeros((C, p))
         for c in range(C):
             xs, _ = cellq[c]
-            Wv = moment1(vN, xs) * math.sqrt(dt) / dt
+            Wv = moment1(vN, xs) * zfac / dt
             bz[c] = project(Wv, c)
         beta[i] = bz
         # Smooth part of v_i and the Y fit.
@@ -155,9 +173,9 @@ def population_solve(w, grid_step=0.02):
         for c in range(C):
             xs, _ = cellq[c]
             vi = spline(xs)
-            if kapz:
+            if kapz or has_drift:
                 zi = clamp(np.sum(phi(xs) * bz[c], axis=1), w.Cz)
-                vi = vi + dt * kapz * (zi ** 2 - sin2e2(i, xs))
+                vi = vi + dt * (kapz * (zi ** 2 - sin2e2(i, xs)) + drift_z(xs, zi))
             ay[c] = project(vi, c)
         alpha[i] = ay
         v_next_smooth, z_next = spline, bz

@@ -120,3 +120,11 @@ def test_batch_rejects_equal_probability_strata(dev):
     with pytest.raises(srmc.SrmcError) as e:
         srmc.Batch([s])
     assert e.value.status == 4
+
+
+def test_batch_rejects_exact_dynamics(dev):
+    torch, srmc = dev
+    s = srmc.Solver(W.cfg2(C=4, N=2, M=64).replace(theta=[1.0, 1.0], dynamics="exact"))
+    with pytest.raises(srmc.SrmcError) as e:
+        srmc.Batch([s])
+    assert e.value.status == 4

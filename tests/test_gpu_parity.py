@@ -143,6 +143,21 @@ def test_per_stratum_path_counts(dev, orc, prec):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("dynamics", ["euler", "exact"])
+def test_affine_drift_dynamics(dev, orc, prec, dynamics):
+    # Drift b - theta x (Ornstein-Uhlenbeck) moved by the Euler scheme (Alg. 2)
+    # or by the exact transition (Alg. 1, two normal blocks per step); the cos
+    # model's driver then carries -(1/s0) b(x).z.  d = 1, 2 and 3 (one axis
+    # without mean reversion), with z in the driver through kapz too.
+    cases = [W.cfg1(C=8, N=5, M=300).replace(b=[0.3], theta=[1.2]),
+             W.cfg2(C=6, N=4, M=256, kapz=0.2).replace(b=[0.1, -0.2], theta=[0.8, 2.5]),
+             W.cos_model("ou3", d=3, N=3, C=3, a=2.0, M=200, s0=0.3, lam=0.2, kap=0.5)
+              .replace(b=[0.0, 0.2, -0.1], theta=[0.0, 1.0, 3.0])]
+    for w in cases:
+        _full_parity(dev, orc, w.replace(precision=prec, dynamics=dynamics))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_paper_logistic_model(dev, orc, prec):
     # The test BSDE of Sec. 5.1 (driver uses sum z), d=3, strata on [-6.5,6.5]^3
     _full_parity(dev, orc, W.logistic_paper(d=3, N=4, C=3, M=200, precision=prec))
@@ -271,6 +286,19 @@ def test_cfg3_full_size_sampled(dev, orc):
     # 12^4 strata, N=50, M=16384, kapz=0.2, FP32 form
     w = W.cfg3()
     _sampled_parity(dev, orc, w, steps=[w.N - 1, w.N - 2], n_strata=3)
+
+
+def test_cfg5_full_size_sampled(dev, orc):
+    # 8^6 = 262144 strata on [-3,3]^6, N = 40, M = 4096, FP32 form (the plain
+    # arm of the control-variate comparison)
+    w = W.cfg5()
+    _sampled_parity(dev, orc, w, steps=[w.N - 1, w.N - 2], n_strata=2)
+
+
+def test_cfg2_shape_equal_probability_sampled(dev, orc):
+    # the benchmark's launch configuration with equal-probability strata
+    w = W.cfg2().replace(strata="prob")
+    _sampled_parity(dev, orc, w, steps=[w.N - 1, w.N - 2], n_strata=4)
 
 
 def test_graph_solve_equals_step_launches(dev):

@@ -72,6 +72,9 @@ BF_CASES = [
     dict(d=1, N=3, C=4, M=6, kapz=0.2, basis="lp1", strata="prob"),
     dict(d=2, N=2, C=3, M=6, kapz=0.0, basis="lp1", strata="prob"),
     dict(d=2, N=3, C=2, M=9, kapz=0.1, basis="lp1", M_strata=[3, 9, 5, 7]),
+    dict(d=1, N=3, C=3, M=6, kapz=0.0, basis="lp1", b=[0.2], theta=[0.7]),
+    dict(d=2, N=3, C=2, M=5, kapz=0.2, basis="lp1", b=[0.1, -0.3], theta=[0.5, 1.2], dynamics="exact"),
+    dict(d=1, N=2, C=4, M=7, kapz=0.0, basis="lp0", b=[0.0], theta=[2.0], dynamics="exact"),
 ]
 _BF = {}
 
@@ -80,7 +83,8 @@ def _bf_workload(case):
     w = W.cos_model("bf", d=case["d"], N=case["N"], C=case["C"], a=1.0, M=case["M"], s0=0.5,
                     lam=0.5, kap=0.4, kapz=case["kapz"], basis=case["basis"], seed=11, instance=3)
     return w.replace(Cy=1.5, Cz=1.2, strata=case.get("strata", "size"),   # active truncation somewhere
-                     M_strata=case.get("M_strata"))
+                     M_strata=case.get("M_strata"), b=case.get("b", [0.0] * case["d"]),
+                     theta=case.get("theta", []), dynamics=case.get("dynamics", "euler"))
 
 
 def _brute_force_mismatch(orc, n, library=None):
@@ -108,10 +112,10 @@ def test_brute_force_tiny(orc, n):
     assert _brute_force_mismatch(orc, n) < 1e-10
 
 
-def _population_case(Cy, Cz, basis, strata="size"):
+def _population_case(Cy, Cz, basis, strata="size", dynamics="euler", theta=0.0, b=0.0):
     w = W.cos_model("pop", d=1, N=3, C=4, a=1.0, M=20000, s0=0.5, lam=0.5, kap=0.5,
                     kapz=0.3, basis=basis, seed=5)
-    return w.replace(Cy=Cy, Cz=Cz, strata=strata)
+    return w.replace(Cy=Cy, Cz=Cz, strata=strata, dynamics=dynamics, theta=[theta], b=[b])
 
 
 _POP = {}
@@ -148,7 +152,8 @@ def _population_discrepancy(orc, case, library=None, R=6):
     return worst
 
 
-POP_CASES = [(3.3, 5.7, "lp1"), (0.9, 0.35, "lp1"), (3.3, 5.7, "lp0"), (3.3, 5.7, "lp1", "prob")]
+POP_CASES = [(3.3, 5.7, "lp1"), (0.9, 0.35, "lp1"), (3.3, 5.7, "lp0"), (3.3, 5.7, "lp1", "prob"),
+             (3.3, 5.7, "lp1", "size", "euler", 1.5, 0.4), (3.3, 5.7, "lp1", "size", "exact", 1.5, 0.4)]
 
 
 @pytest.mark.parametrize("case", POP_CASES)
