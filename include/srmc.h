@@ -53,7 +53,11 @@ typedef enum {
     SRMC_ERR_STATE = 5          /* call out of order (e.g. step i before i+1)   */
 } srmc_status;
 
-typedef enum { SRMC_LP0 = 0, SRMC_LP1 = 1 } srmc_basis;        /* Sec. 2, (A_Strat) examples */
+/* Local polynomials (Sec. 2, assumption HS examples; Sec. 4.1): LP0 constants,
+ * LP1 affine functions, LP2 quadratics [1, u_l, u_a u_b (a <= b)] in the
+ * centred coordinates u (higher order than the paper's experiments, which it
+ * notes is possible; built for d <= 3, equal-size strata and Euler dynamics). */
+typedef enum { SRMC_LP0 = 0, SRMC_LP1 = 1, SRMC_LP2 = 2 } srmc_basis;
 typedef enum { SRMC_FP32 = 0, SRMC_FP64 = 1 } srmc_precision;
 
 /* Built-in driver/terminal families.  params[] layouts:

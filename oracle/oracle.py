@@ -24,7 +24,7 @@ _OUT = os.path.join(_HERE, "_build", "libsrmc_oracle.so")
 DMAX = 8
 PMAX = 24
 MODELS = {"cos": 0, "logistic": 1, "affine": 2}
-BASES = {"lp0": 0, "lp1": 1}
+BASES = {"lp0": 0, "lp1": 1, "lp2": 2}
 STRATA = {"size": 0, "prob": 1}
 DYNAMICS = {"euler": 0, "exact": 1}
 

@@ -432,7 +432,7 @@ struct orc_ctx {
     double *control;    /* [N][K][q][dimb] centred-basis control rows, or NULL */
     int own_control;    /* control from the fitted z of later steps        */
     int64_t K;          /* number of strata                                 */
-    int dimb;           /* basis dimension: 1 (LP0) or d+1 (LP1)            */
+    int dimb;           /* basis dimension: 1 (LP0), d+1 (LP1), 1+d+d(d+1)/2 (LP2) */
     int R;              /* row length (1+q)*dimb                            */
     double *rows;       /* [N][K][R], raw basis                             */
     unsigned char *done;/* [N][K]                                           */
@@ -448,7 +448,7 @@ orc_ctx *orc_create(const orc_problem *P)
     C->P = *P;
     C->K = 1;
     for (int l = 0; l < P->d; ++l) C->K *= P->cells[l];
-    C->dimb = (P->basis == ORC_LP0) ? 1 : P->d + 1;
+    C->dimb = P->basis == ORC_LP0 ? 1 : P->basis == ORC_LP1 ? P->d + 1 : 1 + P->d + P->d * (P->d + 1) / 2;
     C->R = (1 + P->q) * C->dimb;
     C->rows = (double *)calloc((size_t)P->N * (size_t)C->K * (size_t)C->R, sizeof(double));
     C->done = (unsigned char *)calloc((size_t)P->N * (size_t)C->K, 1);
@@ -487,19 +487,33 @@ void orc_set_own_control(orc_ctx *C, int on)
     C->own_control = on != 0;
 }
 
-/* zc_j(x) . dw for a point x of stratum k (control rows in the centred basis
- * [1, (x - c_k)/(h/2)], values truncated at C_z). */
+/* The monomials of the basis at the coordinates u: [1] (LP0), [1, u] (LP1),
+ * [1, u, u_a u_b for a <= b in row order] (LP2). */
+static void monomials(const orc_ctx *C, const double *u, double *phi)
+{
+    const int d = C->P.d;
+    phi[0] = 1.0;
+    if (C->dimb > 1)
+        for (int l = 0; l < d; ++l) phi[1 + l] = u[l];
+    if (C->dimb > d + 1) {
+        int e = 1 + d;
+        for (int a = 0; a < d; ++a)
+            for (int b = a; b < d; ++b) phi[e++] = u[a] * u[b];
+    }
+}
+
+/* zc_j(x) . dw for a point x of stratum k (control rows in the monomials of
+ * the centred coordinate u = (x - c_k)/s_k, values truncated at C_z). */
 static double control_dot(const orc_ctx *C, int j, int64_t k, const double *x, const double *dw)
 {
     const orc_problem *P = &C->P;
     const int p = C->dimb;
-    double phi[ORC_DMAX + 1], ctr[ORC_DMAX];
+    double phi[ORC_PBMAX], ctr[ORC_DMAX], u[ORC_DMAX];
     int cells[ORC_DMAX];
     orc_stratum_centre(P, k, ctr);
     orc_stratum_cells(P, k, cells);
-    phi[0] = 1.0;
-    if (p > 1)
-        for (int l = 0; l < P->d; ++l) phi[1 + l] = (x[l] - ctr[l]) / orc_cell_scale(P, l, cells[l]);
+    for (int l = 0; l < P->d; ++l) u[l] = (x[l] - ctr[l]) / orc_cell_scale(P, l, cells[l]);
+    monomials(C, u, phi);
     const double *row = C->control + ((size_t)j * (size_t)C->K + (size_t)k) * (size_t)(P->q * p);
     double s = 0.0;
     for (int l = 0; l < P->q; ++l) {
@@ -519,19 +533,17 @@ const double *orc_row(const orc_ctx *C, int i, int64_t k)
     return C->done[idx] ? C->rows + idx * (size_t)C->R : NULL;
 }
 
-/* Raw basis [1, x_1..x_d] (LP1) or [1] (LP0). */
+/* Raw basis: the monomials of x itself (the fits are made in it, Sec. 4.1). */
 static void basis(const orc_ctx *C, const double *x, double *phi)
 {
-    phi[0] = 1.0;
-    if (C->dimb > 1)
-        for (int l = 0; l < C->P.d; ++l) phi[1 + l] = x[l];
+    monomials(C, x, phi);
 }
 
 /* y_j(x) and z_j(x) from the fitted row of the stratum holding x, both
  * truncated (Alg. SRMDP); y_N = g. */
 static void eval_row(const orc_ctx *C, const double *row, const double *x, double *y, double *z)
 {
-    double phi[ORC_DMAX + 1];
+    double phi[ORC_PBMAX];
     basis(C, x, phi);
     double v = 0.0;
     for (int c = 0; c < C->dimb; ++c) v += row[c] * phi[c];
@@ -579,7 +591,7 @@ static int64_t fit_impl(orc_ctx *C, int i, int64_t k, int lazy)
     double *A = (double *)malloc(sizeof(double) * (size_t)(M * p));
     double *B = (double *)malloc(sizeof(double) * (size_t)(M * (q > 1 ? q : 1)));
     double *coef = (double *)malloc(sizeof(double) * (size_t)(p * (q > 1 ? q : 1)));
-    double row[(1 + ORC_DMAX) * (1 + ORC_DMAX)];
+    double row[(1 + ORC_DMAX) * ORC_PBMAX];
     int64_t steps = 0;
     const int nw = P->dynamics == ORC_EXACT ? 2 : 1;   /* normal blocks per step */
 
@@ -663,7 +675,7 @@ static int64_t fit_impl(orc_ctx *C, int i, int64_t k, int lazy)
         /* Y: OLS of S_{Y,i} = S_{Y,i+1} + f_i(x_i, y_{i+1}(x_{i+1}), z_i(x_i)) dt,
          * where z_i is the truncated fit just made (Z before Y). */
         for (int64_t m = 0; m < M; ++m) {
-            double phi[ORC_DMAX + 1], zi[ORC_DMAX];
+            double phi[ORC_PBMAX], zi[ORC_DMAX];
             basis(C, X0 + m * d, phi);
             for (int l = 0; l < q; ++l) {
                 double w = 0.0;

@@ -19,6 +19,7 @@
  *   - fresh, independent clouds C_{i,k} of M paths                  (Def. "Simulations and empirical measures")
  *   - backward SRMDP recursion: Z-OLS then Y-OLS, truncation T_L    (Alg. SRMDP, eq. PsiM; eq. TL)
  *   - LP0 as the mean, LP1 by Householder QR of A=[1, x_i]          (Sec. 4.1, eqs. lp0/lp1 explicit)
+ *     (LP2: A = [1, x_i, x_i,a x_i,b], the same QR)                  (Sec. 4, footnote on higher orders)
  *   - Philox-4x32-10 counter RNG from its published definition      (Salmon, Moraes, Dror, Shaw, SC'11)
  *   - standard normal by inversion, Phi^{-1}(U), one uniform each
  *   - martingale controls subtracted from the responses (tabulated rows or
@@ -39,7 +40,11 @@ extern "C" {
 #define ORC_PMAX 24
 
 enum { ORC_MODEL_COS = 0, ORC_MODEL_LOGISTIC = 1, ORC_MODEL_AFFINE = 2 };
-enum { ORC_LP0 = 0, ORC_LP1 = 1 };
+/* Local polynomials: constants, affine functions (Sec. 4.1) and quadratics
+ * (LP2: 1, x_l, x_a x_b for a <= b; the higher order the paper mentions as
+ * possible, Sec. 4 footnote).  ORC_PBMAX = the largest basis dimension. */
+enum { ORC_LP0 = 0, ORC_LP1 = 1, ORC_LP2 = 2 };
+#define ORC_PBMAX (1 + ORC_DMAX + ORC_DMAX * (ORC_DMAX + 1) / 2)
 /* Strata (assumption HS): equal size on the box [lo, hi) (example i), or equal
  * probability under nu, nu(H_k) = 1/K (example ii; lo and hi unused). */
 enum { ORC_STRATA_SIZE = 0, ORC_STRATA_PROB = 1 };

@@ -3,8 +3,9 @@
 The step kernel is compiled once per dimension D = 1..8 (-DSRMC_STEP_D=D) so
 that per-path state stays in registers, and once per kind of strata
 (-DSRMC_STEP_KIND: equal size, equal probability) and of dynamics
-(-DSRMC_STEP_DYN: Euler, exact) so that each kernel carries only its own cell
-location and chain step; the objects are compiled in parallel and linked
+(-DSRMC_STEP_DYN: Euler, exact) and of basis (-DSRMC_STEP_BASIS=2: quadratic
+local polynomials, d <= 3) so that each kernel carries only its own cell
+location, chain step and basis; the objects are compiled in parallel and linked
 with the C-ABI translation unit into one shared library under
 ``paper_2407_21085_gb300/_build``.
 """
@@ -23,6 +24,7 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libsrmc.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 DIMS = range(1, 9)
+LP2_DIMS = range(1, 4)          # quadratic local polynomials: d <= 3
 
 
 def _nvcc() -> str:
@@ -66,6 +68,8 @@ def build(force: bool = False, verbose: bool = False, jobs: int | None = None,
              for kind, tag in ((0, ""), (1, "prob_")) for D in DIMS]
     units += [(os.path.join(CSRC, "srmc_step.cu"), os.path.join(out, f"step_exact_d{D}.o"),
                [f"-DSRMC_STEP_D={D}", "-DSRMC_STEP_DYN=1"] + extra_defs) for D in DIMS]
+    units += [(os.path.join(CSRC, "srmc_step.cu"), os.path.join(out, f"step_quad_d{D}.o"),
+               [f"-DSRMC_STEP_D={D}", "-DSRMC_STEP_BASIS=2"] + extra_defs) for D in LP2_DIMS]
     for name in sorted(os.listdir(CSRC)):
         if name.endswith(".cu") and name != "srmc_step.cu":
             units.append((os.path.join(CSRC, name), os.path.join(out, name[:-3] + ".o"), extra_defs))

@@ -68,6 +68,12 @@ void ou_transition(double theta, double dt, double &A, double &B, double &r)
     r = std::sqrt(r2 > 0.0 ? r2 : 0.0);
 }
 
+// Basis dimension: 1 (LP0), d + 1 (LP1), 1 + d + d(d+1)/2 (LP2).
+int basis_dim(int basis, int d)
+{
+    return basis == SRMC_LP0 ? 1 : basis == SRMC_LP1 ? d + 1 : 1 + d + d * (d + 1) / 2;
+}
+
 // F^{-1}(num / (num + den)) of the logistic law with scale mu.
 double logistic_quantile(double num, double den, double mu) { return std::log(num / den) / mu; }
 
@@ -127,6 +133,14 @@ cudaError_t launch_step(const srmc_solver *s, int i, cudaStream_t st)
     P.cv_own = s->cv && s->cv_own ? 1 : 0;
     const int mv = srmc::kernel_mv(s);
     const int grid = (int)(P.K < 2147483647LL ? P.K : 2147483647LL);
+    if (s->lp2) {
+        switch (P.d) {
+        case 1: return srmc::launch_step_quad_d1(P, i, s->fp64, s->lp1, mv, grid, s->threads, st);
+        case 2: return srmc::launch_step_quad_d2(P, i, s->fp64, s->lp1, mv, grid, s->threads, st);
+        case 3: return srmc::launch_step_quad_d3(P, i, s->fp64, s->lp1, mv, grid, s->threads, st);
+        }
+        return cudaErrorInvalidValue;
+    }
     if (s->exact) {
         switch (P.d) {
         case 1: return srmc::launch_step_exact_d1(P, i, s->fp64, s->lp1, mv, grid, s->threads, st);
@@ -281,13 +295,14 @@ __global__ void eval_kernel(const Params P, int i, const double *x, long long n,
                 for (int l = 0; l < P.q; ++l) z[a * P.q + l] = 0.0;
             continue;
         }
-        double phi[srmc::DMAX + 1];
+        double phi[srmc::PBMAX];
         phi[0] = 1.0;
         long long k = 0;
         for (int l = 0; l < P.d; ++l) {
             const int c = srmc::cell_of(P, l, xa[l], phi[1 + l]);
             k += (long long)c * P.stride[l];
         }
+        srmc::add_quadratic_rt(phi, P.d, P.p);
         const long long row = (long long)i * P.K + k;
         const double *al = P.Y64 + row * P.ry64;
         double v = al[0];
@@ -368,13 +383,16 @@ srmc_status srmc_create(const srmc_problem *pr, const srmc_strata *sa, const srm
         if (K > 2147483647LL) return fail(SRMC_ERR_INVALID_ARG, "too many strata (K > 2^31-1)");
     }
     {
-        const int p_ = cf->basis == SRMC_LP1 ? d + 1 : 1;
+        const int p_ = basis_dim(cf->basis, d);
         const long long rmax = (long long)q * std::max(pad_to(p_, 4), half_pad(p_));
         if ((long long)pr->N * K * rmax >= 4294967296LL)
             return fail(SRMC_ERR_UNSUPPORTED, "table too large: N K row-length must be < 2^32");
     }
-    const int p = cf->basis == SRMC_LP1 ? d + 1 : 1;
-    if (cf->basis != SRMC_LP0 && cf->basis != SRMC_LP1) return fail(SRMC_ERR_INVALID_ARG, "basis");
+    if (cf->basis != SRMC_LP0 && cf->basis != SRMC_LP1 && cf->basis != SRMC_LP2)
+        return fail(SRMC_ERR_INVALID_ARG, "basis");
+    const int p = basis_dim(cf->basis, d);
+    if (cf->basis == SRMC_LP2 && (d > SRMC_LP2_DMAX || prob || pr->dynamics != SRMC_DYN_EULER))
+        return fail(SRMC_ERR_UNSUPPORTED, "LP2 is built for d <= 3, equal-size strata and Euler dynamics");
     if (cf->prec != SRMC_FP32 && cf->prec != SRMC_FP64) return fail(SRMC_ERR_INVALID_ARG, "precision");
     if (cf->M < p) return fail(SRMC_ERR_INVALID_ARG, "M must be >= the basis dimension");
     if (cf->M > 4294967295LL) return fail(SRMC_ERR_INVALID_ARG, "M must be < 2^32");
@@ -399,7 +417,8 @@ srmc_status srmc_create(const srmc_problem *pr, const srmc_strata *sa, const srm
     std::memset(&P, 0, sizeof(P));
     cudaGetDevice(&s->device);
     s->fp64 = cf->prec == SRMC_FP64;
-    s->lp1 = cf->basis == SRMC_LP1;
+    s->lp1 = cf->basis != SRMC_LP0;              // the kernels' affine part (LP1 and LP2)
+    s->lp2 = cf->basis == SRMC_LP2;
     s->threads = threads;
     s->done_from = pr->N;
     P.d = d; P.q = q; P.N = pr->N; P.p = p;
@@ -657,13 +676,14 @@ __global__ void point_error_kernel(const Params P, const double *x, long long n,
         for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < n;
              a += (long long)gridDim.x * blockDim.x) {
             const double *xa = x + ((long long)i * n + a) * P.d;
-            double phi[srmc::DMAX + 1], zs[srmc::DMAX], u;
+            double phi[srmc::PBMAX], zs[srmc::DMAX], u;
             phi[0] = 1.0;
             long long k = 0;
             for (int l = 0; l < P.d; ++l) {
                 const int c = srmc::cell_of(P, l, xa[l], phi[1 + l]);
                 k += (long long)c * P.stride[l];
             }
+            srmc::add_quadratic_rt(phi, P.d, P.p);
             closed_form(P, i, xa, u, zs);
             const long long row = (long long)i * P.K + k;
             const double *al = P.Y64 + row * P.ry64;
@@ -703,7 +723,7 @@ __global__ void closed_form_error_kernel(const Params P, bool inner, double *out
     double ymax = 0.0, ysq = 0.0, zmax = 0.0, zsq = 0.0;
     long long cnt = 0;
     for (long long k = threadIdx.x; k < P.K; k += blockDim.x) {
-        double x[srmc::DMAX], phi[srmc::DMAX + 1], zs[srmc::DMAX], u;
+        double x[srmc::DMAX], phi[srmc::PBMAX], zs[srmc::DMAX], u;
         long long rem = k;
         phi[0] = 1.0;
         bool outer = false;
@@ -714,6 +734,7 @@ __global__ void closed_form_error_kernel(const Params P, bool inner, double *out
             x[l] = srmc::cell_centre(P, l, c);
             phi[1 + l] = 0.0;                    // the basis centre of the cell
         }
+        srmc::add_quadratic_rt(phi, P.d, P.p);
         if (inner && outer) continue;
         ++cnt;
         closed_form(P, i, x, u, zs);

@@ -14,6 +14,17 @@
 namespace srmc {
 
 constexpr int DMAX = 8;
+constexpr int PBMAX = 10;            // largest basis dimension: LP1 at d = 8 (9), LP2 at d = 3 (10)
+
+// The quadratic monomials u_a u_b (a <= b, row order) after the linear ones
+// of a basis vector of dimension p, for d only known at run time.
+__host__ __device__ __forceinline__ void add_quadratic_rt(double *phi, int d, int p)
+{
+    if (p <= d + 1) return;
+    int e = 1 + d;
+    for (int a = 0; a < d; ++a)
+        for (int b = a; b < d; ++b) phi[e++] = phi[1 + a] * phi[1 + b];
+}
 constexpr int PMAX = 24;
 constexpr int MAX_THREADS = 256;
 constexpr int MAX_WARPS = MAX_THREADS / 32;

@@ -47,6 +47,10 @@ struct BatchRound {
 #define SRMC_LAUNCH_STEP_PROB_NAME_(D) launch_step_prob_d##D
 #define SRMC_LAUNCH_STEP_EXACT_NAME(D) SRMC_LAUNCH_STEP_EXACT_NAME_(D)
 #define SRMC_LAUNCH_STEP_EXACT_NAME_(D) launch_step_exact_d##D
+#define SRMC_LAUNCH_STEP_QUAD_NAME(D) SRMC_LAUNCH_STEP_QUAD_NAME_(D)
+#define SRMC_LAUNCH_STEP_QUAD_NAME_(D) launch_step_quad_d##D
+// LP2 step kernels are built for d <= SRMC_LP2_DMAX.
+#define SRMC_LP2_DMAX 3
 
 #define SRMC_DECLARE_STEP(D)                                                              \
     cudaError_t launch_step_d##D(const Params &P, int i, bool fp64, bool lp1, int mv, int grid, \
@@ -64,6 +68,12 @@ SRMC_DECLARE_STEP(6)
 SRMC_DECLARE_STEP(7)
 SRMC_DECLARE_STEP(8)
 #undef SRMC_DECLARE_STEP
+cudaError_t launch_step_quad_d1(const Params &P, int i, bool fp64, bool lp1, int mv, int grid, int threads,
+                                cudaStream_t st);
+cudaError_t launch_step_quad_d2(const Params &P, int i, bool fp64, bool lp1, int mv, int grid, int threads,
+                                cudaStream_t st);
+cudaError_t launch_step_quad_d3(const Params &P, int i, bool fp64, bool lp1, int mv, int grid, int threads,
+                                cudaStream_t st);
 
 #define SRMC_DECLARE_BATCH(D)                                                                 \
     cudaError_t launch_batch_d##D(const BatchRound &B, bool fp64, bool lp1, int mv, bool cv,  \
@@ -112,13 +122,14 @@ __device__ __forceinline__ double cell_unit(const Params &P, int l, int c)
 // kernel-side twin of srmc_eval used by the MLP data generator.
 __device__ __forceinline__ double eval_y64(const Params &P, int i, const double *x)
 {
-    double phi[DMAX + 1];
+    double phi[PBMAX];
     phi[0] = 1.0;
     long long k = 0;
     for (int l = 0; l < P.d; ++l) {
         const int c = cell_of(P, l, x[l], phi[1 + l]);
         k += (long long)c * P.stride[l];
     }
+    add_quadratic_rt(phi, P.d, P.p);
     const double *al = P.Y64 + ((long long)i * P.K + k) * P.ry64;
     double v = al[0];
     for (int c = 1; c < P.p; ++c) v += al[c] * phi[c];
@@ -157,6 +168,7 @@ struct srmc_solver {
     bool cv = false;                     // control installed
     bool cv_own = false;                 // ... and it is the run's own fitted z
     bool exact = false;                  // exact dynamics (Alg. 1)
+    bool lp2 = false;                    // quadratic local polynomials
     cudaStream_t cap_stream = nullptr;   // private stream for graph capture
     cudaGraphExec_t graph = nullptr;     // the N step launches of one solve
 };

@@ -36,12 +36,37 @@
 #ifndef SRMC_STEP_DYN
 #define SRMC_STEP_DYN 0
 #endif
+// Local polynomials of the unit's LP1 kernels: 1 affine (Sec. 4.1), 2
+// quadratic (LP2: [1, u, u_a u_b (a <= b)]; launch_step_quad_dD, d <= 3,
+// equal-size strata and Euler dynamics).
+#ifndef SRMC_STEP_BASIS
+#define SRMC_STEP_BASIS 1
+#endif
 
 namespace srmc {
 namespace {
 
 constexpr int FLUSH = 16;
 constexpr int NW = SRMC_STEP_DYN == 1 ? 2 : 1;     // blocks of q normals per step
+
+// Basis dimension: 1 (LP0), d + 1 (LP1) or 1 + d + d(d+1)/2 (LP2 units).
+template <int D, bool LP1>
+struct BasisDim {
+    static constexpr int value = !LP1 ? 1 : SRMC_STEP_BASIS == 2 ? 1 + D + D * (D + 1) / 2 : D + 1;
+};
+
+// The quadratic monomials u_a u_b (a <= b, row order) after the linear ones.
+template <typename R, int D, int p>
+__device__ __forceinline__ void add_quadratic(R (&phi)[p])
+{
+    if constexpr (p > D + 1) {
+        int e = 1 + D;
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+#pragma unroll
+            for (int b = a; b < D; ++b) phi[e++] = phi[1 + a] * phi[1 + b];
+    }
+}
 
 // One step of the chain for coordinate l: X' = A X + c + s1 dW (+ s2 xi2 for
 // the exact dynamics).
@@ -264,9 +289,9 @@ __device__ void chol_solve(const double *L, const double *Linv, const double *r,
 // which the control of the next increment is evaluated.
 template <typename R, int D, bool LP1, int MODEL, bool ZIN, bool CV>
 __device__ __forceinline__ void eval_at(const Params &P, int j, const R (&x)[D], R &y, R (&z)[D],
-                                        R (&phio)[LP1 ? D + 1 : 1], unsigned &rowo)
+                                        R (&phio)[BasisDim<D, LP1>::value], unsigned &rowo)
 {
-    constexpr int p = LP1 ? D + 1 : 1;
+    constexpr int p = BasisDim<D, LP1>::value;
     if (j == P.N) {
         y = model_g<R, D, MODEL>(P, x);
         return;
@@ -292,6 +317,7 @@ __device__ __forceinline__ void eval_at(const Params &P, int j, const R (&x)[D],
             if (LP1) phi[1 + l] = u;
         }
     }
+    add_quadratic<R, D, p>(phi);
     const unsigned row = (unsigned)j * (unsigned)P.K + kk;     // N K < 2^32 (checked at create)
     R a[p];
     load_row<p>(Form<R>::Ytab(P) + row * (unsigned)Form<R>::ry(P), a);
@@ -396,7 +422,7 @@ struct MinBlocks {
 // Shared memory of one stratum block.
 template <typename R, int D, bool LP1>
 struct StepSmem {
-    static constexpr int p = LP1 ? D + 1 : 1;
+    static constexpr int p = BasisDim<D, LP1>::value;
     static constexpr int q = D;
     static constexpr int EG = LP1 ? p * (p + 1) / 2 : 0;
     static constexpr int EA = EG + q * p + p;
@@ -419,7 +445,7 @@ template <typename R, int D, bool LP1, int MODEL, bool ZIN, bool CV>
 __device__ __forceinline__ void solve_stratum(const Params &P, const int i, const long long k,
                                               StepSmem<R, D, LP1> &sm)
 {
-    constexpr int p = LP1 ? D + 1 : 1;
+    constexpr int p = BasisDim<D, LP1>::value;
     constexpr int q = D;
     constexpr int EG = LP1 ? p * (p + 1) / 2 : 0;
     constexpr int EZ = q * p;
@@ -489,6 +515,7 @@ __device__ __forceinline__ void solve_stratum(const Params &P, const int i, cons
                 x[l] = sample_start(ws[l], l);
                 if (LP1) phi[1 + l] = start_phi(x[l], l);
             }
+            add_quadratic<R, D, p>(phi);
         }
         {
             unsigned wd[D], we[D];
@@ -635,6 +662,7 @@ __device__ __forceinline__ void solve_stratum(const Params &P, const int i, cons
                 x[l] = sample_start(ws[l], l);
                 if (LP1) phi[1 + l] = start_phi(x[l], l);
             }
+            add_quadratic<R, D, p>(phi);
         }
         {
             unsigned wd[D], we[D];
@@ -823,7 +851,7 @@ cudaError_t launch_prec(const Params &P, int i, bool lp1, int mv, int grid, int 
 
 }  // namespace
 
-#if SRMC_STEP_KIND == 0 && SRMC_STEP_DYN == 0
+#if SRMC_STEP_KIND == 0 && SRMC_STEP_DYN == 0 && SRMC_STEP_BASIS == 1
 namespace {
 struct BatchLauncher {
     const BatchRound &B; int grid, threads; cudaStream_t st;
@@ -857,7 +885,10 @@ int SRMC_OCC_BATCH_NAME(SRMC_STEP_D)(bool fp64, bool lp1, int mv, bool cv, int t
 
 #endif  // batched form
 
-#if SRMC_STEP_DYN == 1
+#if SRMC_STEP_BASIS == 2
+cudaError_t SRMC_LAUNCH_STEP_QUAD_NAME(SRMC_STEP_D)(const Params &P, int i, bool fp64, bool lp1, int mv,
+                                                     int grid, int threads, cudaStream_t st)
+#elif SRMC_STEP_DYN == 1
 cudaError_t SRMC_LAUNCH_STEP_EXACT_NAME(SRMC_STEP_D)(const Params &P, int i, bool fp64, bool lp1, int mv,
                                                       int grid, int threads, cudaStream_t st)
 #elif SRMC_STEP_KIND == 0

@@ -21,7 +21,7 @@ SRMC_OK = 0
 STATUS = {0: "SRMC_OK", 1: "SRMC_ERR_INVALID_ARG", 2: "SRMC_ERR_CUDA", 3: "SRMC_ERR_OOM",
           4: "SRMC_ERR_UNSUPPORTED", 5: "SRMC_ERR_STATE"}
 MODELS = {"cos": 0, "logistic": 1, "affine": 2}
-BASES = {"lp0": 0, "lp1": 1}
+BASES = {"lp0": 0, "lp1": 1, "lp2": 2}
 PRECISIONS = {"fp32": 0, "fp64": 1}
 STRATA = {"size": 0, "prob": 1}
 DYNAMICS = {"euler": 0, "exact": 1}
@@ -242,7 +242,8 @@ class Solver:
         _check(lib().srmc_clear_control(self._h))
 
     def srmc_read_control(self):
-        p = 1 if self.w.basis == "lp0" else self.w.d + 1
+        d = self.w.d
+        p = {"lp0": 1, "lp1": d + 1, "lp2": 1 + d + d * (d + 1) // 2}[self.w.basis]
         out = np.zeros((self.w.N, self.K, self.w.q, p))
         _check(lib().srmc_read_control(self._h, C.c_void_p(out.ctypes.data)))
         return out

@@ -236,9 +236,10 @@ def control_rows(w: Workload, fn):
     rows [N][K][q][p] in the centred basis [1, (x - c_k)/s_k] (centres and
     units s_k as above): the value at the centre and, for LP1, central
     differences at c +- (s_k/2) e_m (a step of one unit of the centred
-    coordinate)."""
+    coordinate).  LP2 rows carry the same constant and linear parts and zero
+    quadratic coefficients (any fixed function is a valid control)."""
     import numpy as np
-    p = 1 if w.basis == "lp0" else w.d + 1
+    p = {"lp0": 1, "lp1": w.d + 1, "lp2": 1 + w.d + w.d * (w.d + 1) // 2}[w.basis]
     ctr = centres(w)
     unit = cell_units(w)
     rows = np.zeros((w.N, w.K, w.q, p))

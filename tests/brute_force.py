@@ -166,16 +166,25 @@ def clamp(v, L):
     return v if L <= 0 else float(np.clip(v, -L, L))
 
 
-def control_value(w, rows, j, k, x, dw):
-    """zc_j(x).dw with zc_j(x) = T_Cz(beta_{j,k} . [1, (x - c_k)/(h/2)]), c_k the
-    centre of the nominal cell of stratum k (rows [N][K][q][p], centred)."""
-    cs = cells_of(w, k)
+def monomials(basis, u):
+    """[1] (LP0), [1, u] (LP1) or [1, u, u_a u_b for a <= b] (LP2)."""
     v = [1.0]
-    if rows.shape[-1] > 1:
-        for l in range(w.d):
-            c, unit = centre_and_unit(w, l, cs[l])
-            v.append((x[l] - c) / unit)
-    v = np.array(v)
+    if basis != "lp0":
+        v += list(u)
+    if basis == "lp2":
+        v += [u[a] * u[b] for a in range(len(u)) for b in range(a, len(u))]
+    return np.array(v)
+
+
+def control_value(w, rows, j, k, x, dw):
+    """zc_j(x).dw with zc_j(x) = T_Cz(beta_{j,k} . monomials((x - c_k)/s_k)),
+    c_k and s_k the basis centre and unit of stratum k (rows [N][K][q][p])."""
+    cs = cells_of(w, k)
+    u = []
+    for l in range(w.d):
+        c, unit = centre_and_unit(w, l, cs[l])
+        u.append((x[l] - c) / unit)
+    v = monomials(w.basis, u)
     return sum(clamp(float(rows[j, k, l] @ v), w.Cz) * dw[l] for l in range(w.q))
 
 
@@ -189,13 +198,13 @@ def solve(w, control=None):
     itself, no step-i term."""
     N, d, q, M = w.N, w.d, w.q, w.M
     dt = w.T / N
-    p = 1 if w.basis == "lp0" else d + 1
+    p = len(monomials(w.basis, [0.0] * d))
     sig = np.array(w.sigma, dtype=float)
     b = np.array(w.b, dtype=float)
     rows = [dict() for _ in range(N)]
 
     def phi(x):
-        return np.array([1.0]) if p == 1 else np.concatenate([[1.0], x])
+        return monomials(w.basis, x)
 
     def y_and_z(j, x):
         if j == N:

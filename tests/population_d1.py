@@ -80,10 +80,11 @@ def population_solve(w, grid_step=0.02):
 
         def cell(x):
             return np.clip(np.floor((x - w.lo[0]) / h), 0, C - 1).astype(int)
-    p = 1 if w.basis == "lp0" else 2
+    p = {"lp0": 1, "lp1": 2, "lp2": 3}[w.basis]
 
     def phi(x):
-        return np.ones((len(x), 1)) if p == 1 else np.stack([np.ones_like(x), x], axis=1)
+        cols = [np.ones_like(x), x, x * x][:p]
+        return np.stack(cols, axis=1)
 
     def clamp(v, L):
         return v if L <= 0 else np.clip(v, -L, L)

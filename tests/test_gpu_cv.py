@@ -236,3 +236,10 @@ def test_controls_with_exact_dynamics(dev, orc, prec):
     w = W.cfg2(C=6, N=4, M=256, precision=prec).replace(b=[0.1, 0.0], theta=[1.5, 0.5], dynamics="exact")
     _cv_parity(dev, orc, w, W.random_smooth_z(w, seed=6))
     _own_parity(dev, orc, w)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_controls_with_quadratic_polynomials(dev, orc, prec):
+    w = W.cfg2(C=6, N=4, M=256, precision=prec, basis="lp2")
+    _cv_parity(dev, orc, w, W.closed_form_z(w))
+    _own_parity(dev, orc, w)

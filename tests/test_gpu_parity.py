@@ -158,6 +158,36 @@ def test_affine_drift_dynamics(dev, orc, prec, dynamics):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_quadratic_local_polynomials(dev, orc, prec):
+    # LP2: [1, u, u_a u_b] in the centred coordinates, d = 1, 2, 3; cos model
+    # with z in the driver, and the paper's logistic model
+    cases = [W.cfg1(C=8, N=5, M=300),
+             W.cfg2(C=6, N=4, M=256, kapz=0.2),
+             W.cos_model("q3", d=3, N=3, C=3, a=2.0, M=300, s0=0.3, lam=0.2, kap=0.5, kapz=0.1),
+             W.logistic_paper(d=2, N=4, C=4, M=300)]
+    for w in cases:
+        _full_parity(dev, orc, w.replace(basis="lp2", precision=prec))
+
+
+def test_quadratic_local_polynomials_limits(dev):
+    torch, srmc = dev
+    w = W.cfg3(C=2, N=2, M=64).replace(basis="lp2")            # d = 4
+    for bad in (w, W.cfg2(C=4, N=2, M=64, basis="lp2").replace(strata="prob"),
+                W.cfg2(C=4, N=2, M=64, basis="lp2").replace(theta=[1.0, 1.0], dynamics="exact")):
+        with pytest.raises(srmc.SrmcError) as e:
+            srmc.Solver(bad)
+        assert e.value.status == 4
+    s = srmc.Solver(W.cfg2(C=4, N=2, M=64, basis="lp2"))
+    net = srmc.MLP(3)
+    with pytest.raises(srmc.SrmcError) as e:
+        net.srmc_cv_tabulate(s)
+    assert e.value.status == 4
+    with pytest.raises(srmc.SrmcError) as e:
+        srmc.Batch([s])
+    assert e.value.status == 4
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_paper_logistic_model(dev, orc, prec):
     # The test BSDE of Sec. 5.1 (driver uses sum z), d=3, strata on [-6.5,6.5]^3
     _full_parity(dev, orc, W.logistic_paper(d=3, N=4, C=3, M=200, precision=prec))

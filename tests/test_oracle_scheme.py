@@ -28,12 +28,13 @@ def _affine_truth(d, N, T, g0, gv, f0, fv, a, b):
     return out
 
 
-@pytest.mark.parametrize("basis", ["lp1", "lp0"])
+@pytest.mark.parametrize("basis", ["lp1", "lp0", "lp2"])
 def test_exact_fit_affine_deterministic(orc, basis):
-    # sigma = 0: the responses are exact affine functions of x_i, so LP1
-    # reproduces y_i exactly; with LP0 we take gv = fv = 0 (constant solution).
+    # sigma = 0: the responses are exact affine functions of x_i, so LP1 and
+    # LP2 (whose span holds the affine functions) reproduce y_i exactly; with
+    # LP0 we take gv = fv = 0 (constant solution).
     d, N = 2, 5
-    if basis == "lp1":
+    if basis != "lp0":
         gv, fv = [0.3, -0.7], [0.2, 0.05]
     else:
         gv, fv = [0.0, 0.0], [0.0, 0.0]
@@ -51,17 +52,18 @@ def test_exact_fit_affine_deterministic(orc, basis):
     assert o.fallbacks == 0
 
 
-@pytest.mark.parametrize("basis", ["lp1", "lp0"])
+@pytest.mark.parametrize("basis", ["lp1", "lp0", "lp2"])
 def test_constant_solution_with_noise(orc, basis):
     # g = c, f = 0: S_Y = c on every path for any sigma, so y = c to rounding.
-    w = W.affine(d=3, N=4, C=2, M=9, g0=0.75, gv=[0, 0, 0], f0=0.0, fv=[0, 0, 0], a=0.0,
-                 s0=0.6, basis=basis)
+    w = W.affine(d=3, N=4, C=2, M=12 if basis == "lp2" else 9, g0=0.75, gv=[0, 0, 0], f0=0.0,
+                 fv=[0, 0, 0], a=0.0, s0=0.6, basis=basis)
     o = orc.Oracle(w)
     o.solve_full(2)
     x = np.random.default_rng(1).normal(size=(40, 3)) * 2
     for i in range(w.N):
         y, _ = o.eval(i, x)
         assert np.max(np.abs(y - 0.75)) < 1e-13
+    assert o.fallbacks == 0
 
 
 BF_CASES = [
@@ -75,6 +77,8 @@ BF_CASES = [
     dict(d=1, N=3, C=3, M=6, kapz=0.0, basis="lp1", b=[0.2], theta=[0.7]),
     dict(d=2, N=3, C=2, M=5, kapz=0.2, basis="lp1", b=[0.1, -0.3], theta=[0.5, 1.2], dynamics="exact"),
     dict(d=1, N=2, C=4, M=7, kapz=0.0, basis="lp0", b=[0.0], theta=[2.0], dynamics="exact"),
+    dict(d=1, N=3, C=3, M=8, kapz=0.2, basis="lp2"),
+    dict(d=2, N=2, C=2, M=12, kapz=0.1, basis="lp2", strata="prob"),
 ]
 _BF = {}
 
@@ -153,6 +157,7 @@ def _population_discrepancy(orc, case, library=None, R=6):
 
 
 POP_CASES = [(3.3, 5.7, "lp1"), (0.9, 0.35, "lp1"), (3.3, 5.7, "lp0"), (3.3, 5.7, "lp1", "prob"),
+             (3.3, 5.7, "lp2"), (0.9, 0.35, "lp2"),
              (3.3, 5.7, "lp1", "size", "euler", 1.5, 0.4), (3.3, 5.7, "lp1", "size", "exact", 1.5, 0.4)]
 
 
