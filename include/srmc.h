@@ -71,8 +71,12 @@ typedef enum { SRMC_FP32 = 0, SRMC_FP64 = 1 } srmc_precision;
  *   SRMC_MODEL_LOGISTIC: {} ; the test BSDE of Sec. 5.1: w = exp(t + sum x),
  *                        g = w(T,x)/(1+w(T,x)), f = (sum_l z_l)(y - (2+q)/(2q)).
  *   SRMC_MODEL_AFFINE:   {g0, g_1..g_d, f0, f_1..f_d, a}; g = g0 + g.x,
- *                        f_j(x,y,z) = f0 + f.x + a y. */
-typedef enum { SRMC_MODEL_COS = 0, SRMC_MODEL_LOGISTIC = 1, SRMC_MODEL_AFFINE = 2 } srmc_model;
+ *                        f_j(x,y,z) = f0 + f.x + a y.
+ *   SRMC_MODEL_USER:     g and f given as source (srmc_problem.user_source),
+ *                        params passed to them; compiled at srmc_create for the
+ *                        solver's device by NVRTC (see srmc_problem). */
+typedef enum { SRMC_MODEL_COS = 0, SRMC_MODEL_LOGISTIC = 1, SRMC_MODEL_AFFINE = 2,
+               SRMC_MODEL_USER = 3 } srmc_model;
 
 /* Forward SDE, driver, terminal condition and time grid (Sec. 1-2).
  * Drift b_l(x) = b_l - theta_l x_l (theta = 0: constant drift; theta > 0:
@@ -88,7 +92,19 @@ typedef enum { SRMC_MODEL_COS = 0, SRMC_MODEL_LOGISTIC = 1, SRMC_MODEL_AFFINE = 
  *     dW_j, I_l = (B_l/dt) dW_{j,l} + r_l xi_l with r_l^2 = Var I_l - B_l^2/dt,
  *     xi a second standard normal per coordinate and step (draws d + 2(j-i)q + q
  *     + l; dW_j takes d + 2(j-i)q + l).  Equal-size strata only; identical to
- *     Euler when theta = 0 up to the draw layout. */
+ *     Euler when theta = 0 up to the draw layout.
+ * user_source (SRMC_MODEL_USER only, else ignored): C source defining
+ *     SRMC_USER srmc_real srmc_user_g(const srmc_real *x, int d, const double *prm);
+ *     SRMC_USER srmc_real srmc_user_f(srmc_real t, const srmc_real *x, srmc_real y,
+ *                                     const srmc_real *z, int d, const double *prm);
+ *   (g(x) and f(t_j, x, y, z) of eq. MDP; prm = params).  The library
+ *   prepends the typedef of srmc_real (float for the FP32 form, double for
+ *   FP64) and the SRMC_USER qualifiers, compiles it with its step kernel
+ *   (NVRTC, the toolkit headers from SRMC_CUDA_INCLUDE or the build's CUDA
+ *   include directory) and reports compiler messages through
+ *   srmc_last_error (SRMC_ERR_INVALID_ARG).  The source is copied.  User
+ *   models: LP0/LP1, equal-size strata, Euler dynamics; no closed-form
+ *   metrics, no srmc_eval at i == N, no batched form. */
 typedef enum { SRMC_DYN_EULER = 0, SRMC_DYN_EXACT = 1 } srmc_dynamics;
 typedef struct {
     int d, q;
@@ -101,6 +117,7 @@ typedef struct {
     int n_params;
     const double *theta;
     int dynamics;              /* srmc_dynamics */
+    const char *user_source;
 } srmc_problem;
 
 /* Strata (assumption HS): cells[l] half-open cells per dimension, stratum

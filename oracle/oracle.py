@@ -20,10 +20,11 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "srmc_oracle.c")
 _HDR = os.path.join(_HERE, "srmc_oracle.h")
-_OUT = os.path.join(_HERE, "_build", "libsrmc_oracle.so")
+_BUILD = os.path.join(_HERE, "_build")
+_OUT = os.path.join(_BUILD, "libsrmc_oracle.so")
 DMAX = 8
 PMAX = 24
-MODELS = {"cos": 0, "logistic": 1, "affine": 2}
+MODELS = {"cos": 0, "logistic": 1, "affine": 2, "user": 3}
 BASES = {"lp0": 0, "lp1": 1, "lp2": 2}
 STRATA = {"size": 0, "prob": 1}
 DYNAMICS = {"euler": 0, "exact": 1}
@@ -46,6 +47,30 @@ def build(force: bool = False) -> str:
     return _OUT
 
 
+_USER_G = C.CFUNCTYPE(C.c_double, C.POINTER(C.c_double), C.c_int, C.POINTER(C.c_double))
+_USER_F = C.CFUNCTYPE(C.c_double, C.c_double, C.POINTER(C.c_double), C.c_double, C.POINTER(C.c_double),
+                      C.c_int, C.POINTER(C.c_double))
+_user_libs = {}
+
+
+def user_model(source: str):
+    """Compile a user model's source (srmc_user_g, srmc_user_f) as plain C
+    with srmc_real = double, and return its (g, f) function pointers."""
+    import hashlib
+    key = hashlib.sha256(source.encode()).hexdigest()[:16]
+    if key not in _user_libs:
+        out = os.path.join(_BUILD, f"user_{key}.so")
+        src = out[:-3] + ".c"
+        os.makedirs(_BUILD, exist_ok=True)
+        with open(src, "w") as fh:
+            fh.write("#include <math.h>\ntypedef double srmc_real;\n#define SRMC_USER\n" + source + "\n")
+        subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-o", out, src, "-lm"],
+                       check=True)
+        L = C.CDLL(out)
+        _user_libs[key] = (L, _USER_G(("srmc_user_g", L)), _USER_F(("srmc_user_f", L)))
+    return _user_libs[key][1], _user_libs[key][2]
+
+
 class _Problem(C.Structure):
     _fields_ = [
         ("d", C.c_int), ("q", C.c_int), ("N", C.c_int), ("T", C.c_double),
@@ -56,6 +81,7 @@ class _Problem(C.Structure):
         ("seed", C.c_uint64), ("instance", C.c_uint32), ("Cy", C.c_double), ("Cz", C.c_double),
         ("strata", C.c_int), ("M_strata", C.POINTER(C.c_int64)),
         ("theta", C.c_double * DMAX), ("dynamics", C.c_int),
+        ("user_g", _USER_G), ("user_f", _USER_F),
     ]
 
 
@@ -158,6 +184,8 @@ def to_struct(w) -> _Problem:
     for l, v in enumerate(getattr(w, "theta", None) or []):
         p.theta[l] = float(v)
     p.dynamics = DYNAMICS[getattr(w, "dynamics", "euler")]
+    if w.model == "user":
+        p.user_g, p.user_f = user_model(w.user_source)
     ms = getattr(w, "M_strata", None)
     if ms is not None:
         arr = np.ascontiguousarray(ms, dtype=np.int64)

@@ -306,6 +306,7 @@ static double sum_over_sqrt_d(const orc_problem *P, const double *x)
 
 double orc_g(const orc_problem *P, const double *x)
 {
+    if (P->model == ORC_MODEL_USER) return P->user_g(x, P->d, P->params);
     switch (P->model) {
     case ORC_MODEL_COS:
         return cos(sum_over_sqrt_d(P, x));
@@ -357,6 +358,8 @@ double orc_f(const orc_problem *P, int j, const double *x, double y, const doubl
         for (int l = 0; l < P->q; ++l) sz += z[l];
         return sz * (y - (2.0 + P->q) / (2.0 * P->q));
     }
+    case ORC_MODEL_USER:
+        return P->user_f(tj, x, y, z, P->d, P->params);
     case ORC_MODEL_AFFINE: {
         int d = P->d;
         double v = P->params[1 + d];

@@ -39,7 +39,7 @@ extern "C" {
 #define ORC_DMAX 8
 #define ORC_PMAX 24
 
-enum { ORC_MODEL_COS = 0, ORC_MODEL_LOGISTIC = 1, ORC_MODEL_AFFINE = 2 };
+enum { ORC_MODEL_COS = 0, ORC_MODEL_LOGISTIC = 1, ORC_MODEL_AFFINE = 2, ORC_MODEL_USER = 3 };
 /* Local polynomials: constants, affine functions (Sec. 4.1) and quadratics
  * (LP2: 1, x_l, x_a x_b for a <= b; the higher order the paper mentions as
  * possible, Sec. 4 footnote).  ORC_PBMAX = the largest basis dimension. */
@@ -73,6 +73,9 @@ typedef struct {
     const int64_t *M_strata;        /* [K] paths of each stratum, or NULL: M */
     double theta[ORC_DMAX];         /* mean reversion of the drift (0: constant) */
     int dynamics;                   /* ORC_EULER / ORC_EXACT (diagonal sigma)  */
+    /* ORC_MODEL_USER: g(x) and f(t, x, y, z) supplied as functions (params = prm) */
+    double (*user_g)(const double *x, int d, const double *prm);
+    double (*user_f)(double t, const double *x, double y, const double *z, int d, const double *prm);
 } orc_problem;
 
 /* ---- primitives ---------------------------------------------------------- */

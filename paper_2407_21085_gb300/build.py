@@ -39,6 +39,37 @@ def _flags():
                    "-fPIC,-ffp-contract=off", "--expt-relaxed-constexpr"]
 
 
+def _cuda_include(nvcc: str) -> str:
+    """The toolkit's include directory (NVRTC compiles user models against it)."""
+    return os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(nvcc))), "include")
+
+
+def _nvrtc_lib(nvcc: str) -> str:
+    """The toolkit's NVRTC library (opened at run time for user models)."""
+    root = os.path.dirname(os.path.dirname(os.path.realpath(nvcc)))
+    for sub in ("lib64", "lib", os.path.join("targets", "sbsa-linux", "lib"),
+                os.path.join("targets", "x86_64-linux", "lib")):
+        cand = os.path.join(root, sub, "libnvrtc.so")
+        if os.path.exists(cand):
+            return cand
+    return "libnvrtc.so"
+
+
+def _embed_sources(out: str) -> str:
+    """Write a unit holding the step-kernel sources as strings, which the
+    library hands to NVRTC when it compiles a user model."""
+    path = os.path.join(out, "rtc_sources.cu")
+    lines = ["// generated by build.py: the step-kernel sources for run-time compilation"]
+    for name, sym in (("srmc_device.cuh", "srmc_rtc_device_cuh"), ("srmc_step.cu", "srmc_rtc_step_cu")):
+        with open(os.path.join(CSRC, name)) as fh:
+            text = fh.read()
+        body = ", ".join(str(b) for b in text.encode()) + ", 0"
+        lines.append(f"extern const char {sym}[] = {{{body}}};")
+    with open(path, "w") as fh:
+        fh.write("\n".join(lines) + "\n")
+    return path
+
+
 def _sources():
     srcs = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cu", ".cuh", ".h"))]
     srcs.append(os.path.join(INCLUDE, "srmc.h"))
@@ -72,7 +103,10 @@ def build(force: bool = False, verbose: bool = False, jobs: int | None = None,
                [f"-DSRMC_STEP_D={D}", "-DSRMC_STEP_BASIS=2"] + extra_defs) for D in LP2_DIMS]
     for name in sorted(os.listdir(CSRC)):
         if name.endswith(".cu") and name != "srmc_step.cu":
-            units.append((os.path.join(CSRC, name), os.path.join(out, name[:-3] + ".o"), extra_defs))
+            units.append((os.path.join(CSRC, name), os.path.join(out, name[:-3] + ".o"),
+                          extra_defs + [f'-DSRMC_CUDA_INCLUDE="{_cuda_include(nvcc)}"',
+                                        f'-DSRMC_NVRTC_LIB="{_nvrtc_lib(nvcc)}"']))
+    units.append((_embed_sources(out), os.path.join(out, "rtc_sources.o"), []))
 
     def compile_one(u):
         src, obj, extra = u
@@ -88,7 +122,7 @@ def build(force: bool = False, verbose: bool = False, jobs: int | None = None,
     with cf.ThreadPoolExecutor(max_workers=jobs) as ex:
         objs = list(ex.map(compile_one, units))
     tmp = lib + f".{os.getpid()}.tmp"
-    subprocess.run([nvcc] + ARCH + ["-shared", "-o", tmp] + objs, check=True)
+    subprocess.run([nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-ldl"], check=True)
     os.replace(tmp, lib)
     return lib
 

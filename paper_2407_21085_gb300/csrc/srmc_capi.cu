@@ -122,8 +122,22 @@ void free_all(srmc_solver *s)
     cudaFree(s->stepc); cudaFree(s->stepc_f);
     cudaFree(s->Y32); cudaFree(s->Z32); cudaFree(s->Y64); cudaFree(s->Z64); cudaFree(s->stats);
     cudaFree(s->C16); cudaFree(s->C64); cudaFree(s->order); cudaFree(s->Mk);
+    srmc::rtc_release(s->rtc[0]);
+    srmc::rtc_release(s->rtc[1]);
 }
 
+}  // namespace
+
+int srmc_prepare_user_control(srmc_solver *s)
+{
+    if (s->P.model != srmc::MODEL_USER || s->rtc[1].kernel) return SRMC_OK;
+    std::string log;
+    if (!srmc::rtc_compile(s->user_source, s->P.d, s->fp64, s->lp1, true, s->rtc[1], log))
+        return fail(SRMC_ERR_INVALID_ARG, "user model, control-variate kernel: " + log);
+    return SRMC_OK;
+}
+
+namespace {
 cudaError_t launch_step(const srmc_solver *s, int i, cudaStream_t st)
 {
     Params P = s->P;
@@ -133,6 +147,11 @@ cudaError_t launch_step(const srmc_solver *s, int i, cudaStream_t st)
     P.cv_own = s->cv && s->cv_own ? 1 : 0;
     const int mv = srmc::kernel_mv(s);
     const int grid = (int)(P.K < 2147483647LL ? P.K : 2147483647LL);
+    if (P.model == srmc::MODEL_USER) {
+        const srmc::RtcKernel &k = s->rtc[s->cv ? 1 : 0];
+        if (!k.kernel) return cudaErrorInvalidValue;
+        return srmc::rtc_launch(k, P, i, grid, s->threads, st);
+    }
     if (s->lp2) {
         switch (P.d) {
         case 1: return srmc::launch_step_quad_d1(P, i, s->fp64, s->lp1, mv, grid, s->threads, st);
@@ -351,8 +370,10 @@ srmc_status srmc_create(const srmc_problem *pr, const srmc_strata *sa, const srm
         for (int r = 0; r < q; ++r)
             if (l != r && pr->sigma[l * q + r] != 0.0)
                 return fail(SRMC_ERR_UNSUPPORTED, "this build requires a diagonal sigma");
-    if (pr->model < SRMC_MODEL_COS || pr->model > SRMC_MODEL_AFFINE)
+    if (pr->model < SRMC_MODEL_COS || pr->model > SRMC_MODEL_USER)
         return fail(SRMC_ERR_INVALID_ARG, "unknown model");
+    if (pr->model == SRMC_MODEL_USER && (!pr->user_source || !pr->user_source[0]))
+        return fail(SRMC_ERR_INVALID_ARG, "a user model needs its source");
     if (pr->dynamics != SRMC_DYN_EULER && pr->dynamics != SRMC_DYN_EXACT)
         return fail(SRMC_ERR_INVALID_ARG, "unknown dynamics");
     bool has_drift = false;
@@ -430,6 +451,20 @@ srmc_status srmc_create(const srmc_problem *pr, const srmc_strata *sa, const srm
     s->mv = pr->model == SRMC_MODEL_COS ? (kapz != 0.0 || has_drift ? srmc::MV_COS_Z : srmc::MV_COS)
           : pr->model == SRMC_MODEL_LOGISTIC ? srmc::MV_LOGISTIC : srmc::MV_AFFINE;
     s->exact = pr->dynamics == SRMC_DYN_EXACT;
+    if (pr->model == SRMC_MODEL_USER) {
+        // user model: the run-time compiled kernels read z at every path point
+        s->mv = srmc::MV_COS_Z;
+        s->user_source = pr->user_source;
+        if (s->lp2 || prob || s->exact) {
+            delete s;
+            return fail(SRMC_ERR_UNSUPPORTED, "user models: LP0/LP1, equal-size strata, Euler dynamics");
+        }
+        std::string log;
+        if (!srmc::rtc_compile(s->user_source, d, s->fp64, s->lp1, false, s->rtc[0], log)) {
+            delete s;
+            return fail(SRMC_ERR_INVALID_ARG, "user model: " + log);
+        }
+    }
     P.drift = pr->model == SRMC_MODEL_COS && has_drift ? 1 : 0;
     P.zin = (s->mv == srmc::MV_COS_Z || s->mv == srmc::MV_LOGISTIC);
     P.ry32 = pad_to(p, 4); P.rz32 = pad_to(q * p, 4);
@@ -785,8 +820,8 @@ __global__ void closed_form_error_kernel(const Params P, bool inner, double *out
 srmc_status srmc_closed_form_error(const srmc_solver *s, double *out, void *stream)
 {
     if (!s || !out) return fail(SRMC_ERR_INVALID_ARG, "srmc_closed_form_error: NULL argument");
-    if (s->P.model == srmc::MODEL_AFFINE)
-        return fail(SRMC_ERR_UNSUPPORTED, "srmc_closed_form_error: no closed form for the affine model");
+    if (s->P.model == srmc::MODEL_AFFINE || s->P.model == srmc::MODEL_USER)
+        return fail(SRMC_ERR_UNSUPPORTED, "srmc_closed_form_error: no closed form for the affine and user models");
     if (s->done_from > 0) return fail(SRMC_ERR_STATE, "srmc_closed_form_error: solve not finished");
     closed_form_error_kernel<<<s->P.N, 256, 0, (cudaStream_t)stream>>>(s->P, false, out);
     SRMC_CUDA(cudaGetLastError(), "closed form error kernel launch");
@@ -798,8 +833,8 @@ srmc_status srmc_point_error(const srmc_solver *s, const double *x, long long n,
     if (!s || !out) return fail(SRMC_ERR_INVALID_ARG, "srmc_point_error: NULL argument");
     if (n < 0) return fail(SRMC_ERR_INVALID_ARG, "srmc_point_error: n < 0");
     if (n > 0 && !x) return fail(SRMC_ERR_INVALID_ARG, "srmc_point_error: NULL points");
-    if (s->P.model == srmc::MODEL_AFFINE)
-        return fail(SRMC_ERR_UNSUPPORTED, "srmc_point_error: no closed form for the affine model");
+    if (s->P.model == srmc::MODEL_AFFINE || s->P.model == srmc::MODEL_USER)
+        return fail(SRMC_ERR_UNSUPPORTED, "srmc_point_error: no closed form for the affine and user models");
     if (s->done_from > 0) return fail(SRMC_ERR_STATE, "srmc_point_error: solve not finished");
     SRMC_CUDA(cudaMemsetAsync(out, 0, sizeof(double) * 2 * (size_t)s->P.N, (cudaStream_t)stream),
               "srmc_point_error: clear");
@@ -815,8 +850,8 @@ srmc_status srmc_point_error(const srmc_solver *s, const double *x, long long n,
 srmc_status srmc_closed_form_error_inner(const srmc_solver *s, double *out, void *stream)
 {
     if (!s || !out) return fail(SRMC_ERR_INVALID_ARG, "srmc_closed_form_error_inner: NULL argument");
-    if (s->P.model == srmc::MODEL_AFFINE)
-        return fail(SRMC_ERR_UNSUPPORTED, "srmc_closed_form_error_inner: no closed form for the affine model");
+    if (s->P.model == srmc::MODEL_AFFINE || s->P.model == srmc::MODEL_USER)
+        return fail(SRMC_ERR_UNSUPPORTED, "srmc_closed_form_error_inner: no closed form for the affine and user models");
     for (int l = 0; l < s->P.d; ++l)
         if (s->P.cells[l] < 3) return fail(SRMC_ERR_INVALID_ARG, "srmc_closed_form_error_inner: no inner strata");
     if (s->done_from > 0) return fail(SRMC_ERR_STATE, "srmc_closed_form_error_inner: solve not finished");
@@ -834,6 +869,8 @@ srmc_status srmc_eval(const srmc_solver *s, int i, const double *x, long long n,
     if (n == 0) return SRMC_OK;
     if (!x || !y) return fail(SRMC_ERR_INVALID_ARG, "srmc_eval: NULL buffer");
     if (i < s->P.N && s->done_from > i) return fail(SRMC_ERR_STATE, "srmc_eval: step i not solved");
+    if (i == s->P.N && s->P.model == srmc::MODEL_USER)
+        return fail(SRMC_ERR_UNSUPPORTED, "srmc_eval: g of a user model is not evaluated here (i == N)");
     eval_kernel<<<grid_for(n, 128), 128, 0, (cudaStream_t)stream>>>(s->P, i, x, n, y, z);
     SRMC_CUDA(cudaGetLastError(), "eval kernel launch");
     return SRMC_OK;
@@ -896,6 +933,7 @@ srmc_status srmc_set_control(srmc_solver *s, const double *rows)
     if (!s || !rows) return fail(SRMC_ERR_INVALID_ARG, "srmc_set_control: NULL argument");
     if (!s->lp1) return fail(SRMC_ERR_UNSUPPORTED, "srmc_set_control: LP1 solvers only");
     if (s->mv == srmc::MV_AFFINE) return fail(SRMC_ERR_UNSUPPORTED, "srmc_set_control: not for the affine model");
+    if (const int st = srmc_prepare_user_control(s)) return (srmc_status)st;
     const size_t nrow = (size_t)s->P.N * (size_t)s->P.K;
     const size_t n = nrow * (size_t)(s->P.q * s->P.p);
     if (!s->C64) {
@@ -937,6 +975,7 @@ srmc_status srmc_set_own_control(srmc_solver *s)
     if (!s->lp1) return fail(SRMC_ERR_UNSUPPORTED, "srmc_set_own_control: LP1 solvers only");
     if (s->mv == srmc::MV_AFFINE)
         return fail(SRMC_ERR_UNSUPPORTED, "srmc_set_own_control: not for the affine model");
+    if (const int st = srmc_prepare_user_control(s)) return (srmc_status)st;
     s->cv = true;
     s->cv_own = true;
     if (s->graph) { cudaGraphExecDestroy(s->graph); s->graph = nullptr; }

@@ -5,11 +5,12 @@
 // overloads of the same definition.
 #pragma once
 
-#include <cstdint>
-#include <type_traits>
+// Compiled by nvcc into the library and, for user models, by NVRTC at run
+// time (__CUDACC_RTC__: device code only, no host headers).
+#ifndef __CUDACC_RTC__
 #include <cuda_runtime.h>
+#endif
 #include <cuda_fp16.h>
-#include <math_constants.h>
 
 namespace srmc {
 
@@ -29,7 +30,7 @@ constexpr int PMAX = 24;
 constexpr int MAX_THREADS = 256;
 constexpr int MAX_WARPS = MAX_THREADS / 32;
 
-enum Model { MODEL_COS = 0, MODEL_LOGISTIC = 1, MODEL_AFFINE = 2 };
+enum Model { MODEL_COS = 0, MODEL_LOGISTIC = 1, MODEL_AFFINE = 2, MODEL_USER = 3 };
 
 // Everything a step launch needs, passed by value as the kernel parameter.
 struct Params {
@@ -148,12 +149,17 @@ struct Words {
     }
 };
 
-// Compile-time loop: f(integral_constant<int, g>) for g = G0 .. G-1.
+// A compile-time integer, and a compile-time choice of type.
+template <int V> struct IntC { static constexpr int value = V; };
+template <bool B, typename T, typename F> struct Select { using type = T; };
+template <typename T, typename F> struct Select<false, T, F> { using type = F; };
+
+// Compile-time loop: f(IntC<g>) for g = G0 .. G-1.
 template <int G0, int G, typename F>
 __device__ __forceinline__ void static_for(F &&f)
 {
     if constexpr (G0 < G) {
-        f(std::integral_constant<int, G0>{});
+        f(IntC<G0>{});
         static_for<G0 + 1, G>(f);
     }
 }
@@ -362,6 +368,10 @@ __device__ __forceinline__ double sqrtd_of(const Params &P, double) { return P.s
 template <typename R, int D, int MODEL>
 __device__ __forceinline__ R model_g(const Params &P, const R (&x)[D])
 {
+#ifdef SRMC_USER_MODEL
+    // user model (run-time compiled units): srmc_real is R there
+    if constexpr (MODEL == MODEL_USER) return srmc_user_g(x, D, P.prm);
+#endif
     R s = x[0];
 #pragma unroll
     for (int l = 1; l < D; ++l) s += x[l];
@@ -383,6 +393,9 @@ __device__ __forceinline__ R model_g(const Params &P, const R (&x)[D])
 template <typename R, int D, int MODEL, bool ZIN>
 __device__ __forceinline__ R model_f(const Params &P, int j, const R (&x)[D], R y, const R *z)
 {
+#ifdef SRMC_USER_MODEL
+    if constexpr (MODEL == MODEL_USER) return srmc_user_f((R)j * Form<R>::dt(P), x, y, z, D, P.prm);
+#endif
     if (MODEL == MODEL_COS) {
         R s = x[0];
 #pragma unroll

@@ -143,6 +143,23 @@ using srmc::Params;
 // One step launch of a single-instance solver on a stream (srmc_capi.cu).
 cudaError_t srmc_launch_solver_step(const struct srmc_solver *s, int i, cudaStream_t st);
 
+namespace srmc {
+// A run-time compiled step kernel (user models, srmc_rtc.cu).
+struct RtcKernel {
+    cudaLibrary_t lib = nullptr;
+    cudaKernel_t kernel = nullptr;
+};
+bool rtc_compile(const std::string &user_source, int d, bool fp64, bool lp1, bool cv, RtcKernel &out,
+                 std::string &log);
+cudaError_t rtc_launch(const RtcKernel &k, const Params &P, int i, int grid, int threads, cudaStream_t st);
+void rtc_release(RtcKernel &k);
+}  // namespace srmc
+
+// For a user-model solver, compile its control-variate step kernel if it is
+// not compiled yet (called when a control is installed, outside any stream
+// capture).  Returns 0, or a status with srmc_last_error set.
+int srmc_prepare_user_control(struct srmc_solver *s);
+
 // The solver object behind the opaque srmc_solver handle.
 struct srmc_solver {
     Params P;                   // device pointers inside point to the buffers below
@@ -169,6 +186,8 @@ struct srmc_solver {
     bool cv_own = false;                 // ... and it is the run's own fitted z
     bool exact = false;                  // exact dynamics (Alg. 1)
     bool lp2 = false;                    // quadratic local polynomials
+    std::string user_source;             // user model (SRMC_MODEL_USER): g and f as source
+    srmc::RtcKernel rtc[2];              // its step kernels: plain, control variate
     cudaStream_t cap_stream = nullptr;   // private stream for graph capture
     cudaGraphExec_t graph = nullptr;     // the N step launches of one solve
 };

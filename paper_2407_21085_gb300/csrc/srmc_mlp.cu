@@ -816,6 +816,7 @@ srmc_status srmc_cv_tabulate(const srmc_mlp *m, srmc_solver *s, void *stream)
     if (!m || !s) return mfail(SRMC_ERR_INVALID_ARG, "srmc_cv_tabulate: NULL argument");
     if (!s->lp1 || s->lp2 || s->P.d > 7 || m->nin != s->P.d + 1 || s->mv == srmc::MV_AFFINE)
         return mfail(SRMC_ERR_UNSUPPORTED, "srmc_cv_tabulate: LP1, d <= 7, n_in = d + 1 only");
+    if (const int st = srmc_prepare_user_control(s)) return (srmc_status)st;
     const size_t nrow = (size_t)s->P.N * (size_t)s->P.K;
     if (!s->C64) {
         MLP_CUDA(cudaMalloc(&s->C64, sizeof(double) * nrow * s->P.rz64), "cudaMalloc control");

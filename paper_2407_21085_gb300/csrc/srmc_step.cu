@@ -19,7 +19,15 @@
 // accumulates in float per thread over blocks of FLUSH paths, then reduces
 // each entry across the warp and carries the warp sums in double, so the
 // rounding error of a moment does not grow with M.
+//
+// The same source is compiled at run time by NVRTC for user models
+// (__CUDACC_RTC__, -DSRMC_USER_MODEL): device code only, with the entry
+// kernel srmc_user_step at the end; the host launchers are left out.
+#ifdef __CUDACC_RTC__
+#include "srmc_device.cuh"
+#else
 #include "srmc_internal.h"
+#endif
 
 #ifndef SRMC_STEP_D
 #error "compile with -DSRMC_STEP_D=<dimension>"
@@ -452,7 +460,7 @@ __device__ __forceinline__ void solve_stratum(const Params &P, const int i, cons
     constexpr int EA = EG + EZ + p;
     constexpr int EB = p;
     constexpr bool RS = sizeof(R) == 4 && EA > 24;
-    using MA = typename std::conditional<RS, MomentsRS<EA>, typename MomentsOf<R, EA>::type>::type;
+    using MA = typename Select<RS, MomentsRS<EA>, typename MomentsOf<R, EA>::type>::type;
     using MB = typename MomentsOf<R, EB>::type;
     auto &redA = sm.redA;
     auto &totA = sm.totA;
@@ -740,6 +748,7 @@ step_kernel(const Params P, const int i)
     }
 }
 
+#ifndef __CUDACC_RTC__
 // Batched form: one launch per round and group of instances with the same
 // kernel variant.  Work item t is stratum t - kofs[a] of active instance a;
 // the block copies that instance's parameters into shared memory whenever
@@ -902,5 +911,26 @@ cudaError_t SRMC_LAUNCH_STEP_PROB_NAME(SRMC_STEP_D)(const Params &P, int i, bool
     return fp64 ? launch_prec<double>(P, i, lp1, mv, grid, threads, st)
                 : launch_prec<float>(P, i, lp1, mv, grid, threads, st);
 }
+#else
+}  // namespace (the unit-local one; in library builds it closes above)
+#endif  // !__CUDACC_RTC__
 
 }  // namespace srmc
+
+#ifdef __CUDACC_RTC__
+// Entry point of a run-time compiled unit: a user model (MODEL_USER, z read at
+// every path point) in the precision SRMC_RTC_REAL, with the affine part of the
+// basis when SRMC_RTC_LP1 and the control variate when SRMC_RTC_CV.
+extern "C" __global__ void
+__launch_bounds__(srmc::MAX_THREADS,
+                  srmc::MinBlocks<SRMC_RTC_REAL, SRMC_STEP_D, SRMC_RTC_CV != 0, true>::value)
+srmc_user_step(const srmc::Params P, const int i)
+{
+    __shared__ srmc::StepSmem<SRMC_RTC_REAL, SRMC_STEP_D, SRMC_RTC_LP1 != 0> sm;
+    for (long long t = blockIdx.x; t < P.K; t += gridDim.x) {
+        const long long k = P.order ? (long long)__ldg(P.order + t) : t;
+        srmc::solve_stratum<SRMC_RTC_REAL, SRMC_STEP_D, SRMC_RTC_LP1 != 0, srmc::MODEL_USER, true,
+                            SRMC_RTC_CV != 0>(P, i, k, sm);
+    }
+}
+#endif

@@ -20,7 +20,7 @@ LIB_PATH = os.environ.get("SRMC_LIBRARY") or os.path.join(_HERE, "_build", "libs
 SRMC_OK = 0
 STATUS = {0: "SRMC_OK", 1: "SRMC_ERR_INVALID_ARG", 2: "SRMC_ERR_CUDA", 3: "SRMC_ERR_OOM",
           4: "SRMC_ERR_UNSUPPORTED", 5: "SRMC_ERR_STATE"}
-MODELS = {"cos": 0, "logistic": 1, "affine": 2}
+MODELS = {"cos": 0, "logistic": 1, "affine": 2, "user": 3}
 BASES = {"lp0": 0, "lp1": 1, "lp2": 2}
 PRECISIONS = {"fp32": 0, "fp64": 1}
 STRATA = {"size": 0, "prob": 1}
@@ -37,7 +37,8 @@ class srmc_problem(C.Structure):
     _fields_ = [("d", C.c_int), ("q", C.c_int), ("N", C.c_int), ("T", C.c_double),
                 ("b", C.POINTER(C.c_double)), ("sigma", C.POINTER(C.c_double)),
                 ("model", C.c_int), ("params", C.POINTER(C.c_double)), ("n_params", C.c_int),
-                ("theta", C.POINTER(C.c_double)), ("dynamics", C.c_int)]
+                ("theta", C.POINTER(C.c_double)), ("dynamics", C.c_int),
+                ("user_source", C.c_char_p)]
 
 
 class srmc_strata(C.Structure):
@@ -174,7 +175,8 @@ class Solver:
         self._theta = _darr(th) if th else None
         pr = srmc_problem(d, q, int(w.N), float(w.T), self._b, self._sig, MODELS[w.model],
                           self._prm, len(w.params), self._theta,
-                          DYNAMICS.get(getattr(w, "dynamics", "euler"), -1))
+                          DYNAMICS.get(getattr(w, "dynamics", "euler"), -1),
+                          (getattr(w, "user_source", None) or "").encode() or None)
         sa = srmc_strata(self._cells, self._lo, self._hi, float(w.mu),
                          STRATA.get(getattr(w, "strata", "size"), -1))
         ms = getattr(w, "M_strata", None)

@@ -50,6 +50,7 @@ class Workload:
     M_strata: Optional[List[int]] = None   # paths of each stratum (overrides M), [K]
     theta: List[float] = field(default_factory=list)   # drift b_l - theta_l x_l (empty: 0)
     dynamics: str = "euler"        # "euler" (Alg. 2) | "exact" (Alg. 1)
+    user_source: Optional[str] = None   # model "user": srmc_user_g / srmc_user_f as source
 
     def __post_init__(self):
         if self.q == 0:

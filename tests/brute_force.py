@@ -103,7 +103,14 @@ def locate(w, x):
     return k
 
 
+def _user(w):
+    from tests.user_models import PY
+    return PY[w.user_source]
+
+
 def g(w, x):
+    if w.model == "user":
+        return _user(w)[0](x, w.params)
     if w.model == "cos":
         return math.cos(x.sum() / math.sqrt(w.d))
     if w.model == "logistic":
@@ -115,6 +122,8 @@ def g(w, x):
 
 def f(w, j, x, y, z):
     t = j * w.T / w.N
+    if w.model == "user":
+        return _user(w)[1](t, x, y, z, w.params)
     if w.model == "cos":
         lam, kap, kapz, s0 = w.params[:4]
         s = x.sum() / math.sqrt(w.d)
