@@ -7,12 +7,13 @@
  * multistep-forward dynamic programming equation on the grid t_i = i T/N,
  *     Y_i    = E_i[ g(X_N) + sum_{j=i}^{N-1} f_j(X_j, Y_{j+1}, Z_j) dt ],
  *     dt Z_i = E_i[ (g(X_N) + sum_{j=i+1}^{N-1} f_j(X_j, Y_{j+1}, Z_j) dt) dW_i ],
- * with X the Euler chain X_{j+1} = X_j + b dt + sigma dW_j (Alg. 2), approximated
- * by Alg. SRMDP: for every time step i = N-1..0 and every hypercube stratum
- * H_k, draw M fresh paths started from the restricted logistic law nu_k
- * (assumption A_nu, Alg. 3), simulate them to t_N, and fit the Z-response then
- * the Y-response by least squares on LP0 (constants) or LP1 (affine functions)
- * local to H_k (eq. PsiM; Sec. 4.1), truncating the fitted values (eq. TL).
+ * with X the Euler chain X_{j+1} = X_j + b(X_j) dt + sigma dW_j (Alg. 2) or the
+ * SDE itself (Alg. 1, affine drift), approximated by Alg. SRMDP: for every time
+ * step i = N-1..0 and every hypercube stratum H_k, draw M fresh paths started
+ * from the restricted logistic law nu_k (assumption A_nu, Alg. 3), simulate
+ * them to t_N, and fit the Z-response then the Y-response by least squares on
+ * LP0 (constants), LP1 (affine functions) or LP2 (quadratics) local to H_k
+ * (eq. PsiM; Sec. 4.1), truncating the fitted values (eq. TL).
  *
  * Conventions for every call:
  *   - Host arrays passed in are read during the call and copied; the caller
@@ -27,7 +28,8 @@
  *   - Random numbers: Philox-4x32-10 (Salmon et al., SC'11) with
  *     key = (seed_lo ^ instance, seed_hi) and counter = (n/4, m, k, i) for word
  *     n of path m of cloud C_{i,k}; words 0..d-1 draw the start point,
- *     words d + (j-i) q + l the normal of component l of dW_j.  Uniforms are
+ *     words d + (j-i) q + l the normal of component l of dW_j (the exact
+ *     dynamics draw two blocks per step, see srmc_problem).  Uniforms are
  *     U = (w + 1/2) 2^-32 and normals Phi^{-1}(U).  Nothing is stored: a path
  *     is regenerated from its counter whenever it is needed.
  */
@@ -97,7 +99,15 @@ typedef enum { SRMC_MODEL_COS = 0, SRMC_MODEL_LOGISTIC = 1, SRMC_MODEL_AFFINE = 
  *     SRMC_USER srmc_real srmc_user_g(const srmc_real *x, int d, const double *prm);
  *     SRMC_USER srmc_real srmc_user_f(srmc_real t, const srmc_real *x, srmc_real y,
  *                                     const srmc_real *z, int d, const double *prm);
- *   (g(x) and f(t_j, x, y, z) of eq. MDP; prm = params).  The library
+ *   (g(x) and f(t_j, x, y, z) of eq. MDP; prm = params); with user_dynamics
+ *   != 0 also
+ *     SRMC_USER srmc_real srmc_user_b(srmc_real t, const srmc_real *x, int l, int d,
+ *                                     const double *prm);
+ *     SRMC_USER srmc_real srmc_user_sigma(srmc_real t, const srmc_real *x, int l, int d,
+ *                                         const double *prm);
+ *   the drift b_l(t, x) and diagonal diffusion sigma_l(t, x) (assumption HX), taken
+ *   by the Euler step X_{j+1,l} = X_{j,l} + b_l(t_j, X_j) dt + sigma_l(t_j, X_j) dW_{j,l}
+ *   (Alg. 2; b, theta and sigma of the problem are then unused).  The library
  *   prepends the typedef of srmc_real (float for the FP32 form, double for
  *   FP64) and the SRMC_USER qualifiers, compiles it with its step kernel
  *   (NVRTC, the toolkit headers from SRMC_CUDA_INCLUDE or the build's CUDA
@@ -118,6 +128,7 @@ typedef struct {
     const double *theta;
     int dynamics;              /* srmc_dynamics */
     const char *user_source;
+    int user_dynamics;         /* user model also supplies b and sigma (see above) */
 } srmc_problem;
 
 /* Strata (assumption HS): cells[l] half-open cells per dimension, stratum

@@ -50,12 +50,14 @@ def build(force: bool = False) -> str:
 _USER_G = C.CFUNCTYPE(C.c_double, C.POINTER(C.c_double), C.c_int, C.POINTER(C.c_double))
 _USER_F = C.CFUNCTYPE(C.c_double, C.c_double, C.POINTER(C.c_double), C.c_double, C.POINTER(C.c_double),
                       C.c_int, C.POINTER(C.c_double))
+_USER_B = C.CFUNCTYPE(C.c_double, C.c_double, C.POINTER(C.c_double), C.c_int, C.c_int, C.POINTER(C.c_double))
 _user_libs = {}
 
 
 def user_model(source: str):
-    """Compile a user model's source (srmc_user_g, srmc_user_f) as plain C
-    with srmc_real = double, and return its (g, f) function pointers."""
+    """Compile a user model's source (srmc_user_g, srmc_user_f, optionally
+    srmc_user_b and srmc_user_sigma) as plain C with srmc_real = double, and
+    return its (g, f, b, sigma) function pointers (b, sigma None if absent)."""
     import hashlib
     key = hashlib.sha256(source.encode()).hexdigest()[:16]
     if key not in _user_libs:
@@ -67,8 +69,11 @@ def user_model(source: str):
         subprocess.run(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off", "-o", out, src, "-lm"],
                        check=True)
         L = C.CDLL(out)
-        _user_libs[key] = (L, _USER_G(("srmc_user_g", L)), _USER_F(("srmc_user_f", L)))
-    return _user_libs[key][1], _user_libs[key][2]
+        dyn = hasattr(L, "srmc_user_b") and hasattr(L, "srmc_user_sigma")
+        _user_libs[key] = (L, _USER_G(("srmc_user_g", L)), _USER_F(("srmc_user_f", L)),
+                           _USER_B(("srmc_user_b", L)) if dyn else None,
+                           _USER_B(("srmc_user_sigma", L)) if dyn else None)
+    return _user_libs[key][1:]
 
 
 class _Problem(C.Structure):
@@ -81,7 +86,7 @@ class _Problem(C.Structure):
         ("seed", C.c_uint64), ("instance", C.c_uint32), ("Cy", C.c_double), ("Cz", C.c_double),
         ("strata", C.c_int), ("M_strata", C.POINTER(C.c_int64)),
         ("theta", C.c_double * DMAX), ("dynamics", C.c_int),
-        ("user_g", _USER_G), ("user_f", _USER_F),
+        ("user_g", _USER_G), ("user_f", _USER_F), ("user_b", _USER_B), ("user_sigma", _USER_B),
     ]
 
 
@@ -185,7 +190,12 @@ def to_struct(w) -> _Problem:
         p.theta[l] = float(v)
     p.dynamics = DYNAMICS[getattr(w, "dynamics", "euler")]
     if w.model == "user":
-        p.user_g, p.user_f = user_model(w.user_source)
+        g, f, b, s = user_model(w.user_source)
+        p.user_g, p.user_f = g, f
+        if getattr(w, "user_dynamics", False):
+            if b is None:
+                raise ValueError("user_dynamics: the source defines no srmc_user_b / srmc_user_sigma")
+            p.user_b, p.user_sigma = b, s
     ms = getattr(w, "M_strata", None)
     if ms is not None:
         arr = np.ascontiguousarray(ms, dtype=np.int64)

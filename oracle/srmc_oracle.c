@@ -619,6 +619,12 @@ static int64_t fit_impl(orc_ctx *C, int i, int64_t k, int lazy)
                     const double I = (B / dt) * dw[l] + r * xi2;
                     xn[l] = x[l] * A + P->b[l] * B + P->sigma[l * q + l] * I;
                 }
+            } else if (P->user_b) {
+                /* Euler step with the user's b(t, x) and diagonal sigma(t, x) at (t_j, X_j) */
+                const double tj = (double)j * dt;
+                for (int l = 0; l < d; ++l)
+                    xn[l] = x[l] + P->user_b(tj, x, l, d, P->params) * dt
+                            + P->user_sigma(tj, x, l, d, P->params) * dw[l];
             } else {
                 /* Euler step, Alg. 2, read with the coefficients at (t_j, X_j). */
                 for (int l = 0; l < d; ++l) {

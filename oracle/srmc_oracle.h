@@ -76,6 +76,10 @@ typedef struct {
     /* ORC_MODEL_USER: g(x) and f(t, x, y, z) supplied as functions (params = prm) */
     double (*user_g)(const double *x, int d, const double *prm);
     double (*user_f)(double t, const double *x, double y, const double *z, int d, const double *prm);
+    /* optional: drift b_l(t, x) and diagonal diffusion sigma_l(t, x) for the
+     * Euler step (both NULL: b - theta x and sigma above) */
+    double (*user_b)(double t, const double *x, int l, int d, const double *prm);
+    double (*user_sigma)(double t, const double *x, int l, int d, const double *prm);
 } orc_problem;
 
 /* ---- primitives ---------------------------------------------------------- */

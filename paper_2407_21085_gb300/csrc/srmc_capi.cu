@@ -132,7 +132,7 @@ int srmc_prepare_user_control(srmc_solver *s)
 {
     if (s->P.model != srmc::MODEL_USER || s->rtc[1].kernel) return SRMC_OK;
     std::string log;
-    if (!srmc::rtc_compile(s->user_source, s->P.d, s->fp64, s->lp1, true, s->rtc[1], log))
+    if (!srmc::rtc_compile(s->user_source, s->P.d, s->fp64, s->lp1, true, s->user_dynamics, s->rtc[1], log))
         return fail(SRMC_ERR_INVALID_ARG, "user model, control-variate kernel: " + log);
     return SRMC_OK;
 }
@@ -374,6 +374,8 @@ srmc_status srmc_create(const srmc_problem *pr, const srmc_strata *sa, const srm
         return fail(SRMC_ERR_INVALID_ARG, "unknown model");
     if (pr->model == SRMC_MODEL_USER && (!pr->user_source || !pr->user_source[0]))
         return fail(SRMC_ERR_INVALID_ARG, "a user model needs its source");
+    if (pr->user_dynamics && pr->model != SRMC_MODEL_USER)
+        return fail(SRMC_ERR_INVALID_ARG, "user_dynamics needs a user model");
     if (pr->dynamics != SRMC_DYN_EULER && pr->dynamics != SRMC_DYN_EXACT)
         return fail(SRMC_ERR_INVALID_ARG, "unknown dynamics");
     bool has_drift = false;
@@ -455,18 +457,18 @@ srmc_status srmc_create(const srmc_problem *pr, const srmc_strata *sa, const srm
         // user model: the run-time compiled kernels read z at every path point
         s->mv = srmc::MV_COS_Z;
         s->user_source = pr->user_source;
+        s->user_dynamics = pr->user_dynamics != 0;
         if (s->lp2 || prob || s->exact) {
             delete s;
             return fail(SRMC_ERR_UNSUPPORTED, "user models: LP0/LP1, equal-size strata, Euler dynamics");
         }
         std::string log;
-        if (!srmc::rtc_compile(s->user_source, d, s->fp64, s->lp1, false, s->rtc[0], log)) {
+        if (!srmc::rtc_compile(s->user_source, d, s->fp64, s->lp1, false, s->user_dynamics, s->rtc[0], log)) {
             delete s;
             return fail(SRMC_ERR_INVALID_ARG, "user model: " + log);
         }
     }
     P.drift = pr->model == SRMC_MODEL_COS && has_drift ? 1 : 0;
-    P.zin = (s->mv == srmc::MV_COS_Z || s->mv == srmc::MV_LOGISTIC);
     P.ry32 = pad_to(p, 4); P.rz32 = pad_to(q * p, 4);
     P.ry64 = pad_to(p, 2); P.rz64 = pad_to(q * p, 2);
     P.ph = half_pad(p); P.rc16 = q * P.ph;

@@ -37,7 +37,7 @@ struct Params {
     int d, q, N, p;                 // dims, steps, basis dimension
     int ry32, rz32, ry64, rz64;     // row strides of the coefficient tables
     long long K, M;
-    int model, zin;
+    int model;
     int cells[DMAX];
     int stride[DMAX];               // stratum index stride of each dimension
     int cell_off[DMAX];             // offset of dimension l in cellF

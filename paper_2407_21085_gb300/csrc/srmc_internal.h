@@ -149,8 +149,8 @@ struct RtcKernel {
     cudaLibrary_t lib = nullptr;
     cudaKernel_t kernel = nullptr;
 };
-bool rtc_compile(const std::string &user_source, int d, bool fp64, bool lp1, bool cv, RtcKernel &out,
-                 std::string &log);
+bool rtc_compile(const std::string &user_source, int d, bool fp64, bool lp1, bool cv, bool user_dynamics,
+                 RtcKernel &out, std::string &log);
 cudaError_t rtc_launch(const RtcKernel &k, const Params &P, int i, int grid, int threads, cudaStream_t st);
 void rtc_release(RtcKernel &k);
 }  // namespace srmc
@@ -187,6 +187,7 @@ struct srmc_solver {
     bool exact = false;                  // exact dynamics (Alg. 1)
     bool lp2 = false;                    // quadratic local polynomials
     std::string user_source;             // user model (SRMC_MODEL_USER): g and f as source
+    bool user_dynamics = false;          // ... with its own drift and diffusion
     srmc::RtcKernel rtc[2];              // its step kernels: plain, control variate
     cudaStream_t cap_stream = nullptr;   // private stream for graph capture
     cudaGraphExec_t graph = nullptr;     // the N step launches of one solve

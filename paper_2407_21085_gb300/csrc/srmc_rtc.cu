@@ -78,8 +78,8 @@ void rtc_release(RtcKernel &k)
     k.kernel = nullptr;
 }
 
-bool rtc_compile(const std::string &user_source, int d, bool fp64, bool lp1, bool cv, RtcKernel &out,
-                 std::string &log)
+bool rtc_compile(const std::string &user_source, int d, bool fp64, bool lp1, bool cv, bool user_dynamics,
+                 RtcKernel &out, std::string &log)
 {
     rtc_release(out);
     const Nvrtc &rt = nvrtc();
@@ -114,7 +114,8 @@ bool rtc_compile(const std::string &user_source, int d, bool fp64, bool lp1, boo
     const std::string o_lp1 = std::string("-DSRMC_RTC_LP1=") + (lp1 ? "1" : "0");
     const std::string o_cv = std::string("-DSRMC_RTC_CV=") + (cv ? "1" : "0");
     const char *opts[] = {o_arch.c_str(), "-std=c++17", "-default-device", o_inc.c_str(), o_d.c_str(),
-                          "-DSRMC_USER_MODEL", o_r.c_str(), o_lp1.c_str(), o_cv.c_str()};
+                          "-DSRMC_USER_MODEL", o_r.c_str(), o_lp1.c_str(), o_cv.c_str(),
+                          user_dynamics ? "-DSRMC_USER_DYNAMICS" : "-DSRMC_USER_DYNAMICS_OFF"};
     const nvrtcResult r = rt.compile(prog, (int)(sizeof(opts) / sizeof(opts[0])), opts);
     size_t n = 0;
     rt.log_size(prog, &n);

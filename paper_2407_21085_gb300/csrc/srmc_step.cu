@@ -86,6 +86,21 @@ __device__ __forceinline__ R chain_step(const Params &P, int l, R x, R dw, R xi2
     return v;
 }
 
+// Coordinate l of the step from X_j = x (the whole vector): the affine-drift
+// step above, or, for user models with their own dynamics (run-time units,
+// -DSRMC_USER_DYNAMICS), the Euler step (Alg. 2) with the user's drift and
+// diagonal diffusion at (t_j, X_j).
+template <typename R, int D>
+__device__ __forceinline__ R next_coord(const Params &P, int j, int l, const R (&x)[D], R dw, R xi2)
+{
+#ifdef SRMC_USER_DYNAMICS
+    const R t = (R)j * Form<R>::dt(P);
+    return x[l] + srmc_user_b(t, x, l, D, P.prm) * Form<R>::dt(P) + srmc_user_sigma(t, x, l, D, P.prm) * dw;
+#else
+    return chain_step<R>(P, l, x[l], dw, xi2);
+#endif
+}
+
 template <int E>
 struct Moments64 {
     double a[E];
@@ -532,7 +547,7 @@ __device__ __forceinline__ void solve_stratum(const Params &P, const int i, cons
 #pragma unroll
             for (int l = 0; l < D; ++l) {
                 dwi[l] = sdt * normal_of(wd[l], (R)0);
-                xj[l] = chain_step<R>(P, l, x[l], dwi[l], NW == 2 ? normal_of(we[l], (R)0) : (R)0);
+                xj[l] = next_coord<R, D>(P, i, l, x, dwi[l], NW == 2 ? normal_of(we[l], (R)0) : (R)0);
             }
         }
         // Martingale control: CI = zc_i(x_i).dW_i (stratum k), CZ = sum_{j>i} zc_j(X_j).dW_j,
@@ -561,7 +576,7 @@ __device__ __forceinline__ void solve_stratum(const Params &P, const int i, cons
 #pragma unroll
                 for (int l = 0; l < D; ++l) {
                     dw[l] = sdt * normal_of(wn[l], (R)0);
-                    xn[l] = chain_step<R>(P, l, xj[l], dw[l], NW == 2 ? normal_of(we[l], (R)0) : (R)0);
+                    xn[l] = next_coord<R, D>(P, j, l, xj, dw[l], NW == 2 ? normal_of(we[l], (R)0) : (R)0);
                 }
                 if constexpr (CV) {
                     // own control: z_j(X_j), already evaluated for the driver
@@ -679,7 +694,7 @@ __device__ __forceinline__ void solve_stratum(const Params &P, const int i, cons
 #pragma unroll
             for (int l = 0; l < D; ++l) {
                 const R dw = sdt * normal_of(wd[l], (R)0);
-                x1[l] = chain_step<R>(P, l, x[l], dw, NW == 2 ? normal_of(we[l], (R)0) : (R)0);
+                x1[l] = next_coord<R, D>(P, i, l, x, dw, NW == 2 ? normal_of(we[l], (R)0) : (R)0);
             }
         }
         {

@@ -38,7 +38,7 @@ class srmc_problem(C.Structure):
                 ("b", C.POINTER(C.c_double)), ("sigma", C.POINTER(C.c_double)),
                 ("model", C.c_int), ("params", C.POINTER(C.c_double)), ("n_params", C.c_int),
                 ("theta", C.POINTER(C.c_double)), ("dynamics", C.c_int),
-                ("user_source", C.c_char_p)]
+                ("user_source", C.c_char_p), ("user_dynamics", C.c_int)]
 
 
 class srmc_strata(C.Structure):
@@ -176,7 +176,8 @@ class Solver:
         pr = srmc_problem(d, q, int(w.N), float(w.T), self._b, self._sig, MODELS[w.model],
                           self._prm, len(w.params), self._theta,
                           DYNAMICS.get(getattr(w, "dynamics", "euler"), -1),
-                          (getattr(w, "user_source", None) or "").encode() or None)
+                          (getattr(w, "user_source", None) or "").encode() or None,
+                          1 if getattr(w, "user_dynamics", False) else 0)
         sa = srmc_strata(self._cells, self._lo, self._hi, float(w.mu),
                          STRATA.get(getattr(w, "strata", "size"), -1))
         ms = getattr(w, "M_strata", None)

@@ -51,6 +51,7 @@ class Workload:
     theta: List[float] = field(default_factory=list)   # drift b_l - theta_l x_l (empty: 0)
     dynamics: str = "euler"        # "euler" (Alg. 2) | "exact" (Alg. 1)
     user_source: Optional[str] = None   # model "user": srmc_user_g / srmc_user_f as source
+    user_dynamics: bool = False    # the user source also defines srmc_user_b / srmc_user_sigma
 
     def __post_init__(self):
         if self.q == 0:

@@ -240,6 +240,11 @@ def solve(w, control=None):
                     if exact:
                         xi2 = [normal(word(w, i, k, m, base + q + l)) for l in range(q)]
                         path.append(ou_step(w, path[-1], dw, xi2))
+                    elif getattr(w, "user_dynamics", False):
+                        _, _, ub, us = _user(w)
+                        xc, t = path[-1], j * dt
+                        path.append(np.array([xc[l] + ub(t, xc, l, w.params) * dt
+                                              + us(t, xc, l, w.params) * dw[l] for l in range(d)]))
                     else:
                         path.append(path[-1] + _drift(w, path[-1]) * dt + sig @ dw)
                 cz = ci = 0.0

@@ -95,3 +95,24 @@ def test_user_model_errors(dev):
     with pytest.raises(srmc.SrmcError) as e:
         srmc.Solver(_quad(2, "fp32").replace(strata="prob"))
     assert e.value.status == 4
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("d", [1, 2])
+def test_user_dynamics_vs_oracle(dev, orc, prec, d):
+    # the user's drift b(t, x) and diffusion sigma(t, x) in the Euler step
+    torch, srmc = dev
+    w = _quad(d, prec).replace(user_source=U.QUAD_DYN, user_dynamics=True)
+    s = srmc.Solver(w)
+    s.srmc_solve()
+    o = orc.Oracle(w)
+    o.solve_full(0)
+    x = s.centres()
+    xn = x.cpu().numpy()
+    for i in range(w.N):
+        gy, gz = s.evaluate(i, x)
+        ry, rz = o.eval(i, xn)
+        _check(w, gy.cpu().numpy(), gz.cpu().numpy(), ry, rz, where=f"step {i}")
+    with pytest.raises(srmc.SrmcError) as e:
+        srmc.Solver(W.cfg2(C=4, N=2, M=64).replace(user_dynamics=True))    # not a user model
+    assert e.value.status == 1

@@ -35,3 +35,26 @@ def test_user_model_brute_force_tiny(orc):
                 yb, zb = y_and_z(i, x[a])
                 worst = max(worst, abs(y[a] - yb), float(np.max(np.abs(z[a] - zb))))
         assert worst < 1e-10, (d, worst)
+
+
+def test_user_dynamics_brute_force_tiny(orc):
+    # the user's own drift b(t, x) and diffusion sigma(t, x) in the Euler step
+    for d, C, M in ((1, 3, 6), (2, 2, 7)):
+        w = W.cos_model("userdyn", d=d, N=3, C=C, a=1.0, M=M, s0=0.5, lam=0.5, kap=0.4, seed=12,
+                        instance=4).replace(model="user", user_source=U.QUAD_DYN, params=[0.7, -0.4],
+                                            user_dynamics=True)
+        y_and_z = bf.solve(w)[1]
+        o = orc.Oracle(w)
+        o.solve_full(1)
+        x = np.random.default_rng(4).uniform(-2, 2, size=(20, d))
+        worst = 0.0
+        for i in range(w.N):
+            y, z = o.eval(i, x)
+            for a in range(len(x)):
+                yb, zb = y_and_z(i, x[a])
+                worst = max(worst, abs(y[a] - yb), float(np.max(np.abs(z[a] - zb))))
+        assert worst < 1e-10, (d, worst)
+        # the dynamics are in use: the same source without them differs
+        o2 = orc.Oracle(w.replace(user_dynamics=False))
+        o2.solve_full(1)
+        assert np.max(np.abs(o2.eval(0, x)[0] - o.eval(0, x)[0])) > 1e-6

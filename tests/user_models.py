@@ -53,3 +53,31 @@ def quad_f(t, x, y, z, prm):
 
 
 PY = {QUAD: (quad_g, quad_f)}
+
+
+# QUAD with its own dynamics: a mean-reverting drift with a time-dependent
+# level and a state-dependent diffusion (prm = {a, c}).
+QUAD_DYN = QUAD + r"""
+SRMC_USER srmc_real srmc_user_b(srmc_real t, const srmc_real *x, int l, int d, const double *prm)
+{
+    return -(srmc_real)0.5 * x[l] + (srmc_real)0.1 * sin(t + (srmc_real)l);
+}
+
+SRMC_USER srmc_real srmc_user_sigma(srmc_real t, const srmc_real *x, int l, int d, const double *prm)
+{
+    return (srmc_real)0.3 * ((srmc_real)1 + (srmc_real)0.2 * cos(x[l]));
+}
+"""
+
+
+def quad_dyn_b(t, x, l, prm):
+    import math
+    return -0.5 * x[l] + 0.1 * math.sin(t + l)
+
+
+def quad_dyn_sigma(t, x, l, prm):
+    import math
+    return 0.3 * (1.0 + 0.2 * math.cos(x[l]))
+
+
+PY[QUAD_DYN] = (quad_g, quad_f, quad_dyn_b, quad_dyn_sigma)
