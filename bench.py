@@ -423,10 +423,18 @@ def cv_compare(args, stream):
 
 # ---- the paper's own experiment (Sec. 5.1): error indicators over many runs ----------
 def paper_table_rows(table: str):
-    """Rows (N, cells per dimension, M, runs) of the d = 4 tables of Sec. 5.2:
-    LP1 with #C = floor(3 sqrt(d sqrt(N)) - 5), M = (d+1) N^2; LP0 with
-    #C = floor(4 sqrt(N)), M = N^2.  The run counts are ours (10^3 in the
-    paper), fewer where one run takes seconds."""
+    """Rows (N, cells per dimension, M, runs) of tables of Sec. 5.2: d = 4 LP1
+    with #C = floor(3 sqrt(d sqrt(N)) - 5), M = (d+1) N^2 and LP0 with
+    #C = floor(4 sqrt(N)), M = N^2; d = 6 LP1 with #C = floor(1.5 sqrt(d sqrt(N))
+    - 3), M = (d+1) N^2 and LP0 with #C = floor(2 sqrt(N)), M = N^2.  The run
+    counts are ours (10^3 in the paper), fewer where one run takes seconds."""
+    if table == "lp1_d6":
+        d, rows = 6, [(5, 1000), (10, 1000), (20, 200), (50, 3)]
+        return d, "lp1", [(N, int(math.floor(1.5 * math.sqrt(d * math.sqrt(N)) - 3)), (d + 1) * N * N, R)
+                          for N, R in rows]
+    if table == "lp0_d6":
+        d, rows = 6, [(5, 1000), (10, 200), (20, 40)]
+        return d, "lp0", [(N, int(math.floor(2 * math.sqrt(N))), N * N, R) for N, R in rows]
     d = 4
     if table == "lp1_d4":
         rows = [(5, 1000), (10, 1000), (20, 1000), (50, 10)]
@@ -440,7 +448,7 @@ def paper_table_rows(table: str):
 
 def paper_table(args, stream):
     """The error indicators of Sec. 5.1 (eq. mse) for the paper's test BSDE
-    (X = W, logistic model, mu = 1, T = 1, strata on [-6.5, 6.5]^4, FP32 paths):
+    (X = W, logistic model, mu = 1, T = 1, strata on [-6.5, 6.5]^d, FP32 paths):
     R independent runs (Philox seeds 1..R), each evaluated against the closed
     form at n points per step drawn i.i.d. from nu independently of the
     clouds; MSE_Y,max = ln(max_i S_i^y / (R n)), MSE_Y,av = ln(sum_i S_i^y /
@@ -605,7 +613,7 @@ def main():
                     help="time the control-variate step kernel (rows from an untrained network)")
     ap.add_argument("--control-own", action="store_true",
                     help="time the step kernel with the run's own z control")
-    ap.add_argument("--paper-table", choices=["lp1_d4", "lp0_d4"], default=None,
+    ap.add_argument("--paper-table", choices=["lp1_d4", "lp0_d4", "lp1_d6", "lp0_d6"], default=None,
                     help="instead of the benchmark: the error indicators of Sec. 5.1 over many runs")
     ap.add_argument("--paper-points", type=int, default=1000, help="nu points per step per run")
     ap.add_argument("--cv-M", type=int, default=1024)
