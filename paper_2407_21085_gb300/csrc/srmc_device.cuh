@@ -184,6 +184,32 @@ __device__ __forceinline__ double normal_of(unsigned w, double)
 // Phi^{-1}; max relative error 6e-9 and 9e-8 on the two pieces).  y is
 // formed from the integer complement so that it keeps full relative
 // precision next to p = 1/2.
+// Coefficients of h, highest degree first: central piece (in w - 5/2) and
+// tail piece (in sqrt(w) - 3.435767889).
+__device__ constexpr float NRM_C[10] = {
+    -1.243243108e-08f, 3.285592243e-08f, 6.592648560e-07f, -4.897004146e-06f, -7.019233635e-06f,
+    3.087856749e-04f, -1.771644573e-03f, -5.907717161e-03f, 3.488020301e-01f, 2.123313427e+00f};
+__device__ constexpr float NRM_T[10] = {
+    6.402532017e-05f, -3.551483360e-06f, -4.645976005e-04f, 9.079263546e-04f, -1.158809988e-03f,
+    1.824696665e-03f, -3.379537957e-03f, 5.249740090e-03f, 1.424003482e+00f, 4.625601292e+00f};
+
+__device__ __forceinline__ float normal_h(float wv)
+{
+    float h;
+    if (wv < 5.0f) {
+        const float s = wv - 2.5f;
+        h = NRM_C[0];
+#pragma unroll
+        for (int c = 1; c < 10; ++c) h = fmaf(h, s, NRM_C[c]);
+    } else {
+        const float s = sqrtf(wv) - 3.435767889f;
+        h = NRM_T[0];
+#pragma unroll
+        for (int c = 1; c < 10; ++c) h = fmaf(h, s, NRM_T[c]);
+    }
+    return h;
+}
+
 __device__ __forceinline__ float normal_of(unsigned w, float)
 {
     const bool up = w >= 0x80000000u;
@@ -191,34 +217,66 @@ __device__ __forceinline__ float normal_of(unsigned w, float)
     const float p = fmaf(__uint2float_rn(v), 0x1p-32f, 0x1p-33f);
     const float y = fmaf(__uint2float_rn(0x7FFFFFFFu - v), -0x1p-31f, -0x1p-32f);   // 2p - 1
     const float wv = -__logf(4.0f * (p * (1.0f - p)));
-    float h;
-    if (wv < 5.0f) {
-        const float s = wv - 2.5f;
-        h = -1.243243108e-08f;
-        h = fmaf(h, s, 3.285592243e-08f);
-        h = fmaf(h, s, 6.592648560e-07f);
-        h = fmaf(h, s, -4.897004146e-06f);
-        h = fmaf(h, s, -7.019233635e-06f);
-        h = fmaf(h, s, 3.087856749e-04f);
-        h = fmaf(h, s, -1.771644573e-03f);
-        h = fmaf(h, s, -5.907717161e-03f);
-        h = fmaf(h, s, 3.488020301e-01f);
-        h = fmaf(h, s, 2.123313427e+00f);
-    } else {
-        const float s = sqrtf(wv) - 3.435767889f;
-        h = 6.402532017e-05f;
-        h = fmaf(h, s, -3.551483360e-06f);
-        h = fmaf(h, s, -4.645976005e-04f);
-        h = fmaf(h, s, 9.079263546e-04f);
-        h = fmaf(h, s, -1.158809988e-03f);
-        h = fmaf(h, s, 1.824696665e-03f);
-        h = fmaf(h, s, -3.379537957e-03f);
-        h = fmaf(h, s, 5.249740090e-03f);
-        h = fmaf(h, s, 1.424003482e+00f);
-        h = fmaf(h, s, 4.625601292e+00f);
-    }
-    const float x = y * h;
+    const float x = y * normal_h(wv);
     return up ? -x : x;
+}
+
+// Two normals at once with the packed two-wide FP32 instructions of the
+// sm_100 family (one instruction issue computes both values).  The operations
+// and roundings are those of normal_of(w, float) for each word, so the values
+// are identical; a pair with a word in the tail piece takes the scalar path.
+#ifndef SRMC_NORMAL_PAIRS
+#define SRMC_NORMAL_PAIRS 1
+#endif
+#if SRMC_NORMAL_PAIRS && !defined(__CUDACC_RTC__)
+__device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 normal_pair(unsigned w0, unsigned w1)
+{
+    const bool up0 = w0 >= 0x80000000u, up1 = w1 >= 0x80000000u;
+    const unsigned v0 = up0 ? ~w0 : w0, v1 = up1 ? ~w1 : w1;
+    const float2 p = __ffma2_rn(make_float2(__uint2float_rn(v0), __uint2float_rn(v1)),
+                                f2(0x1p-32f), f2(0x1p-33f));
+    const float2 y = __ffma2_rn(make_float2(__uint2float_rn(0x7FFFFFFFu - v0),
+                                            __uint2float_rn(0x7FFFFFFFu - v1)),
+                                f2(-0x1p-31f), f2(-0x1p-32f));
+    const float2 r = __fmul2_rn(f2(4.0f), __fmul2_rn(p, __ffma2_rn(p, f2(-1.0f), f2(1.0f))));
+    const float2 wv = make_float2(-__logf(r.x), -__logf(r.y));
+    float2 h;
+    if (wv.x < 5.0f && wv.y < 5.0f) {
+        const float2 s = __fadd2_rn(wv, f2(-2.5f));
+        h = f2(NRM_C[0]);
+#pragma unroll
+        for (int c = 1; c < 10; ++c) h = __ffma2_rn(h, s, f2(NRM_C[c]));
+    } else {
+        h = make_float2(normal_h(wv.x), normal_h(wv.y));
+    }
+    const float2 x = __fmul2_rn(y, h);
+    return make_float2(up0 ? -x.x : x.x, up1 ? -x.y : x.y);
+}
+#endif
+
+// out[l] = sdt Phi^{-1}(U(w[l])): the Brownian increments of one step.
+template <int D>
+__device__ __forceinline__ void scaled_normals(const unsigned (&w)[D], double sdt, double (&out)[D])
+{
+#pragma unroll
+    for (int l = 0; l < D; ++l) out[l] = sdt * normal_of(w[l], 0.0);
+}
+template <int D>
+__device__ __forceinline__ void scaled_normals(const unsigned (&w)[D], float sdt, float (&out)[D])
+{
+#if SRMC_NORMAL_PAIRS && !defined(__CUDACC_RTC__)
+#pragma unroll
+    for (int l = 0; l + 1 < D; l += 2) {
+        const float2 v = __fmul2_rn(f2(sdt), normal_pair(w[l], w[l + 1]));
+        out[l] = v.x;
+        out[l + 1] = v.y;
+    }
+    if constexpr ((D & 1) != 0) out[D - 1] = sdt * normal_of(w[D - 1], 0.0f);
+#else
+#pragma unroll
+    for (int l = 0; l < D; ++l) out[l] = sdt * normal_of(w[l], 0.0f);
+#endif
 }
 
 // ---- restricted logistic sampler (assumption A_nu, Alg. 3) ------------------

@@ -12,7 +12,8 @@
 //   Z fit    Cholesky of the Gram matrix in FP64, beta = G^{-1} r_Z.
 //   phase B  per path: regenerate x_i, dW_i, X_{i+1} from the same counters,
 //            f_i(x_i, y_{i+1}(X_{i+1}), z_i(x_i)) with the new beta (Z before Y),
-//            add phi f_i to the moments.
+//            add phi f_i to the moments.  Only drivers that read z need it:
+//            otherwise f_i is added to the Y response in phase A.
 //   Y fit    alpha = G^{-1} (r_S + dt r_F); write row (i, k).
 //
 // Moments: FP64 form accumulates in double per thread.  FP32 form
@@ -544,9 +545,9 @@ __device__ __forceinline__ void solve_stratum(const Params &P, const int i, cons
             unsigned wd[D], we[D];
             W.template take<D % 4, D, false>(P, wd);
             if constexpr (NW == 2) W.template take<(2 * D) % 4, D, false>(P, we);
+            scaled_normals<D>(wd, sdt, dwi);
 #pragma unroll
             for (int l = 0; l < D; ++l) {
-                dwi[l] = sdt * normal_of(wd[l], (R)0);
                 xj[l] = next_coord<R, D>(P, i, l, x, dwi[l], NW == 2 ? normal_of(we[l], (R)0) : (R)0);
             }
         }
@@ -560,6 +561,10 @@ __device__ __forceinline__ void solve_stratum(const Params &P, const int i, cons
             if (!P.cv_own) CI = control_dot<R, D, p>(P, (unsigned)i * (unsigned)P.K + (unsigned)k, phi, dwi);
         }
         eval_at<R, D, LP1, MODEL, ZIN, CV>(P, i + 1, xj, yn, zj, phij, rowj);
+        // A driver that does not read z: f_i(x_i, y_{i+1}(X_{i+1})) is known
+        // here, so the Y response is complete in phase A (no phase B).
+        [[maybe_unused]] R fdt = (R)0;
+        if constexpr (!ZIN) fdt = dt * model_f<R, D, MODEL, ZIN>(P, i, x, yn, zj);
         R S = (R)0;
         // Steps j = i+1 .. N-1 in groups of G, so that the word phase of
         // every step in a group is a compile-time constant.
@@ -573,9 +578,9 @@ __device__ __forceinline__ void solve_stratum(const Params &P, const int i, cons
                 W.template take<(D + NW * D * (1 + g)) % 4, D, false>(P, wn);
                 if constexpr (NW == 2) W.template take<(2 * D + NW * D * (1 + g)) % 4, D, false>(P, we);
                 R xn[D], zn[D], dw[D];
+                scaled_normals<D>(wn, sdt, dw);
 #pragma unroll
                 for (int l = 0; l < D; ++l) {
-                    dw[l] = sdt * normal_of(wn[l], (R)0);
                     xn[l] = next_coord<R, D>(P, j, l, xj, dw[l], NW == 2 ? normal_of(we[l], (R)0) : (R)0);
                 }
                 if constexpr (CV) {
@@ -600,6 +605,7 @@ __device__ __forceinline__ void solve_stratum(const Params &P, const int i, cons
         // Z response uses S - CZ; the phase-A part of the Y response S - CZ - CI.
         R SZ = S, SY = S;
         if constexpr (CV) { SZ = S - CZ; SY = SZ - CI; }
+        if constexpr (!ZIN) SY += fdt;
         if constexpr (RS) {
             // this path's products (zero for lanes past M)
             const float Sv = valid ? (float)SZ : 0.0f;
@@ -667,59 +673,64 @@ __device__ __forceinline__ void solve_stratum(const Params &P, const int i, cons
     __syncthreads();
 
     // ---------------- phase B: the f_i term of the Y response ----------------
-    MB mB;
-    mB.zero();
-    since_flush = 0;
-    for (long long m0 = 0; m0 < Mk; m0 += blockDim.x) {
-        const long long m = m0 + threadIdx.x;
-        const bool valid = m < Mk;
-        Words W;
-        W.init(P, (unsigned)m, (unsigned)k, (unsigned)i);
-        R x[D], phi[p], x1[D], y1, z1[D], zi[D];
-        phi[0] = (R)1;
-        {
-            unsigned ws[D];
-            W.template take<0, D, true>(P, ws);
+    // Only for drivers that read z: f_i then needs z_i(x_i) from the Z fit
+    // above (Z before Y), so the paths of the cloud are regenerated.
+    if constexpr (ZIN) {
+        MB mB;
+        mB.zero();
+        since_flush = 0;
+        for (long long m0 = 0; m0 < Mk; m0 += blockDim.x) {
+            const long long m = m0 + threadIdx.x;
+            const bool valid = m < Mk;
+            Words W;
+            W.init(P, (unsigned)m, (unsigned)k, (unsigned)i);
+            R x[D], phi[p], x1[D], y1, z1[D], zi[D];
+            phi[0] = (R)1;
+            {
+                unsigned ws[D];
+                W.template take<0, D, true>(P, ws);
 #pragma unroll
-            for (int l = 0; l < D; ++l) {
-                x[l] = sample_start(ws[l], l);
-                if (LP1) phi[1 + l] = start_phi(x[l], l);
+                for (int l = 0; l < D; ++l) {
+                    x[l] = sample_start(ws[l], l);
+                    if (LP1) phi[1 + l] = start_phi(x[l], l);
+                }
+                add_quadratic<R, D, p>(phi);
             }
-            add_quadratic<R, D, p>(phi);
-        }
-        {
-            unsigned wd[D], we[D];
-            W.template take<D % 4, D, false>(P, wd);
-            if constexpr (NW == 2) W.template take<(2 * D) % 4, D, false>(P, we);
+            {
+                unsigned wd[D], we[D];
+                W.template take<D % 4, D, false>(P, wd);
+                if constexpr (NW == 2) W.template take<(2 * D) % 4, D, false>(P, we);
+                R dwb[D];
+                scaled_normals<D>(wd, sdt, dwb);
 #pragma unroll
-            for (int l = 0; l < D; ++l) {
-                const R dw = sdt * normal_of(wd[l], (R)0);
-                x1[l] = next_coord<R, D>(P, i, l, x, dw, NW == 2 ? normal_of(we[l], (R)0) : (R)0);
+                for (int l = 0; l < D; ++l) {
+                    x1[l] = next_coord<R, D>(P, i, l, x, dwb[l], NW == 2 ? normal_of(we[l], (R)0) : (R)0);
+                }
             }
+            {
+                [[maybe_unused]] R phi1[p];
+                [[maybe_unused]] unsigned row1;
+                eval_at<R, D, LP1, MODEL, ZIN, false>(P, i + 1, x1, y1, z1, phi1, row1);
+            }
+#pragma unroll
+            for (int l = 0; l < q; ++l) {
+                R w = beta_r[l * p];
+#pragma unroll
+                for (int a = 1; a < p; ++a) w += beta_r[l * p + a] * phi[a];
+                zi[l] = clamp_r(w, Form<R>::Cz(P));
+            }
+            const R fi = model_f<R, D, MODEL, ZIN>(P, i, x, y1, zi);
+            if (valid) {
+#pragma unroll
+                for (int a = 0; a < p; ++a) mB.add(a, phi[a] * fi);
+            }
+            if (++since_flush == FLUSH) { mB.flush(lane); since_flush = 0; }
         }
         {
-            [[maybe_unused]] R phi1[p];
-            [[maybe_unused]] unsigned row1;
-            eval_at<R, D, LP1, MODEL, ZIN, false>(P, i + 1, x1, y1, z1, phi1, row1);
+            double lv[(EB + 31) / 32];
+            mB.finish(lv, lane);
+            block_totals<EB>(lv, redB, totB, lane, warp, nwarps);
         }
-#pragma unroll
-        for (int l = 0; l < q; ++l) {
-            R w = beta_r[l * p];
-#pragma unroll
-            for (int a = 1; a < p; ++a) w += beta_r[l * p + a] * phi[a];
-            zi[l] = clamp_r(w, Form<R>::Cz(P));
-        }
-        const R fi = model_f<R, D, MODEL, ZIN>(P, i, x, y1, zi);
-        if (valid) {
-#pragma unroll
-            for (int a = 0; a < p; ++a) mB.add(a, phi[a] * fi);
-        }
-        if (++since_flush == FLUSH) { mB.flush(lane); since_flush = 0; }
-    }
-    {
-        double lv[(EB + 31) / 32];
-        mB.finish(lv, lane);
-        block_totals<EB>(lv, redB, totB, lane, warp, nwarps);
     }
 
     // ---------------- Y fit (FP64) and the row (i, k) -----------------------
@@ -727,7 +738,7 @@ __device__ __forceinline__ void solve_stratum(const Params &P, const int i, cons
         const double Md = (double)Mk;
         const double dtd = P.dt;
         double *alpha = totB;                      // solved in place
-        for (int a = 0; a < p; ++a) alpha[a] = totA[EG + EZ + a] + dtd * totB[a];
+        for (int a = 0; a < p; ++a) alpha[a] = totA[EG + EZ + a] + (ZIN ? dtd * totB[a] : 0.0);
         if (LP1 && ok_s) {
             chol_solve<p>(Ls, Linv, alpha, alpha);
         } else {
