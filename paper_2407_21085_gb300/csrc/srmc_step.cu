@@ -102,6 +102,84 @@ __device__ __forceinline__ R next_coord(const Params &P, int j, int l, const R (
 #endif
 }
 
+// Whether the FP32 Euler step and cell location of equal-size strata take
+// coordinates two at a time with the packed FP32 instructions (same
+// operations and roundings as the scalar forms).
+#ifndef SRMC_COORD_PAIRS
+#define SRMC_COORD_PAIRS 1
+#endif
+#if SRMC_COORD_PAIRS && SRMC_NORMAL_PAIRS && !defined(__CUDACC_RTC__) && SRMC_STEP_DYN == 0
+#define SRMC_PAIRS_ON 1
+#else
+#define SRMC_PAIRS_ON 0
+#endif
+
+// X_{j+1} from X_j = x and the increments dw (the whole vector).
+template <typename R, int D>
+__device__ __forceinline__ void advance(const Params &P, int j, const R (&x)[D], const R (&dw)[D],
+                                        R (&xn)[D])
+{
+#if SRMC_PAIRS_ON && !defined(SRMC_USER_DYNAMICS)
+    if constexpr (sizeof(R) == 4) {
+#pragma unroll
+        for (int l = 0; l + 1 < D; l += 2) {
+            const float2 v = __ffma2_rn(make_float2(P.s1_f[l], P.s1_f[l + 1]), make_float2(dw[l], dw[l + 1]),
+                                        __ffma2_rn(make_float2(P.A_f[l], P.A_f[l + 1]),
+                                                   make_float2(x[l], x[l + 1]),
+                                                   make_float2(P.c_f[l], P.c_f[l + 1])));
+            xn[l] = v.x;
+            xn[l + 1] = v.y;
+        }
+        if constexpr ((D & 1) != 0) xn[D - 1] = next_coord<R, D>(P, j, D - 1, x, dw[D - 1], (R)0);
+        return;
+    }
+#endif
+#pragma unroll
+    for (int l = 0; l < D; ++l) xn[l] = next_coord<R, D>(P, j, l, x, dw[l], (R)0);
+}
+
+// Cells of x on equal-size strata: kk = sum_l c_l stride_l, and (LP1) the
+// centred coordinates phi[1 + l] = 2 (t_l - c_l) - 1, t_l = (x_l - lo_l) / h_l.
+template <typename R, int D, bool LP1, int p>
+__device__ __forceinline__ unsigned locate_point(const Params &P, const R (&x)[D], R (&phi)[p])
+{
+    unsigned kk = 0;
+#if SRMC_PAIRS_ON
+    if constexpr (sizeof(R) == 4) {
+#pragma unroll
+        for (int l = 0; l + 1 < D; l += 2) {
+            const float2 t = __fmul2_rn(__fadd2_rn(make_float2(x[l], x[l + 1]),
+                                                   make_float2(-P.lo_f[l], -P.lo_f[l + 1])),
+                                        make_float2(P.r_f[l], P.r_f[l + 1]));
+            const float c0 = fminf(fmaxf(floorf(t.x), 0.0f), (float)(P.cells[l] - 1));
+            const float c1 = fminf(fmaxf(floorf(t.y), 0.0f), (float)(P.cells[l + 1] - 1));
+            kk += (unsigned)(int)c0 * (unsigned)P.stride[l] + (unsigned)(int)c1 * (unsigned)P.stride[l + 1];
+            if (LP1) {
+                const float2 u = __ffma2_rn(make_float2(2.0f, 2.0f), __fadd2_rn(t, make_float2(-c0, -c1)),
+                                            make_float2(-1.0f, -1.0f));
+                phi[1 + l] = u.x;
+                phi[2 + l] = u.y;
+            }
+        }
+        if constexpr ((D & 1) != 0) {
+            R t;
+            const int c = locate_dim(x[D - 1], P.lo_f[D - 1], P.r_f[D - 1], P.cells[D - 1], t);
+            kk += (unsigned)c * (unsigned)P.stride[D - 1];
+            if (LP1) phi[D] = 2.0f * (t - (float)c) - 1.0f;
+        }
+        return kk;
+    }
+#endif
+#pragma unroll
+    for (int l = 0; l < D; ++l) {
+        R t;
+        const int c = locate_dim(x[l], Form<R>::lo(P, l), Form<R>::scale(P, l), P.cells[l], t);
+        kk += (unsigned)c * (unsigned)P.stride[l];
+        if (LP1) phi[1 + l] = (R)2 * (t - (R)c) - (R)1;
+    }
+    return kk;
+}
+
 template <int E>
 struct Moments64 {
     double a[E];
@@ -324,13 +402,7 @@ __device__ __forceinline__ void eval_at(const Params &P, int j, const R (&x)[D],
     R phi[p];
     phi[0] = (R)1;
     if constexpr (SRMC_STEP_KIND == 0) {
-#pragma unroll
-        for (int l = 0; l < D; ++l) {
-            R t;
-            const int c = locate_dim(x[l], Form<R>::lo(P, l), Form<R>::scale(P, l), P.cells[l], t);
-            kk += (unsigned)c * (unsigned)P.stride[l];
-            if (LP1) phi[1 + l] = (R)2 * (t - (R)c) - (R)1;
-        }
+        kk = locate_point<R, D, LP1, p>(P, x, phi);
     } else {
 #pragma unroll
         for (int l = 0; l < D; ++l) {
@@ -574,14 +646,18 @@ __device__ __forceinline__ void solve_stratum(const Params &P, const int i, cons
                 constexpr int g = decltype(gc)::value;
                 const int j = j0 + g;
                 if (j >= P.N) return;
-                unsigned wn[D], we[D];
+                unsigned wn[D];
+                [[maybe_unused]] unsigned we[D];
                 W.template take<(D + NW * D * (1 + g)) % 4, D, false>(P, wn);
                 if constexpr (NW == 2) W.template take<(2 * D + NW * D * (1 + g)) % 4, D, false>(P, we);
                 R xn[D], zn[D], dw[D];
                 scaled_normals<D>(wn, sdt, dw);
+                if constexpr (NW == 1) {
+                    advance<R, D>(P, j, xj, dw, xn);
+                } else {
 #pragma unroll
-                for (int l = 0; l < D; ++l) {
-                    xn[l] = next_coord<R, D>(P, j, l, xj, dw[l], NW == 2 ? normal_of(we[l], (R)0) : (R)0);
+                    for (int l = 0; l < D; ++l)
+                        xn[l] = next_coord<R, D>(P, j, l, xj, dw[l], normal_of(we[l], (R)0));
                 }
                 if constexpr (CV) {
                     // own control: z_j(X_j), already evaluated for the driver
