@@ -447,6 +447,42 @@ __device__ __forceinline__ R model_g(const Params &P, const R (&x)[D])
     }
 }
 
+// Drivers that do not read z (the cos family without kapz, the affine
+// model) are a part in x plus a part in y: f_j(x, y) = fy(y) + fx_j(x).  The
+// step kernel takes fx_j(X_j) before the next point is located, so that X_j
+// need not stay live across the gather.
+template <typename R, int D, int MODEL>
+__device__ __forceinline__ R model_f_x(const Params &P, int j, const R (&x)[D])
+{
+    if constexpr (MODEL == MODEL_COS) {
+        R s = x[0];
+#pragma unroll
+        for (int l = 1; l < D; ++l) s += x[l];
+        s = (sizeof(R) == 8) ? s / (R)P.sqrt_d : s * (R)P.inv_sqrt_d_f;
+        const R c1 = __ldg(Form<R>::stepc(P) + 2 * j);     // kap e_j^2
+        const R cs = cos_r(s);
+        return -(c1 * cs * cs);
+    } else if constexpr (MODEL == MODEL_AFFINE) {
+        R v = Form<R>::prm(P, 1 + D);
+#pragma unroll
+        for (int l = 0; l < D; ++l) v += Form<R>::prm(P, 2 + D + l) * x[l];
+        return v;
+    } else {
+        return (R)0;
+    }
+}
+template <typename R, int D, int MODEL>
+__device__ __forceinline__ R model_f_y(const Params &P, R y, R fx)
+{
+    if constexpr (MODEL == MODEL_COS) {
+        return Form<R>::lin(P) * y + Form<R>::prm(P, 1) * y * y + fx;   // (lam + s0^2/2) y + kap y^2
+    } else if constexpr (MODEL == MODEL_AFFINE) {
+        return fx + Form<R>::prm(P, 2 + 2 * D) * y;
+    } else {
+        return fx;
+    }
+}
+
 // f_j(x, y, z); z is used only when ZIN.
 template <typename R, int D, int MODEL, bool ZIN>
 __device__ __forceinline__ R model_f(const Params &P, int j, const R (&x)[D], R y, const R *z)
@@ -455,6 +491,7 @@ __device__ __forceinline__ R model_f(const Params &P, int j, const R (&x)[D], R 
     if constexpr (MODEL == MODEL_USER) return srmc_user_f((R)j * Form<R>::dt(P), x, y, z, D, P.prm);
 #endif
     if (MODEL == MODEL_COS) {
+        if (!ZIN) return model_f_y<R, D, MODEL>(P, y, model_f_x<R, D, MODEL>(P, j, x));
         R s = x[0];
 #pragma unroll
         for (int l = 1; l < D; ++l) s += x[l];
@@ -487,10 +524,7 @@ __device__ __forceinline__ R model_f(const Params &P, int j, const R (&x)[D], R 
         for (int l = 0; l < D; ++l) sz += z[l];
         return sz * (y - (R)(2 + D) / (R)(2 * D));
     } else {
-        R v = Form<R>::prm(P, 1 + D);
-#pragma unroll
-        for (int l = 0; l < D; ++l) v += Form<R>::prm(P, 2 + D + l) * x[l];
-        return v + Form<R>::prm(P, 2 + 2 * D) * y;
+        return model_f_y<R, D, MODEL>(P, y, model_f_x<R, D, MODEL>(P, j, x));
     }
 }
 

@@ -632,11 +632,13 @@ __device__ __forceinline__ void solve_stratum(const Params &P, const int i, cons
         if constexpr (CV) {
             if (!P.cv_own) CI = control_dot<R, D, p>(P, (unsigned)i * (unsigned)P.K + (unsigned)k, phi, dwi);
         }
-        eval_at<R, D, LP1, MODEL, ZIN, CV>(P, i + 1, xj, yn, zj, phij, rowj);
         // A driver that does not read z: f_i(x_i, y_{i+1}(X_{i+1})) is known
-        // here, so the Y response is complete in phase A (no phase B).
+        // after this first step, so the Y response is complete in phase A (no
+        // phase B).  Its part in x_i is taken before X_{i+1} is located.
         [[maybe_unused]] R fdt = (R)0;
-        if constexpr (!ZIN) fdt = dt * model_f<R, D, MODEL, ZIN>(P, i, x, yn, zj);
+        if constexpr (!ZIN) fdt = model_f_x<R, D, MODEL>(P, i, x);
+        eval_at<R, D, LP1, MODEL, ZIN, CV>(P, i + 1, xj, yn, zj, phij, rowj);
+        if constexpr (!ZIN) fdt = dt * model_f_y<R, D, MODEL>(P, yn, fdt);
         R S = (R)0;
         // Steps j = i+1 .. N-1 in groups of G, so that the word phase of
         // every step in a group is a compile-time constant.
@@ -671,8 +673,11 @@ __device__ __forceinline__ void solve_stratum(const Params &P, const int i, cons
                     }
                     if (!own) CZ += control_dot<R, D, p>(P, rowj, phij, dw);
                 }
+                [[maybe_unused]] R fx = (R)0;
+                if constexpr (!ZIN) fx = model_f_x<R, D, MODEL>(P, j, xj);
                 eval_at<R, D, LP1, MODEL, ZIN, CV>(P, j + 1, xn, yn, zn, phij, rowj);
-                S += dt * model_f<R, D, MODEL, ZIN>(P, j, xj, yn, zj);
+                if constexpr (ZIN) S += dt * model_f<R, D, MODEL, ZIN>(P, j, xj, yn, zj);
+                else S += dt * model_f_y<R, D, MODEL>(P, yn, fx);
 #pragma unroll
                 for (int l = 0; l < D; ++l) { xj[l] = xn[l]; zj[l] = zn[l]; }
             });
