@@ -233,6 +233,31 @@ def test_deterministic(dev):
     assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
 
 
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32", 1e-5)])
+def test_one_pass_equals_two_passes(dev, prec, tol):
+    # A driver without z is solved in one pass over each cloud (f_i added to
+    # the Y response in phase A); kapz = 1e-300 selects the z-reading kernel,
+    # which regenerates the cloud for f_i after the Z fit (phase B), on a
+    # driver whose z term vanishes in rounding.  Both must give the same fits.
+    torch, srmc = dev
+    for w in (W.cfg2(C=12, N=6, M=384, precision=prec),
+              W.cfg2(C=12, N=6, M=384, precision=prec, basis="lp0"),
+              W.cos_model("d6", d=6, N=3, C=2, a=2.0, M=96, s0=0.3, lam=0.2, kap=0.5, precision=prec)):
+        lam, kap, _, s0 = w.params
+        w2 = w.replace(params=[lam, kap, 1e-300, s0])
+        a, b = srmc.Solver(w), srmc.Solver(w2)
+        a.srmc_solve()
+        b.srmc_solve()
+        x = a.centres()
+        for i in range(w.N):
+            ya, za = (t.cpu().numpy() for t in a.evaluate(i, x))
+            yb, zb = (t.cpu().numpy() for t in b.evaluate(i, x))
+            assert np.max(np.abs(ya - yb) / (1 + np.abs(yb))) <= tol, (w.name, w.basis, i)
+            assert np.max(np.abs(za - zb) / (1 + np.abs(zb))) <= tol, (w.name, w.basis, i)
+        a.close()
+        b.close()
+
+
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-11), ("fp32", 2e-5)])
 def test_exact_affine_fit(dev, prec, tol):
     # sigma = 0: y_i is affine and LP1 must reproduce it (exact up to rounding)
