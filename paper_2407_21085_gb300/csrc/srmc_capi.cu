@@ -469,6 +469,7 @@ srmc_status srmc_create(const srmc_problem *pr, const srmc_strata *sa, const srm
         }
     }
     P.drift = pr->model == SRMC_MODEL_COS && has_drift ? 1 : 0;
+    // The step kernels take these paddings as constants of their basis dimension (row_pad).
     P.ry32 = pad_to(p, 4); P.rz32 = pad_to(q * p, 4);
     P.ry64 = pad_to(p, 2); P.rz64 = pad_to(q * p, 2);
     P.ph = half_pad(p); P.rc16 = q * P.ph;

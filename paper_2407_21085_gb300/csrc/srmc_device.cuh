@@ -224,7 +224,8 @@ __device__ __forceinline__ float normal_of(unsigned w, float)
 // Two normals at once with the packed two-wide FP32 instructions of the
 // sm_100 family (one instruction issue computes both values).  The operations
 // and roundings are those of normal_of(w, float) for each word, so the values
-// are identical; a pair with a word in the tail piece takes the scalar path.
+// are identical.  The central piece is evaluated for both words, the tail
+// piece (rare) only when a word of the pair needs it.
 #ifndef SRMC_NORMAL_PAIRS
 #define SRMC_NORMAL_PAIRS 1
 #endif
@@ -242,13 +243,22 @@ __device__ __forceinline__ float2 normal_pair(unsigned w0, unsigned w1)
     const float2 r = __fmul2_rn(f2(4.0f), __fmul2_rn(p, __ffma2_rn(p, f2(-1.0f), f2(1.0f))));
     const float2 wv = make_float2(-__logf(r.x), -__logf(r.y));
     float2 h;
-    if (wv.x < 5.0f && wv.y < 5.0f) {
+    // central piece for both words; the tail piece (w >= 5, rare) only when a
+    // word needs it, and only for that word
+    {
         const float2 s = __fadd2_rn(wv, f2(-2.5f));
         h = f2(NRM_C[0]);
 #pragma unroll
         for (int c = 1; c < 10; ++c) h = __ffma2_rn(h, s, f2(NRM_C[c]));
-    } else {
-        h = make_float2(normal_h(wv.x), normal_h(wv.y));
+    }
+    const bool tx = !(wv.x < 5.0f), ty = !(wv.y < 5.0f);
+    if (tx || ty) {
+        const float2 s = __fadd2_rn(make_float2(sqrtf(wv.x), sqrtf(wv.y)), f2(-3.435767889f));
+        float2 ht = f2(NRM_T[0]);
+#pragma unroll
+        for (int c = 1; c < 10; ++c) ht = __ffma2_rn(ht, s, f2(NRM_T[c]));
+        if (tx) h.x = ht.x;
+        if (ty) h.y = ht.y;
     }
     const float2 x = __fmul2_rn(y, h);
     return make_float2(up0 ? -x.x : x.x, up1 ? -x.y : x.y);

@@ -385,6 +385,11 @@ __device__ void chol_solve(const double *L, const double *Linv, const double *r,
     }
 }
 
+// Padded length of a table row of n entries: 16 bytes (4 floats or 2
+// doubles) per vector load.
+template <typename R>
+__host__ __device__ constexpr int row_pad(int n) { return sizeof(R) == 4 ? (n + 3) / 4 * 4 : (n + 1) / 2 * 2; }
+
 // y_{j}(x), z_{j}(x) from the row of the stratum holding x (truncated), or
 // g(x) when j == N.
 // With CV, also hands back phi(x) and the row index of (j, stratum of x), from
@@ -415,15 +420,18 @@ __device__ __forceinline__ void eval_at(const Params &P, int j, const R (&x)[D],
     }
     add_quadratic<R, D, p>(phi);
     const unsigned row = (unsigned)j * (unsigned)P.K + kk;     // N K < 2^32 (checked at create)
+    // The row strides are those srmc_create sets (rows padded to 16 bytes),
+    // as constants of the kernel's basis dimension.
+    constexpr unsigned RY = (unsigned)row_pad<R>(p), RZ = (unsigned)row_pad<R>(D * p);
     R a[p];
-    load_row<p>(Form<R>::Ytab(P) + row * (unsigned)Form<R>::ry(P), a);
+    load_row<p>(Form<R>::Ytab(P) + row * RY, a);
     R v = a[0];
 #pragma unroll
     for (int c = 1; c < p; ++c) v += a[c] * phi[c];
     y = clamp_r(v, Form<R>::Cy(P));
     if (ZIN) {
         R bz[D * p];
-        load_row<D * p>(Form<R>::Ztab(P) + row * (unsigned)Form<R>::rz(P), bz);
+        load_row<D * p>(Form<R>::Ztab(P) + row * RZ, bz);
 #pragma unroll
         for (int l = 0; l < D; ++l) {
             R w = bz[l * p];
