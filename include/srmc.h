@@ -410,7 +410,10 @@ srmc_status srmc_philox(const uint32_t *dev_ctr, const uint32_t key[2], long lon
                         uint32_t *dev_out, void *stream);
 
 /* Standard normals xi = Phi^{-1}((w + 1/2) 2^-32) of n words; FP64 into
- * dev_out64 and/or the single-precision form into dev_out32 (either NULL). */
+ * dev_out64 and/or the single-precision form into dev_out32 (either NULL).
+ * The single-precision form takes words 2t and 2t + 1 as a pair, as the FP32
+ * step kernels do for the increments of a step, and an unpaired last word
+ * alone; both ways give the same values. */
 srmc_status srmc_normals(const uint32_t *dev_words, long long n, double *dev_out64,
                          float *dev_out32, void *stream);
 

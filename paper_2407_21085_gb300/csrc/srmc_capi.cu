@@ -221,12 +221,30 @@ __global__ void philox_kernel(const uint32_t *ctr, uint32_t k0, uint32_t k1, lon
     }
 }
 
+// FP64: one word per item.  FP32: words (2t, 2t + 1) taken as a pair by the
+// packed form the step kernels use for the increments of a step; a last word
+// without a partner takes the scalar form (the same values).
 __global__ void normals_kernel(const uint32_t *w, long long n, double *o64, float *o32)
 {
     for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < n;
          a += (long long)gridDim.x * blockDim.x) {
         if (o64) o64[a] = srmc::normal_of(w[a], 0.0);
-        if (o32) o32[a] = srmc::normal_of(w[a], 0.0f);
+    }
+    if (!o32) return;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; 2 * t < n;
+         t += (long long)gridDim.x * blockDim.x) {
+        const long long a = 2 * t;
+#if SRMC_NORMAL_PAIRS
+        if (a + 1 < n) {
+            const float2 v = srmc::normal_pair(w[a], w[a + 1]);
+            o32[a] = v.x;
+            o32[a + 1] = v.y;
+            continue;
+        }
+#else
+        if (a + 1 < n) o32[a + 1] = srmc::normal_of(w[a + 1], 0.0f);
+#endif
+        o32[a] = srmc::normal_of(w[a], 0.0f);
     }
 }
 

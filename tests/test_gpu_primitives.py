@@ -64,8 +64,23 @@ def test_normals(dev, orc):
     # the upper half is the mirror of the lower half: xi(~w) = -xi(w)
     comp = _u32_tensor(torch, ~words)
     c64 = torch.empty(len(words), dtype=torch.float64, device="cuda")
-    srmc.srmc_normals(comp, c64, None)
+    c32 = torch.empty(len(words), dtype=torch.float32, device="cuda")
+    srmc.srmc_normals(comp, c64, c32)
     assert np.array_equal(c64.cpu().numpy(), -g64)
+    assert np.array_equal(c32.cpu().numpy(), -o32.cpu().numpy())
+    # FP32 words are taken in pairs (the packed form of the step kernels); a
+    # single word takes the scalar form.  Both must give the same bits, for
+    # central words, tail words (w >= 5 in the erfinv reduction) and pairs
+    # mixing the two: the first eight words, every tail word, 40 others.
+    p = (np.minimum(words, ~words).astype(np.float64) + 0.5) * 2.0 ** -32
+    tail = np.nonzero(4 * p * (1 - p) <= np.exp(-5.0) * (1 + 1e-6))[0]
+    pick = np.unique(np.concatenate([np.arange(8), tail, rng.integers(8, len(words), 40)]))
+    assert len(tail) > 20
+    bits = o32.cpu().numpy().view(np.uint32)
+    one = torch.empty(1, dtype=torch.float32, device="cuda")
+    for a in pick:
+        srmc.srmc_normals(_u32_tensor(torch, words[a:a + 1]), None, one)
+        assert one.cpu().numpy().view(np.uint32)[0] == bits[a], (int(words[a]), a)
 
 
 def _edge_points(w, rng, n_random=4000):
