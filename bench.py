@@ -176,21 +176,32 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
-        rows = []
         with open(self.path) as fh:
-            for line in fh:
-                v = [a.strip() for a in line.split(",")]
-                if len(v) >= 9:
-                    rows.append(v)
+            lines = fh.readlines()
         os.unlink(self.path)
-        if not rows:
-            return None
-        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[c] for r in rows for c in range(4) if r[5 + c].lower() == "active"})
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(rows)}
+        return summarize_clocks(lines)
+
+
+THROTTLE_REASONS = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+
+
+def summarize_clocks(lines):
+    """Median SM clock, maximum SM clock and the throttle reasons seen in
+    nvidia-smi samples of ClockSampler.FIELDS (CSV, no header, no units);
+    None when no complete sample was taken.  Fields that are not numbers
+    (e.g. "[N/A]") are left out of the clock figures."""
+    rows = []
+    for line in lines:
+        v = [a.strip() for a in line.split(",")]
+        if len(v) >= 9:
+            rows.append(v)
+    if not rows:
+        return None
+    sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+    mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+    reasons = sorted({THROTTLE_REASONS[c] for r in rows for c in range(4) if r[5 + c].lower() == "active"})
+    return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+            "reasons": reasons, "samples": len(rows)}
 
 
 # ---- the GPU arm ---------------------------------------------------------------
