@@ -298,7 +298,7 @@ srmc_status srmc_mlp_loss_grad(srmc_mlp *m, const float *dev_a, const float *dev
  * strata k uniform, x ~ nu_k, a = (t_i, x), target y_i(x) from its FP64 table.
  * iters Adam steps on consecutive batches (lr decays geometrically to lr/10).
  * dev_loss_curve [iters] (may be NULL) receives the batch losses.
- * n_data must be a multiple of batch. */
+ * n_data must be a multiple of batch and at most 2^40. */
 srmc_status srmc_mlp_fit(srmc_mlp *m, const srmc_solver *coarse, long long n_data, int iters,
                          int batch, float lr, unsigned long long seed, float *dev_loss_curve,
                          void *stream);
@@ -314,8 +314,12 @@ srmc_status srmc_mlp_fit(srmc_mlp *m, const srmc_solver *coarse, long long n_dat
  * library holds it until the process exits) instead of allocating them:
  *   - limit: n_data * (n_in + 1) + nparams + 64 <= 2^21 floats (8 MiB);
  *     larger requests fail with SRMC_ERR_INVALID_ARG and a message;
- *   - the first call on a device looks the array up on that device (make it
- *     current first); make that first call before any stream capture;
+ *   - the network's device must be the current device (else
+ *     SRMC_ERR_INVALID_ARG); the first call on a device looks the array up
+ *     on that device and keeps its address for the life of the process, so
+ *     make that first call before any stream capture; a cudaDeviceReset (or
+ *     anything else that tears down the device's primary context) leaves the
+ *     kept address stale: do not call this entry point after one;
  *   - every call on a device shares the one array, so calls whose work
  *     overlaps on the GPU (different streams or threads) race; serialise
  *     them.  The parts that must start at zero are cleared by each call.

@@ -728,6 +728,9 @@ srmc_status srmc_mlp_fit(srmc_mlp *m, const srmc_solver *s, long long n_data, in
         return mfail(SRMC_ERR_INVALID_ARG, "srmc_mlp_fit: bad argument");
     if (m->nin != s->P.d + 1) return mfail(SRMC_ERR_INVALID_ARG, "srmc_mlp_fit: n_in must be d + 1");
     if (s->done_from > 0) return mfail(SRMC_ERR_STATE, "srmc_mlp_fit: the coarse solve is not finished");
+    // 2^40 points (16 TiB of inputs at d = 3) is beyond any device, and keeps
+    // the byte counts below far from wrapping
+    if (n_data > (1LL << 40)) return mfail(SRMC_ERR_INVALID_ARG, "srmc_mlp_fit: n_data > 2^40");
     cudaStream_t st = (cudaStream_t)stream;
     float *a = nullptr, *y = nullptr;
     MLP_CUDA(cudaMalloc(&a, sizeof(float) * n_data * m->nin), "cudaMalloc training inputs");
@@ -771,6 +774,18 @@ srmc_status srmc_mlp_fit_noalloc(srmc_mlp *m, const srmc_solver *s, long long n_
         return mfail(SRMC_ERR_INVALID_ARG, "srmc_mlp_fit_noalloc: bad argument");
     if (m->nin != s->P.d + 1) return mfail(SRMC_ERR_INVALID_ARG, "srmc_mlp_fit_noalloc: n_in must be d + 1");
     if (s->done_from > 0) return mfail(SRMC_ERR_STATE, "srmc_mlp_fit_noalloc: the coarse solve is not finished");
+    {
+        // the scratch is looked up on the current device, where the network must live
+        int dev = -1;
+        MLP_CUDA(cudaGetDevice(&dev), "srmc_mlp_fit_noalloc: cudaGetDevice");
+        if (dev != m->device)
+            return mfail(SRMC_ERR_INVALID_ARG, "srmc_mlp_fit_noalloc: the network's device is not the current one");
+    }
+    // bound n_data first, so that the size below cannot wrap
+    if (n_data > kNoallocFloats)
+        return mfail(SRMC_ERR_INVALID_ARG,
+                     "srmc_mlp_fit_noalloc: n_data exceeds the 2^21-float scratch of the allocation-free path "
+                     "(use srmc_mlp_fit)");
     // scratch layout (floats): [gradient, padded to 64][loss slot, 64][inputs n_data x n_in][targets n_data]
     const long long gpad = ((long long)m->P + 63) / 64 * 64;
     const long long need = gpad + 64 + n_data * (long long)(m->nin + 1);

@@ -51,6 +51,13 @@ def test_noalloc_fit_matches_fit_on_two_calls_in_a_row(dev):
         assert _rel(pn, pr) < TOL, (seed, _rel(pn, pr))
         assert _rel(cn.cpu().numpy(), cr.cpu().numpy()) < TOL
         assert cn[-10:].mean().item() < cn[:5].mean().item()   # it trains
+    # a third call without a loss curve: the losses go to the library's own slot
+    # (srmc_mlp_fit) and to the scratch array's (srmc_mlp_fit_noalloc)
+    ref.srmc_mlp_fit(coarse, n_data=1 << 15, iters=100, batch=4096, lr=3e-3, seed=23)
+    nal.srmc_mlp_fit_noalloc(coarse, n_data=1 << 15, iters=100, batch=4096, lr=3e-3, seed=23)
+    torch.cuda.synchronize()
+    pr, pn = ref.srmc_mlp_get_params(), nal.srmc_mlp_get_params()
+    assert _rel(pn, pr) < TOL, _rel(pn, pr)
 
 
 def test_noalloc_fit_rejects_requests_beyond_its_scratch(dev):
@@ -61,3 +68,12 @@ def test_noalloc_fit_rejects_requests_beyond_its_scratch(dev):
     with pytest.raises(srmc.SrmcError) as e:
         net.srmc_mlp_fit_noalloc(coarse, n_data=1 << 19, iters=1, batch=1 << 19, lr=1e-3, seed=1)
     assert e.value.status == 1 and "scratch" in str(e.value)
+    # sizes whose float count would wrap a 64-bit product are refused before any
+    # arithmetic on them (and before any launch)
+    for n in (1 << 60, (1 << 62) + (1 << 40)):
+        with pytest.raises(srmc.SrmcError) as e:
+            net.srmc_mlp_fit_noalloc(coarse, n_data=n, iters=1, batch=1 << 30, lr=1e-3, seed=1)
+        assert e.value.status == 1 and "scratch" in str(e.value)
+        with pytest.raises(srmc.SrmcError) as e:
+            net.srmc_mlp_fit(coarse, n_data=n, iters=1, batch=1 << 30, lr=1e-3, seed=1)
+        assert e.value.status == 1
