@@ -152,6 +152,11 @@ def _bind(L):
     L.orc_path_steps.argtypes = [C.c_void_p]; L.orc_path_steps.restype = C.c_int64
     L.orc_set_control.argtypes = [C.c_void_p, dp]; L.orc_set_control.restype = C.c_int
     L.orc_set_own_control.argtypes = [C.c_void_p, C.c_int]; L.orc_set_own_control.restype = None
+    L.orc_set_rows_centred.argtypes = [C.c_void_p, C.c_int, dp, C.c_int64, dp, C.c_int64]
+    L.orc_set_rows_centred.restype = C.c_int
+    L.orc_fit_many.argtypes = [C.c_void_p, C.c_int, C.c_int64, C.POINTER(C.c_int64), C.c_int]
+    L.orc_fit_many.restype = C.c_int64
+    L.orc_set_missing_zero.argtypes = [C.c_void_p, C.c_int]; L.orc_set_missing_zero.restype = None
     fp = C.POINTER(C.c_float)
     L.orc_mlp_nparams.argtypes = [C.c_int, C.c_int]; L.orc_mlp_nparams.restype = C.c_int
     L.orc_bf16.argtypes = [C.c_double]; L.orc_bf16.restype = C.c_float
@@ -368,6 +373,29 @@ class Oracle:
         """Control from the run's own fitted z of the later steps."""
         self._control = None
         self._L.orc_set_own_control(self._ctx, 1 if on else 0)
+
+    def set_rows_centred(self, i: int, yrows, zrows):
+        """Install the rows of step i of every stratum from tables in the
+        centred basis: yrows [K][>= p] (alpha), zrows [K][>= q p] (beta, row
+        by row per component); extra columns (padding) are skipped."""
+        y = np.ascontiguousarray(yrows, dtype=np.float64)
+        z = np.ascontiguousarray(zrows, dtype=np.float64)
+        if y.shape[0] != self.K or z.shape[0] != self.K:
+            raise ValueError("set_rows_centred: tables need one row per stratum")
+        if self._L.orc_set_rows_centred(self._ctx, int(i), _dptr(y), y.shape[1], _dptr(z), z.shape[1]) != 0:
+            raise ValueError(f"set_rows_centred: invalid step {i}")
+
+    def fit_many(self, i: int, ks, nthreads: int = 0) -> None:
+        """Fit the strata ks of step i in parallel (rows of later steps must exist)."""
+        ks = np.ascontiguousarray(ks, dtype=np.int64)
+        miss = self._L.orc_fit_many(self._ctx, int(i), ks.shape[0], ks.ctypes.data_as(C.POINTER(C.c_int64)),
+                                    int(nthreads))
+        if miss != 0:
+            raise RuntimeError(f"oracle: fits of step {i} were missing {miss} rows")
+
+    def set_missing_zero(self, on: bool = True) -> None:
+        """Timing aid: missing rows of later steps read as the zero function."""
+        self._L.orc_set_missing_zero(self._ctx, 1 if on else 0)
 
     @property
     def fallbacks(self) -> int:

@@ -441,6 +441,7 @@ struct orc_ctx {
     unsigned char *done;/* [N][K]                                           */
     int64_t fallbacks;
     int64_t path_steps;
+    int missing_zero;   /* timing aid: a missing row reads as zero        */
 };
 
 orc_ctx *orc_create(const orc_problem *P)
@@ -563,10 +564,13 @@ static void eval_row(const orc_ctx *C, const double *row, const double *x, doubl
 
 /* Row (j, k) for a lookup; in lazy mode a missing row is fitted first.
  * Returns NULL (and counts) when the row is missing and lazy is off. */
+static const double zero_row[(1 + ORC_DMAX) * ORC_PBMAX];
+
 static const double *need_row(orc_ctx *C, int j, int64_t k, int lazy, int64_t *missing)
 {
     const double *row = orc_row(C, j, k);
     if (row) return row;
+    if (C->missing_zero) return zero_row;
     if (lazy) {
         orc_fit_lazy(C, j, k);
         row = orc_row(C, j, k);
@@ -726,6 +730,73 @@ int orc_fit_lazy(orc_ctx *C, int i, int64_t k)
     if (i < 0 || i >= C->P.N || k < 0 || k >= C->K) return -1;
     if (orc_row(C, i, k)) return 0;
     return fit_impl(C, i, k, 1) == 0 ? 0 : 1;
+}
+
+void orc_set_missing_zero(orc_ctx *C, int on) { C->missing_zero = on != 0; }
+
+/* A row given in the monomials of u = (x - c)/s, written out in the monomials
+ * of x: 1 stays 1; u_l = x_l / s_l - c_l / s_l; u_a u_b = (x_a x_b - c_b x_a
+ * - c_a x_b + c_a c_b) / (s_a s_b).  cen and raw hold dimb coefficients. */
+static void centred_to_raw(const orc_ctx *C, int64_t k, const double *cen, double *raw)
+{
+    const orc_problem *P = &C->P;
+    const int d = P->d, p = C->dimb;
+    double ctr[ORC_DMAX], sc[ORC_DMAX];
+    int cells[ORC_DMAX];
+    orc_stratum_centre(P, k, ctr);
+    orc_stratum_cells(P, k, cells);
+    for (int l = 0; l < d; ++l) sc[l] = orc_cell_scale(P, l, cells[l]);
+    for (int c = 0; c < p; ++c) raw[c] = 0.0;
+    raw[0] = cen[0];
+    if (p > 1) {
+        for (int l = 0; l < d; ++l) {
+            raw[1 + l] += cen[1 + l] / sc[l];
+            raw[0] -= cen[1 + l] * ctr[l] / sc[l];
+        }
+    }
+    if (p > d + 1) {
+        int e = 1 + d;
+        for (int a = 0; a < d; ++a)
+            for (int b = a; b < d; ++b, ++e) {
+                const double w = cen[e] / (sc[a] * sc[b]);
+                raw[e] += w;
+                raw[1 + a] -= w * ctr[b];
+                raw[1 + b] -= w * ctr[a];
+                raw[0] += w * ctr[a] * ctr[b];
+            }
+    }
+}
+
+int orc_set_rows_centred(orc_ctx *C, int i, const double *yrows, int64_t ystride,
+                         const double *zrows, int64_t zstride)
+{
+    if (i < 0 || i >= C->P.N) return 1;
+    const int p = C->dimb, q = C->P.q;
+    for (int64_t k = 0; k < C->K; ++k) {
+        const size_t idx = (size_t)i * (size_t)C->K + (size_t)k;
+        double *row = C->rows + idx * (size_t)C->R;
+        centred_to_raw(C, k, yrows + k * ystride, row);
+        for (int l = 0; l < q; ++l)
+            centred_to_raw(C, k, zrows + k * zstride + (int64_t)l * p, row + p * (1 + l));
+        C->done[idx] = 1;
+    }
+    return 0;
+}
+
+int64_t orc_fit_many(orc_ctx *C, int i, int64_t n, const int64_t *ks, int nthreads)
+{
+    if (i < 0 || i >= C->P.N) return -1;
+    for (int64_t a = 0; a < n; ++a)
+        if (ks[a] < 0 || ks[a] >= C->K) return -1;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+    int64_t missing = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : missing)
+    for (int64_t a = 0; a < n; ++a) missing += fit_impl(C, i, ks[a], 0);
+    return missing;
 }
 
 int orc_solve_full(orc_ctx *C, int nthreads)

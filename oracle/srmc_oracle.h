@@ -142,6 +142,28 @@ int      orc_set_control(orc_ctx *C, const double *rows);
  * orc_set_control(C, NULL) or on = 0 removes it. */
 void     orc_set_own_control(orc_ctx *C, int on);
 
+/* ---- teacher forcing: a step fitted from given later rows ----------------
+ * Install the rows of step i of every stratum from a table in the monomials
+ * of the centred coordinate u_l = (x_l - c_{k,l}) / s_{k,l} (c_k and s from
+ * orc_stratum_centre and orc_cell_scale; the basis of the control rows):
+ * yrows[k * ystride + c] = alpha_c, zrows[k * zstride + l * dimb + c] =
+ * beta_{l,c}.  Each row is expanded into the raw monomials of x, in which the
+ * oracle fits and evaluates (the same function on H_k), and marked fitted, so
+ * that fits of steps i' < i read it.  A fit of step i' reads rows of steps
+ * > i' only, so fits taken in increasing i' never see a row of their own step
+ * that they wrote.  Returns 0, or 1 for an invalid step. */
+int      orc_set_rows_centred(orc_ctx *C, int i, const double *yrows, int64_t ystride,
+                              const double *zrows, int64_t zstride);
+/* Fit the n strata ks[] of step i (OpenMP over the list with nthreads
+ * threads, 0 = default), each as orc_fit_one; returns the number of rows of
+ * later steps they were missing (0 on success). */
+int64_t  orc_fit_many(orc_ctx *C, int i, int64_t n, const int64_t *ks, int nthreads);
+/* Timing aid: with on != 0 a missing row of a later step reads as the zero
+ * function (y = 0, z = 0) instead of being counted as missing, so that a fit
+ * of any (i, k) runs all of its arithmetic without the rows it depends on.
+ * Fits made so are stored like others; not for results. */
+void     orc_set_missing_zero(orc_ctx *C, int on);
+
 /* Number of (i,k) fits that fell back to LP0 because R was singular. */
 int64_t  orc_fallbacks(const orc_ctx *C);
 /* Path-steps simulated so far (diagnostic; one unit = one Euler step). */

@@ -4,6 +4,7 @@ import numpy as np
 import pytest
 
 from paper_2407_21085_gb300 import workloads as W
+from tests import controls as CT
 
 pytestmark = pytest.mark.gpu
 
@@ -96,7 +97,7 @@ def test_batch_with_controls_equals_single_solves(dev, mode):
     def make(w, h):
         s = srmc.Solver(w, block_threads=256)
         if h == "rows":
-            s.srmc_set_control(W.control_rows(w, W.closed_form_z(w)))
+            s.srmc_set_control(CT.control_rows(w, CT.closed_form_z(w)))
         elif h == "own":
             s.srmc_set_own_control()
         return s

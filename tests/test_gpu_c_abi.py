@@ -8,6 +8,7 @@ import numpy as np
 import pytest
 
 from paper_2407_21085_gb300 import workloads as W
+from tests import controls as CT
 from tests.test_gpu_parity import _check
 
 pytestmark = pytest.mark.gpu
@@ -53,7 +54,7 @@ def test_c_consumer_matches_the_oracle(consumer, orc, prec):
     w = W.cos_model("c_abi", precision="fp64" if prec == 64 else "fp32", seed=1, instance=0, **c)
     o = orc.Oracle(w)
     o.solve_full(0)
-    x = W.centres(w)
+    x = CT.centres(w)
     for i in range(w.N):
         sel = rows[:, 0] == i
         assert np.array_equal(rows[sel, 1], np.arange(w.K))

@@ -5,6 +5,7 @@ import numpy as np
 import pytest
 
 from paper_2407_21085_gb300 import workloads as W
+from tests import controls as CT
 from tests.test_gpu_parity import _check
 
 pytestmark = pytest.mark.gpu
@@ -22,7 +23,7 @@ def dev():
 def _rows(w, fn):
     """Control rows for w; for the FP32 form rounded to binary16, the form in
     which that solver keeps them, so that both sides use the same control."""
-    rows = W.control_rows(w, fn)
+    rows = CT.control_rows(w, fn)
     if w.precision == "fp32":
         rows = rows.astype(np.float16).astype(np.float64)
     return rows
@@ -49,24 +50,24 @@ def _cv_parity(dev, orc, w, fn):
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_cv_cos_d2(dev, orc, prec):
     w = W.cfg2(C=12, N=6, M=384, precision=prec)
-    _cv_parity(dev, orc, w, W.closed_form_z(w))
+    _cv_parity(dev, orc, w, CT.closed_form_z(w))
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_cv_cos_d4_with_z_in_driver(dev, orc, prec):
     w = W.cfg3(C=3, N=4, M=200, precision=prec)
-    _cv_parity(dev, orc, w, W.random_smooth_z(w, seed=3))
+    _cv_parity(dev, orc, w, CT.random_smooth_z(w, seed=3))
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_cv_paper_logistic_d3(dev, orc, prec):
     w = W.logistic_paper(d=3, N=4, C=3, M=160, precision=prec)
-    _cv_parity(dev, orc, w, W.random_smooth_z(w, seed=4, scale=0.1))
+    _cv_parity(dev, orc, w, CT.random_smooth_z(w, seed=4, scale=0.1))
 
 
 def test_cv_d6(dev, orc):
     w = W.cos_model("d6", d=6, N=3, C=2, a=2.0, M=96, s0=0.3, lam=0.2, kap=0.5, precision="fp32")
-    _cv_parity(dev, orc, w, W.closed_form_z(w))
+    _cv_parity(dev, orc, w, CT.closed_form_z(w))
 
 
 def test_fp32_form_rounds_rows_to_binary16(dev):
@@ -76,7 +77,7 @@ def test_fp32_form_rounds_rows_to_binary16(dev):
     # as given.
     torch, srmc = dev
     w = W.cfg3(C=3, N=3, M=128)
-    rows = W.control_rows(w, W.random_smooth_z(w, seed=5))
+    rows = CT.control_rows(w, CT.random_smooth_z(w, seed=5))
     rows[0, 0, 0, 0] = 1e6                         # saturates to 65504
     r16 = np.clip(rows, -65504, 65504).astype(np.float16).astype(np.float64)
     assert not np.array_equal(rows, r16)
@@ -97,7 +98,7 @@ def test_clear_control_restores_the_plain_scheme(dev):
     plain.srmc_solve()
     s = srmc.Solver(w)
     s.srmc_solve()
-    s.srmc_set_control(W.control_rows(w, W.closed_form_z(w)))
+    s.srmc_set_control(CT.control_rows(w, CT.closed_form_z(w)))
     s.srmc_solve()                                 # graph re-captured with the control
     x = s.centres()
     yc, _ = s.evaluate(0, x)
@@ -123,7 +124,7 @@ def test_exact_control_cuts_the_spread_on_gpu(dev):
     # (and the means agree): the variance reduction the control is for.
     torch, srmc = dev
     w0 = W.cfg2(C=16, N=10, M=1024)
-    rows = W.control_rows(w0, W.closed_form_z(w0))
+    rows = CT.control_rows(w0, CT.closed_form_z(w0))
     ys = {"plain": [], "cv": []}
     for seed in range(8):
         w = w0.replace(seed=seed + 10)
@@ -180,7 +181,7 @@ def test_own_control_state(dev):
     plain = srmc.Solver(w)
     plain.srmc_solve()
     s = srmc.Solver(w)
-    s.srmc_set_control(W.control_rows(w, W.closed_form_z(w)))
+    s.srmc_set_control(CT.control_rows(w, CT.closed_form_z(w)))
     s.srmc_set_own_control()                       # replaces the rows
     with pytest.raises(srmc.SrmcError) as e:
         s.srmc_read_control()
@@ -226,7 +227,7 @@ def test_controls_on_equal_probability_strata(dev, orc, prec):
     # control rows in the centred basis of equal-probability cells (median
     # centre, quantile unit) and the run's own control
     w = W.cfg2(C=7, N=5, M=256, precision=prec).replace(strata="prob")
-    _cv_parity(dev, orc, w, W.closed_form_z(w))
+    _cv_parity(dev, orc, w, CT.closed_form_z(w))
     _own_parity(dev, orc, w)
 
 
@@ -234,12 +235,12 @@ def test_controls_on_equal_probability_strata(dev, orc, prec):
 def test_controls_with_exact_dynamics(dev, orc, prec):
     # the controls use dW_j, the first normal block of each exact step
     w = W.cfg2(C=6, N=4, M=256, precision=prec).replace(b=[0.1, 0.0], theta=[1.5, 0.5], dynamics="exact")
-    _cv_parity(dev, orc, w, W.random_smooth_z(w, seed=6))
+    _cv_parity(dev, orc, w, CT.random_smooth_z(w, seed=6))
     _own_parity(dev, orc, w)
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_controls_with_quadratic_polynomials(dev, orc, prec):
     w = W.cfg2(C=6, N=4, M=256, precision=prec, basis="lp2")
-    _cv_parity(dev, orc, w, W.closed_form_z(w))
+    _cv_parity(dev, orc, w, CT.closed_form_z(w))
     _own_parity(dev, orc, w)

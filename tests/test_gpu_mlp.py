@@ -7,6 +7,7 @@ import numpy as np
 import pytest
 
 from paper_2407_21085_gb300 import workloads as W
+from tests import controls as CT
 from tests.test_oracle_cv import _params
 
 pytestmark = pytest.mark.gpu
@@ -89,7 +90,7 @@ def test_tabulated_control_rows_vs_oracle(dev, orc, strata):
         A = np.column_stack([np.full(len(X), np.float32(t)), X]).astype(np.float32).astype(np.float64)
         _, g = orc.mlp_eval(prm, 4, 64, A, bf16_round=True)
         return 0.35 * g[:, 1:]
-    want = W.control_rows(w, fn)
+    want = CT.control_rows(w, fn)
     assert _rel(got, want) < 2e-2, _rel(got, want)
 
 

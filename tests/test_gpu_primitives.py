@@ -8,6 +8,7 @@ import numpy as np
 import pytest
 
 from paper_2407_21085_gb300 import workloads as W
+from tests import controls as CT
 
 pytestmark = pytest.mark.gpu
 
@@ -192,7 +193,7 @@ def test_prob_start_points_and_centres(dev, orc, prec):
     w = _prob_workloads()[1].replace(precision=prec)
     s = srmc.Solver(w)
     c = s.centres().cpu().numpy()
-    assert np.allclose(c, W.centres(w), rtol=1e-15, atol=1e-15)
+    assert np.allclose(c, CT.centres(w), rtol=1e-15, atol=1e-15)
     assert np.allclose(c, np.array([orc.stratum_centre(w, k) for k in range(w.K)]), rtol=1e-15, atol=1e-15)
     rng = np.random.default_rng(8)
     for (i, k) in [(0, 0), (3, w.K - 1), (2, int(rng.integers(0, w.K)))]:

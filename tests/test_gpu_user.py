@@ -5,6 +5,7 @@ import numpy as np
 import pytest
 
 from paper_2407_21085_gb300 import workloads as W
+from tests import controls as CT
 from tests import user_models as U
 from tests.test_gpu_parity import _check
 
@@ -70,7 +71,7 @@ def test_user_cos_matches_the_builtin_kernel(dev, prec):
 def test_user_model_with_controls(dev, orc, prec):
     from tests.test_gpu_cv import _cv_parity, _own_parity
     w = _quad(2, prec)
-    _cv_parity(dev, orc, w, W.random_smooth_z(w, seed=8, scale=0.2))
+    _cv_parity(dev, orc, w, CT.random_smooth_z(w, seed=8, scale=0.2))
     _own_parity(dev, orc, w)
 
 

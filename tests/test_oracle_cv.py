@@ -8,6 +8,7 @@ import numpy as np
 import pytest
 
 from paper_2407_21085_gb300 import workloads as W
+from tests import controls as CT
 from tests import brute_force as bf
 from tests.test_oracle_scheme import BF_CASES, POP_CASES, POP_XS, _bf_workload, _population, _population_case
 
@@ -87,7 +88,7 @@ def test_mlp_bf16_emulation_stays_close(orc):
 def _pop_disc_with_control(orc, case, control_fn, library=None, R=6):
     w = _population_case(*case)
     pop = _population(case)
-    rows = W.control_rows(w, control_fn(w))
+    rows = CT.control_rows(w, control_fn(w))
     ys, zs = [], []
     for r in range(R):
         o = orc.Oracle(w.replace(seed=100 + r), library=library)
@@ -111,7 +112,7 @@ def _pop_disc_with_control(orc, case, control_fn, library=None, R=6):
 
 @pytest.mark.parametrize("which", ["closed_form", "random"])
 def test_control_leaves_the_population_limit_unchanged(orc, which):
-    fn = W.closed_form_z if which == "closed_form" else (lambda w: W.random_smooth_z(w, seed=9))
+    fn = CT.closed_form_z if which == "closed_form" else (lambda w: CT.random_smooth_z(w, seed=9))
     worst, _ = _pop_disc_with_control(orc, POP_CASES[0], fn)
     assert worst <= 1.0
 
@@ -121,10 +122,10 @@ def test_good_control_reduces_the_spread(orc):
     # - sum z dW is y_i(x_i) up to O(dt) terms, so the seed-to-seed spread of
     # the fitted y drops while its mean does not move.
     w = W.cos_model("v", d=1, N=10, C=8, a=2.0, M=2000, s0=0.5, lam=0.5, kap=0.5, kapz=0.0)
-    xs = W.centres(w)[2:6]
+    xs = CT.centres(w)[2:6]
     out = {}
-    for name, fn in [("plain", lambda t, X: np.zeros((len(X), 1))), ("cv", W.closed_form_z(w))]:
-        rows = W.control_rows(w, fn)
+    for name, fn in [("plain", lambda t, X: np.zeros((len(X), 1))), ("cv", CT.closed_form_z(w))]:
+        rows = CT.control_rows(w, fn)
         ys = []
         for r in range(6):
             o = orc.Oracle(w.replace(seed=100 + r))
@@ -155,7 +156,7 @@ def test_population_pin_catches_control_mistakes(orc, tmp_path, name):
     src = orc.source_text()
     assert src.count(old) == 1
     lib = orc.compile_variant(src.replace(old, new), str(tmp_path / f"cmut_{name}.so"))
-    worst, _ = _pop_disc_with_control(orc, POP_CASES[0], W.closed_form_z, library=lib, R=4)
+    worst, _ = _pop_disc_with_control(orc, POP_CASES[0], CT.closed_form_z, library=lib, R=4)
     assert worst > 1.5, (name, worst)
 
 
@@ -166,7 +167,7 @@ def _control_mismatch(orc, n, mode):
     if mode == "own":
         control = "own"
     else:
-        control = W.control_rows(w, W.random_smooth_z(w, seed=n + 1, scale=0.8))
+        control = CT.control_rows(w, CT.random_smooth_z(w, seed=n + 1, scale=0.8))
     y_and_z = bf.solve(w, control)[1]
     o = orc.Oracle(w)
     if mode == "own":
@@ -233,7 +234,7 @@ def test_own_control_reduces_the_spread(orc):
     # removes most of the response noise of the later steps: the seed-to-seed
     # spread of y_0 drops (less than with the exact z), the mean stays.
     w = W.cos_model("v", d=1, N=10, C=8, a=2.0, M=2000, s0=0.5, lam=0.5, kap=0.5, kapz=0.0)
-    xs = W.centres(w)[2:6]
+    xs = CT.centres(w)[2:6]
     out = {}
     for name in ("plain", "own"):
         ys = []

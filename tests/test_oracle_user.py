@@ -5,6 +5,7 @@ restatement (which evaluates the same g and f restated in Python)."""
 import numpy as np
 
 from paper_2407_21085_gb300 import workloads as W
+from tests import controls as CT
 from tests import brute_force as bf
 from tests import user_models as U
 
@@ -14,7 +15,7 @@ def test_user_cos_reproduces_the_builtin_model(orc):
     a, b = orc.Oracle(w), orc.Oracle(w.replace(model="user", user_source=U.COS))
     a.solve_full(0)
     b.solve_full(0)
-    x = W.centres(w)
+    x = CT.centres(w)
     for i in range(w.N):
         (ya, za), (yb, zb) = a.eval(i, x), b.eval(i, x)
         assert np.max(np.abs(ya - yb)) < 1e-13 and np.max(np.abs(za - zb)) < 1e-13
