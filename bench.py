@@ -4,7 +4,7 @@ One step = one whole backward solve of Alg. SRMDP (N step launches over all
 strata) on the selected workload, inputs already resident on the device.
 The metric is stratum-path-steps per second: K M N (N+1) / 2 units per solve.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload cfg2]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload cfg5]
                   [--impl reference] [--no-cpu-baseline]
 
 With N > 1 (torchrun, one process per GPU) every rank solves its own
@@ -44,8 +44,33 @@ def flops_per_path_step(d: int) -> float:
 
 
 def fp32_peak_tflops(sms: int, mhz: float) -> float:
-    """FP32 FMA pipe peak: SMs x 128 lanes x 2 FLOP x clock."""
+    """FP32 FMA pipe peak from unit counts: SMs x 128 lanes x 2 FLOP x clock."""
     return sms * 128 * 2 * mhz * 1e6 / 1e12
+
+
+def measured_fp32_peak(sms: int, stream, iters: int = 400000, reps: int = 3):
+    """FP32 FMA throughput measured with the library's probe kernel
+    (srmc_fp32_fma_probe: independent FFMA2 or FFMA chains, 4 blocks of 256
+    threads per SM), best of reps CUDA-event timings per form; returns
+    {"tflops": max over forms, "packed": ..., "scalar": ...}."""
+    import torch
+    from paper_2407_21085_gb300 import srmc
+    grid, threads = 4 * sms, 256
+    out = torch.empty(grid * threads, dtype=torch.float32, device="cuda")
+    res = {}
+    for packed, name in ((1, "packed"), (0, "scalar")):
+        srmc.srmc_fp32_fma_probe(grid, threads, 1000, packed, out, stream)
+        best = 0.0
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            srmc.srmc_fp32_fma_probe(grid, threads, iters, packed, out, stream)
+            b.record(stream)
+            b.synchronize()
+            best = max(best, grid * threads * iters * 32.0 / (a.elapsed_time(b) / 1e3) / 1e12)
+        res[name] = best
+    res["tflops"] = max(res["packed"], res["scalar"])
+    return res
 
 
 STEP_KERNEL_SOURCES = ("srmc_step.cu", "srmc_device.cuh", "srmc_internal.h")
@@ -257,6 +282,8 @@ def run_gpu(args):
         step_ms.append(ev[w.N - 1][0].elapsed_time(ev[0][1]))
     torch.cuda.synchronize()
     barrier()
+    # the FP32 FMA peak of this GPU at this moment (inside the clock sampling window)
+    fma_peak = measured_fp32_peak(sms, stream)
     clocks = sampler.stop()
     total_ms = sum(step_ms)
     value, total_ms_max = whole_job_rate(units, ws, args.steps, total_ms, dev)
@@ -289,7 +316,8 @@ def run_gpu(args):
     flops_per_launch = flops_per_path_step(w.d) * units / w.N
     achieved = flops_per_launch / avg_launch_s / 1e12
     peak_mhz = 2070.0
-    peak = fp32_peak_tflops(sms, peak_mhz)
+    peak_units = fp32_peak_tflops(sms, peak_mhz)
+    peak = fma_peak["tflops"]
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -307,7 +335,12 @@ def run_gpu(args):
                      "traffic": args.traffic if args.traffic is not None
                      else recorded_traffic(w.name, control_kind(args)),
                      "kernel": "step_kernel", "flops_per_unit": flops_per_path_step(w.d),
-                     "peak_basis": f"{sms} SMs x 128 FP32 lanes x 2 x {peak_mhz:.0f} MHz"},
+                     "peak_basis": "measured in this run: FP32 FMA probe kernel (srmc_fp32_fma_probe), "
+                                   "best of packed FFMA2 and scalar FFMA chains",
+                     "peak_probe": fma_peak,
+                     "peak_unit_count": peak_units,
+                     "frac_of_unit_count": achieved / peak_units,
+                     "unit_count_basis": f"{sms} SMs x 128 FP32 lanes x 2 x {peak_mhz:.0f} MHz"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": tab_bytes},
         "gpu_launches": w.N * args.steps,
         "clocks": clocks,
@@ -555,23 +588,103 @@ def batched_compare(args, stream):
 
 
 # ---- the CPU oracle (cpu_baseline leg and the reference arm) -------------------
-def oracle_sample(w: W.Workload, M_sample: int, threads: int):
-    """Time the FP64 oracle's full backward solve of the workload with M
-    reduced to M_sample (all strata, all steps) on `threads` host threads."""
-    from oracle import oracle as o
-    o.build()
-    ws = w.replace(M=M_sample, precision="fp64")
-    t0 = time.perf_counter()
-    orc = o.Oracle(ws)
-    orc.solve_full(threads)
-    dt = time.perf_counter() - t0
-    steps = orc.path_steps
-    orc.close()
-    return steps / dt, dt, f"{w.name} with M={M_sample} (all {w.K} strata, all {w.N} steps), FP64"
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu), or the platform string."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
 
 
 def cpu_cores():
     return os.cpu_count() or 1
+
+
+def oracle_fits(w: W.Workload, plan, threads: int, seed: int = 0):
+    """Time the FP64 oracle's fits of sampled strata of the workload at its
+    full M: plan = [(step i, number of strata)], each group fitted in
+    parallel over `threads` host threads (orc_fit_many).  The rows of the
+    later steps a fit reads are not there, so the oracle is told to read
+    them as the zero function (orc_set_missing_zero): every operation of the
+    fit -- start points, all N - i Euler steps with their normals, cell
+    location, row evaluation, driver, least squares -- runs as in a full
+    solve, only the table values differ.  Returns [(i, n, seconds,
+    path_steps)]."""
+    import numpy as np
+    from oracle import oracle as o
+    o.build()
+    orc = o.Oracle(w.replace(precision="fp64"))
+    orc.set_missing_zero(True)
+    rng = np.random.default_rng(seed)
+    out = []
+    for i, n in plan:
+        ks = rng.choice(w.K, size=min(n, w.K), replace=False)
+        before = orc.path_steps
+        t0 = time.perf_counter()
+        orc.fit_many(i, ks, threads)
+        out.append((i, len(ks), time.perf_counter() - t0, orc.path_steps - before))
+    orc.close()
+    return out
+
+
+def extrapolate_full(w: W.Workload, fits):
+    """Seconds of a full backward solve (all K strata, all N steps) on the
+    threads the fits used: the wall time of n fits at step i is modelled as
+    (n / threads_batch) (a + b (N - i)), fitted by least squares over the
+    measured steps, and summed over i = 0..N-1 for K strata."""
+    import numpy as np
+    A = np.array([[1.0, w.N - i] for i, n, sec, _ in fits])
+    y = np.array([sec / n for i, n, sec, _ in fits])
+    a, b = np.linalg.lstsq(A, y, rcond=None)[0]
+    return float(sum(w.K * (a + b * (w.N - i)) for i in range(w.N)))
+
+
+def oracle_plan(w: W.Workload, threads: int, single: bool):
+    """Sampled steps 0, N/2, N-1; strata per step sized to about 10 s of CPU
+    work in total per workload (fewer single-threaded)."""
+    per = max(1, threads) * (1 if w.d >= 4 else 4)
+    if single:
+        return [(0, 1), (w.N // 2, 1), (w.N - 1, 4)]
+    return [(0, per), (w.N // 2, per), (w.N - 1, 4 * per)]
+
+
+def cpu_baseline(w: W.Workload):
+    """The oracle timed on this host on bounded samples of the workload (and
+    of cfg3, cfg2 for context): all cores and one thread, with the full-solve
+    time extrapolated from the samples (marked as extrapolated)."""
+    cores = cpu_cores()
+    res = {"kind": "oracle", "cores": cores, "cpu_model": cpu_model(), "unit": UNIT,
+           "sample": (f"{w.name}: oracle fits of sampled strata at steps 0, N/2, N-1 with the full "
+                      f"M={w.M} (later rows read as zero: same arithmetic), FP64"),
+           "workloads": {}}
+    for ww in (w, W.cfg3(), W.cfg2()):
+        if ww.name in res["workloads"]:
+            continue
+        entry = {}
+        for label, th in (("all_cores", cores), ("one_thread", 1)):
+            fits = oracle_fits(ww, oracle_plan(ww, th, th == 1), th)
+            sec = sum(f[2] for f in fits)
+            steps = sum(f[3] for f in fits)
+            full = extrapolate_full(ww, fits)
+            entry[label] = {"threads": th, "path_steps_per_s": steps / sec, "sample_seconds": sec,
+                            "sample_path_steps": steps,
+                            "fits": [{"i": i, "strata": n, "seconds": t} for i, n, t, _ in fits],
+                            "full_solve_seconds_extrapolated": full,
+                            "full_solve_path_steps_per_s_extrapolated": ww.path_steps() / full}
+        res["workloads"][ww.name] = entry
+    main = res["workloads"][w.name]["all_cores"]
+    res["value"] = main["path_steps_per_s"]
+    res["seconds"] = main["sample_seconds"]
+    return res
+
+
+# the sampled steps of the reference arm, cycled through by its steps
+REF_STEPS = (0, 10, 20, 30, 39)
 
 
 def run_reference(args):
@@ -580,25 +693,31 @@ def run_reference(args):
         return None
     w = workload(args.workload)
     cores = cpu_cores()
-    M_s = args.ref_M
-    for _ in range(args.warmup):
-        oracle_sample(w, M_s, cores)
-    rates, times = [], []
-    for _ in range(args.steps):
-        r, dt, sample = oracle_sample(w, M_s, cores)
-        rates.append(r)
-        times.append(dt)
-    units = sum(rates[i] * times[i] for i in range(len(rates)))
-    value = units / sum(times)
+    n = args.ref_strata or cores
+
+    def one(k):
+        i = REF_STEPS[k % len(REF_STEPS)] * (w.N - 1) // 39
+        return oracle_fits(w, [(i, n)], cores, seed=k)[0]
+    for k in range(args.warmup):
+        one(k)
+    secs, units = 0.0, 0
+    for k in range(args.steps):
+        _, _, sec, st = one(args.warmup + k)
+        secs += sec
+        units += st
+    value = units / secs
+    sample = (f"{w.name}: per step, oracle fits of {n} sampled strata at one step i (cycling through "
+              f"{', '.join(str(v * (w.N - 1) // 39) for v in REF_STEPS)}) with the full M={w.M}, "
+              "later rows read as zero (same arithmetic), FP64")
     return {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
         "config": {"workload": w.name, "d": w.d, "strata": w.K, "N": w.N, "M": w.M, "basis": w.basis,
-                   "sample_M": M_s},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": sample},
+                   "sample_strata_per_step": n},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+                         "cpu_model": cpu_model()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
 
@@ -606,14 +725,14 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--workload", default="cfg2")
+    ap.add_argument("--workload", default="cfg5")
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-M", type=int, default=128, help="M of the bounded oracle sample")
-    ap.add_argument("--ref-M", type=int, default=32, help="M of each reference-arm step")
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--ref-strata", type=int, default=0,
+                    help="strata fitted per reference-arm step (0: one per host core)")
+    ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--block-threads", type=int, default=0, help="threads per stratum block (0: library)")
     ap.add_argument("--no-cv-compare", action="store_true", help="skip the CV-vs-plain comparison (cfg5)")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-form measurement (cfg4)")
@@ -659,9 +778,7 @@ def main():
         out["batched_cfg4"] = batched_compare(args, torch.cuda.current_stream())
     if rank == 0:
         if not args.no_cpu_baseline and out["n_gpus"] == 1:
-            r, dt, sample = oracle_sample(w, args.cpu_M, cpu_cores())
-            out["cpu_baseline"] = {"value": r, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
-                                   "sample": sample, "seconds": dt}
+            out["cpu_baseline"] = cpu_baseline(w)
         else:
             out["cpu_baseline"] = None
         print(json.dumps(out), flush=True)

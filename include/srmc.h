@@ -431,6 +431,17 @@ srmc_status srmc_locate(const srmc_solver *s, const double *dev_x64, const float
 srmc_status srmc_start_points(const srmc_solver *s, int i, long long k, long long m0,
                               long long n, double *dev_x, void *stream);
 
+/* ---- measurement aid (not part of the method) ------------------------------ */
+
+/* FP32 FMA throughput probe for the roofline of the path kernels: grid blocks
+ * of `threads` threads each run iters rounds of 16 independent fused
+ * multiply-adds, as 8 packed two-wide FFMA2 (packed != 0) or 16 scalar FFMA,
+ * i.e. grid * threads * iters * 32 FLOP; dev_out [grid * threads] float
+ * receives one value per thread.  threads a multiple of 32 in [32, 1024].
+ * Asynchronous on stream; the caller times it. */
+srmc_status srmc_fp32_fma_probe(int grid, int threads, int iters, int packed, float *dev_out,
+                                void *stream);
+
 /* Message of the last error on this thread ("" if none). */
 const char *srmc_last_error(void);
 

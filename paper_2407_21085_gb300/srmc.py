@@ -113,6 +113,8 @@ def lib():
             L.srmc_normals.argtypes = [vp, ll, vp, vp, vp]
             L.srmc_locate.argtypes = [vp, vp, vp, ll, vp, vp]
             L.srmc_start_points.argtypes = [vp, i_, ll, ll, ll, vp, vp]
+            L.srmc_fp32_fma_probe.argtypes = [i_, i_, i_, i_, vp, vp]
+            L.srmc_fp32_fma_probe.restype = C.c_int
             L.srmc_last_error.restype = C.c_char_p
             L.srmc_version.restype = C.c_int
             for name in ("srmc_create", "srmc_solve", "srmc_solve_step", "srmc_eval", "srmc_centres",
@@ -154,7 +156,8 @@ def exported_symbols():
                         "srmc_centres", "srmc_table", "srmc_read_table", "srmc_closed_form_error",
                         "srmc_stats", "srmc_philox",
                         "srmc_normals",
-                        "srmc_locate", "srmc_start_points", "srmc_last_error", "srmc_version")
+                        "srmc_locate", "srmc_start_points", "srmc_fp32_fma_probe", "srmc_last_error",
+                        "srmc_version")
             if hasattr(L, n)]
 
 
@@ -307,6 +310,12 @@ def srmc_philox(ctr, key, out, stream=None):
 
 def srmc_normals(words, out64=None, out32=None, stream=None):
     _check(lib().srmc_normals(_ptr(words), words.shape[0], _ptr(out64), _ptr(out32), _stream(stream)))
+
+
+def srmc_fp32_fma_probe(grid, threads, iters, packed, out, stream=None):
+    """FP32 FMA throughput probe: grid * threads * iters * 32 FLOP."""
+    _check(lib().srmc_fp32_fma_probe(int(grid), int(threads), int(iters), int(bool(packed)), _ptr(out),
+                                     _stream(stream)))
 
 
 def srmc_version() -> int:

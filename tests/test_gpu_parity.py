@@ -2,15 +2,17 @@
 Philox streams.
 
 Tolerances (stated per test): FP64 form |dy|, |dz| <= 1e-10 at stratum
-centres; FP32 form |dy| <= 1e-4 (1 + |y|) and |dz| <= 1e-4 (1 + |z|).
-Full-size workloads are checked on sampled strata of the last steps, which
-the oracle fits lazily (each fit computes every row its paths visit)."""
+centres and at 2d points a quarter cell off each centre; FP32 form |dy| <= 1e-4 (1 + |y|) and |dz| <= 1e-4 (1 + |z|).
+Full-size workloads are checked step by step at depth: the oracle refits
+sampled strata of steps 0, N/2 and N-1 from the GPU's own tables of the later
+steps (teacher forcing, tests/teacher.py), at centres and off-centre points."""
 import math
 
 import numpy as np
 import pytest
 
 from paper_2407_21085_gb300 import workloads as W
+from tests import teacher as T
 
 pytestmark = pytest.mark.gpu
 
@@ -40,10 +42,14 @@ def _check(w, gy, gz, ry, rz, where=""):
 
 
 def _full_parity(dev, orc, w, block_threads=0, points=None):
+    # default points: every stratum's centre and the 2d points a quarter cell
+    # (half a basis unit) off it along each axis, so that slopes are compared too
     torch, srmc = dev
     s = srmc.Solver(w, block_threads=block_threads)
     s.srmc_solve()
-    x = s.centres() if points is None else torch.from_numpy(points).cuda()
+    if points is None:
+        points = T.probe_points(w, np.arange(w.K))
+    x = torch.from_numpy(points).cuda()
     xn = x.cpu().numpy()
     o = orc.Oracle(w)
     o.solve_full(0)
@@ -308,52 +314,57 @@ def test_invalid_arguments(dev):
     s.srmc_eval(2, empty, y)                     # n = 0 is a no-op
 
 
-# ---- full-size workloads, sampled strata of the last steps ------------------
+# ---- full-size workloads: teacher-forced steps at every depth ----------------
+# The GPU's own FP64 tables of the later steps are given to the oracle, which
+# refits ~256 sampled strata of a step from them; compared at the centres and
+# at 2d off-centre points (tests/teacher.py).  Steps 0, N/2 and N-1.
 
-def _sampled_parity(dev, orc, w, steps, n_strata, seed=0):
+def _deep(dev, orc, w, n_strata=256, steps=None, block_threads=0):
     torch, srmc = dev
-    s = srmc.Solver(w)
+    s = srmc.Solver(w, block_threads=block_threads)
     s.srmc_solve()
     torch.cuda.synchronize()
-    rng = np.random.default_rng(seed)
-    o = orc.Oracle(w)
-    xs_all = s.centres().cpu().numpy()
-    for i in steps:
-        ks = rng.choice(w.K, size=n_strata, replace=False)
-        for k in ks:
-            o.fit_lazy(i, int(k))
-        xs = xs_all[ks]
-        gy, gz = s.evaluate(i, torch.from_numpy(xs).cuda())
-        ry, rz = o.eval(i, xs)
-        _check(w, gy.cpu().numpy(), gz.cpu().numpy(), ry, rz, where=f"step {i}")
-    st = s.srmc_stats()
-    assert st["nonfinite"] == 0
+    steps = steps if steps is not None else [0, w.N // 2, w.N - 1]
+    res = T.teacher_forced(torch, orc, s, steps, n_strata)
+    print(w.name, w.precision, {i: ("%.2e" % a, "%.2e" % b) for i, (a, b) in res.items()})
+    T.assert_within(w, res)
+    assert s.srmc_stats()["nonfinite"] == 0
+    s.close()
+    return res
 
 
 @pytest.mark.parametrize("prec", ["fp32", "fp64"])
-def test_cfg2_full_size_sampled(dev, orc, prec):
-    # 64x64 strata, N=20, M=4096: the benchmark's launch configuration
-    w = W.cfg2(precision=prec)
-    _sampled_parity(dev, orc, w, steps=[w.N - 1, w.N - 2, w.N - 3], n_strata=4)
+def test_cfg2_full_size_teacher_forced(dev, orc, prec):
+    # 64x64 strata on [-4,4]^2, N=20, M=4096, LP1: the launch configuration of
+    # the d = 2 benchmark line
+    _deep(dev, orc, W.cfg2(precision=prec))
 
 
-def test_cfg3_full_size_sampled(dev, orc):
-    # 12^4 strata, N=50, M=16384, kapz=0.2, FP32 form
-    w = W.cfg3()
-    _sampled_parity(dev, orc, w, steps=[w.N - 1, w.N - 2], n_strata=3)
+def test_cfg2_lp0_full_size_teacher_forced(dev, orc):
+    _deep(dev, orc, W.cfg2(basis="lp0", precision="fp64"))
 
 
-def test_cfg5_full_size_sampled(dev, orc):
-    # 8^6 = 262144 strata on [-3,3]^6, N = 40, M = 4096, FP32 form (the plain
-    # arm of the control-variate comparison)
-    w = W.cfg5()
-    _sampled_parity(dev, orc, w, steps=[w.N - 1, w.N - 2], n_strata=2)
+def test_cfg3_full_size_teacher_forced(dev, orc):
+    # 12^4 strata on [-3.5,3.5]^4, N=50, M=16384, kapz=0.2 (z in the driver),
+    # FP32 paths + FP64 solves
+    _deep(dev, orc, W.cfg3())
 
 
-def test_cfg2_shape_equal_probability_sampled(dev, orc):
-    # the benchmark's launch configuration with equal-probability strata
-    w = W.cfg2().replace(strata="prob")
-    _sampled_parity(dev, orc, w, steps=[w.N - 1, w.N - 2], n_strata=4)
+def test_cfg3_shape_fp64_teacher_forced(dev, orc):
+    # the all-FP64 form on cfg3's strata, N and driver with M = 1024 (the FP64
+    # form runs at the GB300's FP64 rate, far below its FP32 rate)
+    _deep(dev, orc, W.cfg3(M=1024, precision="fp64"), n_strata=128)
+
+
+def test_cfg5_full_size_teacher_forced(dev, orc):
+    # 8^6 = 262144 strata on [-3,3]^6, N = 40, M = 4096, FP32: the benchmark's
+    # headline launch configuration
+    _deep(dev, orc, W.cfg5())
+
+
+def test_cfg2_shape_equal_probability_teacher_forced(dev, orc):
+    # cfg2's launch configuration with equal-probability strata
+    _deep(dev, orc, W.cfg2().replace(strata="prob"))
 
 
 def test_graph_solve_equals_step_launches(dev):
