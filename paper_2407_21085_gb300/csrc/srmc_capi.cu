@@ -496,7 +496,9 @@ srmc_status srmc_create(const srmc_problem *pr, const srmc_strata *sa, const srm
     P.kind = prob ? 1 : 0;
     for (int l = 0; l < d; ++l) {
         P.cells[l] = sa->cells[l];
-        P.stride[l] = stride; stride *= sa->cells[l];
+        P.stride[l] = stride;
+        P.kbias += 0x4B000000u * (unsigned)stride;     // wraps mod 2^32 (see locate_point)
+        stride *= sa->cells[l];
         P.cell_off[l] = off; off += sa->cells[l];
         // (equal-probability strata use the per-cell table; lo = 0, h = 1 unused)
         const double lo = prob ? 0.0 : sa->lo[l], hi = prob ? (double)sa->cells[l] : sa->hi[l];

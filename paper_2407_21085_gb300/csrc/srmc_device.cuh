@@ -40,6 +40,7 @@ struct Params {
     int model;
     int cells[DMAX];
     int stride[DMAX];               // stratum index stride of each dimension
+    unsigned kbias;                 // sum_l 0x4B000000 stride_l mod 2^32 (cell location by rounding)
     int cell_off[DMAX];             // offset of dimension l in cellF
     double lo[DMAX], h[DMAX], b[DMAX], sig[DMAX];
     float lo_f[DMAX], r_f[DMAX], b_f[DMAX], sig_f[DMAX];
@@ -80,13 +81,34 @@ struct Params {
 };
 
 // ---- Philox-4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11) --------------------
+// The 32 x 32 -> 64-bit product of a round's multiplier and counter word, as
+// (hi, lo).  With SRMC_PHILOX_WIDE the product is one mul.wide.u32 whose two
+// halves are the high and low words; otherwise the high and low words are
+// formed separately (__umulhi and the wrapping product).
+#ifndef SRMC_PHILOX_WIDE
+#define SRMC_PHILOX_WIDE 1
+#endif
+__device__ __forceinline__ void mul_hilo(unsigned a, unsigned b, unsigned &hi, unsigned &lo)
+{
+#if SRMC_PHILOX_WIDE && !defined(__CUDACC_RTC__)
+    unsigned long long r;
+    asm("mul.wide.u32 %0, %1, %2;" : "=l"(r) : "r"(a), "r"(b));
+    lo = (unsigned)r;
+    hi = (unsigned)(r >> 32);
+#else
+    hi = __umulhi(a, b);
+    lo = a * b;
+#endif
+}
+
 __device__ __forceinline__ void philox10(unsigned &c0, unsigned &c1, unsigned &c2, unsigned &c3,
                                          const unsigned (&rk0)[10], const unsigned (&rk1)[10])
 {
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
-        const unsigned hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
-        const unsigned hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
+        unsigned hi0, lo0, hi1, lo1;
+        mul_hilo(0xD2511F53u, c0, hi0, lo0);
+        mul_hilo(0xCD9E8D57u, c2, hi1, lo1);
         const unsigned n0 = hi1 ^ c1 ^ rk0[r];
         const unsigned n2 = hi0 ^ c3 ^ rk1[r];
         c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
@@ -99,8 +121,9 @@ __device__ __forceinline__ void philox10(unsigned &c0, unsigned &c1, unsigned &c
 {
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
-        const unsigned hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
-        const unsigned hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
+        unsigned hi0, lo0, hi1, lo1;
+        mul_hilo(0xD2511F53u, c0, hi0, lo0);
+        mul_hilo(0xCD9E8D57u, c2, hi1, lo1);
         const unsigned n0 = hi1 ^ c1 ^ k0;
         const unsigned n2 = hi0 ^ c3 ^ k1;
         c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
@@ -210,15 +233,17 @@ __device__ __forceinline__ float normal_h(float wv)
     return h;
 }
 
+// The sign of the normal is that of y = 2U - 1, U = (w + 1/2) 2^-32, formed
+// as (w - 2^31 + 1/2) 2^-31 from the signed integer w - 2^31 (exact next to
+// U = 1/2); h depends on U only through 4 U (1 - U), which is formed from the
+// smaller of U and 1 - U, p = (min(w, ~w) + 1/2) 2^-32 <= 1/2.
 __device__ __forceinline__ float normal_of(unsigned w, float)
 {
-    const bool up = w >= 0x80000000u;
-    const unsigned v = up ? ~w : w;                                     // p <= 1/2
+    const unsigned v = min(w, ~w);                                      // p <= 1/2
     const float p = fmaf(__uint2float_rn(v), 0x1p-32f, 0x1p-33f);
-    const float y = fmaf(__uint2float_rn(0x7FFFFFFFu - v), -0x1p-31f, -0x1p-32f);   // 2p - 1
+    const float y = fmaf(__int2float_rn((int)(w ^ 0x80000000u)), 0x1p-31f, 0x1p-32f);   // 2U - 1
     const float wv = -__logf(4.0f * (p * (1.0f - p)));
-    const float x = y * normal_h(wv);
-    return up ? -x : x;
+    return y * normal_h(wv);
 }
 
 // Two normals at once with the packed two-wide FP32 instructions of the
@@ -233,13 +258,12 @@ __device__ __forceinline__ float normal_of(unsigned w, float)
 __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
 __device__ __forceinline__ float2 normal_pair(unsigned w0, unsigned w1)
 {
-    const bool up0 = w0 >= 0x80000000u, up1 = w1 >= 0x80000000u;
-    const unsigned v0 = up0 ? ~w0 : w0, v1 = up1 ? ~w1 : w1;
+    const unsigned v0 = min(w0, ~w0), v1 = min(w1, ~w1);
     const float2 p = __ffma2_rn(make_float2(__uint2float_rn(v0), __uint2float_rn(v1)),
                                 f2(0x1p-32f), f2(0x1p-33f));
-    const float2 y = __ffma2_rn(make_float2(__uint2float_rn(0x7FFFFFFFu - v0),
-                                            __uint2float_rn(0x7FFFFFFFu - v1)),
-                                f2(-0x1p-31f), f2(-0x1p-32f));
+    const float2 y = __ffma2_rn(make_float2(__int2float_rn((int)(w0 ^ 0x80000000u)),
+                                            __int2float_rn((int)(w1 ^ 0x80000000u))),
+                                f2(0x1p-31f), f2(0x1p-32f));
     const float2 r = __fmul2_rn(f2(4.0f), __fmul2_rn(p, __ffma2_rn(p, f2(-1.0f), f2(1.0f))));
     const float2 wv = make_float2(-__logf(r.x), -__logf(r.y));
     float2 h;
@@ -260,8 +284,7 @@ __device__ __forceinline__ float2 normal_pair(unsigned w0, unsigned w1)
         if (tx) h.x = ht.x;
         if (ty) h.y = ht.y;
     }
-    const float2 x = __fmul2_rn(y, h);
-    return make_float2(up0 ? -x.x : x.x, up1 ? -x.y : x.y);
+    return __fmul2_rn(y, h);
 }
 #endif
 

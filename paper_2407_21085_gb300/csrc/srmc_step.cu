@@ -140,11 +140,48 @@ __device__ __forceinline__ void advance(const Params &P, int j, const R (&x)[D],
 
 // Cells of x on equal-size strata: kk = sum_l c_l stride_l, and (LP1) the
 // centred coordinates phi[1 + l] = 2 (t_l - c_l) - 1, t_l = (x_l - lo_l) / h_l.
+//
+// With SRMC_LOCATE_RD the FP32 cell c = clamp(floor(t), 0, C - 1) is taken by
+// one addition rounded toward -inf: for 0 <= tc < 2^23, tc + 2^23 rounded down
+// is exactly 2^23 + floor(tc), whose bits are 0x4B000000 + floor(tc), so with
+// tc = clamp(t, 0, C - 1) (NaN -> 0) the bits are 0x4B000000 + c and the float
+// minus 2^23 is c itself: the same decision and basis value as floorf, with no
+// conversion.  The stride-weighted 0x4B000000 terms are removed at the end
+// (P.kbias, all modulo 2^32).
+#ifndef SRMC_LOCATE_RD
+#define SRMC_LOCATE_RD 1
+#endif
 template <typename R, int D, bool LP1, int p>
 __device__ __forceinline__ unsigned locate_point(const Params &P, const R (&x)[D], R (&phi)[p])
 {
     unsigned kk = 0;
-#if SRMC_PAIRS_ON
+#if SRMC_PAIRS_ON && SRMC_LOCATE_RD
+    if constexpr (sizeof(R) == 4) {
+#pragma unroll
+        for (int l = 0; l + 1 < D; l += 2) {
+            const float2 t = __fmul2_rn(__fadd2_rn(make_float2(x[l], x[l + 1]),
+                                                   make_float2(-P.lo_f[l], -P.lo_f[l + 1])),
+                                        make_float2(P.r_f[l], P.r_f[l + 1]));
+            const float2 tc = make_float2(fminf(fmaxf(t.x, 0.0f), (float)(P.cells[l] - 1)),
+                                          fminf(fmaxf(t.y, 0.0f), (float)(P.cells[l + 1] - 1)));
+            const float2 f = __fadd2_rd(tc, f2(0x1p23f));
+            kk += __float_as_uint(f.x) * (unsigned)P.stride[l] + __float_as_uint(f.y) * (unsigned)P.stride[l + 1];
+            if (LP1) {
+                const float2 c = __fadd2_rn(f, f2(-0x1p23f));
+                const float2 u = __ffma2_rn(f2(2.0f), __fadd2_rn(t, make_float2(-c.x, -c.y)), f2(-1.0f));
+                phi[1 + l] = u.x;
+                phi[2 + l] = u.y;
+            }
+        }
+        if constexpr ((D & 1) != 0) {
+            const float t = __fmul_rn(__fsub_rn(x[D - 1], P.lo_f[D - 1]), P.r_f[D - 1]);
+            const float f = __fadd_rd(fminf(fmaxf(t, 0.0f), (float)(P.cells[D - 1] - 1)), 0x1p23f);
+            kk += __float_as_uint(f) * (unsigned)P.stride[D - 1];
+            if (LP1) phi[D] = 2.0f * (t - (f - 0x1p23f)) - 1.0f;
+        }
+        return kk - P.kbias;
+    }
+#elif SRMC_PAIRS_ON
     if constexpr (sizeof(R) == 4) {
 #pragma unroll
         for (int l = 0; l + 1 < D; l += 2) {
@@ -523,11 +560,27 @@ struct MinBlocks {
                                     : (D <= 2 ? SRMC_MINB_LO : SRMC_MINB_HI);
 };
 
+// Whether phase A parks a path's basis values phi(x_i) and increments dW_i
+// in shared memory across its time loop (FP32 form, d >= SRMC_STAGE_MIN_D):
+// they are needed only for the moments after the loop, and in registers they
+// would stay live through every step (at d = 6, 12 registers, which made the
+// kernel spill at its 64-register budget).  One column per thread, read back
+// with volatile loads so that the compiler cannot keep the values instead.
+#ifndef SRMC_STAGE_MIN_D
+#define SRMC_STAGE_MIN_D 5
+#endif
+template <typename R, int D>
+struct Stage {
+    static constexpr bool value = sizeof(R) == 4 && D >= SRMC_STAGE_MIN_D;
+};
+
 // Shared memory of one stratum block.
 template <typename R, int D, bool LP1>
 struct StepSmem {
     static constexpr int p = BasisDim<D, LP1>::value;
     static constexpr int q = D;
+    static constexpr int NST = Stage<R, D>::value ? (p - 1) + D : 1;   // staged values per path
+    float stage[NST][Stage<R, D>::value ? MAX_THREADS : 1];
     static constexpr int EG = LP1 ? p * (p + 1) / 2 : 0;
     static constexpr int EA = EG + q * p + p;
     static constexpr int EB = p;
@@ -631,15 +684,22 @@ __device__ __forceinline__ void solve_stratum(const Params &P, const int i, cons
                 xj[l] = next_coord<R, D>(P, i, l, x, dwi[l], NW == 2 ? normal_of(we[l], (R)0) : (R)0);
             }
         }
-        // Martingale control: CI = zc_i(x_i).dW_i (stratum k), CZ = sum_{j>i} zc_j(X_j).dW_j,
-        // zc_j evaluated at X_j from the control row of (j, stratum of X_j); with the
-        // run's own control zc_j = z_j, the fitted z of step j, and CI = 0.
+        // (CI below reads phi and dwi before they are parked)
         [[maybe_unused]] R CI = (R)0, CZ = (R)0;
-        [[maybe_unused]] R phij[p];
-        [[maybe_unused]] unsigned rowj = 0;
         if constexpr (CV) {
             if (!P.cv_own) CI = control_dot<R, D, p>(P, (unsigned)i * (unsigned)P.K + (unsigned)k, phi, dwi);
         }
+        if constexpr (Stage<R, D>::value) {
+#pragma unroll
+            for (int a = 1; a < p; ++a) sm.stage[a - 1][threadIdx.x] = (float)phi[a];
+#pragma unroll
+            for (int l = 0; l < D; ++l) sm.stage[p - 1 + l][threadIdx.x] = (float)dwi[l];
+        }
+        // Martingale control: CI = zc_i(x_i).dW_i (stratum k), CZ = sum_{j>i} zc_j(X_j).dW_j,
+        // zc_j evaluated at X_j from the control row of (j, stratum of X_j); with the
+        // run's own control zc_j = z_j, the fitted z of step j, and CI = 0.
+        [[maybe_unused]] R phij[p];
+        [[maybe_unused]] unsigned rowj = 0;
         // A driver that does not read z: f_i(x_i, y_{i+1}(X_{i+1})) is known
         // after this first step, so the Y response is complete in phase A (no
         // phase B).  Its part in x_i is taken before X_{i+1} is located.
@@ -691,6 +751,13 @@ __device__ __forceinline__ void solve_stratum(const Params &P, const int i, cons
             });
         }
         S += model_g<R, D, MODEL>(P, xj);
+        if constexpr (Stage<R, D>::value) {
+            const volatile float *st = &sm.stage[0][threadIdx.x];
+#pragma unroll
+            for (int a = 1; a < p; ++a) phi[a] = (R)st[(a - 1) * MAX_THREADS];
+#pragma unroll
+            for (int l = 0; l < D; ++l) dwi[l] = (R)st[(p - 1 + l) * MAX_THREADS];
+        }
         // Z response uses S - CZ; the phase-A part of the Y response S - CZ - CI.
         R SZ = S, SY = S;
         if constexpr (CV) { SZ = S - CZ; SY = SZ - CI; }
