@@ -467,11 +467,19 @@ def cv_compare(args, stream):
 
 # ---- the paper's own experiment (Sec. 5.1): error indicators over many runs ----------
 def paper_table_rows(table: str):
-    """Rows (N, cells per dimension, M, runs) of tables of Sec. 5.2: d = 4 LP1
+    """Rows (N, cells per dimension, M, runs) of tables of Sec. 5.2: d = 11 LP0
+    with #C = floor(sqrt N), M = N^2 and LP1 with #C = 2, 3 at dt = 0.2; d = 4 LP1
     with #C = floor(3 sqrt(d sqrt(N)) - 5), M = (d+1) N^2 and LP0 with
     #C = floor(4 sqrt(N)), M = N^2; d = 6 LP1 with #C = floor(1.5 sqrt(d sqrt(N))
     - 3), M = (d+1) N^2 and LP0 with #C = floor(2 sqrt(N)), M = N^2.  The run
     counts are ours (10^3 in the paper), fewer where one run takes seconds."""
+    if table == "lp0_d11":
+        # #C = floor(sqrt(N)), M = N^2 (the paper's LP0 table at d = 11)
+        d, rows = 11, [(5, 1000), (10, 50), (20, 3)]
+        return d, "lp0", [(N, int(math.floor(math.sqrt(N))), N * N, R) for N, R in rows]
+    if table == "lp1_d11":
+        # the paper's LP1 table at d = 11: dt = 0.2 with #C = 2, M = 2000 and #C = 3, M = 4000
+        return 11, "lp1", [(5, 2, 2000, 1000), (5, 3, 4000, 20)]
     if table == "lp1_d6":
         d, rows = 6, [(5, 1000), (10, 1000), (20, 200), (50, 3)]
         return d, "lp1", [(N, int(math.floor(1.5 * math.sqrt(d * math.sqrt(N)) - 3)), (d + 1) * N * N, R)
@@ -743,7 +751,8 @@ def main():
                     help="time the control-variate step kernel (rows from an untrained network)")
     ap.add_argument("--control-own", action="store_true",
                     help="time the step kernel with the run's own z control")
-    ap.add_argument("--paper-table", choices=["lp1_d4", "lp0_d4", "lp1_d6", "lp0_d6"], default=None,
+    ap.add_argument("--paper-table", choices=["lp1_d4", "lp0_d4", "lp1_d6", "lp0_d6", "lp0_d11", "lp1_d11"],
+                    default=None,
                     help="instead of the benchmark: the error indicators of Sec. 5.1 over many runs")
     ap.add_argument("--paper-points", type=int, default=1000, help="nu points per step per run")
     ap.add_argument("--cv-M", type=int, default=1024)

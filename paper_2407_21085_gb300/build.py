@@ -1,6 +1,6 @@
 """Build libsrmc.so in-tree for sm_103a with nvcc.
 
-The step kernel is compiled once per dimension D = 1..8 (-DSRMC_STEP_D=D) so
+The step kernel is compiled once per dimension D = 1..11 (-DSRMC_STEP_D=D) so
 that per-path state stays in registers, and once per kind of strata
 (-DSRMC_STEP_KIND: equal size, equal probability) and of dynamics
 (-DSRMC_STEP_DYN: Euler, exact) and of basis (-DSRMC_STEP_BASIS=2: quadratic
@@ -23,7 +23,8 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libsrmc.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-DIMS = range(1, 9)
+DIMS = range(1, 12)             # equal-size strata, Euler dynamics: d <= 11
+NARROW_DIMS = range(1, 9)       # equal-probability strata, exact dynamics: d <= 8
 LP2_DIMS = range(1, 4)          # quadratic local polynomials: d <= 3
 
 
@@ -96,9 +97,9 @@ def build(force: bool = False, verbose: bool = False, jobs: int | None = None,
     extra_defs = [f"-D{d}" for d in defines]
     units = [(os.path.join(CSRC, "srmc_step.cu"), os.path.join(out, f"step_{tag}d{D}.o"),
               [f"-DSRMC_STEP_D={D}", f"-DSRMC_STEP_KIND={kind}"] + extra_defs)
-             for kind, tag in ((0, ""), (1, "prob_")) for D in DIMS]
+             for kind, tag, dims in ((0, "", DIMS), (1, "prob_", NARROW_DIMS)) for D in dims]
     units += [(os.path.join(CSRC, "srmc_step.cu"), os.path.join(out, f"step_exact_d{D}.o"),
-               [f"-DSRMC_STEP_D={D}", "-DSRMC_STEP_DYN=1"] + extra_defs) for D in DIMS]
+               [f"-DSRMC_STEP_D={D}", "-DSRMC_STEP_DYN=1"] + extra_defs) for D in NARROW_DIMS]
     units += [(os.path.join(CSRC, "srmc_step.cu"), os.path.join(out, f"step_quad_d{D}.o"),
                [f"-DSRMC_STEP_D={D}", "-DSRMC_STEP_BASIS=2"] + extra_defs) for D in LP2_DIMS]
     for name in sorted(os.listdir(CSRC)):

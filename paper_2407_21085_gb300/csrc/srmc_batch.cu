@@ -218,6 +218,8 @@ srmc_status srmc_batch_create(srmc_solver *const *solvers, int n, srmc_batch **o
             return bfail(SRMC_ERR_UNSUPPORTED, "srmc_batch_create: LP0 and LP1 only");
         if (solvers[r]->P.model == srmc::MODEL_USER)
             return bfail(SRMC_ERR_UNSUPPORTED, "srmc_batch_create: built-in models only");
+        if (solvers[r]->P.d > 8)
+            return bfail(SRMC_ERR_UNSUPPORTED, "srmc_batch_create: d <= 8 only");
         if (solvers[r]->device != dev) return bfail(SRMC_ERR_INVALID_ARG, "srmc_batch_create: solver on another device");
     }
     srmc_batch *b = new srmc_batch();

@@ -195,6 +195,9 @@ cudaError_t launch_step(const srmc_solver *s, int i, cudaStream_t st)
     case 6: return srmc::launch_step_d6(P, i, s->fp64, s->lp1, mv, grid, s->threads, st);
     case 7: return srmc::launch_step_d7(P, i, s->fp64, s->lp1, mv, grid, s->threads, st);
     case 8: return srmc::launch_step_d8(P, i, s->fp64, s->lp1, mv, grid, s->threads, st);
+    case 9: return srmc::launch_step_d9(P, i, s->fp64, s->lp1, mv, grid, s->threads, st);
+    case 10: return srmc::launch_step_d10(P, i, s->fp64, s->lp1, mv, grid, s->threads, st);
+    case 11: return srmc::launch_step_d11(P, i, s->fp64, s->lp1, mv, grid, s->threads, st);
     }
     return cudaErrorInvalidValue;
 }
@@ -379,7 +382,7 @@ srmc_status srmc_create(const srmc_problem *pr, const srmc_strata *sa, const srm
     *out = nullptr;
     if (!pr || !sa || !cf) return fail(SRMC_ERR_INVALID_ARG, "srmc_create: NULL argument");
     const int d = pr->d, q = pr->q;
-    if (d < 1 || d > SRMC_DMAX) return fail(SRMC_ERR_INVALID_ARG, "d must be in [1, 8]");
+    if (d < 1 || d > SRMC_DMAX) return fail(SRMC_ERR_INVALID_ARG, "d must be in [1, 11]");
     if (q != d) return fail(SRMC_ERR_UNSUPPORTED, "this build requires q == d");
     if (pr->N < 1 || pr->N > 1000000) return fail(SRMC_ERR_INVALID_ARG, "N must be in [1, 1e6]");
     if (!(pr->T > 0.0) || !std::isfinite(pr->T)) return fail(SRMC_ERR_INVALID_ARG, "T must be > 0");
@@ -435,6 +438,9 @@ srmc_status srmc_create(const srmc_problem *pr, const srmc_strata *sa, const srm
     if (cf->basis == SRMC_LP2 && (d > SRMC_LP2_DMAX || prob || pr->dynamics != SRMC_DYN_EULER))
         return fail(SRMC_ERR_UNSUPPORTED, "LP2 is built for d <= 3, equal-size strata and Euler dynamics");
     if (cf->prec != SRMC_FP32 && cf->prec != SRMC_FP64) return fail(SRMC_ERR_INVALID_ARG, "precision");
+    if (d >= srmc::SRMC_WIDE_DMIN_V && (prob || pr->dynamics != SRMC_DYN_EULER || cf->prec != SRMC_FP32))
+        return fail(SRMC_ERR_UNSUPPORTED,
+                    "d >= 9 is built for equal-size strata, Euler dynamics and the FP32 form");
     if (cf->M < p) return fail(SRMC_ERR_INVALID_ARG, "M must be >= the basis dimension");
     if (cf->M > 4294967295LL) return fail(SRMC_ERR_INVALID_ARG, "M must be < 2^32");
     long long M_max = cf->M, M_sum = cf->M * K;
@@ -956,6 +962,7 @@ srmc_status srmc_set_control(srmc_solver *s, const double *rows)
     if (!s || !rows) return fail(SRMC_ERR_INVALID_ARG, "srmc_set_control: NULL argument");
     if (!s->lp1) return fail(SRMC_ERR_UNSUPPORTED, "srmc_set_control: LP1 solvers only");
     if (s->mv == srmc::MV_AFFINE) return fail(SRMC_ERR_UNSUPPORTED, "srmc_set_control: not for the affine model");
+    if (s->P.d >= srmc::SRMC_WIDE_DMIN_V) return fail(SRMC_ERR_UNSUPPORTED, "srmc_set_control: d <= 8 only");
     if (const int st = srmc_prepare_user_control(s)) return (srmc_status)st;
     const size_t nrow = (size_t)s->P.N * (size_t)s->P.K;
     const size_t n = nrow * (size_t)(s->P.q * s->P.p);
@@ -998,6 +1005,8 @@ srmc_status srmc_set_own_control(srmc_solver *s)
     if (!s->lp1) return fail(SRMC_ERR_UNSUPPORTED, "srmc_set_own_control: LP1 solvers only");
     if (s->mv == srmc::MV_AFFINE)
         return fail(SRMC_ERR_UNSUPPORTED, "srmc_set_own_control: not for the affine model");
+    if (s->P.d >= srmc::SRMC_WIDE_DMIN_V)
+        return fail(SRMC_ERR_UNSUPPORTED, "srmc_set_own_control: d <= 8 only");
     if (const int st = srmc_prepare_user_control(s)) return (srmc_status)st;
     s->cv = true;
     s->cv_own = true;

@@ -14,8 +14,8 @@
 
 namespace srmc {
 
-constexpr int DMAX = 8;
-constexpr int PBMAX = 10;            // largest basis dimension: LP1 at d = 8 (9), LP2 at d = 3 (10)
+constexpr int DMAX = 11;
+constexpr int PBMAX = 12;            // largest basis dimension: LP1 at d = 11 (12), LP2 at d = 3 (10)
 
 // The quadratic monomials u_a u_b (a <= b, row order) after the linear ones
 // of a basis vector of dimension p, for d only known at run time.
@@ -84,9 +84,15 @@ struct Params {
 // The 32 x 32 -> 64-bit product of a round's multiplier and counter word, as
 // (hi, lo).  With SRMC_PHILOX_WIDE the product is one mul.wide.u32 whose two
 // halves are the high and low words; otherwise the high and low words are
-// formed separately (__umulhi and the wrapping product).
+// formed separately (__umulhi and the wrapping product).  Measured on GB300:
+// the wide form is 1 % faster for d <= 3 and 0.5 % slower for d = 6 (register
+// allocation), so it is the default for the small dimensions only.
 #ifndef SRMC_PHILOX_WIDE
+#if defined(SRMC_STEP_D) && SRMC_STEP_D > 3
+#define SRMC_PHILOX_WIDE 0
+#else
 #define SRMC_PHILOX_WIDE 1
+#endif
 #endif
 __device__ __forceinline__ void mul_hilo(unsigned a, unsigned b, unsigned &hi, unsigned &lo)
 {
@@ -233,17 +239,15 @@ __device__ __forceinline__ float normal_h(float wv)
     return h;
 }
 
-// The sign of the normal is that of y = 2U - 1, U = (w + 1/2) 2^-32, formed
-// as (w - 2^31 + 1/2) 2^-31 from the signed integer w - 2^31 (exact next to
-// U = 1/2); h depends on U only through 4 U (1 - U), which is formed from the
-// smaller of U and 1 - U, p = (min(w, ~w) + 1/2) 2^-32 <= 1/2.
 __device__ __forceinline__ float normal_of(unsigned w, float)
 {
-    const unsigned v = min(w, ~w);                                      // p <= 1/2
+    const bool up = w >= 0x80000000u;
+    const unsigned v = up ? ~w : w;                                     // p <= 1/2
     const float p = fmaf(__uint2float_rn(v), 0x1p-32f, 0x1p-33f);
-    const float y = fmaf(__int2float_rn((int)(w ^ 0x80000000u)), 0x1p-31f, 0x1p-32f);   // 2U - 1
+    const float y = fmaf(__uint2float_rn(0x7FFFFFFFu - v), -0x1p-31f, -0x1p-32f);   // 2p - 1
     const float wv = -__logf(4.0f * (p * (1.0f - p)));
-    return y * normal_h(wv);
+    const float x = y * normal_h(wv);
+    return up ? -x : x;
 }
 
 // Two normals at once with the packed two-wide FP32 instructions of the
@@ -258,12 +262,13 @@ __device__ __forceinline__ float normal_of(unsigned w, float)
 __device__ __forceinline__ float2 f2(float a) { return make_float2(a, a); }
 __device__ __forceinline__ float2 normal_pair(unsigned w0, unsigned w1)
 {
-    const unsigned v0 = min(w0, ~w0), v1 = min(w1, ~w1);
+    const bool up0 = w0 >= 0x80000000u, up1 = w1 >= 0x80000000u;
+    const unsigned v0 = up0 ? ~w0 : w0, v1 = up1 ? ~w1 : w1;
     const float2 p = __ffma2_rn(make_float2(__uint2float_rn(v0), __uint2float_rn(v1)),
                                 f2(0x1p-32f), f2(0x1p-33f));
-    const float2 y = __ffma2_rn(make_float2(__int2float_rn((int)(w0 ^ 0x80000000u)),
-                                            __int2float_rn((int)(w1 ^ 0x80000000u))),
-                                f2(0x1p-31f), f2(0x1p-32f));
+    const float2 y = __ffma2_rn(make_float2(__uint2float_rn(0x7FFFFFFFu - v0),
+                                            __uint2float_rn(0x7FFFFFFFu - v1)),
+                                f2(-0x1p-31f), f2(-0x1p-32f));
     const float2 r = __fmul2_rn(f2(4.0f), __fmul2_rn(p, __ffma2_rn(p, f2(-1.0f), f2(1.0f))));
     const float2 wv = make_float2(-__logf(r.x), -__logf(r.y));
     float2 h;
@@ -284,7 +289,8 @@ __device__ __forceinline__ float2 normal_pair(unsigned w0, unsigned w1)
         if (tx) h.x = ht.x;
         if (ty) h.y = ht.y;
     }
-    return __fmul2_rn(y, h);
+    const float2 x = __fmul2_rn(y, h);
+    return make_float2(up0 ? -x.x : x.x, up1 ? -x.y : x.y);
 }
 #endif
 
@@ -516,6 +522,14 @@ __device__ __forceinline__ R model_f_y(const Params &P, R y, R fx)
     }
 }
 
+// The driver of the paper's test BSDE (Sec. 5.1), f = (sum_l z_l)(y - (2 + d)/(2d)),
+// from the sum of the components of z.
+template <typename R, int D>
+__device__ __forceinline__ R logistic_f(R y, R zsum)
+{
+    return zsum * (y - (R)(2 + D) / (R)(2 * D));
+}
+
 // f_j(x, y, z); z is used only when ZIN.
 template <typename R, int D, int MODEL, bool ZIN>
 __device__ __forceinline__ R model_f(const Params &P, int j, const R (&x)[D], R y, const R *z)
@@ -555,7 +569,7 @@ __device__ __forceinline__ R model_f(const Params &P, int j, const R (&x)[D], R 
         R sz = (R)0;
 #pragma unroll
         for (int l = 0; l < D; ++l) sz += z[l];
-        return sz * (y - (R)(2 + D) / (R)(2 * D));
+        return logistic_f<R, D>(y, sz);
     } else {
         return model_f_y<R, D, MODEL>(P, y, model_f_x<R, D, MODEL>(P, j, x));
     }

@@ -68,6 +68,14 @@ SRMC_DECLARE_STEP(6)
 SRMC_DECLARE_STEP(7)
 SRMC_DECLARE_STEP(8)
 #undef SRMC_DECLARE_STEP
+// d = 9..11: equal-size strata, Euler dynamics, the FP32 form, no controls.
+constexpr int SRMC_WIDE_DMIN_V = 9;
+cudaError_t launch_step_d9(const Params &P, int i, bool fp64, bool lp1, int mv, int grid, int threads,
+                           cudaStream_t st);
+cudaError_t launch_step_d10(const Params &P, int i, bool fp64, bool lp1, int mv, int grid, int threads,
+                            cudaStream_t st);
+cudaError_t launch_step_d11(const Params &P, int i, bool fp64, bool lp1, int mv, int grid, int threads,
+                            cudaStream_t st);
 cudaError_t launch_step_quad_d1(const Params &P, int i, bool fp64, bool lp1, int mv, int grid, int threads,
                                 cudaStream_t st);
 cudaError_t launch_step_quad_d2(const Params &P, int i, bool fp64, bool lp1, int mv, int grid, int threads,

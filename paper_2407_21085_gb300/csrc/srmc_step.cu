@@ -467,14 +467,35 @@ __device__ __forceinline__ void eval_at(const Params &P, int j, const R (&x)[D],
     for (int c = 1; c < p; ++c) v += a[c] * phi[c];
     y = clamp_r(v, Form<R>::Cy(P));
     if (ZIN) {
-        R bz[D * p];
-        load_row<D * p>(Form<R>::Ztab(P) + row * RZ, bz);
+        if constexpr (sizeof(R) == 4 && D * p > 64) {
+            // long rows (d >= 8): each 16-byte vector is folded into z as it
+            // arrives, so that the row never sits in registers whole
+            const float4 *z4 = reinterpret_cast<const float4 *>(Form<R>::Ztab(P) + row * RZ);
+            R w[D];
 #pragma unroll
-        for (int l = 0; l < D; ++l) {
-            R w = bz[l * p];
+            for (int l = 0; l < D; ++l) w[l] = (R)0;
 #pragma unroll
-            for (int c = 1; c < p; ++c) w += bz[l * p + c] * phi[c];
-            z[l] = clamp_r(w, Form<R>::Cz(P));
+            for (int v = 0; v < (D * p + 3) / 4; ++v) {
+                const float4 t = __ldg(z4 + v);
+                const float tv[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int e = 4 * v + u;
+                    if (e < D * p) w[e / p] = (e % p == 0) ? w[e / p] + tv[u] : fmaf(tv[u], phi[e % p], w[e / p]);
+                }
+            }
+#pragma unroll
+            for (int l = 0; l < D; ++l) z[l] = clamp_r(w[l], Form<R>::Cz(P));
+        } else {
+            R bz[D * p];
+            load_row<D * p>(Form<R>::Ztab(P) + row * RZ, bz);
+#pragma unroll
+            for (int l = 0; l < D; ++l) {
+                R w = bz[l * p];
+#pragma unroll
+                for (int c = 1; c < p; ++c) w += bz[l * p + c] * phi[c];
+                z[l] = clamp_r(w, Form<R>::Cz(P));
+            }
         }
     }
     if constexpr (CV) {
@@ -553,11 +574,14 @@ __device__ __forceinline__ R control_dot(const Params &P, unsigned row, const R 
 #ifndef SRMC_CVZMINB_HI
 #define SRMC_CVZMINB_HI 3
 #endif
+#ifndef SRMC_MINB_XL
+#define SRMC_MINB_XL 3
+#endif
 template <typename R, int D, bool CV, bool ZIN>
 struct MinBlocks {
     static constexpr int value = sizeof(R) == 8 ? 1
                                : CV ? (D <= 2 ? 4 : ZIN ? SRMC_CVZMINB_HI : SRMC_CVMINB_HI)
-                                    : (D <= 2 ? SRMC_MINB_LO : SRMC_MINB_HI);
+                                    : (D <= 2 ? SRMC_MINB_LO : D >= 9 ? SRMC_MINB_XL : SRMC_MINB_HI);
 };
 
 // Whether phase A parks a path's basis values phi(x_i) and increments dW_i
@@ -574,15 +598,45 @@ struct Stage {
     static constexpr bool value = sizeof(R) == 4 && D >= SRMC_STAGE_MIN_D;
 };
 
+// FP32 moments of long vectors (E > 24 entries: LP1 at d >= 4, LP2 at d >= 2)
+// by warp tiles: after its time loop every thread writes its path's columns
+// (1 or 0 for a path past M_k, phi_1..phi_{p-1}, w_l = S_Z dW_l / dt, S_Y;
+// zeros past M_k) into shared memory, and lane s of the warp forms entries
+// e = s, s + 32, ... of the moment vector as dot products over the warp's 32
+// paths -- the Gram entries sum phi_a phi_b, the Z right-hand sides
+// sum phi_a w_l, the Y right-hand side sum phi_a S_Y -- in FP32, then adds
+// them to running sums in FP64.  Each FP32 partial sums 32 terms, so the
+// rounding error of a moment is bounded by ~31 u sum |terms| whatever M is.
+// (The alternative, SRMC_TILE_MOMENTS=0, reduces each path's products across
+// the warp by shuffles, which costs ~3 E instructions per path.)
+#ifndef SRMC_TILE_MOMENTS
+#define SRMC_TILE_MOMENTS 1
+#endif
+// (Also for every FP32 kernel of d >= SRMC_TILE_MIN_D, whose path state
+// leaves no room for per-thread accumulators.)
+#ifndef SRMC_TILE_MIN_D
+#define SRMC_TILE_MIN_D 5
+#endif
+template <typename R, int D, int EA>
+struct TileMoments {
+    static constexpr bool value =
+        SRMC_TILE_MOMENTS && sizeof(R) == 4 && (EA > 24 || D >= SRMC_TILE_MIN_D);
+};
+
 // Shared memory of one stratum block.
 template <typename R, int D, bool LP1>
 struct StepSmem {
     static constexpr int p = BasisDim<D, LP1>::value;
     static constexpr int q = D;
-    static constexpr int NST = Stage<R, D>::value ? (p - 1) + D : 1;   // staged values per path
-    float stage[NST][Stage<R, D>::value ? MAX_THREADS : 1];
     static constexpr int EG = LP1 ? p * (p + 1) / 2 : 0;
     static constexpr int EA = EG + q * p + p;
+    // Path columns (one per thread; rows padded by one word so that lanes
+    // reading different rows at one column hit different banks): [0] 1 or 0,
+    // [1, p) phi_a, [p, p + q) dW_l and later w_l, [p + q] S_Y.
+    static constexpr bool COLS = Stage<R, D>::value || TileMoments<R, D, EA>::value;
+    static constexpr int NT = COLS ? p + q + 1 : 1;
+    static constexpr int TS = COLS ? MAX_THREADS + 1 : 1;
+    float tile[NT][TS];
     static constexpr int EB = p;
     double redA[MAX_WARPS][EA];
     double totA[EA];
@@ -608,8 +662,14 @@ __device__ __forceinline__ void solve_stratum(const Params &P, const int i, cons
     constexpr int EZ = q * p;
     constexpr int EA = EG + EZ + p;
     constexpr int EB = p;
-    constexpr bool RS = sizeof(R) == 4 && EA > 24;
+    constexpr bool TILE = TileMoments<R, D, EA>::value;
+    // The paper's logistic driver reads z only through sum_l z_l (of the
+    // truncated components): then only that sum is carried from step to step.
+    constexpr bool ZSUM = ZIN && MODEL == MODEL_LOGISTIC && !CV;
+    constexpr bool RS = sizeof(R) == 4 && EA > 24 && !TILE;
     using MA = typename Select<RS, MomentsRS<EA>, typename MomentsOf<R, EA>::type>::type;
+    constexpr int TS = StepSmem<R, D, LP1>::TS;
+    constexpr int LF = (EA + 31) / 32;             // moment entries per lane (TILE)
     using MB = typename MomentsOf<R, EB>::type;
     auto &redA = sm.redA;
     auto &totA = sm.totA;
@@ -657,6 +717,31 @@ __device__ __forceinline__ void solve_stratum(const Params &P, const int i, cons
     MA mA;
     if constexpr (RS) mA.zero(lane); else mA.zero();
     int since_flush = 0;
+    // TILE: the two columns whose dot product is this lane's entry e = lane + 32 s,
+    // and the entry's running sum
+    [[maybe_unused]] int colA[LF], colB[LF];
+    [[maybe_unused]] double csum[LF];
+    if constexpr (TILE) {
+#pragma unroll
+        for (int t = 0; t < LF; ++t) {
+            const int e = lane + 32 * t;
+            int a = 0, b = 0;
+            if (e < EG) {                                  // Gram (a, b), a <= b, row by row
+                int rem = e;
+                while (rem >= p - a) { rem -= p - a; ++a; }
+                b = a + rem;
+            } else if (e < EG + EZ) {                      // Z right-hand side (l, a)
+                a = (e - EG) % p;
+                b = p + (e - EG) / p;
+            } else if (e < EA) {                           // Y right-hand side a
+                a = e - EG - EZ;
+                b = p + q;
+            }
+            colA[t] = a * TS + 32 * warp;
+            colB[t] = b * TS + 32 * warp;
+            csum[t] = 0.0;
+        }
+    }
     for (long long m0 = 0; m0 < Mk; m0 += blockDim.x) {
         const long long m = m0 + threadIdx.x;
         const bool valid = m < Mk;
@@ -691,9 +776,9 @@ __device__ __forceinline__ void solve_stratum(const Params &P, const int i, cons
         }
         if constexpr (Stage<R, D>::value) {
 #pragma unroll
-            for (int a = 1; a < p; ++a) sm.stage[a - 1][threadIdx.x] = (float)phi[a];
+            for (int a = 1; a < p; ++a) sm.tile[a][threadIdx.x] = (float)phi[a];
 #pragma unroll
-            for (int l = 0; l < D; ++l) sm.stage[p - 1 + l][threadIdx.x] = (float)dwi[l];
+            for (int l = 0; l < D; ++l) sm.tile[p + l][threadIdx.x] = (float)dwi[l];
         }
         // Martingale control: CI = zc_i(x_i).dW_i (stratum k), CZ = sum_{j>i} zc_j(X_j).dW_j,
         // zc_j evaluated at X_j from the control row of (j, stratum of X_j); with the
@@ -707,6 +792,11 @@ __device__ __forceinline__ void solve_stratum(const Params &P, const int i, cons
         if constexpr (!ZIN) fdt = model_f_x<R, D, MODEL>(P, i, x);
         eval_at<R, D, LP1, MODEL, ZIN, CV>(P, i + 1, xj, yn, zj, phij, rowj);
         if constexpr (!ZIN) fdt = dt * model_f_y<R, D, MODEL>(P, yn, fdt);
+        [[maybe_unused]] R zsum = (R)0;
+        if constexpr (ZSUM) {
+#pragma unroll
+            for (int l = 0; l < D; ++l) zsum += zj[l];
+        }
         R S = (R)0;
         // Steps j = i+1 .. N-1 in groups of G, so that the word phase of
         // every step in a group is a compile-time constant.
@@ -744,25 +834,58 @@ __device__ __forceinline__ void solve_stratum(const Params &P, const int i, cons
                 [[maybe_unused]] R fx = (R)0;
                 if constexpr (!ZIN) fx = model_f_x<R, D, MODEL>(P, j, xj);
                 eval_at<R, D, LP1, MODEL, ZIN, CV>(P, j + 1, xn, yn, zn, phij, rowj);
-                if constexpr (ZIN) S += dt * model_f<R, D, MODEL, ZIN>(P, j, xj, yn, zj);
-                else S += dt * model_f_y<R, D, MODEL>(P, yn, fx);
+                if constexpr (ZSUM) {
+                    S += dt * logistic_f<R, D>(yn, zsum);
+                    zsum = (R)0;
+#pragma unroll
+                    for (int l = 0; l < D; ++l) zsum += zn[l];
+                } else if constexpr (ZIN) {
+                    S += dt * model_f<R, D, MODEL, ZIN>(P, j, xj, yn, zj);
+                } else {
+                    S += dt * model_f_y<R, D, MODEL>(P, yn, fx);
+                }
 #pragma unroll
                 for (int l = 0; l < D; ++l) { xj[l] = xn[l]; zj[l] = zn[l]; }
             });
         }
         S += model_g<R, D, MODEL>(P, xj);
         if constexpr (Stage<R, D>::value) {
-            const volatile float *st = &sm.stage[0][threadIdx.x];
+            const volatile float *st = &sm.tile[0][threadIdx.x];
+            if constexpr (!TILE) {
 #pragma unroll
-            for (int a = 1; a < p; ++a) phi[a] = (R)st[(a - 1) * MAX_THREADS];
+                for (int a = 1; a < p; ++a) phi[a] = (R)st[a * TS];
+            }
 #pragma unroll
-            for (int l = 0; l < D; ++l) dwi[l] = (R)st[(p - 1 + l) * MAX_THREADS];
+            for (int l = 0; l < D; ++l) dwi[l] = (R)st[(p + l) * TS];
         }
         // Z response uses S - CZ; the phase-A part of the Y response S - CZ - CI.
         R SZ = S, SY = S;
         if constexpr (CV) { SZ = S - CZ; SY = SZ - CI; }
         if constexpr (!ZIN) SY += fdt;
-        if constexpr (RS) {
+        if constexpr (TILE) {
+            // this path's columns (zeros past M_k), then the warp's dot products
+            float *col = &sm.tile[0][threadIdx.x];
+            col[0] = valid ? 1.0f : 0.0f;
+            if (!Stage<R, D>::value || !valid) {
+#pragma unroll
+                for (int a = 1; a < p; ++a) col[a * TS] = valid ? (float)phi[a] : 0.0f;
+            }
+#pragma unroll
+            for (int l = 0; l < q; ++l) col[(p + l) * TS] = valid ? (float)(SZ * dwi[l] * inv_dt) : 0.0f;
+            col[(p + q) * TS] = valid ? (float)SY : 0.0f;
+            __syncwarp();
+            const float *tb = &sm.tile[0][0];
+            float acc[LF];
+#pragma unroll
+            for (int t = 0; t < LF; ++t) acc[t] = 0.0f;
+#pragma unroll 8
+            for (int r = 0; r < 32; ++r)
+#pragma unroll
+                for (int t = 0; t < LF; ++t) acc[t] = fmaf(tb[colA[t] + r], tb[colB[t] + r], acc[t]);
+#pragma unroll
+            for (int t = 0; t < LF; ++t) csum[t] += (double)acc[t];
+            __syncwarp();
+        } else if constexpr (RS) {
             // this path's products (zero for lanes past M)
             const float Sv = valid ? (float)SZ : 0.0f;
             const float Sy = valid ? (float)SY : 0.0f;
@@ -800,7 +923,9 @@ __device__ __forceinline__ void solve_stratum(const Params &P, const int i, cons
             if (++since_flush == FLUSH) { mA.flush(lane); since_flush = 0; }
         }
     }
-    if constexpr (RS) {
+    if constexpr (TILE) {
+        block_totals<EA>(csum, redA, totA, lane, warp, nwarps);
+    } else if constexpr (RS) {
         block_totals_rs<EA>(mA.c, mA.base, mA.rend, redA, totA, warp, nwarps);
     } else {
         double lv[(EA + 31) / 32];
@@ -868,12 +993,19 @@ __device__ __forceinline__ void solve_stratum(const Params &P, const int i, cons
                 [[maybe_unused]] unsigned row1;
                 eval_at<R, D, LP1, MODEL, ZIN, false>(P, i + 1, x1, y1, z1, phi1, row1);
             }
+            {
+                // z_i(x_i) from the fresh Z fit; long coefficient vectors are read
+                // from shared memory at every path (volatile) rather than hoisted
+                // into registers for the whole loop
+                using BR = typename Select<(q * p > 24), const volatile R, const R>::type;
+                BR *br = beta_r;
 #pragma unroll
-            for (int l = 0; l < q; ++l) {
-                R w = beta_r[l * p];
+                for (int l = 0; l < q; ++l) {
+                    R w = br[l * p];
 #pragma unroll
-                for (int a = 1; a < p; ++a) w += beta_r[l * p + a] * phi[a];
-                zi[l] = clamp_r(w, Form<R>::Cz(P));
+                    for (int a = 1; a < p; ++a) w += br[l * p + a] * phi[a];
+                    zi[l] = clamp_r(w, Form<R>::Cz(P));
+                }
             }
             const R fi = model_f<R, D, MODEL, ZIN>(P, i, x, y1, zi);
             if (valid) {
@@ -1014,11 +1146,20 @@ cudaError_t launch_one(const Params &P, int i, int grid, int threads, cudaStream
     return cudaGetLastError();
 }
 
+// Units of d >= 9 carry the FP32 form without controls only (create rejects
+// the rest), which keeps their compile time and code size down.
+constexpr bool WIDE_UNIT = SRMC_STEP_D >= 9;
+
 template <typename R>
 cudaError_t launch_prec(const Params &P, int i, bool lp1, int mv, int grid, int threads,
                         cudaStream_t st)
 {
+    if constexpr (WIDE_UNIT && sizeof(R) == 8) {
+        return cudaErrorInvalidValue;
+    } else {
     if (P.C64 != nullptr || P.cv_own) { // control variate form (LP1 only)
+        if constexpr (WIDE_UNIT) return cudaErrorInvalidValue;
+        else {
         if (!lp1) return cudaErrorInvalidValue;
         switch (mv) {
         case MV_COS:      return launch_one<R, true, MODEL_COS, false, true>(P, i, grid, threads, st);
@@ -1026,6 +1167,7 @@ cudaError_t launch_prec(const Params &P, int i, bool lp1, int mv, int grid, int 
         case MV_LOGISTIC: return launch_one<R, true, MODEL_LOGISTIC, true, true>(P, i, grid, threads, st);
         }
         return cudaErrorInvalidValue;
+        }
     }
     switch (mv) {
     case MV_COS:      return lp1 ? launch_one<R, true, MODEL_COS, false>(P, i, grid, threads, st)
@@ -1038,11 +1180,12 @@ cudaError_t launch_prec(const Params &P, int i, bool lp1, int mv, int grid, int 
                                  : launch_one<R, false, MODEL_AFFINE, false>(P, i, grid, threads, st);
     }
     return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace
 
-#if SRMC_STEP_KIND == 0 && SRMC_STEP_DYN == 0 && SRMC_STEP_BASIS == 1
+#if SRMC_STEP_KIND == 0 && SRMC_STEP_DYN == 0 && SRMC_STEP_BASIS == 1 && SRMC_STEP_D <= 8
 namespace {
 struct BatchLauncher {
     const BatchRound &B; int grid, threads; cudaStream_t st;

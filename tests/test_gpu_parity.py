@@ -103,6 +103,43 @@ def test_other_dimensions(dev, orc, d, C, N, M, prec):
     _full_parity(dev, orc, w)
 
 
+@pytest.mark.parametrize("d,N,M", [(9, 3, 64), (10, 2, 48), (11, 3, 40)])
+@pytest.mark.parametrize("model", ["cos", "cos_z", "logistic", "logistic_lp0"])
+def test_wide_dimensions(dev, orc, d, N, M, model):
+    # d = 9..11 (the paper's d = 11 experiments of Sec. 5.2): FP32 form,
+    # 2^d strata; the cos model with and without z in its driver, and the
+    # paper's logistic model (driver sum z (y - (2 + d)/(2d))) with LP1 and LP0
+    if model.startswith("logistic"):
+        w = W.logistic_paper(d=d, N=N, C=2, M=M, basis="lp0" if model.endswith("lp0") else "lp1")
+    else:
+        w = W.cos_model(f"d{d}", d=d, N=N, C=2, a=2.0, M=M, s0=0.3, lam=0.2, kap=0.5,
+                        kapz=0.1 if model == "cos_z" else 0.0)
+    _full_parity(dev, orc, w)
+
+
+def test_wide_dimensions_limits(dev):
+    # d >= 9: FP32, equal-size strata, Euler dynamics, no controls
+    torch, srmc = dev
+    w = W.cos_model("d9", d=9, N=2, C=2, a=2.0, M=64, s0=0.3, lam=0.2, kap=0.5)
+    for bad in (w.replace(precision="fp64"), w.replace(strata="prob"),
+                w.replace(theta=[1.0] * 9, dynamics="exact"), w.replace(basis="lp2")):
+        with pytest.raises(srmc.SrmcError) as e:
+            srmc.Solver(bad)
+        assert e.value.status == 4
+    s = srmc.Solver(w)
+    for call in (s.srmc_set_own_control,
+                 lambda: s.srmc_set_control(np.zeros((w.N, w.K, w.d, w.d + 1)))):
+        with pytest.raises(srmc.SrmcError) as e:
+            call()
+        assert e.value.status == 4
+    with pytest.raises(srmc.SrmcError) as e:
+        srmc.Batch([s])
+    assert e.value.status == 4
+    with pytest.raises(srmc.SrmcError) as e:
+        srmc.Solver(W.cos_model("d12", d=12, N=2, C=2, a=2.0, M=64, s0=0.3, lam=0.2, kap=0.5))
+    assert e.value.status == 1
+
+
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_uneven_cells_in_morton_order(dev, orc, prec):
     # d = 3 and 4 with different cell counts per dimension (3, 7, 5 and
