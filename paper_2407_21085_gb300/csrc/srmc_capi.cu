@@ -532,6 +532,8 @@ srmc_status srmc_create(const srmc_problem *pr, const srmc_strata *sa, const srm
         P.A_f[l] = (float)P.A[l]; P.c_f[l] = (float)P.c[l];
         P.s1_f[l] = (float)P.s1[l]; P.s2_f[l] = (float)P.s2[l]; P.theta_f[l] = (float)th;
     }
+    P.unit_drift = 1;
+    for (int l = 0; l < d; ++l) P.unit_drift &= (P.A_f[l] == 1.0f && P.c_f[l] == 0.0f) ? 1 : 0;
     if (P.drift) {
         if (!(pr->params[3] != 0.0)) {
             delete s;

@@ -50,6 +50,7 @@ struct Params {
     double A[DMAX], c[DMAX], s1[DMAX], s2[DMAX], theta[DMAX];
     float A_f[DMAX], c_f[DMAX], s1_f[DMAX], s2_f[DMAX], theta_f[DMAX];
     int drift;                      // cos model: driver carries -(1/s0) b(x).z
+    int unit_drift;                 // A = 1 and c = 0 in every coordinate (FP32 copies)
     double inv_s0;
     float inv_s0_f;
     double T, dt, sdt, mu, sqrt_d;

@@ -121,14 +121,25 @@ __device__ __forceinline__ void advance(const Params &P, int j, const R (&x)[D],
 {
 #if SRMC_PAIRS_ON && !defined(SRMC_USER_DYNAMICS)
     if constexpr (sizeof(R) == 4) {
+        if (P.unit_drift) {
+            // A = 1, c = 0 in every coordinate (no drift): A x + c = x exactly
 #pragma unroll
-        for (int l = 0; l + 1 < D; l += 2) {
-            const float2 v = __ffma2_rn(make_float2(P.s1_f[l], P.s1_f[l + 1]), make_float2(dw[l], dw[l + 1]),
-                                        __ffma2_rn(make_float2(P.A_f[l], P.A_f[l + 1]),
-                                                   make_float2(x[l], x[l + 1]),
-                                                   make_float2(P.c_f[l], P.c_f[l + 1])));
-            xn[l] = v.x;
-            xn[l + 1] = v.y;
+            for (int l = 0; l + 1 < D; l += 2) {
+                const float2 v = __ffma2_rn(make_float2(P.s1_f[l], P.s1_f[l + 1]), make_float2(dw[l], dw[l + 1]),
+                                            make_float2(x[l], x[l + 1]));
+                xn[l] = v.x;
+                xn[l + 1] = v.y;
+            }
+        } else {
+#pragma unroll
+            for (int l = 0; l + 1 < D; l += 2) {
+                const float2 v = __ffma2_rn(make_float2(P.s1_f[l], P.s1_f[l + 1]), make_float2(dw[l], dw[l + 1]),
+                                            __ffma2_rn(make_float2(P.A_f[l], P.A_f[l + 1]),
+                                                       make_float2(x[l], x[l + 1]),
+                                                       make_float2(P.c_f[l], P.c_f[l + 1])));
+                xn[l] = v.x;
+                xn[l + 1] = v.y;
+            }
         }
         if constexpr ((D & 1) != 0) xn[D - 1] = next_coord<R, D>(P, j, D - 1, x, dw[D - 1], (R)0);
         return;
@@ -630,13 +641,14 @@ struct StepSmem {
     static constexpr int q = D;
     static constexpr int EG = LP1 ? p * (p + 1) / 2 : 0;
     static constexpr int EA = EG + q * p + p;
-    // Path columns (one per thread; rows padded by one word so that lanes
-    // reading different rows at one column hit different banks): [0] 1 or 0,
+    // Path columns (one per thread; rows padded by four words, so that rows
+    // stay 16-byte aligned for vector loads along a row and lanes reading
+    // different rows at one column fall in different banks): [0] 1 or 0,
     // [1, p) phi_a, [p, p + q) dW_l and later w_l, [p + q] S_Y.
     static constexpr bool COLS = Stage<R, D>::value || TileMoments<R, D, EA>::value;
     static constexpr int NT = COLS ? p + q + 1 : 1;
-    static constexpr int TS = COLS ? MAX_THREADS + 1 : 1;
-    float tile[NT][TS];
+    static constexpr int TS = COLS ? MAX_THREADS + 4 : 4;
+    __align__(16) float tile[NT][TS];
     static constexpr int EB = p;
     double redA[MAX_WARPS][EA];
     double totA[EA];
@@ -878,10 +890,17 @@ __device__ __forceinline__ void solve_stratum(const Params &P, const int i, cons
             float acc[LF];
 #pragma unroll
             for (int t = 0; t < LF; ++t) acc[t] = 0.0f;
-#pragma unroll 8
-            for (int r = 0; r < 32; ++r)
+#pragma unroll 1
+            for (int r = 0; r < 32; r += 4)
 #pragma unroll
-                for (int t = 0; t < LF; ++t) acc[t] = fmaf(tb[colA[t] + r], tb[colB[t] + r], acc[t]);
+                for (int t = 0; t < LF; ++t) {
+                    const float4 a4 = *reinterpret_cast<const float4 *>(tb + colA[t] + r);
+                    const float4 b4 = *reinterpret_cast<const float4 *>(tb + colB[t] + r);
+                    acc[t] = fmaf(a4.x, b4.x, acc[t]);
+                    acc[t] = fmaf(a4.y, b4.y, acc[t]);
+                    acc[t] = fmaf(a4.z, b4.z, acc[t]);
+                    acc[t] = fmaf(a4.w, b4.w, acc[t]);
+                }
 #pragma unroll
             for (int t = 0; t < LF; ++t) csum[t] += (double)acc[t];
             __syncwarp();
