@@ -130,7 +130,8 @@ def workload(name: str) -> W.Workload:
               "cfg3_M2048": lambda: W.cfg3(M=2048, name="cfg3_d4_K20736_N50_M2048"),
               "cfg5_M512": lambda: W.cfg5(M=512, name="cfg5_d6_K262144_N40_M512"),
               # same cell width as cfg5 (0.75) on a smaller box, for profiler captures
-              "cfg5_small_M512": lambda: W.cfg5(M=512, C=5, a=1.875, name="cfg5small_d6_K15625_N40_M512")}
+              "cfg5_small_M512": lambda: W.cfg5(M=512, C=5, a=1.875, name="cfg5small_d6_K15625_N40_M512"),
+              "cfg5_small": lambda: W.cfg5(C=5, a=1.875, name="cfg5small_d6_K15625_N40_M4096")}
     return makers[name]()
 
 
