@@ -609,6 +609,12 @@ def batched_compare(args, stream):
 
     t_batch = timed(lambda: batch.srmc_batch_solve(stream), args.batch_reps)
     mode = batch.srmc_batch_mode()
+    # both strategies with the tuned block sizes, for the record
+    t_mode = {}
+    for m, name in ((0, "rounds"), (1, "branches")):
+        batch.srmc_batch_set_mode(m)
+        t_mode[name] = timed(lambda: batch.srmc_batch_solve(stream), 1)
+    batch.srmc_batch_set_mode(mode)
 
     def sequential():
         for s in solvers:
@@ -621,6 +627,7 @@ def batched_compare(args, stream):
             "batched_s": t_batch, "batched_path_steps_per_s": units / t_batch,
             "sequential_s": t_seq, "sequential_path_steps_per_s": units / t_seq,
             "speedup": t_seq / t_batch, "tuned_threads_per_group": threads, "tune_s": tune_s,
+            "strategy_s": t_mode,
             "strategy": ["rounds of multi-instance launches", "one graph branch per instance"][mode]}
 
 

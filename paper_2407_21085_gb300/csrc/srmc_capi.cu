@@ -79,7 +79,6 @@ double logistic_quantile(double num, double den, double mu) { return std::log(nu
 
 // Halves per component of a binary16 control row: 4 (one 8-byte load) for
 // p <= 4, else p rounded up to 8 (16-byte loads).
-int half_pad(int p) { return p <= 4 ? 4 : pad_to(p, 8); }
 
 // Stratum locality order: the strata sorted by the Morton code of their
 // cell coordinates (coordinate bits interleaved from the most significant
@@ -428,7 +427,7 @@ srmc_status srmc_create(const srmc_problem *pr, const srmc_strata *sa, const srm
     }
     {
         const int p_ = basis_dim(cf->basis, d);
-        const long long rmax = (long long)q * std::max(pad_to(p_, 4), half_pad(p_));
+        const long long rmax = std::max((long long)q * pad_to(p_, 4), (long long)pad_to(p_ * ((q + 1) / 2 * 2), 8));
         if ((long long)pr->N * K * rmax >= 4294967296LL)
             return fail(SRMC_ERR_UNSUPPORTED, "table too large: N K row-length must be < 2^32");
     }
@@ -496,7 +495,7 @@ srmc_status srmc_create(const srmc_problem *pr, const srmc_strata *sa, const srm
     // The step kernels take these paddings as constants of their basis dimension (row_pad).
     P.ry32 = pad_to(p, 4); P.rz32 = pad_to(q * p, 4);
     P.ry64 = pad_to(p, 2); P.rz64 = pad_to(q * p, 2);
-    P.ph = half_pad(p); P.rc16 = q * P.ph;
+    P.ph = (q + 1) / 2 * 2; P.rc16 = pad_to(p * P.ph, 8);
     int stride = 1;
     int off = 0;
     P.kind = prob ? 1 : 0;
@@ -953,7 +952,7 @@ __global__ void repack_control_kernel(const Params P, const double *src, double 
         for (int a = 0; a < qp; ++a) {
             const double v = src[r * qp + a];
             c64[r * P.rz64 + a] = v;
-            c16[r * P.rc16 + (a / P.p) * P.ph + a % P.p] = __double2half(fmin(fmax(v, -65504.0), 65504.0));
+            c16[r * P.rc16 + srmc::c16_index(P, a / P.p, a % P.p)] = __double2half(fmin(fmax(v, -65504.0), 65504.0));
         }
     }
 }

@@ -72,8 +72,9 @@ struct Params {
     const float *stepc_f;
     float *Y32, *Z32;               // [N][K][ry32], [N][K][rz32]; N K r < 2^32
     double *Y64, *Z64;              // [N][K][ry64], [N][K][rz64]
-    const __half *C16;              // control rows of the FP32 form in binary16: [N][K][q][ph],
-    int ph, rc16;                   // ph = 4 (p <= 4) or p padded to 8; rc16 = q ph
+    const __half *C16;              // control rows of the FP32 form in binary16, coefficient-major:
+    int ph, rc16;                   // half (r, a, l) at r rc16 + a ph + l; ph = q rounded up to even,
+                                    // rc16 = p ph rounded up to 8 (16-byte rows)
     const double *C64;              // control rows [N][K][rz64]
     unsigned long long *stats;      // [0] LP1->LP0 fallbacks, [1] non-finite rows
     const unsigned *order;          // [K] stratum solved by work item t (NULL: t itself)
@@ -211,9 +212,9 @@ __device__ __forceinline__ double normal_of(unsigned w, double)
 // approximated by degree-9 polynomials in (w - 5/2) for w < 5 and in
 // (sqrt(w) - c) for w >= 5, with coefficients fitted by this project
 // (weighted least squares towards minimax relative error against an FP64
-// Phi^{-1}; max relative error 6e-9 and 9e-8 on the two pieces).  y is
-// formed from the integer complement so that it keeps full relative
-// precision next to p = 1/2.
+// Phi^{-1}; max relative error 6e-9 and 9e-8 on the two pieces).  p is
+// formed from the smaller of w and ~w (p <= 1/2), so 1 - p and 4 p (1 - p)
+// keep full precision in the tails; the sign is that of w's upper half.
 // Coefficients of h, highest degree first: central piece (in w - 5/2) and
 // tail piece (in sqrt(w) - 3.435767889).
 __device__ constexpr float NRM_C[10] = {
@@ -240,12 +241,23 @@ __device__ __forceinline__ float normal_h(float wv)
     return h;
 }
 
+// With SRMC_NORMAL_EXACT_Y, y = 2p - 1 comes from the integer complement
+// 2^31 - 1 - v (full relative precision next to p = 1/2, at the price of a
+// second conversion); otherwise from the float p itself, exact to 2^-24
+// absolute -- the effect of rounding U to float, <= 8e-8 in xi next to 0.
+#ifndef SRMC_NORMAL_EXACT_Y
+#define SRMC_NORMAL_EXACT_Y 0
+#endif
 __device__ __forceinline__ float normal_of(unsigned w, float)
 {
     const bool up = w >= 0x80000000u;
     const unsigned v = up ? ~w : w;                                     // p <= 1/2
     const float p = fmaf(__uint2float_rn(v), 0x1p-32f, 0x1p-33f);
+#if SRMC_NORMAL_EXACT_Y
     const float y = fmaf(__uint2float_rn(0x7FFFFFFFu - v), -0x1p-31f, -0x1p-32f);   // 2p - 1
+#else
+    const float y = fmaf(p, 2.0f, -1.0f);                                           // 2p - 1
+#endif
     const float wv = -__logf(4.0f * (p * (1.0f - p)));
     const float x = y * normal_h(wv);
     return up ? -x : x;
@@ -267,9 +279,13 @@ __device__ __forceinline__ float2 normal_pair(unsigned w0, unsigned w1)
     const unsigned v0 = up0 ? ~w0 : w0, v1 = up1 ? ~w1 : w1;
     const float2 p = __ffma2_rn(make_float2(__uint2float_rn(v0), __uint2float_rn(v1)),
                                 f2(0x1p-32f), f2(0x1p-33f));
+#if SRMC_NORMAL_EXACT_Y
     const float2 y = __ffma2_rn(make_float2(__uint2float_rn(0x7FFFFFFFu - v0),
                                             __uint2float_rn(0x7FFFFFFFu - v1)),
                                 f2(-0x1p-31f), f2(-0x1p-32f));
+#else
+    const float2 y = __ffma2_rn(p, f2(2.0f), f2(-1.0f));
+#endif
     const float2 r = __fmul2_rn(f2(4.0f), __fmul2_rn(p, __ffma2_rn(p, f2(-1.0f), f2(1.0f))));
     const float2 wv = make_float2(-__logf(r.x), -__logf(r.y));
     float2 h;
@@ -575,6 +591,9 @@ __device__ __forceinline__ R model_f(const Params &P, int j, const R (&x)[D], R 
         return model_f_y<R, D, MODEL>(P, y, model_f_x<R, D, MODEL>(P, j, x));
     }
 }
+
+// Index of coefficient c of component l in a binary16 control row.
+__host__ __device__ __forceinline__ int c16_index(const Params &P, int l, int c) { return c * P.ph + l; }
 
 // ---- table rows ----------------------------------------------------------
 template <int PP>

@@ -529,7 +529,7 @@ __global__ void __launch_bounds__(WARPS * 32) mlp_tabulate_kernel(Net net, const
             else v = (double)GAs[warp][1 + 2 * (c - 1)][1 + l] - (double)GAs[warp][2 + 2 * (c - 1)][1 + l];
             v *= P.sig[l];
             c64[row * P.rz64 + a] = v;
-            c16[row * P.rc16 + l * P.ph + c] = __double2half(fmin(fmax(v, -65504.0), 65504.0));
+            c16[row * P.rc16 + srmc::c16_index(P, l, c)] = __double2half(fmin(fmax(v, -65504.0), 65504.0));
         }
         __syncwarp();
     }

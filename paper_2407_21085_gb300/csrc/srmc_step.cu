@@ -516,13 +516,6 @@ __device__ __forceinline__ void eval_at(const Params &P, int j, const R (&x)[D],
     }
 }
 
-// The two binary16 values packed in u (low half first), widened to FP32.
-__device__ __forceinline__ void widen_h2(unsigned u, float &lo, float &hi)
-{
-    lo = __half2float(__ushort_as_half((unsigned short)(u & 0xFFFFu)));
-    hi = __half2float(__ushort_as_half((unsigned short)(u >> 16)));
-}
-
 // zc(x) . dw for the control row `row` and the basis values phi of x:
 // sum_l T_Cz(beta_l . phi) dw_l (the martingale control of one increment).
 template <typename R, int D, int p>
@@ -531,30 +524,41 @@ __device__ __forceinline__ R control_dot(const Params &P, unsigned row, const R 
 {
     R acc = (R)0;
     if constexpr (sizeof(R) == 4) {
-        // FP32 form: binary16 rows, component l holding PH halves (4 for
-        // p <= 4: one 8-byte load; else p rounded up to 8: 16-byte loads),
-        // widened to FP32 for the arithmetic.
-        constexpr int PH = p <= 4 ? 4 : (p + 7) / 8 * 8;
-        const unsigned *b = reinterpret_cast<const unsigned *>(P.C16) + row * (unsigned)(D * PH / 2);
+        // FP32 form: binary16 rows, coefficient-major (the halves of a 32-bit
+        // word are coefficient a of components 2m and 2m + 1, c16_index), read
+        // in 16-byte vectors and folded in as they arrive: each word widens to
+        // an FP32 pair that enters both components' dot products with one
+        // packed FMA; the order of the terms of each component is that of the
+        // scalar form (constant first, then a = 1 .. p - 1).
+        constexpr int QH = (D + 1) / 2;                  // component pairs
+        constexpr int NWD = p * QH;                      // 32-bit words of a row in use
+        constexpr int RCW = (2 * NWD + 7) / 8 * 4;       // 32-bit words per row (16-byte rows)
+        const uint4 *b4 = reinterpret_cast<const uint4 *>(reinterpret_cast<const unsigned *>(P.C16) +
+                                                          row * (unsigned)RCW);
+        float2 w2[QH];
 #pragma unroll
-        for (int l = 0; l < D; ++l) {
-            float c[PH];
-            if constexpr (PH == 4) {
-                const uint2 t = __ldg(reinterpret_cast<const uint2 *>(b + l * 2));
-                widen_h2(t.x, c[0], c[1]); widen_h2(t.y, c[2], c[3]);
-            } else {
+        for (int v = 0; v < (NWD + 3) / 4; ++v) {
+            const uint4 t = __ldg(b4 + v);
+            const unsigned tw[4] = {t.x, t.y, t.z, t.w};
 #pragma unroll
-                for (int v = 0; v < PH / 8; ++v) {
-                    const uint4 t = __ldg(reinterpret_cast<const uint4 *>(b + l * (PH / 2)) + v);
-                    widen_h2(t.x, c[8 * v], c[8 * v + 1]); widen_h2(t.y, c[8 * v + 2], c[8 * v + 3]);
-                    widen_h2(t.z, c[8 * v + 4], c[8 * v + 5]); widen_h2(t.w, c[8 * v + 6], c[8 * v + 7]);
+            for (int u = 0; u < 4; ++u) {
+                const int e = 4 * v + u;
+                if (e < NWD) {
+                    const int a = e / QH, m = e % QH;
+                    const float2 c = __half22float2(*reinterpret_cast<const __half2 *>(&tw[u]));
+                    w2[m] = a == 0 ? c : __ffma2_rn(c, make_float2(phi[a], phi[a]), w2[m]);
                 }
             }
-            float w = c[0];
-#pragma unroll
-            for (int a = 1; a < p; ++a) w += c[a] * phi[a];
-            acc += clamp_r(w, Form<R>::Cz(P)) * dw[l];
         }
+        const float L = Form<R>::Cz(P);
+        float2 s2 = make_float2(0.0f, 0.0f);
+#pragma unroll
+        for (int m = 0; m < QH; ++m) {
+            const float2 z2 = make_float2(clamp_r(w2[m].x, L), clamp_r(w2[m].y, L));
+            const float2 d2 = make_float2(dw[2 * m], 2 * m + 1 < D ? dw[2 * m + 1] : 0.0f);
+            s2 = __ffma2_rn(z2, d2, s2);
+        }
+        acc = s2.x + s2.y;
     } else {
         const double *b = P.C64 + row * (unsigned)P.rz64;
 #pragma unroll

@@ -1,10 +1,12 @@
 """The batched form (many instances per launch) through the C ABI: every
-instance's tables must equal those of its own single-instance solve."""
+instance's tables must equal those of its own single-instance solve, and
+every instance must match the FP64 oracle (teacher-forced steps)."""
 import numpy as np
 import pytest
 
 from paper_2407_21085_gb300 import workloads as W
 from tests import controls as CT
+from tests import teacher as T
 
 pytestmark = pytest.mark.gpu
 
@@ -55,6 +57,40 @@ def test_batch_equals_single_solves(dev, mode):
     for a, s in enumerate(solvers):
         y, z = _tables(torch, s)
         assert np.array_equal(y, single[a][0]) and np.array_equal(z, single[a][1]), ws[a].name
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_batch_instances_against_the_oracle(dev, orc, mode):
+    # every batched instance against the FP64 oracle directly: teacher-forced
+    # steps 0, N/2 and N-1 on up to 48 sampled strata each, at centres and
+    # off-centre points, within the FP32 bound 1e-4 (1 + |v|)
+    torch, srmc = dev
+    ws = _instances()
+    solvers = [srmc.Solver(w, block_threads=256) for w in ws]
+    b = srmc.Batch(solvers)
+    b.srmc_batch_set_mode(mode)
+    b.srmc_batch_solve()
+    torch.cuda.synchronize()
+    for w, s in zip(ws, solvers):
+        res = T.teacher_forced(torch, orc, s, [0, w.N // 2, w.N - 1], 48)
+        T.assert_within(w, res, where=f"batched mode {mode}")
+
+
+def test_full_size_batch_instances_against_the_oracle(dev, orc):
+    # the first 32 instances of the 256-instance batched workload at full
+    # size, solved together; the largest instance of each dimension checked
+    # against the oracle by teacher forcing (steps 0, N/2, N-1; 32 strata)
+    torch, srmc = dev
+    ws = W.cfg4_instances()[:32]
+    solvers = [srmc.Solver(w) for w in ws]
+    b = srmc.Batch(solvers)
+    b.srmc_batch_solve()
+    torch.cuda.synchronize()
+    for d in (1, 2, 3):
+        a = max((r for r in range(len(ws)) if ws[r].d == d), key=lambda r: ws[r].path_steps())
+        res = T.teacher_forced(torch, orc, solvers[a], [0, ws[a].N // 2, ws[a].N - 1], 32)
+        print(ws[a].name, ws[a].d, ws[a].K, ws[a].N, ws[a].M, res)
+        T.assert_within(ws[a], res, where="full-size batch")
 
 
 def test_tuned_batch_matches_within_rounding(dev):
