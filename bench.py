@@ -581,8 +581,9 @@ def paper_table(args, stream):
 # ---- the batched form: 256 heterogeneous instances ---------------------------------
 def batched_compare(args, stream):
     """cfg4: 256 seeded instances (d in {1,2,3}, 16..64 cells per dimension,
-    N in {10,20,40}, M in {1024,4096}) solved by the tuned batched form (one
-    graph of per-round, per-variant persistent launches) and, for comparison,
+    N in {10,20,40}, M in {1024,4096}) solved by the tuned batched form (the
+    fastest of: per-round multi-instance launches, one graph branch per
+    instance, one persistent launch per kernel variant) and, for comparison,
     one after another by single-instance solves on the same stream.  Device
     time by CUDA events on the stream, after one untimed pass of each."""
     import torch
@@ -611,7 +612,7 @@ def batched_compare(args, stream):
     mode = batch.srmc_batch_mode()
     # both strategies with the tuned block sizes, for the record
     t_mode = {}
-    for m, name in ((0, "rounds"), (1, "branches")):
+    for m, name in ((0, "rounds"), (1, "branches"), (2, "persistent")):
         batch.srmc_batch_set_mode(m)
         t_mode[name] = timed(lambda: batch.srmc_batch_solve(stream), 1)
     batch.srmc_batch_set_mode(mode)
@@ -628,7 +629,8 @@ def batched_compare(args, stream):
             "sequential_s": t_seq, "sequential_path_steps_per_s": units / t_seq,
             "speedup": t_seq / t_batch, "tuned_threads_per_group": threads, "tune_s": tune_s,
             "strategy_s": t_mode,
-            "strategy": ["rounds of multi-instance launches", "one graph branch per instance"][mode]}
+            "strategy": ["rounds of multi-instance launches", "one graph branch per instance",
+                         "one persistent launch per kernel variant"][mode]}
 
 
 # ---- the CPU oracle (cpu_baseline leg and the reference arm) -------------------

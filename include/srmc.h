@@ -357,8 +357,8 @@ void srmc_batch_destroy(srmc_batch *b);
 /* Pick, for every kernel variant of the batch, the threads per stratum block
  * (64, 128 or 256: 2, 4 or 8 warps per stratum) and the blocks per SM of the
  * persistent grid by timing candidate launches of its first rounds on stream,
- * give every solver of the group that block size, then time both strategies
- * (see srmc_batch_mode) on the whole batch and keep the faster (the tables of
+ * give every solver of the group that block size, then time the three strategies
+ * (see srmc_batch_mode) on the whole batch and keep the fastest (the tables of
  * the solvers are overwritten; solve afterwards).  Optional: an untuned batch
  * uses 256 threads, the occupancy limit and the rounds strategy.  out_threads
  * (may be NULL) receives the chosen threads per variant group, in group order,
@@ -368,12 +368,22 @@ srmc_status srmc_batch_tune(srmc_batch *b, void *stream, int *out_threads, int m
 srmc_status srmc_batch_solve(srmc_batch *b, void *stream);
 
 /* Strategy in use: 0 = rounds of multi-instance launches, 1 = one graph
- * branch per instance (concurrent single-instance launches).  An untuned
- * batch uses 0; srmc_batch_tune keeps the faster of the two. */
+ * branch per instance (concurrent single-instance launches), 2 = one
+ * persistent launch per kernel variant over all rounds: blocks take
+ * (instance, step, stratum) items in round order from a device counter and
+ * each item waits only for the previous step of its own instance (bounded
+ * waits; see srmc_batch_stats).  An untuned batch uses 0; srmc_batch_tune
+ * keeps the fastest. */
 int srmc_batch_mode(const srmc_batch *b);
 
-/* Force a strategy (0 or 1; SRMC_ERR_INVALID_ARG otherwise). */
+/* Force a strategy (0, 1 or 2; SRMC_ERR_INVALID_ARG otherwise). */
 srmc_status srmc_batch_set_mode(srmc_batch *b, int mode);
+
+/* Synchronise the device and report in *timeouts whether a wait of the
+ * persistent strategy (2) ran past its iteration limit (about a second)
+ * since the batch was created: then the tables of that solve are not valid.
+ * 0 in normal operation. */
+srmc_status srmc_batch_stats(srmc_batch *b, unsigned long long *timeouts);
 
 /* Error of the fitted functions against the closed-form solution of the
  * model at the K stratum centres, for every step i = 0..N-1 (the metric of

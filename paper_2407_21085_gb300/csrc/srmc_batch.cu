@@ -10,6 +10,11 @@
 //             (parameters in the constant bank) on its own branch of the
 //             graph, so the launch chains of different instances run
 //             concurrently and small instances fill the GPU together.
+//   FLOW      one persistent launch per variant group over all of its rounds
+//             (step_kernel_flow): blocks take (instance, step, stratum) items
+//             in round order from a counter and wait, item by item, only for
+//             the previous step of their own instance; the groups' launches
+//             run on parallel branches of the graph.
 // The tuner picks, per variant group, the threads per stratum block (and the
 // blocks per SM for ROUNDS) by timing, then times both strategies on the
 // whole batch and keeps the faster.
@@ -38,6 +43,30 @@ srmc_status bfail(srmc_status st, const std::string &m)
 
 using LaunchFn = cudaError_t (*)(const srmc::BatchRound &, bool, bool, int, bool, int, int, cudaStream_t);
 using OccFn = int (*)(bool, bool, int, bool, int);
+using FlowFn = cudaError_t (*)(const srmc::FlowPlan &, bool, int, bool, int, int, cudaStream_t);
+using FlowOccFn = int (*)(bool, int, bool, int);
+
+FlowFn flow_for(int d)
+{
+    switch (d) {
+    case 1: return srmc::launch_flow_d1; case 2: return srmc::launch_flow_d2;
+    case 3: return srmc::launch_flow_d3; case 4: return srmc::launch_flow_d4;
+    case 5: return srmc::launch_flow_d5; case 6: return srmc::launch_flow_d6;
+    case 7: return srmc::launch_flow_d7; case 8: return srmc::launch_flow_d8;
+    }
+    return nullptr;
+}
+
+FlowOccFn flow_occ_for(int d)
+{
+    switch (d) {
+    case 1: return srmc::occupancy_flow_d1; case 2: return srmc::occupancy_flow_d2;
+    case 3: return srmc::occupancy_flow_d3; case 4: return srmc::occupancy_flow_d4;
+    case 5: return srmc::occupancy_flow_d5; case 6: return srmc::occupancy_flow_d6;
+    case 7: return srmc::occupancy_flow_d7; case 8: return srmc::occupancy_flow_d8;
+    }
+    return nullptr;
+}
 
 LaunchFn launch_for(int d)
 {
@@ -76,11 +105,17 @@ struct Group {
     std::vector<Round> rounds;
     int threads = 256;
     int blocks_per_sm = 0;      // 0: occupancy limit
+    // FLOW: the group's segments (round order) on the device
+    int n_seg = 0;
+    long long flow_total = 0;
+    int *f_inst = nullptr, *f_step = nullptr, *f_dep = nullptr;
+    long long *f_kofs = nullptr;
+    unsigned long long *f_done = nullptr;   // [n_seg + 1]: done counters, then the work counter
 };
 
 }  // namespace
 
-enum { MODE_ROUNDS = 0, MODE_BRANCHES = 1 };
+enum { MODE_ROUNDS = 0, MODE_BRANCHES = 1, MODE_FLOW = 2 };
 constexpr int kBranchStreams = 64;
 
 struct srmc_batch {
@@ -92,6 +127,7 @@ struct srmc_batch {
     Params *d_params = nullptr;
     int *d_ints = nullptr;
     long long *d_kofs = nullptr;
+    unsigned *d_error = nullptr;        // FLOW: set when a wait gave up
     int sms = 0;
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t graph = nullptr;
@@ -101,6 +137,10 @@ namespace {
 
 void batch_free(srmc_batch *b)
 {
+    for (auto &g : b->groups) {
+        cudaFree(g.f_inst); cudaFree(g.f_step); cudaFree(g.f_dep); cudaFree(g.f_kofs); cudaFree(g.f_done);
+    }
+    cudaFree(b->d_error);
     for (auto st : b->branch) cudaStreamDestroy(st);
     for (auto e : b->ev) cudaEventDestroy(e);
     if (b->graph) cudaGraphExecDestroy(b->graph);
@@ -136,7 +176,7 @@ cudaError_t launch_round(const srmc_batch *b, const Group &g, const Round &r, in
 // BRANCHES: fork onto kBranchStreams streams, instances dealt out in
 // decreasing order of work (longest first), each stream's instances one
 // after the other, then join.
-cudaError_t enqueue_branches(srmc_batch *b, cudaStream_t st)
+cudaError_t ensure_streams(srmc_batch *b)
 {
     cudaError_t e = cudaSuccess;
     if (b->branch.empty()) {
@@ -150,8 +190,14 @@ cudaError_t enqueue_branches(srmc_batch *b, cudaStream_t st)
             e = cudaEventCreateWithFlags(&x, cudaEventDisableTiming);
             if (e == cudaSuccess) b->ev.push_back(x);
         }
-        if (e != cudaSuccess) return e;
     }
+    return e;
+}
+
+cudaError_t enqueue_branches(srmc_batch *b, cudaStream_t st)
+{
+    cudaError_t e = ensure_streams(b);
+    if (e != cudaSuccess) return e;
     std::vector<int> order(b->solvers.size());
     for (size_t r = 0; r < order.size(); ++r) order[r] = (int)r;
     auto work = [&](int r) {
@@ -170,6 +216,85 @@ cudaError_t enqueue_branches(srmc_batch *b, cudaStream_t st)
             if ((e = srmc_launch_solver_step(s, i, x)) != cudaSuccess) return e;
     }
     for (int a = 0; a < ns; ++a) {
+        if ((e = cudaEventRecord(b->ev[a], b->branch[a])) != cudaSuccess) return e;
+        if ((e = cudaStreamWaitEvent(st, b->ev[a], 0)) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// FLOW: the group segments in round order (built on first use), then per
+// group a cleared counter block and one persistent launch, the groups on
+// parallel branches of the graph.
+cudaError_t ensure_streams(srmc_batch *b);
+
+cudaError_t build_flow(srmc_batch *b)
+{
+    cudaError_t e = cudaSuccess;
+    if (!b->d_error) {
+        if ((e = cudaMalloc(&b->d_error, sizeof(unsigned))) != cudaSuccess) return e;
+        if ((e = cudaMemset(b->d_error, 0, sizeof(unsigned))) != cudaSuccess) return e;
+    }
+    for (auto &g : b->groups) {
+        if (g.f_inst) continue;
+        std::vector<int> inst, step, dep;
+        std::vector<long long> kofs(1, 0);
+        std::vector<int> last(b->solvers.size(), -1);     // segment of each instance in the previous round
+        int smax = 0;
+        for (int r : g.members) smax = std::max(smax, b->solvers[r]->P.N);
+        for (int s = 0; s < smax; ++s)
+            for (int r : g.members) {
+                const Params &P = b->solvers[r]->P;
+                if (P.N <= s) continue;
+                inst.push_back(r);
+                step.push_back(P.N - 1 - s);
+                dep.push_back(last[r]);
+                last[r] = (int)inst.size() - 1;
+                kofs.push_back(kofs.back() + P.K);
+            }
+        g.n_seg = (int)inst.size();
+        g.flow_total = kofs.back();
+        const size_t n = (size_t)g.n_seg;
+        if ((e = cudaMalloc(&g.f_inst, sizeof(int) * n)) != cudaSuccess) return e;
+        if ((e = cudaMalloc(&g.f_step, sizeof(int) * n)) != cudaSuccess) return e;
+        if ((e = cudaMalloc(&g.f_dep, sizeof(int) * n)) != cudaSuccess) return e;
+        if ((e = cudaMalloc(&g.f_kofs, sizeof(long long) * (n + 1))) != cudaSuccess) return e;
+        if ((e = cudaMalloc(&g.f_done, sizeof(unsigned long long) * (n + 1))) != cudaSuccess) return e;
+        if ((e = cudaMemcpy(g.f_inst, inst.data(), sizeof(int) * n, cudaMemcpyHostToDevice)) != cudaSuccess) return e;
+        if ((e = cudaMemcpy(g.f_step, step.data(), sizeof(int) * n, cudaMemcpyHostToDevice)) != cudaSuccess) return e;
+        if ((e = cudaMemcpy(g.f_dep, dep.data(), sizeof(int) * n, cudaMemcpyHostToDevice)) != cudaSuccess) return e;
+        if ((e = cudaMemcpy(g.f_kofs, kofs.data(), sizeof(long long) * (n + 1), cudaMemcpyHostToDevice)) != cudaSuccess)
+            return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t enqueue_flow(srmc_batch *b, cudaStream_t st)
+{
+    cudaError_t e = build_flow(b);
+    if (e != cudaSuccess) return e;
+    if ((e = ensure_streams(b)) != cudaSuccess) return e;
+    const int ng = (int)std::min(b->groups.size(), b->branch.size());
+    if ((e = cudaEventRecord(b->ev[kBranchStreams], st)) != cudaSuccess) return e;
+    for (int a = 0; a < ng; ++a)
+        if ((e = cudaStreamWaitEvent(b->branch[a], b->ev[kBranchStreams], 0)) != cudaSuccess) return e;
+    for (size_t q = 0; q < b->groups.size(); ++q) {
+        const Group &g = b->groups[q];
+        cudaStream_t x = b->branch[q % ng];
+        if ((e = cudaMemsetAsync(g.f_done, 0, sizeof(unsigned long long) * (g.n_seg + 1), x)) != cudaSuccess)
+            return e;
+        srmc::FlowPlan F;
+        F.params = b->d_params;
+        F.inst = g.f_inst; F.step = g.f_step; F.kofs = g.f_kofs; F.dep = g.f_dep;
+        F.done = g.f_done; F.next = g.f_done + g.n_seg; F.error = b->d_error;
+        F.n_seg = g.n_seg; F.total = g.flow_total;
+        const int occ = flow_occ_for(g.d)(g.lp1, g.mv, g.cv, g.threads);
+        if (occ <= 0) return cudaErrorInvalidConfiguration;
+        const int bps = (g.blocks_per_sm > 0 && g.blocks_per_sm < occ) ? g.blocks_per_sm : occ;
+        long long grid = (long long)b->sms * bps;
+        if (grid > g.flow_total) grid = g.flow_total;
+        if ((e = flow_for(g.d)(F, g.lp1, g.mv, g.cv, (int)grid, g.threads, x)) != cudaSuccess) return e;
+    }
+    for (int a = 0; a < ng; ++a) {
         if ((e = cudaEventRecord(b->ev[a], b->branch[a])) != cudaSuccess) return e;
         if ((e = cudaStreamWaitEvent(st, b->ev[a], 0)) != cudaSuccess) return e;
     }
@@ -351,8 +476,8 @@ srmc_status srmc_batch_tune(srmc_batch *b, void *stream, int *out_threads, int m
                 if (s->graph) { cudaGraphExecDestroy(s->graph); s->graph = nullptr; }
             }
         }
-    float tm[2] = {0.0f, 0.0f};
-    for (int mode = 0; mode < 2; ++mode) {
+    float tm[3] = {0.0f, 0.0f, 0.0f};
+    for (int mode = 0; mode < 3; ++mode) {
         b->mode = mode;
         if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
         srmc_status ss = ensure_graph(b);          // capture outside the timed pass
@@ -363,7 +488,9 @@ srmc_status srmc_batch_tune(srmc_batch *b, void *stream, int *out_threads, int m
         BATCH_CUDA(cudaEventSynchronize(e1), "event sync");
         cudaEventElapsedTime(&tm[mode], e0, e1);
     }
-    b->mode = tm[1] < tm[0] ? MODE_BRANCHES : MODE_ROUNDS;
+    b->mode = MODE_ROUNDS;
+    for (int mode = 1; mode < 3; ++mode)
+        if (tm[mode] < tm[b->mode]) b->mode = mode;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
@@ -375,9 +502,19 @@ srmc_status srmc_batch_tune(srmc_batch *b, void *stream, int *out_threads, int m
 
 int srmc_batch_mode(const srmc_batch *b) { return b ? b->mode : -1; }
 
+srmc_status srmc_batch_stats(srmc_batch *b, unsigned long long *timeouts)
+{
+    if (!b || !timeouts) return bfail(SRMC_ERR_INVALID_ARG, "srmc_batch_stats: NULL argument");
+    unsigned e = 0;
+    BATCH_CUDA(cudaDeviceSynchronize(), "srmc_batch_stats: synchronize");
+    if (b->d_error) BATCH_CUDA(cudaMemcpy(&e, b->d_error, sizeof(unsigned), cudaMemcpyDeviceToHost), "srmc_batch_stats");
+    *timeouts = e;
+    return SRMC_OK;
+}
+
 srmc_status srmc_batch_set_mode(srmc_batch *b, int mode)
 {
-    if (!b || (mode != MODE_ROUNDS && mode != MODE_BRANCHES))
+    if (!b || (mode != MODE_ROUNDS && mode != MODE_BRANCHES && mode != MODE_FLOW))
         return bfail(SRMC_ERR_INVALID_ARG, "srmc_batch_set_mode: bad argument");
     if (b->mode != mode && b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
     b->mode = mode;
@@ -403,10 +540,14 @@ srmc_status ensure_graph(srmc_batch *b)
     if (!b->graph) {
         if (!b->cap_stream)
             BATCH_CUDA(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking), "graph stream");
+        // allocations and copies of the FLOW plan happen before the capture
+        if (b->mode != MODE_ROUNDS) BATCH_CUDA(ensure_streams(b), "batch streams");
+        if (b->mode == MODE_FLOW) BATCH_CUDA(build_flow(b), "batch flow plan");
         cudaGraph_t g = nullptr;
         BATCH_CUDA(cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
         cudaError_t le = b->mode == MODE_ROUNDS ? enqueue_all(b, b->cap_stream)
-                                                : enqueue_branches(b, b->cap_stream);
+                         : b->mode == MODE_BRANCHES ? enqueue_branches(b, b->cap_stream)
+                                                    : enqueue_flow(b, b->cap_stream);
         cudaError_t ce = cudaStreamEndCapture(b->cap_stream, &g);
         if (le != cudaSuccess) { if (g) cudaGraphDestroy(g); return bfail(SRMC_ERR_CUDA, std::string("batch capture: ") + cudaGetErrorString(le)); }
         if (ce != cudaSuccess) return bfail(SRMC_ERR_CUDA, std::string("end capture: ") + cudaGetErrorString(ce));

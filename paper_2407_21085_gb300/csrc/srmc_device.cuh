@@ -228,15 +228,15 @@ __device__ __forceinline__ float normal_h(float wv)
 {
     float h;
     if (wv < 5.0f) {
-        const float s = wv - 2.5f;
+        const float s = __fadd_rn(wv, -2.5f);
         h = NRM_C[0];
 #pragma unroll
-        for (int c = 1; c < 10; ++c) h = fmaf(h, s, NRM_C[c]);
+        for (int c = 1; c < 10; ++c) h = __fmaf_rn(h, s, NRM_C[c]);
     } else {
-        const float s = sqrtf(wv) - 3.435767889f;
+        const float s = __fadd_rn(sqrtf(wv), -3.435767889f);
         h = NRM_T[0];
 #pragma unroll
-        for (int c = 1; c < 10; ++c) h = fmaf(h, s, NRM_T[c]);
+        for (int c = 1; c < 10; ++c) h = __fmaf_rn(h, s, NRM_T[c]);
     }
     return h;
 }
@@ -248,18 +248,21 @@ __device__ __forceinline__ float normal_h(float wv)
 #ifndef SRMC_NORMAL_EXACT_Y
 #define SRMC_NORMAL_EXACT_Y 0
 #endif
+// (The scalar form is written with the _rn intrinsics, which the compiler
+// neither contracts nor rearranges, so that every kernel that inlines it --
+// and the packed form, which does the same operations -- gives the same bits.)
 __device__ __forceinline__ float normal_of(unsigned w, float)
 {
     const bool up = w >= 0x80000000u;
     const unsigned v = up ? ~w : w;                                     // p <= 1/2
-    const float p = fmaf(__uint2float_rn(v), 0x1p-32f, 0x1p-33f);
+    const float p = __fmaf_rn(__uint2float_rn(v), 0x1p-32f, 0x1p-33f);
 #if SRMC_NORMAL_EXACT_Y
-    const float y = fmaf(__uint2float_rn(0x7FFFFFFFu - v), -0x1p-31f, -0x1p-32f);   // 2p - 1
+    const float y = __fmaf_rn(__uint2float_rn(0x7FFFFFFFu - v), -0x1p-31f, -0x1p-32f);   // 2p - 1
 #else
-    const float y = fmaf(p, 2.0f, -1.0f);                                           // 2p - 1
+    const float y = __fmaf_rn(p, 2.0f, -1.0f);                                          // 2p - 1
 #endif
-    const float wv = -__logf(4.0f * (p * (1.0f - p)));
-    const float x = y * normal_h(wv);
+    const float wv = -__logf(__fmul_rn(4.0f, __fmul_rn(p, __fmaf_rn(p, -1.0f, 1.0f))));
+    const float x = __fmul_rn(y, normal_h(wv));
     return up ? -x : x;
 }
 
@@ -596,28 +599,36 @@ __device__ __forceinline__ R model_f(const Params &P, int j, const R (&x)[D], R 
 __host__ __device__ __forceinline__ int c16_index(const Params &P, int l, int c) { return c * P.ph + l; }
 
 // ---- table rows ----------------------------------------------------------
-template <int PP>
+// COH: the rows may have been written by other blocks of the same launch (the
+// persistent batched form), so they are read with ordinary cached loads, not
+// through the read-only path.
+template <bool COH>
+__device__ __forceinline__ float4 ld_row4(const float4 *p) { return COH ? __ldca(p) : __ldg(p); }
+template <bool COH>
+__device__ __forceinline__ double2 ld_row2(const double2 *p) { return COH ? __ldca(p) : __ldg(p); }
+
+template <int PP, bool COH = false>
 __device__ __forceinline__ void load_row(const float *ptr, float (&out)[PP])
 {
     constexpr int V = (PP + 3) / 4;
     const float4 *p4 = reinterpret_cast<const float4 *>(ptr);
 #pragma unroll
     for (int v = 0; v < V; ++v) {
-        const float4 t = __ldg(p4 + v);
+        const float4 t = ld_row4<COH>(p4 + v);
         if (4 * v + 0 < PP) out[4 * v + 0] = t.x;
         if (4 * v + 1 < PP) out[4 * v + 1] = t.y;
         if (4 * v + 2 < PP) out[4 * v + 2] = t.z;
         if (4 * v + 3 < PP) out[4 * v + 3] = t.w;
     }
 }
-template <int PP>
+template <int PP, bool COH = false>
 __device__ __forceinline__ void load_row(const double *ptr, double (&out)[PP])
 {
     constexpr int V = (PP + 1) / 2;
     const double2 *p2 = reinterpret_cast<const double2 *>(ptr);
 #pragma unroll
     for (int v = 0; v < V; ++v) {
-        const double2 t = __ldg(p2 + v);
+        const double2 t = ld_row2<COH>(p2 + v);
         if (2 * v + 0 < PP) out[2 * v + 0] = t.x;
         if (2 * v + 1 < PP) out[2 * v + 1] = t.y;
     }

@@ -37,11 +37,36 @@ struct BatchRound {
     long long total;                // kofs[n_active]
 };
 
+// The persistent form of the batched solve: one launch per kernel variant
+// over all of its rounds.  Segment a = (instance inst[a], step step[a]) owns
+// the work items kofs[a] .. kofs[a+1]-1 (its strata); segments are listed in
+// round order.  A block takes the next item from *next, waits until segment
+// dep[a] (the same instance's step step[a] + 1; -1: none) has all its strata
+// done, solves the item and counts it in done[a].  A wait that runs past its
+// iteration limit sets *error and goes on (no hang; the tables are then not
+// valid and srmc_batch_stats reports it).
+struct FlowPlan {
+    const Params *params;           // [instances] on the device
+    const int *inst;                // [n_seg]
+    const int *step;                // [n_seg]
+    const long long *kofs;          // [n_seg + 1]
+    const int *dep;                 // [n_seg]
+    unsigned long long *done;       // [n_seg], zeroed before every launch
+    unsigned long long *next;       // [1], zeroed before every launch
+    unsigned *error;                // [1]
+    int n_seg;
+    long long total;                // kofs[n_seg]
+};
+
 #define SRMC_LAUNCH_STEP_NAME(D) SRMC_LAUNCH_STEP_NAME_(D)
 #define SRMC_LAUNCH_BATCH_NAME(D) SRMC_LAUNCH_BATCH_NAME_(D)
 #define SRMC_LAUNCH_BATCH_NAME_(D) launch_batch_d##D
 #define SRMC_OCC_BATCH_NAME(D) SRMC_OCC_BATCH_NAME_(D)
 #define SRMC_OCC_BATCH_NAME_(D) occupancy_batch_d##D
+#define SRMC_LAUNCH_FLOW_NAME(D) SRMC_LAUNCH_FLOW_NAME_(D)
+#define SRMC_LAUNCH_FLOW_NAME_(D) launch_flow_d##D
+#define SRMC_OCC_FLOW_NAME(D) SRMC_OCC_FLOW_NAME_(D)
+#define SRMC_OCC_FLOW_NAME_(D) occupancy_flow_d##D
 #define SRMC_LAUNCH_STEP_NAME_(D) launch_step_d##D
 #define SRMC_LAUNCH_STEP_PROB_NAME(D) SRMC_LAUNCH_STEP_PROB_NAME_(D)
 #define SRMC_LAUNCH_STEP_PROB_NAME_(D) launch_step_prob_d##D
@@ -86,7 +111,10 @@ cudaError_t launch_step_quad_d3(const Params &P, int i, bool fp64, bool lp1, int
 #define SRMC_DECLARE_BATCH(D)                                                                 \
     cudaError_t launch_batch_d##D(const BatchRound &B, bool fp64, bool lp1, int mv, bool cv,  \
                                   int grid, int threads, cudaStream_t st);                    \
-    int occupancy_batch_d##D(bool fp64, bool lp1, int mv, bool cv, int threads);
+    int occupancy_batch_d##D(bool fp64, bool lp1, int mv, bool cv, int threads);              \
+    cudaError_t launch_flow_d##D(const FlowPlan &F, bool lp1, int mv, bool cv, int grid,      \
+                                 int threads, cudaStream_t st);                              \
+    int occupancy_flow_d##D(bool lp1, int mv, bool cv, int threads);
 SRMC_DECLARE_BATCH(1)
 SRMC_DECLARE_BATCH(2)
 SRMC_DECLARE_BATCH(3)

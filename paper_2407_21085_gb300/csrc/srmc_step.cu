@@ -442,7 +442,7 @@ __host__ __device__ constexpr int row_pad(int n) { return sizeof(R) == 4 ? (n + 
 // g(x) when j == N.
 // With CV, also hands back phi(x) and the row index of (j, stratum of x), from
 // which the control of the next increment is evaluated.
-template <typename R, int D, bool LP1, int MODEL, bool ZIN, bool CV>
+template <typename R, int D, bool LP1, int MODEL, bool ZIN, bool CV, bool FLOW = false>
 __device__ __forceinline__ void eval_at(const Params &P, int j, const R (&x)[D], R &y, R (&z)[D],
                                         R (&phio)[BasisDim<D, LP1>::value], unsigned &rowo)
 {
@@ -472,7 +472,7 @@ __device__ __forceinline__ void eval_at(const Params &P, int j, const R (&x)[D],
     // as constants of the kernel's basis dimension.
     constexpr unsigned RY = (unsigned)row_pad<R>(p), RZ = (unsigned)row_pad<R>(D * p);
     R a[p];
-    load_row<p>(Form<R>::Ytab(P) + row * RY, a);
+    load_row<p, FLOW>(Form<R>::Ytab(P) + row * RY, a);
     R v = a[0];
 #pragma unroll
     for (int c = 1; c < p; ++c) v += a[c] * phi[c];
@@ -487,7 +487,7 @@ __device__ __forceinline__ void eval_at(const Params &P, int j, const R (&x)[D],
             for (int l = 0; l < D; ++l) w[l] = (R)0;
 #pragma unroll
             for (int v = 0; v < (D * p + 3) / 4; ++v) {
-                const float4 t = __ldg(z4 + v);
+                const float4 t = ld_row4<FLOW>(z4 + v);
                 const float tv[4] = {t.x, t.y, t.z, t.w};
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
@@ -499,7 +499,7 @@ __device__ __forceinline__ void eval_at(const Params &P, int j, const R (&x)[D],
             for (int l = 0; l < D; ++l) z[l] = clamp_r(w[l], Form<R>::Cz(P));
         } else {
             R bz[D * p];
-            load_row<D * p>(Form<R>::Ztab(P) + row * RZ, bz);
+            load_row<D * p, FLOW>(Form<R>::Ztab(P) + row * RZ, bz);
 #pragma unroll
             for (int l = 0; l < D; ++l) {
                 R w = bz[l * p];
@@ -668,7 +668,7 @@ struct StepSmem {
 
 // Fits of stratum k at step i (the whole of Alg. SRMDP for one (i, k)) by the
 // calling block: phase A, Z fit, phase B, Y fit, row store.
-template <typename R, int D, bool LP1, int MODEL, bool ZIN, bool CV>
+template <typename R, int D, bool LP1, int MODEL, bool ZIN, bool CV, bool FLOW = false>
 __device__ __forceinline__ void solve_stratum(const Params &P, const int i, const long long k,
                                               StepSmem<R, D, LP1> &sm)
 {
@@ -806,7 +806,7 @@ __device__ __forceinline__ void solve_stratum(const Params &P, const int i, cons
         // phase B).  Its part in x_i is taken before X_{i+1} is located.
         [[maybe_unused]] R fdt = (R)0;
         if constexpr (!ZIN) fdt = model_f_x<R, D, MODEL>(P, i, x);
-        eval_at<R, D, LP1, MODEL, ZIN, CV>(P, i + 1, xj, yn, zj, phij, rowj);
+        eval_at<R, D, LP1, MODEL, ZIN, CV, FLOW>(P, i + 1, xj, yn, zj, phij, rowj);
         if constexpr (!ZIN) fdt = dt * model_f_y<R, D, MODEL>(P, yn, fdt);
         [[maybe_unused]] R zsum = (R)0;
         if constexpr (ZSUM) {
@@ -849,7 +849,7 @@ __device__ __forceinline__ void solve_stratum(const Params &P, const int i, cons
                 }
                 [[maybe_unused]] R fx = (R)0;
                 if constexpr (!ZIN) fx = model_f_x<R, D, MODEL>(P, j, xj);
-                eval_at<R, D, LP1, MODEL, ZIN, CV>(P, j + 1, xn, yn, zn, phij, rowj);
+                eval_at<R, D, LP1, MODEL, ZIN, CV, FLOW>(P, j + 1, xn, yn, zn, phij, rowj);
                 if constexpr (ZSUM) {
                     S += dt * logistic_f<R, D>(yn, zsum);
                     zsum = (R)0;
@@ -1014,7 +1014,7 @@ __device__ __forceinline__ void solve_stratum(const Params &P, const int i, cons
             {
                 [[maybe_unused]] R phi1[p];
                 [[maybe_unused]] unsigned row1;
-                eval_at<R, D, LP1, MODEL, ZIN, false>(P, i + 1, x1, y1, z1, phi1, row1);
+                eval_at<R, D, LP1, MODEL, ZIN, false, FLOW>(P, i + 1, x1, y1, z1, phi1, row1);
             }
             {
                 // z_i(x_i) from the fresh Z fit; long coefficient vectors are read
@@ -1115,6 +1115,89 @@ step_kernel_batch(const BatchRound B)
         }
         solve_stratum<R, D, LP1, MODEL, ZIN, CV>(Ps, __ldg(B.step + lo), t - __ldg(B.kofs + lo), sm);
     }
+}
+
+// The persistent batched form (FlowPlan): one launch per kernel variant over
+// all rounds of all its instances.  Blocks take work items in round order
+// from a global counter; an item of step i waits for the whole step i + 1 of
+// its instance (written by other blocks of the same launch), then reads
+// those rows with cached coherent loads (FLOW) after a device-scope fence.
+// Every item waited for was handed out earlier to a running block whose own
+// waits are for still earlier items, so the waits always end; each also has
+// an iteration limit, after which it flags *error and goes on.
+constexpr unsigned FLOW_SPIN_LIMIT = 1u << 23;      // x ~128 ns sleep: about a second
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long *p)
+{
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+template <typename R, int D, bool LP1, int MODEL, bool ZIN, bool CV>
+__global__ void __launch_bounds__(MAX_THREADS, MinBlocks<R, D, CV, ZIN>::value)
+step_kernel_flow(const FlowPlan F)
+{
+    __shared__ StepSmem<R, D, LP1> sm;
+    __shared__ __align__(16) Params Ps;
+    __shared__ long long item_s;
+    int cur = -1;
+    for (;;) {
+        if (threadIdx.x == 0) item_s = (long long)atomicAdd(F.next, 1ull);
+        __syncthreads();
+        const long long t = item_s;
+        if (t >= F.total) break;
+        int lo = 0, hi = F.n_seg - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (__ldg(F.kofs + mid) <= t) lo = mid; else hi = mid - 1;
+        }
+        if (threadIdx.x == 0) {
+            const int dseg = __ldg(F.dep + lo);
+            if (dseg >= 0) {
+                const unsigned long long need =
+                    (unsigned long long)(__ldg(F.kofs + dseg + 1) - __ldg(F.kofs + dseg));
+                unsigned spins = 0;
+                while (ld_acquire_u64(F.done + dseg) < need) {
+                    if (++spins > FLOW_SPIN_LIMIT) { atomicExch(F.error, 1u); break; }
+                    __nanosleep(128);
+                }
+            }
+            __threadfence();
+        }
+        const int r = __ldg(F.inst + lo);
+        if (r != cur) {                           // the same decision in every thread
+            __syncthreads();
+            const int *src = reinterpret_cast<const int *>(F.params + r);
+            int *dst = reinterpret_cast<int *>(&Ps);
+            for (int e = threadIdx.x; e < (int)(sizeof(Params) / sizeof(int)); e += blockDim.x)
+                dst[e] = __ldg(src + e);
+            cur = r;
+        }
+        __syncthreads();
+        solve_stratum<R, D, LP1, MODEL, ZIN, CV, true>(Ps, __ldg(F.step + lo), t - __ldg(F.kofs + lo), sm);
+        if (threadIdx.x == 0) {
+            __threadfence();                       // the rows of (step, stratum) before the count
+            atomicAdd(F.done + lo, 1ull);
+        }
+    }
+}
+
+template <typename R, bool LP1, int MODEL, bool ZIN, bool CV>
+cudaError_t launch_flow_one(const FlowPlan &F, int grid, int threads, cudaStream_t st)
+{
+    step_kernel_flow<R, SRMC_STEP_D, LP1, MODEL, ZIN, CV><<<grid, threads, 0, st>>>(F);
+    return cudaGetLastError();
+}
+
+template <typename R, bool LP1, int MODEL, bool ZIN, bool CV>
+int occ_flow_one(int threads)
+{
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+            &n, step_kernel_flow<R, SRMC_STEP_D, LP1, MODEL, ZIN, CV>, threads, 0) != cudaSuccess)
+        return 0;
+    return n;
 }
 
 template <typename R, bool LP1, int MODEL, bool ZIN, bool CV>
@@ -1220,7 +1303,32 @@ struct BatchOccupancy {
     template <typename R, bool LP1, int MODEL, bool ZIN, bool CV>
     int operator()() { return occ_batch_one<R, LP1, MODEL, ZIN, CV>(threads); }
 };
+struct FlowLauncher {
+    const FlowPlan &F; int grid, threads; cudaStream_t st;
+    template <typename R, bool LP1, int MODEL, bool ZIN, bool CV>
+    cudaError_t operator()() { return launch_flow_one<R, LP1, MODEL, ZIN, CV>(F, grid, threads, st); }
+};
+struct FlowOccupancy {
+    int threads;
+    template <typename R, bool LP1, int MODEL, bool ZIN, bool CV>
+    int operator()() { return occ_flow_one<R, LP1, MODEL, ZIN, CV>(threads); }
+};
 }  // namespace
+
+cudaError_t SRMC_LAUNCH_FLOW_NAME(SRMC_STEP_D)(const FlowPlan &F, bool lp1, int mv, bool cv, int grid, int threads,
+                                                cudaStream_t st)
+{
+    const bool ok = !(cv && !lp1) && mv >= MV_COS && mv <= MV_AFFINE && !(cv && mv == MV_AFFINE);
+    if (!ok) return cudaErrorInvalidValue;
+    FlowLauncher f{F, grid, threads, st};
+    return dispatch_variant<float>(lp1, mv, cv, f);
+}
+
+int SRMC_OCC_FLOW_NAME(SRMC_STEP_D)(bool lp1, int mv, bool cv, int threads)
+{
+    FlowOccupancy f{threads};
+    return dispatch_variant<float>(lp1, mv, cv, f);
+}
 
 cudaError_t SRMC_LAUNCH_BATCH_NAME(SRMC_STEP_D)(const BatchRound &B, bool fp64, bool lp1, int mv, bool cv,
                                                  int grid, int threads, cudaStream_t st)

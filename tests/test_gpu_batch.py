@@ -38,9 +38,10 @@ def _instances():
         W.cfg2(C=6, N=4, M=300, kapz=0.2), W.cfg2(C=5, N=3, M=257, basis="lp0")]
 
 
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 2])
 def test_batch_equals_single_solves(dev, mode):
-    # mode 0: rounds of multi-instance launches; mode 1: one graph branch per instance
+    # mode 0: rounds of multi-instance launches; mode 1: one graph branch per
+    # instance; mode 2: one persistent launch per kernel variant
     torch, srmc = dev
     ws = _instances()
     single = []
@@ -54,12 +55,13 @@ def test_batch_equals_single_solves(dev, mode):
     assert b.srmc_batch_mode() == mode
     b.srmc_batch_solve()
     b.srmc_batch_solve()                       # graph replay
+    assert b.srmc_batch_stats() == 0
     for a, s in enumerate(solvers):
         y, z = _tables(torch, s)
         assert np.array_equal(y, single[a][0]) and np.array_equal(z, single[a][1]), ws[a].name
 
 
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 2])
 def test_batch_instances_against_the_oracle(dev, orc, mode):
     # every batched instance against the FP64 oracle directly: teacher-forced
     # steps 0, N/2 and N-1 on up to 48 sampled strata each, at centres and
@@ -78,14 +80,16 @@ def test_batch_instances_against_the_oracle(dev, orc, mode):
 
 def test_full_size_batch_instances_against_the_oracle(dev, orc):
     # the first 32 instances of the 256-instance batched workload at full
-    # size, solved together; the largest instance of each dimension checked
+    # size, solved together by the persistent strategy; the largest instance
+    # of each dimension checked
     # against the oracle by teacher forcing (steps 0, N/2, N-1; 32 strata)
     torch, srmc = dev
     ws = W.cfg4_instances()[:32]
     solvers = [srmc.Solver(w) for w in ws]
     b = srmc.Batch(solvers)
+    b.srmc_batch_set_mode(2)                  # the persistent strategy
     b.srmc_batch_solve()
-    torch.cuda.synchronize()
+    assert b.srmc_batch_stats() == 0
     for d in (1, 2, 3):
         a = max((r for r in range(len(ws)) if ws[r].d == d), key=lambda r: ws[r].path_steps())
         res = T.teacher_forced(torch, orc, solvers[a], [0, ws[a].N // 2, ws[a].N - 1], 32)
@@ -120,7 +124,7 @@ def test_batch_rejects_fp64(dev):
     assert e.value.status == 4
 
 
-@pytest.mark.parametrize("mode", [0, 1])
+@pytest.mark.parametrize("mode", [0, 1, 2])
 def test_batch_with_controls_equals_single_solves(dev, mode):
     # instances with tabulated control rows, with the run's own control (the
     # cos model without z in its driver then runs the z-evaluating variant)
