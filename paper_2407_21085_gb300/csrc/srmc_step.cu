@@ -516,13 +516,11 @@ __device__ __forceinline__ void eval_at(const Params &P, int j, const R (&x)[D],
     }
 }
 
-// zc(x) . dw for the control row `row` and the basis values phi of x:
-// sum_l T_Cz(beta_l . phi) dw_l (the martingale control of one increment).
+// zc(x) = T_Cz(beta_l . phi) for the control row `row` and the basis values
+// phi of x: the values of the martingale control's integrand (clamped).
 template <typename R, int D, int p>
-__device__ __forceinline__ R control_dot(const Params &P, unsigned row, const R (&phi)[p],
-                                         const R (&dw)[D])
+__device__ __forceinline__ void control_vals(const Params &P, unsigned row, const R (&phi)[p], R (&zc)[D])
 {
-    R acc = (R)0;
     if constexpr (sizeof(R) == 4) {
         // FP32 form: binary16 rows, coefficient-major (the halves of a 32-bit
         // word are coefficient a of components 2m and 2m + 1, c16_index), read
@@ -551,14 +549,11 @@ __device__ __forceinline__ R control_dot(const Params &P, unsigned row, const R 
             }
         }
         const float L = Form<R>::Cz(P);
-        float2 s2 = make_float2(0.0f, 0.0f);
 #pragma unroll
         for (int m = 0; m < QH; ++m) {
-            const float2 z2 = make_float2(clamp_r(w2[m].x, L), clamp_r(w2[m].y, L));
-            const float2 d2 = make_float2(dw[2 * m], 2 * m + 1 < D ? dw[2 * m + 1] : 0.0f);
-            s2 = __ffma2_rn(z2, d2, s2);
+            zc[2 * m] = clamp_r(w2[m].x, L);
+            if (2 * m + 1 < D) zc[2 * m + 1] = clamp_r(w2[m].y, L);
         }
-        acc = s2.x + s2.y;
     } else {
         const double *b = P.C64 + row * (unsigned)P.rz64;
 #pragma unroll
@@ -566,10 +561,37 @@ __device__ __forceinline__ R control_dot(const Params &P, unsigned row, const R 
             double w = __ldg(b + l * p);
 #pragma unroll
             for (int a = 1; a < p; ++a) w += __ldg(b + l * p + a) * phi[a];
-            acc += clamp_r(w, Form<R>::Cz(P)) * dw[l];
+            zc[l] = clamp_r(w, Form<R>::Cz(P));
         }
     }
-    return acc;
+}
+
+// zc . dw: the martingale control of one increment (FP32: two components
+// per packed FMA, the pair sums added at the end).
+template <typename R, int D>
+__device__ __forceinline__ R control_apply(const R (&zc)[D], const R (&dw)[D])
+{
+    if constexpr (sizeof(R) == 4) {
+        float2 s2 = make_float2(0.0f, 0.0f);
+#pragma unroll
+        for (int m = 0; m < (D + 1) / 2; ++m)
+            s2 = __ffma2_rn(make_float2(zc[2 * m], 2 * m + 1 < D ? zc[2 * m + 1] : 0.0f),
+                            make_float2(dw[2 * m], 2 * m + 1 < D ? dw[2 * m + 1] : 0.0f), s2);
+        return s2.x + s2.y;
+    } else {
+        R acc = (R)0;
+#pragma unroll
+        for (int l = 0; l < D; ++l) acc += zc[l] * dw[l];
+        return acc;
+    }
+}
+
+template <typename R, int D, int p>
+__device__ __forceinline__ R control_dot(const Params &P, unsigned row, const R (&phi)[p], const R (&dw)[D])
+{
+    R zc[D];
+    control_vals<R, D, p>(P, row, phi, zc);
+    return control_apply<R, D>(zc, dw);
 }
 
 // Blocks per SM the compiler must fit (register budget): FP32 forms of
@@ -799,14 +821,20 @@ __device__ __forceinline__ void solve_stratum(const Params &P, const int i, cons
         // Martingale control: CI = zc_i(x_i).dW_i (stratum k), CZ = sum_{j>i} zc_j(X_j).dW_j,
         // zc_j evaluated at X_j from the control row of (j, stratum of X_j); with the
         // run's own control zc_j = z_j, the fitted z of step j, and CI = 0.
+        // the control's integrand zc_j(X_j) (from the control row of (j, stratum
+        // of X_j)), evaluated when X_j is located and carried to step j
         [[maybe_unused]] R phij[p];
         [[maybe_unused]] unsigned rowj = 0;
+        [[maybe_unused]] R zcj[D];
         // A driver that does not read z: f_i(x_i, y_{i+1}(X_{i+1})) is known
         // after this first step, so the Y response is complete in phase A (no
         // phase B).  Its part in x_i is taken before X_{i+1} is located.
         [[maybe_unused]] R fdt = (R)0;
         if constexpr (!ZIN) fdt = model_f_x<R, D, MODEL>(P, i, x);
         eval_at<R, D, LP1, MODEL, ZIN, CV, FLOW>(P, i + 1, xj, yn, zj, phij, rowj);
+        if constexpr (CV) {
+            if (!P.cv_own && i + 1 < P.N) control_vals<R, D, p>(P, rowj, phij, zcj);
+        }
         if constexpr (!ZIN) fdt = dt * model_f_y<R, D, MODEL>(P, yn, fdt);
         [[maybe_unused]] R zsum = (R)0;
         if constexpr (ZSUM) {
@@ -845,11 +873,14 @@ __device__ __forceinline__ void solve_stratum(const Params &P, const int i, cons
                             for (int l = 0; l < D; ++l) CZ += zj[l] * dw[l];
                         }
                     }
-                    if (!own) CZ += control_dot<R, D, p>(P, rowj, phij, dw);
+                    if (!own) CZ += control_apply<R, D>(zcj, dw);
                 }
                 [[maybe_unused]] R fx = (R)0;
                 if constexpr (!ZIN) fx = model_f_x<R, D, MODEL>(P, j, xj);
                 eval_at<R, D, LP1, MODEL, ZIN, CV, FLOW>(P, j + 1, xn, yn, zn, phij, rowj);
+                if constexpr (CV) {
+                    if (!P.cv_own && j + 1 < P.N) control_vals<R, D, p>(P, rowj, phij, zcj);
+                }
                 if constexpr (ZSUM) {
                     S += dt * logistic_f<R, D>(yn, zsum);
                     zsum = (R)0;

@@ -52,3 +52,18 @@ def test_traffic_record_needs_the_captured_sources(tmp_path, monkeypatch):
     assert bench.recorded_traffic("other", False) is None
     monkeypatch.setattr(bench, "kernel_source_hash", lambda: "0" * 64)
     assert bench.recorded_traffic("w", False) is None
+
+
+def test_oracle_time_extrapolation():
+    # per-stratum fit times a + b (N - i) measured at three steps (wall time of
+    # n fits), summed over all K strata and N steps: exact for that model
+    from paper_2407_21085_gb300 import workloads as W
+    w = W.cfg2(C=8, N=10, M=64)
+    a, b = 0.002, 0.0005
+    fits = [(i, n, n * (a + b * (w.N - i)), 0) for i, n in ((0, 4), (5, 4), (9, 16))]
+    want = sum(w.K * (a + b * (w.N - i)) for i in range(w.N))
+    assert abs(bench.extrapolate_full(w, fits) - want) < 1e-9 * want
+    # the sampled steps are 0, N/2 and N-1, with more strata at the cheap last step
+    plan = bench.oracle_plan(w, 8, single=False)
+    assert [i for i, _ in plan] == [0, w.N // 2, w.N - 1] and plan[2][1] > plan[0][1]
+    assert all(n == 1 for _, n in bench.oracle_plan(w, 1, single=True)[:2])
