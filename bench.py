@@ -610,12 +610,8 @@ def batched_compare(args, stream):
 
     t_batch = timed(lambda: batch.srmc_batch_solve(stream), args.batch_reps)
     mode = batch.srmc_batch_mode()
-    # both strategies with the tuned block sizes, for the record
-    t_mode = {}
-    for m, name in ((0, "rounds"), (1, "branches"), (2, "persistent")):
-        batch.srmc_batch_set_mode(m)
-        t_mode[name] = timed(lambda: batch.srmc_batch_solve(stream), 1)
-    batch.srmc_batch_set_mode(mode)
+    # the three strategies as timed by the tuner (one whole-batch solve each)
+    t_mode = dict(zip(("rounds", "branches", "persistent"), (v / 1e3 for v in batch.srmc_batch_strategy_ms())))
 
     def sequential():
         for s in solvers:

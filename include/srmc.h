@@ -379,6 +379,10 @@ int srmc_batch_mode(const srmc_batch *b);
 /* Force a strategy (0, 1 or 2; SRMC_ERR_INVALID_ARG otherwise). */
 srmc_status srmc_batch_set_mode(srmc_batch *b, int mode);
 
+/* The device time in ms of one whole-batch solve by each strategy (0, 1, 2)
+ * as measured by the last srmc_batch_tune (-1 before any tuning). */
+srmc_status srmc_batch_strategy_ms(const srmc_batch *b, float out_ms[3]);
+
 /* Synchronise the device and report in *timeouts whether a wait of the
  * persistent strategy (2) ran past its iteration limit (about a second)
  * since the batch was created: then the tables of that solve are not valid.

@@ -131,6 +131,7 @@ struct srmc_batch {
     int sms = 0;
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t graph = nullptr;
+    float strategy_ms[3] = {-1.0f, -1.0f, -1.0f};   // the tuner's timings of the strategies
 };
 
 namespace {
@@ -491,6 +492,7 @@ srmc_status srmc_batch_tune(srmc_batch *b, void *stream, int *out_threads, int m
     b->mode = MODE_ROUNDS;
     for (int mode = 1; mode < 3; ++mode)
         if (tm[mode] < tm[b->mode]) b->mode = mode;
+    for (int mode = 0; mode < 3; ++mode) b->strategy_ms[mode] = tm[mode];
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (b->graph) { cudaGraphExecDestroy(b->graph); b->graph = nullptr; }
@@ -501,6 +503,13 @@ srmc_status srmc_batch_tune(srmc_batch *b, void *stream, int *out_threads, int m
 }
 
 int srmc_batch_mode(const srmc_batch *b) { return b ? b->mode : -1; }
+
+srmc_status srmc_batch_strategy_ms(const srmc_batch *b, float out_ms[3])
+{
+    if (!b || !out_ms) return bfail(SRMC_ERR_INVALID_ARG, "srmc_batch_strategy_ms: NULL argument");
+    for (int a = 0; a < 3; ++a) out_ms[a] = b->strategy_ms[a];
+    return SRMC_OK;
+}
 
 srmc_status srmc_batch_stats(srmc_batch *b, unsigned long long *timeouts)
 {

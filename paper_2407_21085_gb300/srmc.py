@@ -104,6 +104,8 @@ def lib():
             L.srmc_batch_mode.argtypes = [vp]; L.srmc_batch_mode.restype = i_
             L.srmc_batch_set_mode.argtypes = [vp, i_]; L.srmc_batch_set_mode.restype = C.c_int
             L.srmc_batch_stats.argtypes = [vp, C.POINTER(C.c_ulonglong)]; L.srmc_batch_stats.restype = C.c_int
+            L.srmc_batch_strategy_ms.argtypes = [vp, C.POINTER(C.c_float)]
+            L.srmc_batch_strategy_ms.restype = C.c_int
             for name in ("srmc_batch_create", "srmc_batch_tune", "srmc_batch_solve"):
                 getattr(L, name).restype = C.c_int
             for name in ("srmc_read_control", "srmc_mlp_create", "srmc_mlp_set_params",
@@ -415,6 +417,12 @@ class Batch:
 
     def srmc_batch_set_mode(self, mode: int):
         _check(lib().srmc_batch_set_mode(self._h, int(mode)))
+
+    def srmc_batch_strategy_ms(self):
+        """[rounds, branches, persistent] whole-batch ms measured by the last tune."""
+        out = (C.c_float * 3)()
+        _check(lib().srmc_batch_strategy_ms(self._h, out))
+        return [float(v) for v in out]
 
     def srmc_batch_stats(self) -> int:
         """Number of waits of the persistent strategy that gave up (0 normally)."""

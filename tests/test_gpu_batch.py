@@ -109,6 +109,8 @@ def test_tuned_batch_matches_within_rounding(dev):
     b = srmc.Batch(solvers)
     threads = b.srmc_batch_tune()
     assert threads and all(t in (64, 128, 256) for t in threads)
+    ms = b.srmc_batch_strategy_ms()                 # the tuner keeps the fastest strategy
+    assert all(v > 0 for v in ms) and b.srmc_batch_mode() == int(np.argmin(ms))
     b.srmc_batch_solve()
     for a, s in enumerate(solvers):
         y, z = _tables(torch, s)
