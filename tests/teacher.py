@@ -51,14 +51,17 @@ def errors(gy, gz, ry, rz):
             float(np.max(np.abs(gz - rz) / (1 + np.abs(rz)))))
 
 
-def teacher_forced(torch, orc, s, steps, n_strata, seed=0, nthreads=0):
+def teacher_forced(torch, orc, s, steps, n_strata, seed=0, nthreads=0, control=None):
     """Compare the solved GPU solver s with the oracle at the given steps on
     n_strata sampled strata each; returns {i: (err_y, err_z, err_y_centres,
     err_z_centres)} (not asserted): the first two over all probe points, the
-    last two at the centres alone."""
+    last two at the centres alone.  control: the control rows [N][K][q][p]
+    (centred basis) the GPU solver used, given to the oracle too."""
     w = s.w
     Y, Z = gpu_tables(torch, s)
     o = orc.Oracle(w)
+    if control is not None:
+        o.set_control(control)
     lo = min(steps)
     for j in range(lo + 1, w.N):
         o.set_rows_centred(j, Y[j].cpu().numpy(), Z[j].cpu().numpy())

@@ -6,6 +6,7 @@ import pytest
 
 from paper_2407_21085_gb300 import workloads as W
 from tests import controls as CT
+from tests import teacher as T
 from tests.test_gpu_parity import _check
 
 pytestmark = pytest.mark.gpu
@@ -244,3 +245,29 @@ def test_controls_with_quadratic_polynomials(dev, orc, prec):
     w = W.cfg2(C=6, N=4, M=256, precision=prec, basis="lp2")
     _cv_parity(dev, orc, w, CT.closed_form_z(w))
     _own_parity(dev, orc, w)
+
+
+def test_cfg5_learned_control_full_size_teacher_forced(dev, orc):
+    # the learned control at full size, as the CV half of the benchmark runs
+    # it: coarse M = 256 solve -> network trained on it -> sigma grad u_theta
+    # tabulated as binary16 control rows -> M = 1024 solve on 8^6 strata.  The
+    # oracle gets the same rows (read back and rounded to binary16, the form
+    # the FP32 kernel reads) and the GPU's tables of the later steps, and
+    # refits 128 sampled strata of steps 0, N/2 and N-1.
+    torch, srmc = dev
+    w = W.cfg5(M=1024)
+    coarse = srmc.Solver(W.cfg5(M=256, seed=w.seed + 100))
+    coarse.srmc_solve()
+    net = srmc.MLP(w.d + 1, seed=1)
+    net.srmc_mlp_fit(coarse, n_data=1 << 18, iters=300, batch=8192, lr=3e-3, seed=2)
+    coarse.close()
+    s = srmc.Solver(w)
+    net.srmc_cv_tabulate(s)
+    s.srmc_solve()
+    net.close()
+    rows = s.srmc_read_control().astype(np.float16).astype(np.float64)
+    assert np.any(rows != 0)
+    res = T.teacher_forced(torch, orc, s, [0, w.N // 2, w.N - 1], 128, control=rows)
+    print(w.name, "learned control", {i: tuple("%.2e" % v for v in e) for i, e in res.items()})
+    T.assert_within(w, res)
+    s.close()
