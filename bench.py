@@ -509,6 +509,12 @@ def paper_table_rows(table: str):
     if table == "lp1_d11":
         # the paper's LP1 table at d = 11: dt = 0.2 with #C = 2, M = 2000 and #C = 3, M = 4000
         return 11, "lp1", [(5, 2, 2000, 1000), (5, 3, 4000, 20)]
+    if table == "lp1_d12_19":
+        # the paper's LP1 tables at d = 12..19 (dt = 0.2): rows (N, #C, M, runs, d)
+        return 12, "lp1", [(5, 2, 2000, 100, 12), (5, 3, 4000, 3, 12), (5, 2, 3000, 100, 13),
+                           (5, 2, 4000, 100, 13), (5, 2, 2000, 100, 14), (5, 2, 4000, 50, 14),
+                           (5, 2, 5000, 20, 15), (5, 2, 6000, 10, 16), (5, 2, 5000, 5, 17),
+                           (5, 2, 4000, 3, 18), (5, 2, 3200, 3, 19)]
     if table == "lp1_d6":
         d, rows = 6, [(5, 1000), (10, 1000), (20, 200), (50, 3)]
         return d, "lp1", [(N, int(math.floor(1.5 * math.sqrt(d * math.sqrt(N)) - 3)), (d + 1) * N * N, R)
@@ -545,7 +551,9 @@ def paper_table(args, stream):
     out = []
     gen = torch.Generator(device="cuda")
     gen.manual_seed(12345)
-    for N, C, M, R in rows:
+    for row in rows:
+        N, C, M, R = row[:4]
+        d = row[4] if len(row) > 4 else d
         w0 = W.logistic_paper(d=d, N=N, C=C, M=M, basis=basis)
         sums = torch.zeros((N, 2), dtype=torch.float64, device="cuda")
         part = torch.empty((N, 2), dtype=torch.float64, device="cuda")
@@ -567,7 +575,7 @@ def paper_table(args, stream):
             s.close()
         wall = time.perf_counter() - t0
         S = sums.cpu().numpy()
-        out.append({"dt": 1.0 / N, "N": N, "cells_per_dim": C, "K": C ** d, "M": M, "runs": R,
+        out.append({"d": d, "dt": 1.0 / N, "N": N, "cells_per_dim": C, "K": C ** d, "M": M, "runs": R,
                     "points_per_step_per_run": n,
                     "MSE_Y_max": float(math.log(S[:, 0].max() / (R * n))),
                     "MSE_Y_av": float(math.log(S[:, 0].sum() / (R * n * N))),
@@ -575,7 +583,7 @@ def paper_table(args, stream):
                     "gpu_ms_per_run": statistics.median(ms), "wall_s_all_runs": wall,
                     "path_steps_per_run": w0.path_steps()})
     return {"paper_table": args.paper_table, "model": "logistic (Sec. 5.1)", "precision": "fp32",
-            "basis": basis, "d": d, "rows": out}
+            "basis": basis, "rows": out}
 
 
 # ---- the batched form: 256 heterogeneous instances ---------------------------------
@@ -785,7 +793,8 @@ def main():
                     help="time the control-variate step kernel (rows from an untrained network)")
     ap.add_argument("--control-own", action="store_true",
                     help="time the step kernel with the run's own z control")
-    ap.add_argument("--paper-table", choices=["lp1_d4", "lp0_d4", "lp1_d6", "lp0_d6", "lp0_d11", "lp1_d11"],
+    ap.add_argument("--paper-table", choices=["lp1_d4", "lp0_d4", "lp1_d6", "lp0_d6", "lp0_d11", "lp1_d11",
+                                              "lp1_d12_19"],
                     default=None,
                     help="instead of the benchmark: the error indicators of Sec. 5.1 over many runs")
     ap.add_argument("--paper-points", type=int, default=1000, help="nu points per step per run")

@@ -43,7 +43,7 @@
 extern "C" {
 #endif
 
-#define SRMC_DMAX 11    /* largest dimension d supported                    */
+#define SRMC_DMAX 19    /* largest dimension d supported                    */
 #define SRMC_PMAX 24    /* length of the model parameter array             */
 
 typedef enum {
@@ -181,10 +181,10 @@ typedef struct srmc_solver srmc_solver;   /* opaque, library-owned */
 
 /* Validate the problem and allocate the solver's device tables on the
  * current device: coefficient rows of every (i, k), i < N, in FP64 (and FP32
- * for the FP32 form), zero-filled.  1 <= d <= SRMC_DMAX (11; the paper runs
- * d up to 19 in Sec. 5.2); d = 9..11 is built for equal-size strata, Euler
- * dynamics and the FP32 form, without controls (SRMC_ERR_UNSUPPORTED
- * otherwise).  Errors: SRMC_ERR_INVALID_ARG, SRMC_ERR_UNSUPPORTED,
+ * for the FP32 form), zero-filled.  1 <= d <= SRMC_DMAX (19, the largest
+ * dimension of the paper's Sec. 5.2); d = 9..19 is built for equal-size
+ * strata, Euler dynamics and the FP32 form, without controls, and user
+ * models for d <= 11 (SRMC_ERR_UNSUPPORTED otherwise).  Errors: SRMC_ERR_INVALID_ARG, SRMC_ERR_UNSUPPORTED,
  * SRMC_ERR_OOM, SRMC_ERR_CUDA; *out is NULL on error. */
 srmc_status srmc_create(const srmc_problem *problem, const srmc_strata *strata,
                         const srmc_config *config, srmc_solver **out);

@@ -22,7 +22,7 @@ _SRC = os.path.join(_HERE, "srmc_oracle.c")
 _HDR = os.path.join(_HERE, "srmc_oracle.h")
 _BUILD = os.path.join(_HERE, "_build")
 _OUT = os.path.join(_BUILD, "libsrmc_oracle.so")
-DMAX = 11
+DMAX = 19
 PMAX = 24
 MODELS = {"cos": 0, "logistic": 1, "affine": 2, "user": 3}
 BASES = {"lp0": 0, "lp1": 1, "lp2": 2}

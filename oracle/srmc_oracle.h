@@ -36,7 +36,7 @@
 extern "C" {
 #endif
 
-#define ORC_DMAX 11
+#define ORC_DMAX 19
 #define ORC_PMAX 24
 
 enum { ORC_MODEL_COS = 0, ORC_MODEL_LOGISTIC = 1, ORC_MODEL_AFFINE = 2, ORC_MODEL_USER = 3 };

@@ -1,6 +1,6 @@
 """Build libsrmc.so in-tree for sm_103a with nvcc.
 
-The step kernel is compiled once per dimension D = 1..11 (-DSRMC_STEP_D=D) so
+The step kernel is compiled once per dimension D = 1..19 (-DSRMC_STEP_D=D) so
 that per-path state stays in registers, and once per kind of strata
 (-DSRMC_STEP_KIND: equal size, equal probability) and of dynamics
 (-DSRMC_STEP_DYN: Euler, exact) and of basis (-DSRMC_STEP_BASIS=2: quadratic
@@ -23,7 +23,7 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libsrmc.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-DIMS = range(1, 12)             # equal-size strata, Euler dynamics: d <= 11
+DIMS = range(1, 20)             # equal-size strata, Euler dynamics: d <= 19
 NARROW_DIMS = range(1, 9)       # equal-probability strata, exact dynamics: d <= 8
 LP2_DIMS = range(1, 4)          # quadratic local polynomials: d <= 3
 

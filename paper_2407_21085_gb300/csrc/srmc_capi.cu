@@ -197,6 +197,14 @@ cudaError_t launch_step(const srmc_solver *s, int i, cudaStream_t st)
     case 9: return srmc::launch_step_d9(P, i, s->fp64, s->lp1, mv, grid, s->threads, st);
     case 10: return srmc::launch_step_d10(P, i, s->fp64, s->lp1, mv, grid, s->threads, st);
     case 11: return srmc::launch_step_d11(P, i, s->fp64, s->lp1, mv, grid, s->threads, st);
+    case 12: return srmc::launch_step_d12(P, i, s->fp64, s->lp1, mv, grid, s->threads, st);
+    case 13: return srmc::launch_step_d13(P, i, s->fp64, s->lp1, mv, grid, s->threads, st);
+    case 14: return srmc::launch_step_d14(P, i, s->fp64, s->lp1, mv, grid, s->threads, st);
+    case 15: return srmc::launch_step_d15(P, i, s->fp64, s->lp1, mv, grid, s->threads, st);
+    case 16: return srmc::launch_step_d16(P, i, s->fp64, s->lp1, mv, grid, s->threads, st);
+    case 17: return srmc::launch_step_d17(P, i, s->fp64, s->lp1, mv, grid, s->threads, st);
+    case 18: return srmc::launch_step_d18(P, i, s->fp64, s->lp1, mv, grid, s->threads, st);
+    case 19: return srmc::launch_step_d19(P, i, s->fp64, s->lp1, mv, grid, s->threads, st);
     }
     return cudaErrorInvalidValue;
 }
@@ -381,7 +389,7 @@ srmc_status srmc_create(const srmc_problem *pr, const srmc_strata *sa, const srm
     *out = nullptr;
     if (!pr || !sa || !cf) return fail(SRMC_ERR_INVALID_ARG, "srmc_create: NULL argument");
     const int d = pr->d, q = pr->q;
-    if (d < 1 || d > SRMC_DMAX) return fail(SRMC_ERR_INVALID_ARG, "d must be in [1, 11]");
+    if (d < 1 || d > SRMC_DMAX) return fail(SRMC_ERR_INVALID_ARG, "d must be in [1, 19]");
     if (q != d) return fail(SRMC_ERR_UNSUPPORTED, "this build requires q == d");
     if (pr->N < 1 || pr->N > 1000000) return fail(SRMC_ERR_INVALID_ARG, "N must be in [1, 1e6]");
     if (!(pr->T > 0.0) || !std::isfinite(pr->T)) return fail(SRMC_ERR_INVALID_ARG, "T must be > 0");
@@ -440,6 +448,8 @@ srmc_status srmc_create(const srmc_problem *pr, const srmc_strata *sa, const srm
     if (d >= srmc::SRMC_WIDE_DMIN_V && (prob || pr->dynamics != SRMC_DYN_EULER || cf->prec != SRMC_FP32))
         return fail(SRMC_ERR_UNSUPPORTED,
                     "d >= 9 is built for equal-size strata, Euler dynamics and the FP32 form");
+    if (d >= 12 && pr->model == SRMC_MODEL_USER)
+        return fail(SRMC_ERR_UNSUPPORTED, "user models are built for d <= 11");
     if (cf->M < p) return fail(SRMC_ERR_INVALID_ARG, "M must be >= the basis dimension");
     if (cf->M > 4294967295LL) return fail(SRMC_ERR_INVALID_ARG, "M must be < 2^32");
     long long M_max = cf->M, M_sum = cf->M * K;
@@ -458,6 +468,22 @@ srmc_status srmc_create(const srmc_problem *pr, const srmc_strata *sa, const srm
     if (threads < 32 || threads > srmc::MAX_THREADS || threads % 32)
         return fail(SRMC_ERR_INVALID_ARG, "block_threads must be a multiple of 32 in [32, 256]");
 
+    if (d >= 12) {
+        // the kernels of d >= 12 keep their shared memory dynamically: allow it
+        // (per device, before any launch, outside stream capture)
+        cudaError_t pe = cudaSuccess;
+        switch (d) {
+        case 12: pe = srmc::prepare_step_d12(); break;
+        case 13: pe = srmc::prepare_step_d13(); break;
+        case 14: pe = srmc::prepare_step_d14(); break;
+        case 15: pe = srmc::prepare_step_d15(); break;
+        case 16: pe = srmc::prepare_step_d16(); break;
+        case 17: pe = srmc::prepare_step_d17(); break;
+        case 18: pe = srmc::prepare_step_d18(); break;
+        case 19: pe = srmc::prepare_step_d19(); break;
+        }
+        if (pe != cudaSuccess) return cuda_fail(pe, "srmc_create: shared memory of the d >= 12 kernels");
+    }
     srmc_solver *s = new srmc_solver();
     Params &P = s->P;
     std::memset(&P, 0, sizeof(P));

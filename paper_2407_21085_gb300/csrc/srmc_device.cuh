@@ -14,8 +14,8 @@
 
 namespace srmc {
 
-constexpr int DMAX = 11;
-constexpr int PBMAX = 12;            // largest basis dimension: LP1 at d = 11 (12), LP2 at d = 3 (10)
+constexpr int DMAX = 19;
+constexpr int PBMAX = 20;            // largest basis dimension: LP1 at d = 19 (20), LP2 at d = 3 (10)
 
 // The quadratic monomials u_a u_b (a <= b, row order) after the linear ones
 // of a basis vector of dimension p, for d only known at run time.

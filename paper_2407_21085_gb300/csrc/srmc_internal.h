@@ -101,6 +101,23 @@ cudaError_t launch_step_d10(const Params &P, int i, bool fp64, bool lp1, int mv,
                             cudaStream_t st);
 cudaError_t launch_step_d11(const Params &P, int i, bool fp64, bool lp1, int mv, int grid, int threads,
                             cudaStream_t st);
+// d = 12..19: the same, with the block's shared memory dynamic (prepare_step_dD
+// sets the kernels' attribute once, at solver creation).
+#define SRMC_PREPARE_STEP_NAME(D) SRMC_PREPARE_STEP_NAME_(D)
+#define SRMC_PREPARE_STEP_NAME_(D) prepare_step_d##D
+#define SRMC_DECLARE_XL(D)                                                                     \
+    cudaError_t launch_step_d##D(const Params &P, int i, bool fp64, bool lp1, int mv, int grid, \
+                                 int threads, cudaStream_t st);                                \
+    cudaError_t prepare_step_d##D();
+SRMC_DECLARE_XL(12)
+SRMC_DECLARE_XL(13)
+SRMC_DECLARE_XL(14)
+SRMC_DECLARE_XL(15)
+SRMC_DECLARE_XL(16)
+SRMC_DECLARE_XL(17)
+SRMC_DECLARE_XL(18)
+SRMC_DECLARE_XL(19)
+#undef SRMC_DECLARE_XL
 cudaError_t launch_step_quad_d1(const Params &P, int i, bool fp64, bool lp1, int mv, int grid, int threads,
                                 cudaStream_t st);
 cudaError_t launch_step_quad_d2(const Params &P, int i, bool fp64, bool lp1, int mv, int grid, int threads,

@@ -618,8 +618,13 @@ template <typename R, int D, bool CV, bool ZIN>
 struct MinBlocks {
     static constexpr int value = sizeof(R) == 8 ? 1
                                : CV ? (D <= 2 ? 4 : ZIN ? SRMC_CVZMINB_HI : SRMC_CVMINB_HI)
-                                    : (D <= 2 ? SRMC_MINB_LO : D >= 9 ? SRMC_MINB_XL : SRMC_MINB_HI);
+                                    : (D <= 2 ? SRMC_MINB_LO : D >= 12 ? 2 : D >= 9 ? SRMC_MINB_XL
+                                                                                     : SRMC_MINB_HI);
 };
+
+// Units of d >= 12 hold their block's shared memory dynamically (above the
+// 48 KB of static shared memory a block may declare; about 94 KB at d = 19).
+constexpr bool DYN_SMEM = SRMC_STEP_D >= 12;
 
 // Whether phase A parks a path's basis values phi(x_i) and increments dW_i
 // in shared memory across its time loop (FP32 form, d >= SRMC_STAGE_MIN_D):
@@ -675,6 +680,10 @@ struct StepSmem {
     static constexpr int NT = COLS ? p + q + 1 : 1;
     static constexpr int TS = COLS ? MAX_THREADS + 4 : 4;
     __align__(16) float tile[NT][TS];
+    // Warp tiles with more than 8 entries per lane (d >= 12) keep their running
+    // sums in redA (each warp its own row) and their column pairs here.
+    static constexpr bool TSM = TileMoments<R, D, EA>::value && (EA + 31) / 32 > 8;
+    short2 tcol[TSM ? EA : 1];
     static constexpr int EB = p;
     double redA[MAX_WARPS][EA];
     double totA[EA];
@@ -707,7 +716,8 @@ __device__ __forceinline__ void solve_stratum(const Params &P, const int i, cons
     constexpr bool RS = sizeof(R) == 4 && EA > 24 && !TILE;
     using MA = typename Select<RS, MomentsRS<EA>, typename MomentsOf<R, EA>::type>::type;
     constexpr int TS = StepSmem<R, D, LP1>::TS;
-    constexpr int LF = (EA + 31) / 32;             // moment entries per lane (TILE)
+    constexpr bool TSM = StepSmem<R, D, LP1>::TSM;  // tile sums in shared memory
+    constexpr int LF = TSM ? 1 : (EA + 31) / 32;   // moment entries per lane held in registers (TILE)
     using MB = typename MomentsOf<R, EB>::type;
     auto &redA = sm.redA;
     auto &totA = sm.totA;
@@ -759,22 +769,36 @@ __device__ __forceinline__ void solve_stratum(const Params &P, const int i, cons
     // and the entry's running sum
     [[maybe_unused]] int colA[LF], colB[LF];
     [[maybe_unused]] double csum[LF];
-    if constexpr (TILE) {
+    // The column pair (a, b) of moment entry e: Gram (a, b) row by row for
+    // a <= b, then the Z right-hand sides (phi_a, w_l), then the Y one (phi_a, S_Y).
+    auto tile_pair = [&](int e, int &a, int &b) {
+        a = 0; b = 0;
+        if (e < EG) {
+            int rem = e;
+            while (rem >= p - a) { rem -= p - a; ++a; }
+            b = a + rem;
+        } else if (e < EG + EZ) {
+            a = (e - EG) % p;
+            b = p + (e - EG) / p;
+        } else if (e < EA) {
+            a = e - EG - EZ;
+            b = p + q;
+        }
+    };
+    if constexpr (TSM) {
+        for (int e = threadIdx.x; e < EA; e += blockDim.x) {
+            int a, b;
+            tile_pair(e, a, b);
+            sm.tcol[e] = make_short2((short)a, (short)b);
+        }
+        for (int e = lane; e < EA; e += 32) redA[warp][e] = 0.0;
+        __syncthreads();
+    } else if constexpr (TILE) {
 #pragma unroll
         for (int t = 0; t < LF; ++t) {
             const int e = lane + 32 * t;
-            int a = 0, b = 0;
-            if (e < EG) {                                  // Gram (a, b), a <= b, row by row
-                int rem = e;
-                while (rem >= p - a) { rem -= p - a; ++a; }
-                b = a + rem;
-            } else if (e < EG + EZ) {                      // Z right-hand side (l, a)
-                a = (e - EG) % p;
-                b = p + (e - EG) / p;
-            } else if (e < EA) {                           // Y right-hand side a
-                a = e - EG - EZ;
-                b = p + q;
-            }
+            int a, b;
+            tile_pair(e, a, b);
             colA[t] = a * TS + 32 * warp;
             colB[t] = b * TS + 32 * warp;
             csum[t] = 0.0;
@@ -922,6 +946,24 @@ __device__ __forceinline__ void solve_stratum(const Params &P, const int i, cons
             col[(p + q) * TS] = valid ? (float)SY : 0.0f;
             __syncwarp();
             const float *tb = &sm.tile[0][0];
+            if constexpr (TSM) {
+                for (int e = lane; e < EA; e += 32) {
+                    const short2 c = sm.tcol[e];
+                    const float *ca = tb + c.x * TS + 32 * warp, *cb = tb + c.y * TS + 32 * warp;
+                    float acc1 = 0.0f;
+#pragma unroll 2
+                    for (int r = 0; r < 32; r += 4) {
+                        const float4 a4 = *reinterpret_cast<const float4 *>(ca + r);
+                        const float4 b4 = *reinterpret_cast<const float4 *>(cb + r);
+                        acc1 = fmaf(a4.x, b4.x, acc1);
+                        acc1 = fmaf(a4.y, b4.y, acc1);
+                        acc1 = fmaf(a4.z, b4.z, acc1);
+                        acc1 = fmaf(a4.w, b4.w, acc1);
+                    }
+                    redA[warp][e] += (double)acc1;
+                }
+                __syncwarp();
+            } else {
             float acc[LF];
 #pragma unroll
             for (int t = 0; t < LF; ++t) acc[t] = 0.0f;
@@ -939,6 +981,7 @@ __device__ __forceinline__ void solve_stratum(const Params &P, const int i, cons
 #pragma unroll
             for (int t = 0; t < LF; ++t) csum[t] += (double)acc[t];
             __syncwarp();
+            }
         } else if constexpr (RS) {
             // this path's products (zero for lanes past M)
             const float Sv = valid ? (float)SZ : 0.0f;
@@ -977,7 +1020,15 @@ __device__ __forceinline__ void solve_stratum(const Params &P, const int i, cons
             if (++since_flush == FLUSH) { mA.flush(lane); since_flush = 0; }
         }
     }
-    if constexpr (TILE) {
+    if constexpr (TSM) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < EA; e += blockDim.x) {
+            double v = 0.0;
+            for (int w = 0; w < nwarps; ++w) v += redA[w][e];
+            totA[e] = v;
+        }
+        __syncthreads();
+    } else if constexpr (TILE) {
         block_totals<EA>(csum, redA, totA, lane, warp, nwarps);
     } else if constexpr (RS) {
         block_totals_rs<EA>(mA.c, mA.base, mA.rend, redA, totA, warp, nwarps);
@@ -1109,10 +1160,18 @@ template <typename R, int D, bool LP1, int MODEL, bool ZIN, bool CV>
 __global__ void __launch_bounds__(MAX_THREADS, MinBlocks<R, D, CV, ZIN>::value)
 step_kernel(const Params P, const int i)
 {
-    __shared__ StepSmem<R, D, LP1> sm;
-    for (long long t = blockIdx.x; t < P.K; t += gridDim.x) {
-        const long long k = P.order ? (long long)__ldg(P.order + t) : t;
-        solve_stratum<R, D, LP1, MODEL, ZIN, CV>(P, i, k, sm);
+    auto strata = [&](StepSmem<R, D, LP1> &sm) {
+        for (long long t = blockIdx.x; t < P.K; t += gridDim.x) {
+            const long long k = P.order ? (long long)__ldg(P.order + t) : t;
+            solve_stratum<R, D, LP1, MODEL, ZIN, CV>(P, i, k, sm);
+        }
+    };
+    if constexpr (DYN_SMEM) {
+        extern __shared__ __align__(16) unsigned char srmc_dyn_smem[];
+        strata(*reinterpret_cast<StepSmem<R, D, LP1> *>(srmc_dyn_smem));
+    } else {
+        __shared__ StepSmem<R, D, LP1> sm;
+        strata(sm);
     }
 }
 
@@ -1279,8 +1338,24 @@ auto dispatch_variant(bool lp1, int mv, bool cv, F &&f) -> decltype(f.template o
 template <typename R, bool LP1, int MODEL, bool ZIN, bool CV = false>
 cudaError_t launch_one(const Params &P, int i, int grid, int threads, cudaStream_t st)
 {
-    step_kernel<R, SRMC_STEP_D, LP1, MODEL, ZIN, CV><<<grid, threads, 0, st>>>(P, i);
+    const size_t smem = DYN_SMEM ? sizeof(StepSmem<R, SRMC_STEP_D, LP1>) : 0;
+    step_kernel<R, SRMC_STEP_D, LP1, MODEL, ZIN, CV><<<grid, threads, smem, st>>>(P, i);
     return cudaGetLastError();
+}
+
+// Units of d >= 12: allow each FP32 LP0/LP1 kernel its dynamic shared memory
+// (a function attribute, set once before the first launch, outside any
+// stream capture).
+template <typename R, bool LP1, int MODEL, bool ZIN>
+cudaError_t allow_smem_one()
+{
+    if constexpr (!DYN_SMEM) {
+        return cudaSuccess;
+    } else {
+        return cudaFuncSetAttribute(step_kernel<R, SRMC_STEP_D, LP1, MODEL, ZIN, false>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)sizeof(StepSmem<R, SRMC_STEP_D, LP1>));
+    }
 }
 
 // Units of d >= 9 carry the FP32 form without controls only (create rejects
@@ -1380,6 +1455,21 @@ int SRMC_OCC_BATCH_NAME(SRMC_STEP_D)(bool fp64, bool lp1, int mv, bool cv, int t
 }
 
 #endif  // batched form
+
+#if SRMC_STEP_KIND == 0 && SRMC_STEP_DYN == 0 && SRMC_STEP_BASIS == 1 && SRMC_STEP_D >= 12
+cudaError_t SRMC_PREPARE_STEP_NAME(SRMC_STEP_D)()
+{
+    cudaError_t e = cudaSuccess;
+    const cudaError_t r[8] = {
+        allow_smem_one<float, true, MODEL_COS, false>(), allow_smem_one<float, false, MODEL_COS, false>(),
+        allow_smem_one<float, true, MODEL_COS, true>(), allow_smem_one<float, false, MODEL_COS, true>(),
+        allow_smem_one<float, true, MODEL_LOGISTIC, true>(), allow_smem_one<float, false, MODEL_LOGISTIC, true>(),
+        allow_smem_one<float, true, MODEL_AFFINE, false>(), allow_smem_one<float, false, MODEL_AFFINE, false>()};
+    for (cudaError_t v : r)
+        if (v != cudaSuccess) e = v;
+    return e;
+}
+#endif
 
 #if SRMC_STEP_BASIS == 2
 cudaError_t SRMC_LAUNCH_STEP_QUAD_NAME(SRMC_STEP_D)(const Params &P, int i, bool fp64, bool lp1, int mv,

@@ -117,6 +117,29 @@ def test_wide_dimensions(dev, orc, d, N, M, model):
     _full_parity(dev, orc, w)
 
 
+@pytest.mark.parametrize("d,N,M", [(12, 3, 48), (15, 2, 40), (19, 3, 64)])
+@pytest.mark.parametrize("model", ["cos", "cos_z", "logistic", "logistic_lp0"])
+def test_dimensions_12_to_19(dev, orc, d, N, M, model):
+    # d = 12..19 (the paper's Tables LP1d12 to LP1d15_19): 2 cells in the first
+    # three dimensions and one (the whole line) in the others, so that the
+    # oracle solves in full while every coordinate is simulated, located and
+    # fitted (the kernels hold their shared memory dynamically from d = 12)
+    cells = [2, 2, 2] + [1] * (d - 3)
+    if model.startswith("logistic"):
+        w = W.logistic_paper(d=d, N=N, C=2, M=M, basis="lp0" if model.endswith("lp0") else "lp1")
+    else:
+        w = W.cos_model(f"d{d}", d=d, N=N, C=2, a=2.0, M=M, s0=0.3, lam=0.2, kap=0.5,
+                        kapz=0.1 if model == "cos_z" else 0.0)
+    _full_parity(dev, orc, w.replace(cells=cells))
+
+
+def test_d19_teacher_forced(dev, orc):
+    # the paper's d = 19 row (LP1, logistic model, dt = 0.2, M = 3200) on 2^10
+    # strata (2 cells in ten dimensions): steps 0, 2 and 4 on 64 strata
+    w = W.logistic_paper(d=19, N=5, C=2, M=3200).replace(cells=[2] * 10 + [1] * 9)
+    _deep(dev, orc, w, n_strata=64)
+
+
 def test_wide_dimensions_limits(dev):
     # d >= 9: FP32, equal-size strata, Euler dynamics, no controls
     torch, srmc = dev
@@ -136,7 +159,7 @@ def test_wide_dimensions_limits(dev):
         srmc.Batch([s])
     assert e.value.status == 4
     with pytest.raises(srmc.SrmcError) as e:
-        srmc.Solver(W.cos_model("d12", d=12, N=2, C=2, a=2.0, M=64, s0=0.3, lam=0.2, kap=0.5))
+        srmc.Solver(W.cos_model("d20", d=20, N=2, C=1, a=2.0, M=64, s0=0.3, lam=0.2, kap=0.5))
     assert e.value.status == 1
 
 
