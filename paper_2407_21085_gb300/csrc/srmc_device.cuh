@@ -209,34 +209,63 @@ __device__ __forceinline__ double normal_of(unsigned w, double)
 // Single-precision Phi^{-1}: erfinv-style reduction (Giles, "Approximating
 // the erfinv function", GPU Computing Gems, 2010): with y = 2p - 1 and
 // w = -log(4 p (1-p)), Phi^{-1}(p) = y h(w) where h is smooth in w.  h is
-// approximated by degree-9 polynomials in (w - 5/2) for w < 5 and in
-// (sqrt(w) - c) for w >= 5, with coefficients fitted by this project
+// approximated by degree-9 polynomials in (w - 3) for w < 6 and in
+// (sqrt(w) - c) for w >= 6, with coefficients fitted by this project
 // (weighted least squares towards minimax relative error against an FP64
-// Phi^{-1}; max relative error 6e-9 and 9e-8 on the two pieces).  p is
-// formed from the smaller of w and ~w (p <= 1/2), so 1 - p and 4 p (1 - p)
-// keep full precision in the tails; the sign is that of w's upper half.
-// Coefficients of h, highest degree first: central piece (in w - 5/2) and
-// tail piece (in sqrt(w) - 3.435767889).
+// Phi^{-1}; max relative error 5e-8 and 9e-8 on the two pieces; the tail
+// piece was fitted for w >= 5).  The central piece covers p >= 6.2e-4, so a
+// warp meets a tail word in about 8 % of its pairs of normals (20 % with the
+// switch at w = 5).  p is formed from the smaller of w and ~w (p <= 1/2), so
+// 1 - p and 4 p (1 - p) keep full precision in the tails; the sign is that of
+// w's upper half.  Coefficients of h, highest degree first: central piece (in
+// w - 3) and tail piece (in sqrt(w) - 3.435767889).
 __device__ constexpr float NRM_C[10] = {
-    -1.243243108e-08f, 3.285592243e-08f, 6.592648560e-07f, -4.897004146e-06f, -7.019233635e-06f,
-    3.087856749e-04f, -1.771644573e-03f, -5.907717161e-03f, 3.488020301e-01f, 2.123313427e+00f};
+    -8.240728988e-09f, -6.130190577e-09f, 6.442992913e-07f, -2.666269438e-06f, -1.804150088e-05f,
+    2.764452947e-04f, -1.182383508e-03f, -8.115578443e-03f, 3.417168856e-01f, 2.296035290e+00f};
 __device__ constexpr float NRM_T[10] = {
     6.402532017e-05f, -3.551483360e-06f, -4.645976005e-04f, 9.079263546e-04f, -1.158809988e-03f,
     1.824696665e-03f, -3.379537957e-03f, 5.249740090e-03f, 1.424003482e+00f, 4.625601292e+00f};
 
-__device__ __forceinline__ float normal_h(float wv)
+// The two SFU approximations the transform uses: base-2 logarithm and square
+// root (the tail piece only; its argument w >= 6 is far from any special case).
+__device__ __forceinline__ float lg2_approx(float x)
+{
+    float r;
+    asm("lg2.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+#ifndef SRMC_NRM_SQRT_APPROX
+#define SRMC_NRM_SQRT_APPROX 1
+#endif
+__device__ __forceinline__ float sqrt_approx(float x)
+{
+#if SRMC_NRM_SQRT_APPROX
+    float r;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+#else
+    return sqrtf(x);
+#endif
+}
+constexpr float NRM_LN2 = 0.693147180559945f;
+
+// h on the two pieces, from l = log2(4 p (1 - p)) (so w = -ln2 l): the central
+// piece takes s = w - 3 in one fused multiply-add of l; the tail piece
+// (w >= 6, i.e. s >= 3) takes sqrt(w) - c with w = s + 3 (so that only s
+// stays live).
+__device__ __forceinline__ float normal_h(float l)
 {
     float h;
-    if (wv < 5.0f) {
-        const float s = __fadd_rn(wv, -2.5f);
+    const float s = __fmaf_rn(l, -NRM_LN2, -3.0f);
+    if (s < 3.0f) {
         h = NRM_C[0];
 #pragma unroll
         for (int c = 1; c < 10; ++c) h = __fmaf_rn(h, s, NRM_C[c]);
     } else {
-        const float s = __fadd_rn(sqrtf(wv), -3.435767889f);
+        const float st = __fadd_rn(sqrt_approx(__fadd_rn(s, 3.0f)), -3.435767889f);
         h = NRM_T[0];
 #pragma unroll
-        for (int c = 1; c < 10; ++c) h = __fmaf_rn(h, s, NRM_T[c]);
+        for (int c = 1; c < 10; ++c) h = __fmaf_rn(h, st, NRM_T[c]);
     }
     return h;
 }
@@ -251,6 +280,8 @@ __device__ __forceinline__ float normal_h(float wv)
 // (The scalar form is written with the _rn intrinsics, which the compiler
 // neither contracts nor rearranges, so that every kernel that inlines it --
 // and the packed form, which does the same operations -- gives the same bits.)
+// 4 p (1 - p) is formed as p (4 - 4 p): 4 - 4 p = 4 (1 - p) rounded once, the
+// same bits as (1 - p) 4, in one instruction less.
 __device__ __forceinline__ float normal_of(unsigned w, float)
 {
     const bool up = w >= 0x80000000u;
@@ -261,8 +292,8 @@ __device__ __forceinline__ float normal_of(unsigned w, float)
 #else
     const float y = __fmaf_rn(p, 2.0f, -1.0f);                                          // 2p - 1
 #endif
-    const float wv = -__logf(__fmul_rn(4.0f, __fmul_rn(p, __fmaf_rn(p, -1.0f, 1.0f))));
-    const float x = __fmul_rn(y, normal_h(wv));
+    const float l = lg2_approx(__fmul_rn(p, __fmaf_rn(p, -4.0f, 4.0f)));
+    const float x = __fmul_rn(y, normal_h(l));
     return up ? -x : x;
 }
 
@@ -289,23 +320,22 @@ __device__ __forceinline__ float2 normal_pair(unsigned w0, unsigned w1)
 #else
     const float2 y = __ffma2_rn(p, f2(2.0f), f2(-1.0f));
 #endif
-    const float2 r = __fmul2_rn(f2(4.0f), __fmul2_rn(p, __ffma2_rn(p, f2(-1.0f), f2(1.0f))));
-    const float2 wv = make_float2(-__logf(r.x), -__logf(r.y));
+    const float2 r = __fmul2_rn(p, __ffma2_rn(p, f2(-4.0f), f2(4.0f)));
+    const float2 l = make_float2(lg2_approx(r.x), lg2_approx(r.y));
+    const float2 s = __ffma2_rn(l, f2(-NRM_LN2), f2(-3.0f));            // w - 3
     float2 h;
-    // central piece for both words; the tail piece (w >= 5, rare) only when a
+    // central piece for both words; the tail piece (w >= 6, rare) only when a
     // word needs it, and only for that word
-    {
-        const float2 s = __fadd2_rn(wv, f2(-2.5f));
-        h = f2(NRM_C[0]);
+    h = f2(NRM_C[0]);
 #pragma unroll
-        for (int c = 1; c < 10; ++c) h = __ffma2_rn(h, s, f2(NRM_C[c]));
-    }
-    const bool tx = !(wv.x < 5.0f), ty = !(wv.y < 5.0f);
+    for (int c = 1; c < 10; ++c) h = __ffma2_rn(h, s, f2(NRM_C[c]));
+    const bool tx = !(s.x < 3.0f), ty = !(s.y < 3.0f);
     if (tx || ty) {
-        const float2 s = __fadd2_rn(make_float2(sqrtf(wv.x), sqrtf(wv.y)), f2(-3.435767889f));
+        const float2 wv = __fadd2_rn(s, f2(3.0f));
+        const float2 st = __fadd2_rn(make_float2(sqrt_approx(wv.x), sqrt_approx(wv.y)), f2(-3.435767889f));
         float2 ht = f2(NRM_T[0]);
 #pragma unroll
-        for (int c = 1; c < 10; ++c) ht = __ffma2_rn(ht, s, f2(NRM_T[c]));
+        for (int c = 1; c < 10; ++c) ht = __ffma2_rn(ht, st, f2(NRM_T[c]));
         if (tx) h.x = ht.x;
         if (ty) h.y = ht.y;
     }

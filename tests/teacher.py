@@ -15,7 +15,14 @@ import numpy as np
 from tests import controls as CT
 
 TOL64 = 1e-10           # |dy| / (1 + |y|), |dz| / (1 + |z|) in the FP64 form
-TOL32 = 1e-4            # the same in the FP32 form
+TOL32 = 1e-4            # the same in the FP32 form, at the stratum centres
+# FP32 at the off-centre probe points: a path whose FP32 position falls on the
+# other side of a cell edge than its FP64 twin changes its response by some
+# delta; in the centred LP1 basis (u nearly uniform on [-1, 1], Gram ~ M
+# diag(1, 1/3, ..)) that moves the intercept by ~delta/M and each slope by up to
+# ~3 delta/M, so the value half a unit off the centre moves by up to
+# (1 + 3/2) delta/M: 2.5 times the centre's bound.
+TOL32_OFF = 2.5 * TOL32
 
 
 def probe_points(w, ks):
@@ -89,6 +96,10 @@ def teacher_forced(torch, orc, s, steps, n_strata, seed=0, nthreads=0, control=N
 
 
 def assert_within(w, res, where=""):
+    """Centres within TOL64 / TOL32; all probe points within TOL64 (FP64) or
+    TOL32_OFF (FP32: one edge flip weighs more on the slopes)."""
     tol = TOL64 if w.precision == "fp64" else TOL32
+    tol_all = TOL64 if w.precision == "fp64" else TOL32_OFF
     for i, e in res.items():
-        assert max(e) <= tol, (where, w.name, w.precision, i, e)
+        assert max(e[2], e[3]) <= tol, (where, w.name, w.precision, i, e, "centres")
+        assert max(e[0], e[1]) <= tol_all, (where, w.name, w.precision, i, e, "probe points")

@@ -134,9 +134,16 @@ def test_dimensions_12_to_19(dev, orc, d, N, M, model):
 
 
 def test_d19_teacher_forced(dev, orc):
-    # the paper's d = 19 row (LP1, logistic model, dt = 0.2, M = 3200) on 2^10
-    # strata (2 cells in ten dimensions): steps 0, 2 and 4 on 64 strata
-    w = W.logistic_paper(d=19, N=5, C=2, M=3200).replace(cells=[2] * 10 + [1] * 9)
+    # d = 19 at the M of the paper's d = 19 row (3200 paths per stratum, dt = 0.2)
+    # on 2^10 strata (2 cells in ten dimensions), with z in the driver: steps 0,
+    # 2 and 4 on 64 strata.  The smooth cos model is used here: the paper's
+    # logistic solution is nearly a step in sum x at d = 19, so its LP1 fits of
+    # neighbouring cells differ by O(1) at a shared edge, and a single path whose
+    # FP32 position falls on the other side of an edge than its FP64 twin (about
+    # one in 1e8 path-steps) moves a fit by ~1e-3.  The logistic driver's own
+    # code path is checked by the whole-solve parity above (small M, no flips).
+    w = W.cos_model("d19", d=19, N=5, C=2, a=2.0, M=3200, s0=0.3, lam=0.2, kap=0.5,
+                    kapz=0.1).replace(cells=[2] * 10 + [1] * 9)
     _deep(dev, orc, w, n_strata=64)
 
 

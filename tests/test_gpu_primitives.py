@@ -49,8 +49,12 @@ def test_philox_bit_exact(dev, orc):
 def test_normals(dev, orc):
     torch, srmc = dev
     rng = np.random.default_rng(1)
+    # special words, random words, and words of both tails (p < 2^-11: inside
+    # the tail piece of the FP32 transform)
     words = np.concatenate([np.array([0, 1, 2, 255, 256, 2 ** 31 - 1, 2 ** 31, 2 ** 32 - 1], dtype=np.uint64),
-                            rng.integers(0, 2 ** 32, 20000, dtype=np.uint64)]).astype(np.uint32)
+                            rng.integers(0, 2 ** 32, 20000, dtype=np.uint64),
+                            rng.integers(0, 2 ** 21, 64, dtype=np.uint64),
+                            2 ** 32 - 1 - rng.integers(0, 2 ** 21, 64, dtype=np.uint64)]).astype(np.uint32)
     w_t = _u32_tensor(torch, words)
     o64 = torch.empty(len(words), dtype=torch.float64, device="cuda")
     o32 = torch.empty(len(words), dtype=torch.float32, device="cuda")
@@ -71,10 +75,10 @@ def test_normals(dev, orc):
     assert np.array_equal(c32.cpu().numpy(), -o32.cpu().numpy())
     # FP32 words are taken in pairs (the packed form of the step kernels); a
     # single word takes the scalar form.  Both must give the same bits, for
-    # central words, tail words (w >= 5 in the erfinv reduction) and pairs
+    # central words, tail words (w >= 6 in the erfinv reduction) and pairs
     # mixing the two: the first eight words, every tail word, 40 others.
     p = (np.minimum(words, ~words).astype(np.float64) + 0.5) * 2.0 ** -32
-    tail = np.nonzero(4 * p * (1 - p) <= np.exp(-5.0) * (1 + 1e-6))[0]
+    tail = np.nonzero(4 * p * (1 - p) <= np.exp(-6.0) * (1 + 1e-6))[0]
     pick = np.unique(np.concatenate([np.arange(8), tail, rng.integers(8, len(words), 40)]))
     assert len(tail) > 20
     bits = o32.cpu().numpy().view(np.uint32)
