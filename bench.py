@@ -350,6 +350,80 @@ def run_gpu(args):
     return out, rank, w
 
 
+# ---- the precision form (cfg3): FP32 paths + FP64 solves against all-FP64 ---------
+def precision_compare(args, stream):
+    """cfg3 (d = 4, 12^4 strata on [-3.5, 3.5]^4, N = 50, z in the driver): the FP32
+    form (FP32 paths and moments, FP64 Cholesky solves) at full size, device-timed;
+    then the FP32 form and the all-FP64 GPU form on the same Philox streams at
+    cfg3's shape with M = --prec-M, and the FP32 error per result against the
+    FP64 form: y and z of every step at every stratum centre and at the 2d points
+    half a basis unit off it along each axis (the FP64 form matches the FP64
+    oracle within 1e-10 (1 + |y|) in the parity tests)."""
+    import torch
+    from paper_2407_21085_gb300 import srmc
+
+    def solve_timed(w, reps, warm):
+        s = srmc.Solver(w)
+        if warm:
+            s.srmc_solve(stream)
+            torch.cuda.synchronize()
+        ms = []
+        for _ in range(reps):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            s.srmc_solve(stream)
+            b.record(stream)
+            b.synchronize()
+            ms.append(a.elapsed_time(b))
+        return s, statistics.median(ms) / 1e3
+
+    full = W.cfg3()
+    s, sec = solve_timed(full, 2, True)
+    s.close()
+    out = {"workload": full.name, "fp32_full": {"M": full.M, "s_per_solve": sec,
+                                                "path_steps_per_s": full.path_steps() / sec}}
+    w32 = W.cfg3(M=args.prec_M, name=f"cfg3_d4_K20736_N50_M{args.prec_M}")
+    w64 = w32.replace(precision="fp64")
+    s32, t32 = solve_timed(w32, 1, True)
+    s64, t64 = solve_timed(w64, 1, False)
+    ctr = s32.centres()
+    unit = torch.tensor([(w32.hi[l] - w32.lo[l]) / w32.cells[l] / 2 for l in range(w32.d)],
+                        dtype=torch.float64, device=ctr.device)
+    pts = [ctr]
+    for l in range(w32.d):
+        for sgn in (-0.5, 0.5):
+            p = ctr.clone()
+            p[:, l] += sgn * unit[l]
+            pts.append(p)
+    pts = torch.cat(pts)
+    ey_max = ez_max = ey_ss = ez_ss = 0.0
+    n = 0
+    per_step = []
+    for i in range(w32.N):
+        y32, z32 = s32.evaluate(i, pts)
+        y64, z64 = s64.evaluate(i, pts)
+        ey = (y32 - y64).abs() / (1 + y64.abs())
+        ez = (z32 - z64).abs() / (1 + z64.abs())
+        per_step.append((float(ey.max()), float(ez.max())))
+        ey_max, ez_max = max(ey_max, per_step[-1][0]), max(ez_max, per_step[-1][1])
+        ey_ss += float((ey * ey).sum())
+        ez_ss += float((ez * ez).sum())
+        n += ey.numel()
+    nz = n * w32.q
+    s32.close()
+    s64.close()
+    out["same_streams"] = {
+        "M": args.prec_M, "path_steps": w32.path_steps(),
+        "fp32": {"s_per_solve": t32, "path_steps_per_s": w32.path_steps() / t32},
+        "fp64": {"s_per_solve": t64, "path_steps_per_s": w64.path_steps() / t64},
+        "fp32_vs_fp64": {"points_per_step": int(pts.shape[0]), "steps": w32.N,
+                         "y_max": ey_max, "z_max": ez_max,
+                         "y_rms": math.sqrt(ey_ss / n), "z_rms": math.sqrt(ez_ss / nz),
+                         "max_by_step_0_mid_last": [per_step[0], per_step[w32.N // 2], per_step[-1]],
+                         "measure": "|d| / (1 + |FP64 value|) of y and of each z component"}}
+    return out
+
+
 # ---- the second half of the metric: time to sup|y - u| <= eps, CV vs plain ------
 def cv_compare(args, stream):
     """cfg5 (d = 6, 8^6 strata, N = 40): the plain scheme at M = 4096 against the
@@ -786,6 +860,9 @@ def main():
     ap.add_argument("--block-threads", type=int, default=0, help="threads per stratum block (0: library)")
     ap.add_argument("--no-cv-compare", action="store_true", help="skip the CV-vs-plain comparison (cfg5)")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-form measurement (cfg4)")
+    ap.add_argument("--no-precision", action="store_true",
+                    help="skip the precision-form measurement (cfg3: FP32 vs all-FP64)")
+    ap.add_argument("--prec-M", type=int, default=256, help="paths per stratum of the FP32 vs FP64 comparison")
     ap.add_argument("--batch-reps", type=int, default=2)
     ap.add_argument("--cv-small", action="store_true",
                     help="CV comparison on 5^6 strata of the same width (for profiler captures)")
@@ -829,6 +906,9 @@ def main():
     if rank == 0 and out["n_gpus"] == 1 and not args.no_batched:
         import torch
         out["batched_cfg4"] = batched_compare(args, torch.cuda.current_stream())
+    if rank == 0 and out["n_gpus"] == 1 and not args.no_precision:
+        import torch
+        out["precision_cfg3"] = precision_compare(args, torch.cuda.current_stream())
     if rank == 0:
         if not args.no_cpu_baseline and out["n_gpus"] == 1:
             out["cpu_baseline"] = cpu_baseline(w)
