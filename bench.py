@@ -43,6 +43,13 @@ def flops_per_path_step(d: int) -> float:
     return 2.0 * d * d + 13.0 * d + 20.0 + 18.0 * d
 
 
+def z_eval_flops(d: int) -> float:
+    """The part of flops_per_path_step that evaluates z at every path-step: the
+    d (d + 1) multiply-adds of the z row and the 2 d of its clamps.  A driver that
+    does not read z (the cos model without kapz) needs none of it."""
+    return 2.0 * d * (d + 1) + 2.0 * d
+
+
 def fp32_peak_tflops(sms: int, mhz: float) -> float:
     """FP32 FMA pipe peak from unit counts: SMs x 128 lanes x 2 FLOP x clock."""
     return sms * 128 * 2 * mhz * 1e6 / 1e12
@@ -319,6 +326,9 @@ def run_gpu(args):
     peak_mhz = 2070.0
     peak_units = fp32_peak_tflops(sms, peak_mhz)
     peak = fma_peak["tflops"]
+    reads_z = (w.model != "cos" or (len(w.params) > 2 and w.params[2] != 0.0) or control_kind(args) is not False
+               or any(v != 0.0 for v in list(w.b or []) + list(w.theta or [])))
+    needed = flops_per_path_step(w.d) - (0.0 if reads_z else z_eval_flops(w.d))
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -341,6 +351,11 @@ def run_gpu(args):
                      "peak_probe": fma_peak,
                      "peak_unit_count": peak_units,
                      "frac_of_unit_count": achieved / peak_units,
+                     "flops_per_unit_needed": needed,
+                     "frac_of_needed_flops": achieved * needed / flops_per_path_step(w.d) / peak,
+                     "needed_basis": "flops_per_unit less the z evaluation (z_eval_flops) when the driver "
+                                     "does not read z and no control runs: the work this workload's "
+                                     "kernel must do",
                      "unit_count_basis": f"{sms} SMs x 128 FP32 lanes x 2 x {peak_mhz:.0f} MHz"},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": tab_bytes},
         "gpu_launches": w.N * args.steps,
@@ -354,38 +369,47 @@ def run_gpu(args):
 def precision_compare(args, stream):
     """cfg3 (d = 4, 12^4 strata on [-3.5, 3.5]^4, N = 50, z in the driver): the FP32
     form (FP32 paths and moments, FP64 Cholesky solves) at full size, device-timed;
-    then the FP32 form and the all-FP64 GPU form on the same Philox streams at
-    cfg3's shape with M = --prec-M, and the FP32 error per result against the
-    FP64 form: y and z of every step at every stratum centre and at the 2d points
-    half a basis unit off it along each axis (the FP64 form matches the FP64
-    oracle within 1e-10 (1 + |y|) in the parity tests)."""
+    then the FP32 error per result against the all-FP64 GPU form on the same Philox
+    streams (the FP64 form matches the FP64 oracle within 1e-10 (1 + |y|) in the
+    parity tests).  The FP32 form solves cfg3's shape with M = --prec-M; an FP64
+    solver is given those rows (srmc_set_rows) and fits steps N-1, N/2 and 0 from
+    them, so both fit each step from the same later functions (teacher forcing on
+    the GPU); y and z are compared at every stratum centre and at the 2d points
+    half a basis unit off it along each axis."""
     import torch
     from paper_2407_21085_gb300 import srmc
 
-    def solve_timed(w, reps, warm):
-        s = srmc.Solver(w)
-        if warm:
-            s.srmc_solve(stream)
-            torch.cuda.synchronize()
-        ms = []
-        for _ in range(reps):
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            s.srmc_solve(stream)
-            b.record(stream)
-            b.synchronize()
-            ms.append(a.elapsed_time(b))
-        return s, statistics.median(ms) / 1e3
+    def ev():
+        return torch.cuda.Event(enable_timing=True)
 
     full = W.cfg3()
-    s, sec = solve_timed(full, 2, True)
+    s = srmc.Solver(full)
+    s.srmc_solve(stream)
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(2):
+        a, b = ev(), ev()
+        a.record(stream)
+        s.srmc_solve(stream)
+        b.record(stream)
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
     s.close()
+    sec = statistics.median(ms) / 1e3
     out = {"workload": full.name, "fp32_full": {"M": full.M, "s_per_solve": sec,
                                                 "path_steps_per_s": full.path_steps() / sec}}
+
     w32 = W.cfg3(M=args.prec_M, name=f"cfg3_d4_K20736_N50_M{args.prec_M}")
     w64 = w32.replace(precision="fp64")
-    s32, t32 = solve_timed(w32, 1, True)
-    s64, t64 = solve_timed(w64, 1, False)
+    s32 = srmc.Solver(w32)
+    s32.srmc_solve(stream)
+    t = s32.srmc_table()
+    y32t = torch.empty((w32.N, w32.K, t["ry"]), dtype=torch.float64, device="cuda")
+    z32t = torch.empty((w32.N, w32.K, t["rz"]), dtype=torch.float64, device="cuda")
+    s32.srmc_read_table(y32t, z32t, stream)
+    s64 = srmc.Solver(w64)
+    for i in range(w64.N - 1, -1, -1):
+        s64.srmc_set_rows(i, y32t[i], z32t[i], stream)
     ctr = s32.centres()
     unit = torch.tensor([(w32.hi[l] - w32.lo[l]) / w32.cells[l] / 2 for l in range(w32.d)],
                         dtype=torch.float64, device=ctr.device)
@@ -396,31 +420,35 @@ def precision_compare(args, stream):
             p[:, l] += sgn * unit[l]
             pts.append(p)
     pts = torch.cat(pts)
-    ey_max = ez_max = ey_ss = ez_ss = 0.0
-    n = 0
-    per_step = []
-    for i in range(w32.N):
+    steps = {}
+    fp64_ms, fp64_units = 0.0, 0
+    for i in (w64.N - 1, w64.N // 2, 0):
+        a, b = ev(), ev()
+        a.record(stream)
+        s64.srmc_solve_step(i, stream)
+        b.record(stream)
+        b.synchronize()
+        fp64_ms += a.elapsed_time(b)
+        fp64_units += w64.K * w64.M * (w64.N - i)
         y32, z32 = s32.evaluate(i, pts)
         y64, z64 = s64.evaluate(i, pts)
         ey = (y32 - y64).abs() / (1 + y64.abs())
         ez = (z32 - z64).abs() / (1 + z64.abs())
-        per_step.append((float(ey.max()), float(ez.max())))
-        ey_max, ez_max = max(ey_max, per_step[-1][0]), max(ez_max, per_step[-1][1])
-        ey_ss += float((ey * ey).sum())
-        ez_ss += float((ez * ez).sum())
-        n += ey.numel()
-    nz = n * w32.q
+        ezm = ez.max(dim=1).values
+        centre = slice(0, ctr.shape[0])
+        steps[str(i)] = {"y_max": float(ey.max()), "z_max": float(ez.max()),
+                         "y_max_centres": float(ey[centre].max()), "z_max_centres": float(ez[centre].max()),
+                         "y_rms": float((ey * ey).mean().sqrt()), "z_rms": float((ez * ez).mean().sqrt()),
+                         "frac_points_within_1e-4": float(((ey <= 1e-4) & (ezm <= 1e-4)).double().mean())}
+        s64.srmc_set_rows(i, y32t[i], z32t[i], stream)
     s32.close()
     s64.close()
-    out["same_streams"] = {
-        "M": args.prec_M, "path_steps": w32.path_steps(),
-        "fp32": {"s_per_solve": t32, "path_steps_per_s": w32.path_steps() / t32},
-        "fp64": {"s_per_solve": t64, "path_steps_per_s": w64.path_steps() / t64},
-        "fp32_vs_fp64": {"points_per_step": int(pts.shape[0]), "steps": w32.N,
-                         "y_max": ey_max, "z_max": ez_max,
-                         "y_rms": math.sqrt(ey_ss / n), "z_rms": math.sqrt(ez_ss / nz),
-                         "max_by_step_0_mid_last": [per_step[0], per_step[w32.N // 2], per_step[-1]],
-                         "measure": "|d| / (1 + |FP64 value|) of y and of each z component"}}
+    out["fp32_vs_fp64"] = {
+        "M": args.prec_M, "points_per_step": int(pts.shape[0]), "by_step": steps,
+        "fp64_path_steps_per_s": fp64_units / (fp64_ms / 1e3),
+        "measure": "|d| / (1 + |FP64 value|) of y and of each z component; step i fitted in FP32 (the "
+                   "FP32 form's own solve) and in FP64 (an FP64 solver given the FP32 solve's rows of "
+                   "steps > i), same Philox streams"}
     return out
 
 
@@ -862,7 +890,7 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-form measurement (cfg4)")
     ap.add_argument("--no-precision", action="store_true",
                     help="skip the precision-form measurement (cfg3: FP32 vs all-FP64)")
-    ap.add_argument("--prec-M", type=int, default=256, help="paths per stratum of the FP32 vs FP64 comparison")
+    ap.add_argument("--prec-M", type=int, default=4096, help="paths per stratum of the FP32 vs FP64 comparison")
     ap.add_argument("--batch-reps", type=int, default=2)
     ap.add_argument("--cv-small", action="store_true",
                     help="CV comparison on 5^6 strata of the same width (for profiler captures)")

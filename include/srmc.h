@@ -231,6 +231,18 @@ srmc_status srmc_table(const srmc_solver *s, const double **dev_y64, const doubl
  * device or pinned destinations; the caller synchronises before reading. */
 srmc_status srmc_read_table(const srmc_solver *s, double *dst_y, double *dst_z, void *stream);
 
+/* Install the fitted rows of step i of every stratum (Alg. SRMDP: the
+ * functions y_i, z_i that the fits of the steps before i read), in place of
+ * the solver's own: src_y [K][ry] and src_z [K][rz] doubles in the layout of
+ * srmc_table (centred basis; e.g. the step-i slice of another solver's tables
+ * on the same strata and basis), caller-owned, device or host (pinned or
+ * pageable).  The FP32 form's copies of the rows are refreshed (round to
+ * nearest).  If the rows of steps i+1..N-1 are present (solved or installed),
+ * srmc_solve_step(i - 1) may follow: with installed rows the fit of step i-1
+ * reads the given functions (teacher forcing).  Asynchronous on stream;
+ * SRMC_ERR_INVALID_ARG for a NULL argument or i outside [0, N). */
+srmc_status srmc_set_rows(srmc_solver *s, int i, const double *src_y, const double *src_z, void *stream);
+
 /* Martingale control variate (an extension of Alg. SRMDP, not in the
  * paper): with rows beta_{j,k} installed, every response of cloud C_{i,k}
  * loses the control built from zc_j(x) = T_Cz(beta_{j,k} . phi(x)), x in H_k:

@@ -967,6 +967,39 @@ srmc_status srmc_read_table(const srmc_solver *s, double *dst_y, double *dst_z, 
 }
 
 namespace {
+// FP32 copies (round to nearest) of the K rows of one step of the FP64 tables.
+__global__ void rows_to_fp32_kernel(const Params P, long long off)
+{
+    const int qp = P.q * P.p;
+    for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < P.K;
+         r += (long long)gridDim.x * blockDim.x) {
+        const long long row = off + r;
+        for (int a = 0; a < P.p; ++a) P.Y32[row * P.ry32 + a] = (float)P.Y64[row * P.ry64 + a];
+        for (int a = 0; a < qp; ++a) P.Z32[row * P.rz32 + a] = (float)P.Z64[row * P.rz64 + a];
+    }
+}
+}  // namespace
+
+srmc_status srmc_set_rows(srmc_solver *s, int i, const double *src_y, const double *src_z, void *stream)
+{
+    if (!s || !src_y || !src_z) return fail(SRMC_ERR_INVALID_ARG, "srmc_set_rows: NULL argument");
+    if (i < 0 || i >= s->P.N) return fail(SRMC_ERR_INVALID_ARG, "srmc_set_rows: i out of range");
+    const cudaStream_t st = (cudaStream_t)stream;
+    const size_t K = (size_t)s->P.K, off = (size_t)i * K;
+    SRMC_CUDA(cudaMemcpyAsync(s->Y64 + off * s->P.ry64, src_y, sizeof(double) * K * s->P.ry64, cudaMemcpyDefault,
+                              st), "srmc_set_rows: copy y");
+    SRMC_CUDA(cudaMemcpyAsync(s->Z64 + off * s->P.rz64, src_z, sizeof(double) * K * s->P.rz64, cudaMemcpyDefault,
+                              st), "srmc_set_rows: copy z");
+    if (s->P.Y32) {
+        const int grid = (int)std::min<size_t>((K + 255) / 256, 65535);
+        rows_to_fp32_kernel<<<grid, 256, 0, st>>>(s->P, (long long)off);
+        SRMC_CUDA(cudaGetLastError(), "srmc_set_rows: FP32 copies");
+    }
+    if (i + 1 == s->done_from) s->done_from = i;      // steps i..N-1 are present
+    return SRMC_OK;
+}
+
+namespace {
 // [N][K][q][p] -> padded rows of the FP64 table and of the binary16 table of
 // the FP32 form (round to nearest even, saturated at +-65504).
 __global__ void repack_control_kernel(const Params P, const double *src, double *c64, __half *c16)

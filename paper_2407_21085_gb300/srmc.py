@@ -78,6 +78,8 @@ def lib():
                                      C.POINTER(i_), C.POINTER(ll)]
             L.srmc_stats.argtypes = [vp, C.POINTER(C.c_ulonglong)]
             L.srmc_read_table.argtypes = [vp, vp, vp, vp]
+            L.srmc_set_rows.argtypes = [vp, i_, vp, vp, vp]
+            L.srmc_set_rows.restype = C.c_int
             L.srmc_closed_form_error.argtypes = [vp, vp, vp]
             L.srmc_closed_form_error_inner.argtypes = [vp, vp, vp]
             L.srmc_closed_form_error_inner.restype = C.c_int
@@ -233,6 +235,11 @@ class Solver:
     def srmc_read_table(self, dst_y, dst_z, stream=None):
         """Copy the FP64 tables into caller tensors (host, pinned or device)."""
         _check(lib().srmc_read_table(self._h, _ptr(dst_y), _ptr(dst_z), _stream(stream)))
+
+    def srmc_set_rows(self, i, src_y, src_z, stream=None):
+        """Install the rows of step i from tensors [K][ry], [K][rz] (float64,
+        the layout of srmc_table; host or device)."""
+        _check(lib().srmc_set_rows(self._h, int(i), _ptr(src_y), _ptr(src_z), _stream(stream)))
 
     def srmc_set_control(self, rows):
         """rows: numpy [N][K][q][p] float64 (host) or a CUDA float64 tensor."""

@@ -67,3 +67,9 @@ def test_oracle_time_extrapolation():
     plan = bench.oracle_plan(w, 8, single=False)
     assert [i for i, _ in plan] == [0, w.N // 2, w.N - 1] and plan[2][1] > plan[0][1]
     assert all(n == 1 for _, n in bench.oracle_plan(w, 1, single=True)[:2])
+
+
+def test_z_evaluation_share_of_the_flop_count():
+    # the z row's multiply-adds d (d + 1) and its d clamps, inside 2 d^2 + 13 d + 20
+    assert [bench.z_eval_flops(d) for d in (1, 2, 6)] == [6.0, 16.0, 96.0]
+    assert bench.flops_per_path_step(6) - bench.z_eval_flops(6) == 182.0

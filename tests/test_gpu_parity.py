@@ -453,6 +453,55 @@ def test_graph_solve_equals_step_launches(dev):
     assert torch.equal(ya, yb) and torch.equal(za, zb)
 
 
+def _tables(torch, s):
+    t = s.srmc_table()
+    w = s.w
+    y = torch.empty((w.N, w.K, t["ry"]), dtype=torch.float64, device="cuda")
+    z = torch.empty((w.N, w.K, t["rz"]), dtype=torch.float64, device="cuda")
+    s.srmc_read_table(y, z)
+    torch.cuda.synchronize()
+    return y, z
+
+
+def test_set_rows_teacher_forcing_on_the_gpu(dev):
+    # srmc_set_rows installs another solver's rows: (1) a fresh solver given all
+    # of A's rows holds A's tables bit for bit, and refitting its step i from A's
+    # rows of the later steps (same precision, same streams) gives A's step i bit
+    # for bit; (2) an FP32 solver given the FP64 solver's rows of the later steps
+    # fits every step within the FP32 bound of the FP64 fit (teacher forcing on
+    # the GPU, the per-step precision check of the bench).
+    torch, srmc = dev
+    w64 = W.cfg2(C=8, N=6, M=512, kapz=0.1, precision="fp64", name="cfg2_set_rows")
+    a = srmc.Solver(w64)
+    a.srmc_solve()
+    ya, za = _tables(torch, a)
+    b = srmc.Solver(w64)
+    with pytest.raises(srmc.SrmcError):
+        b.srmc_solve_step(0)                     # steps > 0 are neither solved nor installed
+    for i in range(w64.N - 1, -1, -1):
+        b.srmc_set_rows(i, ya[i], za[i])
+    yb, zb = _tables(torch, b)
+    assert torch.equal(ya, yb) and torch.equal(za, zb)
+    for i in range(w64.N - 1, -1, -1):
+        b.srmc_solve_step(i)
+        yb, zb = _tables(torch, b)
+        assert torch.equal(ya[i], yb[i]) and torch.equal(za[i], zb[i]), i
+        b.srmc_set_rows(i, ya[i], za[i])
+    c = srmc.Solver(w64.replace(precision="fp32"))
+    for i in range(w64.N - 1, -1, -1):
+        c.srmc_set_rows(i, ya[i], za[i])
+    x = T.probe_points(w64, np.arange(w64.K))
+    xt = torch.from_numpy(x).cuda()
+    for i in range(w64.N - 1, -1, -1):
+        c.srmc_solve_step(i)
+        gy, gz = (t.cpu().numpy() for t in c.evaluate(i, xt))
+        ry, rz = (t.cpu().numpy() for t in a.evaluate(i, xt))
+        _check(w64.replace(precision="fp32"), gy, gz, ry, rz, where=f"step {i}")
+        c.srmc_set_rows(i, ya[i], za[i])
+    for s in (a, b, c):
+        s.close()
+
+
 @pytest.mark.parametrize("model", ["cos", "logistic"])
 def test_closed_form_error_kernel(dev, model):
     # The on-device error reduction equals the same statistics computed on the
