@@ -723,10 +723,30 @@ def batched_compare(args, stream):
     # the three strategies as timed by the tuner (one whole-batch solve each)
     t_mode = dict(zip(("rounds", "branches", "persistent"), (v / 1e3 for v in batch.srmc_batch_strategy_ms())))
 
-    def sequential():
-        for s in solvers:
+    # one after another, with CUDA events around every instance's solve
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in solvers]
+
+    def sequential(record):
+        for s, (a, b) in zip(solvers, evs):
+            if record:
+                a.record(stream)
             s.srmc_solve(stream)
-    t_seq = timed(sequential, 1)
+            if record:
+                b.record(stream)
+    sequential(False)
+    torch.cuda.synchronize()
+    a0, b0 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a0.record(stream)
+    sequential(True)
+    b0.record(stream)
+    torch.cuda.synchronize()
+    t_seq = a0.elapsed_time(b0) / 1e3
+    per_inst = [a.elapsed_time(b) / 1e3 for a, b in evs]
+    # The instances with K >= 4096 strata fill the GPU on their own (every
+    # launch is several waves of stratum blocks): no strategy that keeps the
+    # kernels can solve them in less than the sum of their single solves.
+    big = [r for r, w in enumerate(ws) if w.K >= 4096]
+    floor_s = sum(per_inst[r] for r in big)
     batch.close()
     for s in solvers:
         s.close()
@@ -734,6 +754,10 @@ def batched_compare(args, stream):
             "batched_s": t_batch, "batched_path_steps_per_s": units / t_batch,
             "sequential_s": t_seq, "sequential_path_steps_per_s": units / t_seq,
             "speedup": t_seq / t_batch, "tuned_threads_per_group": threads, "tune_s": tune_s,
+            "floor_s": floor_s, "batched_over_floor": t_batch / floor_s,
+            "floor_basis": f"sum of the single-instance solve times of the {len(big)} instances with "
+                           f"K >= 4096 strata ({100.0 * sum(ws[r].path_steps() for r in big) / units:.0f} % of "
+                           "the path-steps), each of which fills the GPU alone",
             "strategy_s": t_mode,
             "strategy": ["rounds of multi-instance launches", "one graph branch per instance",
                          "one persistent launch per kernel variant"][mode]}
