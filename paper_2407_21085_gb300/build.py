@@ -2,12 +2,12 @@
 
 The step kernel is compiled once per dimension D = 1..19 (-DSRMC_STEP_D=D) so
 that per-path state stays in registers, and once per kind of strata
-(-DSRMC_STEP_KIND: equal size, equal probability) and of dynamics
-(-DSRMC_STEP_DYN: Euler, exact) and of basis (-DSRMC_STEP_BASIS=2: quadratic
-local polynomials, d <= 3) so that each kernel carries only its own cell
-location, chain step and basis; the objects are compiled in parallel and linked
-with the C-ABI translation unit into one shared library under
-``paper_2407_21085_gb300/_build``.
+(-DSRMC_STEP_KIND: equal size, equal probability), of dynamics
+(-DSRMC_STEP_DYN: Euler, exact, Euler with a non-diagonal sigma) and of basis
+(-DSRMC_STEP_BASIS=2: quadratic local polynomials, d <= 3) so that each kernel
+carries only its own cell location, chain step and basis; the objects are
+compiled in parallel and linked with the C-ABI translation unit into one shared
+library under ``paper_2407_21085_gb300/_build``.
 """
 from __future__ import annotations
 
@@ -100,6 +100,8 @@ def build(force: bool = False, verbose: bool = False, jobs: int | None = None,
              for kind, tag, dims in ((0, "", DIMS), (1, "prob_", NARROW_DIMS)) for D in dims]
     units += [(os.path.join(CSRC, "srmc_step.cu"), os.path.join(out, f"step_exact_d{D}.o"),
                [f"-DSRMC_STEP_D={D}", "-DSRMC_STEP_DYN=1"] + extra_defs) for D in NARROW_DIMS]
+    units += [(os.path.join(CSRC, "srmc_step.cu"), os.path.join(out, f"step_dense_d{D}.o"),
+               [f"-DSRMC_STEP_D={D}", "-DSRMC_STEP_DYN=2"] + extra_defs) for D in NARROW_DIMS]
     units += [(os.path.join(CSRC, "srmc_step.cu"), os.path.join(out, f"step_quad_d{D}.o"),
                [f"-DSRMC_STEP_D={D}", "-DSRMC_STEP_BASIS=2"] + extra_defs) for D in LP2_DIMS]
     for name in sorted(os.listdir(CSRC)):

@@ -338,8 +338,8 @@ srmc_status srmc_batch_create(srmc_solver *const *solvers, int n, srmc_batch **o
         if (solvers[r]->fp64) return bfail(SRMC_ERR_UNSUPPORTED, "srmc_batch_create: FP32 solvers only");
         if (solvers[r]->P.kind != 0)
             return bfail(SRMC_ERR_UNSUPPORTED, "srmc_batch_create: equal-size strata only");
-        if (solvers[r]->exact)
-            return bfail(SRMC_ERR_UNSUPPORTED, "srmc_batch_create: Euler dynamics only");
+        if (solvers[r]->exact || solvers[r]->dense)
+            return bfail(SRMC_ERR_UNSUPPORTED, "srmc_batch_create: Euler dynamics with a diagonal sigma only");
         if (solvers[r]->lp2)
             return bfail(SRMC_ERR_UNSUPPORTED, "srmc_batch_create: LP0 and LP1 only");
         if (solvers[r]->P.model == srmc::MODEL_USER)

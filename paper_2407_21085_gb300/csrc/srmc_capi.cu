@@ -159,6 +159,19 @@ cudaError_t launch_step(const srmc_solver *s, int i, cudaStream_t st)
         }
         return cudaErrorInvalidValue;
     }
+    if (s->dense) {
+        switch (P.d) {
+        case 1: return srmc::launch_step_dense_d1(P, i, s->fp64, s->lp1, mv, grid, s->threads, st);
+        case 2: return srmc::launch_step_dense_d2(P, i, s->fp64, s->lp1, mv, grid, s->threads, st);
+        case 3: return srmc::launch_step_dense_d3(P, i, s->fp64, s->lp1, mv, grid, s->threads, st);
+        case 4: return srmc::launch_step_dense_d4(P, i, s->fp64, s->lp1, mv, grid, s->threads, st);
+        case 5: return srmc::launch_step_dense_d5(P, i, s->fp64, s->lp1, mv, grid, s->threads, st);
+        case 6: return srmc::launch_step_dense_d6(P, i, s->fp64, s->lp1, mv, grid, s->threads, st);
+        case 7: return srmc::launch_step_dense_d7(P, i, s->fp64, s->lp1, mv, grid, s->threads, st);
+        case 8: return srmc::launch_step_dense_d8(P, i, s->fp64, s->lp1, mv, grid, s->threads, st);
+        }
+        return cudaErrorInvalidValue;
+    }
     if (s->exact) {
         switch (P.d) {
         case 1: return srmc::launch_step_exact_d1(P, i, s->fp64, s->lp1, mv, grid, s->threads, st);
@@ -394,10 +407,16 @@ srmc_status srmc_create(const srmc_problem *pr, const srmc_strata *sa, const srm
     if (pr->N < 1 || pr->N > 1000000) return fail(SRMC_ERR_INVALID_ARG, "N must be in [1, 1e6]");
     if (!(pr->T > 0.0) || !std::isfinite(pr->T)) return fail(SRMC_ERR_INVALID_ARG, "T must be > 0");
     if (!pr->b || !pr->sigma) return fail(SRMC_ERR_INVALID_ARG, "b and sigma are required");
+    bool dense = false;                  // sigma has an off-diagonal entry
     for (int l = 0; l < d; ++l)
-        for (int r = 0; r < q; ++r)
-            if (l != r && pr->sigma[l * q + r] != 0.0)
-                return fail(SRMC_ERR_UNSUPPORTED, "this build requires a diagonal sigma");
+        for (int r = 0; r < q; ++r) {
+            if (!std::isfinite(pr->sigma[l * q + r])) return fail(SRMC_ERR_INVALID_ARG, "sigma must be finite");
+            if (l != r && pr->sigma[l * q + r] != 0.0) dense = true;
+        }
+    if (dense && (d > srmc::SD_DMAX || pr->dynamics != SRMC_DYN_EULER || pr->model == SRMC_MODEL_USER ||
+                  cf->basis == SRMC_LP2 || sa->kind != SRMC_STRATA_EQUAL_SIZE))
+        return fail(SRMC_ERR_UNSUPPORTED, "a non-diagonal sigma is built for d <= 8, Euler dynamics, "
+                                          "equal-size strata, LP0/LP1 and the built-in models");
     if (pr->model < SRMC_MODEL_COS || pr->model > SRMC_MODEL_USER)
         return fail(SRMC_ERR_INVALID_ARG, "unknown model");
     if (pr->model == SRMC_MODEL_USER && (!pr->user_source || !pr->user_source[0]))
@@ -502,6 +521,7 @@ srmc_status srmc_create(const srmc_problem *pr, const srmc_strata *sa, const srm
     s->mv = pr->model == SRMC_MODEL_COS ? (kapz != 0.0 || has_drift ? srmc::MV_COS_Z : srmc::MV_COS)
           : pr->model == SRMC_MODEL_LOGISTIC ? srmc::MV_LOGISTIC : srmc::MV_AFFINE;
     s->exact = pr->dynamics == SRMC_DYN_EXACT;
+    s->dense = dense;
     if (pr->model == SRMC_MODEL_USER) {
         // user model: the run-time compiled kernels read z at every path point
         s->mv = srmc::MV_COS_Z;
@@ -556,6 +576,14 @@ srmc_status srmc_create(const srmc_problem *pr, const srmc_strata *sa, const srm
         }
         P.A_f[l] = (float)P.A[l]; P.c_f[l] = (float)P.c[l];
         P.s1_f[l] = (float)P.s1[l]; P.s2_f[l] = (float)P.s2[l]; P.theta_f[l] = (float)th;
+    }
+    if (dense) {
+        P.dense = 1;
+        for (int l = 0; l < d; ++l)
+            for (int r = 0; r < d; ++r) {
+                P.sd[l * d + r] = pr->sigma[l * q + r];
+                P.sd_f[l * d + r] = (float)pr->sigma[l * q + r];
+            }
     }
     P.unit_drift = 1;
     for (int l = 0; l < d; ++l) P.unit_drift &= (P.A_f[l] == 1.0f && P.c_f[l] == 0.0f) ? 1 : 0;
@@ -878,6 +906,7 @@ srmc_status srmc_closed_form_error(const srmc_solver *s, double *out, void *stre
     if (!s || !out) return fail(SRMC_ERR_INVALID_ARG, "srmc_closed_form_error: NULL argument");
     if (s->P.model == srmc::MODEL_AFFINE || s->P.model == srmc::MODEL_USER)
         return fail(SRMC_ERR_UNSUPPORTED, "srmc_closed_form_error: no closed form for the affine and user models");
+    if (s->dense) return fail(SRMC_ERR_UNSUPPORTED, "srmc_closed_form_error: no closed form with a non-diagonal sigma");
     if (s->done_from > 0) return fail(SRMC_ERR_STATE, "srmc_closed_form_error: solve not finished");
     closed_form_error_kernel<<<s->P.N, 256, 0, (cudaStream_t)stream>>>(s->P, false, out);
     SRMC_CUDA(cudaGetLastError(), "closed form error kernel launch");
@@ -891,6 +920,7 @@ srmc_status srmc_point_error(const srmc_solver *s, const double *x, long long n,
     if (n > 0 && !x) return fail(SRMC_ERR_INVALID_ARG, "srmc_point_error: NULL points");
     if (s->P.model == srmc::MODEL_AFFINE || s->P.model == srmc::MODEL_USER)
         return fail(SRMC_ERR_UNSUPPORTED, "srmc_point_error: no closed form for the affine and user models");
+    if (s->dense) return fail(SRMC_ERR_UNSUPPORTED, "srmc_point_error: no closed form with a non-diagonal sigma");
     if (s->done_from > 0) return fail(SRMC_ERR_STATE, "srmc_point_error: solve not finished");
     SRMC_CUDA(cudaMemsetAsync(out, 0, sizeof(double) * 2 * (size_t)s->P.N, (cudaStream_t)stream),
               "srmc_point_error: clear");
@@ -908,6 +938,7 @@ srmc_status srmc_closed_form_error_inner(const srmc_solver *s, double *out, void
     if (!s || !out) return fail(SRMC_ERR_INVALID_ARG, "srmc_closed_form_error_inner: NULL argument");
     if (s->P.model == srmc::MODEL_AFFINE || s->P.model == srmc::MODEL_USER)
         return fail(SRMC_ERR_UNSUPPORTED, "srmc_closed_form_error_inner: no closed form for the affine and user models");
+    if (s->dense) return fail(SRMC_ERR_UNSUPPORTED, "srmc_closed_form_error_inner: no closed form with a non-diagonal sigma");
     for (int l = 0; l < s->P.d; ++l)
         if (s->P.cells[l] < 3) return fail(SRMC_ERR_INVALID_ARG, "srmc_closed_form_error_inner: no inner strata");
     if (s->done_from > 0) return fail(SRMC_ERR_STATE, "srmc_closed_form_error_inner: solve not finished");

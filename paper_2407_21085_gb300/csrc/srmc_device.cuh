@@ -15,6 +15,8 @@
 namespace srmc {
 
 constexpr int DMAX = 19;
+// A non-diagonal constant diffusion matrix (q = d) is built for d <= SD_DMAX.
+constexpr int SD_DMAX = 8;
 constexpr int PBMAX = 20;            // largest basis dimension: LP1 at d = 19 (20), LP2 at d = 3 (10)
 
 // The quadratic monomials u_a u_b (a <= b, row order) after the linear ones
@@ -49,6 +51,12 @@ struct Params {
     // srmc_create), and the drift's mean reversion for the driver.
     double A[DMAX], c[DMAX], s1[DMAX], s2[DMAX], theta[DMAX];
     float A_f[DMAX], c_f[DMAX], s1_f[DMAX], s2_f[DMAX], theta_f[DMAX];
+    // A non-diagonal constant sigma (dense != 0, Euler dynamics): the step adds
+    // sum_r sigma[l][r] dW_r to coordinate l; sd holds sigma row-major with
+    // stride d (the dense units read entry l d + r with d their compiled D).
+    int dense;
+    double sd[SD_DMAX * SD_DMAX];
+    float sd_f[SD_DMAX * SD_DMAX];
     int drift;                      // cos model: driver carries -(1/s0) b(x).z
     int unit_drift;                 // A = 1 and c = 0 in every coordinate (FP32 copies)
     double inv_s0;
@@ -451,6 +459,7 @@ template <> struct Form<double> {
     __device__ static double A(const Params &P, int l) { return P.A[l]; }
     __device__ static double c(const Params &P, int l) { return P.c[l]; }
     __device__ static double s1(const Params &P, int l) { return P.s1[l]; }
+    __device__ static double sd(const Params &P, int e) { return P.sd[e]; }
     __device__ static double s2(const Params &P, int l) { return P.s2[l]; }
     __device__ static double theta(const Params &P, int l) { return P.theta[l]; }
     __device__ static double inv_s0(const Params &P) { return P.inv_s0; }
@@ -478,6 +487,7 @@ template <> struct Form<float> {
     __device__ static float A(const Params &P, int l) { return P.A_f[l]; }
     __device__ static float c(const Params &P, int l) { return P.c_f[l]; }
     __device__ static float s1(const Params &P, int l) { return P.s1_f[l]; }
+    __device__ static float sd(const Params &P, int e) { return P.sd_f[e]; }
     __device__ static float s2(const Params &P, int l) { return P.s2_f[l]; }
     __device__ static float theta(const Params &P, int l) { return P.theta_f[l]; }
     __device__ static float inv_s0(const Params &P) { return P.inv_s0_f; }

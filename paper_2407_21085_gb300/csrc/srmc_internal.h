@@ -72,6 +72,8 @@ struct FlowPlan {
 #define SRMC_LAUNCH_STEP_PROB_NAME_(D) launch_step_prob_d##D
 #define SRMC_LAUNCH_STEP_EXACT_NAME(D) SRMC_LAUNCH_STEP_EXACT_NAME_(D)
 #define SRMC_LAUNCH_STEP_EXACT_NAME_(D) launch_step_exact_d##D
+#define SRMC_LAUNCH_STEP_DENSE_NAME(D) SRMC_LAUNCH_STEP_DENSE_NAME_(D)
+#define SRMC_LAUNCH_STEP_DENSE_NAME_(D) launch_step_dense_d##D
 #define SRMC_LAUNCH_STEP_QUAD_NAME(D) SRMC_LAUNCH_STEP_QUAD_NAME_(D)
 #define SRMC_LAUNCH_STEP_QUAD_NAME_(D) launch_step_quad_d##D
 // LP2 step kernels are built for d <= SRMC_LP2_DMAX.
@@ -83,6 +85,8 @@ struct FlowPlan {
     cudaError_t launch_step_prob_d##D(const Params &P, int i, bool fp64, bool lp1, int mv,    \
                                       int grid, int threads, cudaStream_t st);                \
     cudaError_t launch_step_exact_d##D(const Params &P, int i, bool fp64, bool lp1, int mv,   \
+                                       int grid, int threads, cudaStream_t st);                \
+    cudaError_t launch_step_dense_d##D(const Params &P, int i, bool fp64, bool lp1, int mv,   \
                                        int grid, int threads, cudaStream_t st);
 SRMC_DECLARE_STEP(1)
 SRMC_DECLARE_STEP(2)
@@ -238,6 +242,7 @@ struct srmc_solver {
     bool cv = false;                     // control installed
     bool cv_own = false;                 // ... and it is the run's own fitted z
     bool exact = false;                  // exact dynamics (Alg. 1)
+    bool dense = false;                  // Euler dynamics with a non-diagonal constant sigma
     bool lp2 = false;                    // quadratic local polynomials
     std::string user_source;             // user model (SRMC_MODEL_USER): g and f as source
     bool user_dynamics = false;          // ... with its own drift and diffusion

@@ -524,10 +524,19 @@ __global__ void __launch_bounds__(WARPS * 32) mlp_tabulate_kernel(Net net, const
         const long long row = (long long)j * P.K + k;
         for (int a = lane; a < d * p; a += 32) {
             const int l = a / p, c = a % p;
+            // zc = sigma^T grad u: component l of the value (c = 0) or of the
+            // central difference along axis c - 1 (c > 0)
+            auto g = [&](int m) {
+                return c == 0 ? (double)GAs[warp][0][1 + m]
+                              : (double)GAs[warp][1 + 2 * (c - 1)][1 + m] - (double)GAs[warp][2 + 2 * (c - 1)][1 + m];
+            };
             double v;
-            if (c == 0) v = (double)GAs[warp][0][1 + l];
-            else v = (double)GAs[warp][1 + 2 * (c - 1)][1 + l] - (double)GAs[warp][2 + 2 * (c - 1)][1 + l];
-            v *= P.sig[l];
+            if (P.dense) {
+                v = 0.0;
+                for (int m = 0; m < d; ++m) v += P.sd[m * d + l] * g(m);
+            } else {
+                v = P.sig[l] * g(l);
+            }
             c64[row * P.rz64 + a] = v;
             c16[row * P.rc16 + srmc::c16_index(P, l, c)] = __double2half(fmin(fmax(v, -65504.0), 65504.0));
         }

@@ -41,7 +41,9 @@
 #endif
 // Dynamics of the unit: 0 the Euler scheme (Alg. 2), 1 the exact affine-drift
 // SDE (Alg. 1; launch_step_exact_dD), which draws a second block of q normals
-// per step.  Exact dynamics are built for equal-size strata only.
+// per step, 2 the Euler scheme with a non-diagonal constant sigma
+// (launch_step_dense_dD: X'_l = A_l X_l + c_l + sum_r sigma_lr dW_r).  Exact
+// and dense dynamics are built for equal-size strata only.
 #ifndef SRMC_STEP_DYN
 #define SRMC_STEP_DYN 0
 #endif
@@ -119,6 +121,17 @@ template <typename R, int D>
 __device__ __forceinline__ void advance(const Params &P, int j, const R (&x)[D], const R (&dw)[D],
                                         R (&xn)[D])
 {
+#if SRMC_STEP_DYN == 2
+    static_assert(D <= SD_DMAX, "non-diagonal sigma units are built for d <= SD_DMAX");
+    // the full matrix: coordinate l takes every increment
+#pragma unroll
+    for (int l = 0; l < D; ++l) {
+        R v = fma(Form<R>::A(P, l), x[l], Form<R>::c(P, l));
+#pragma unroll
+        for (int r = 0; r < D; ++r) v = fma(Form<R>::sd(P, l * D + r), dw[r], v);
+        xn[l] = v;
+    }
+#else
 #if SRMC_PAIRS_ON && !defined(SRMC_USER_DYNAMICS)
     if constexpr (sizeof(R) == 4) {
         if (P.unit_drift) {
@@ -147,6 +160,7 @@ __device__ __forceinline__ void advance(const Params &P, int j, const R (&x)[D],
 #endif
 #pragma unroll
     for (int l = 0; l < D; ++l) xn[l] = next_coord<R, D>(P, j, l, x, dw[l], (R)0);
+#endif
 }
 
 // Cells of x on equal-size strata: kk = sum_l c_l stride_l, and (LP1) the
@@ -826,9 +840,13 @@ __device__ __forceinline__ void solve_stratum(const Params &P, const int i, cons
             W.template take<D % 4, D, false>(P, wd);
             if constexpr (NW == 2) W.template take<(2 * D) % 4, D, false>(P, we);
             scaled_normals<D>(wd, sdt, dwi);
+            if constexpr (SRMC_STEP_DYN == 2) {
+                advance<R, D>(P, i, x, dwi, xj);
+            } else {
 #pragma unroll
-            for (int l = 0; l < D; ++l) {
-                xj[l] = next_coord<R, D>(P, i, l, x, dwi[l], NW == 2 ? normal_of(we[l], (R)0) : (R)0);
+                for (int l = 0; l < D; ++l) {
+                    xj[l] = next_coord<R, D>(P, i, l, x, dwi[l], NW == 2 ? normal_of(we[l], (R)0) : (R)0);
+                }
             }
         }
         // (CI below reads phi and dwi before they are parked)
@@ -1088,9 +1106,13 @@ __device__ __forceinline__ void solve_stratum(const Params &P, const int i, cons
                 if constexpr (NW == 2) W.template take<(2 * D) % 4, D, false>(P, we);
                 R dwb[D];
                 scaled_normals<D>(wd, sdt, dwb);
+                if constexpr (SRMC_STEP_DYN == 2) {
+                    advance<R, D>(P, i, x, dwb, x1);
+                } else {
 #pragma unroll
-                for (int l = 0; l < D; ++l) {
-                    x1[l] = next_coord<R, D>(P, i, l, x, dwb[l], NW == 2 ? normal_of(we[l], (R)0) : (R)0);
+                    for (int l = 0; l < D; ++l) {
+                        x1[l] = next_coord<R, D>(P, i, l, x, dwb[l], NW == 2 ? normal_of(we[l], (R)0) : (R)0);
+                    }
                 }
             }
             {
@@ -1476,6 +1498,9 @@ cudaError_t SRMC_LAUNCH_STEP_QUAD_NAME(SRMC_STEP_D)(const Params &P, int i, bool
                                                      int grid, int threads, cudaStream_t st)
 #elif SRMC_STEP_DYN == 1
 cudaError_t SRMC_LAUNCH_STEP_EXACT_NAME(SRMC_STEP_D)(const Params &P, int i, bool fp64, bool lp1, int mv,
+                                                      int grid, int threads, cudaStream_t st)
+#elif SRMC_STEP_DYN == 2
+cudaError_t SRMC_LAUNCH_STEP_DENSE_NAME(SRMC_STEP_D)(const Params &P, int i, bool fp64, bool lp1, int mv,
                                                       int grid, int threads, cudaStream_t st)
 #elif SRMC_STEP_KIND == 0
 cudaError_t SRMC_LAUNCH_STEP_NAME(SRMC_STEP_D)(const Params &P, int i, bool fp64, bool lp1, int mv,

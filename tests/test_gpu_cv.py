@@ -241,6 +241,14 @@ def test_controls_with_exact_dynamics(dev, orc, prec):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_controls_with_non_diagonal_sigma(dev, orc, prec):
+    # correlated coordinates: the controls still use dW_j, the step's increments
+    w = W.cfg2(C=6, N=4, M=256, precision=prec, kapz=0.2).replace(sigma=[[0.3, 0.12], [-0.1, 0.25]])
+    _cv_parity(dev, orc, w, CT.random_smooth_z(w, seed=7))
+    _own_parity(dev, orc, w)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_controls_with_quadratic_polynomials(dev, orc, prec):
     w = W.cfg2(C=6, N=4, M=256, precision=prec, basis="lp2")
     _cv_parity(dev, orc, w, CT.closed_form_z(w))

@@ -133,6 +133,58 @@ def test_dimensions_12_to_19(dev, orc, d, N, M, model):
     _full_parity(dev, orc, w.replace(cells=cells))
 
 
+# Non-diagonal constant diffusion matrices (correlated coordinates; the Euler
+# step adds sum_r sigma_lr dW_r to coordinate l): no row is proportional to
+# another and none is symmetric, so a transposed or diagonal-only step fails.
+SIGMA_DENSE = {
+    2: [[0.3, 0.12], [-0.1, 0.25]],
+    3: [[0.3, 0.1, 0.0], [0.15, 0.25, -0.08], [0.0, -0.12, 0.35]],
+    6: [[0.3 if l == r else 0.05 * ((l + 2 * r) % 5 - 2) for r in range(6)] for l in range(6)],
+}
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("case", ["cos_z_d2", "cos_drift_d3", "logistic_d3", "affine_d2", "cos_d6", "lp0_d2"])
+def test_non_diagonal_sigma(dev, orc, prec, case):
+    if case == "cos_z_d2":
+        w = W.cfg2(C=4, N=4, M=256, kapz=0.2)
+    elif case == "cos_drift_d3":
+        w = W.cos_model("d3", d=3, N=3, C=3, a=2.0, M=128, s0=0.3, lam=0.2, kap=0.5).replace(
+            b=[0.1, 0.0, -0.2], theta=[0.5, 0.0, 0.0])
+    elif case == "logistic_d3":
+        w = W.logistic_paper(d=3, N=3, C=3, M=128)
+    elif case == "affine_d2":
+        w = W.affine(d=2, N=3, C=3, M=64, g0=0.5, gv=[0.3, -0.2], f0=0.1, fv=[0.05, 0.02], a=-0.3,
+                     s0=0.3)
+    elif case == "cos_d6":
+        w = W.cos_model("d6", d=6, N=3, C=2, a=2.0, M=64, s0=0.3, lam=0.2, kap=0.5)
+    else:
+        w = W.cfg2(C=4, N=4, M=512, basis="lp0")
+    _full_parity(dev, orc, w.replace(sigma=SIGMA_DENSE[w.d], precision=prec))
+
+
+def test_non_diagonal_sigma_limits(dev):
+    torch, srmc = dev
+    dense = W.cfg2(C=4, N=2, M=64).replace(sigma=SIGMA_DENSE[2])
+    bad = [dense.replace(theta=[1.0, 1.0], dynamics="exact"), dense.replace(strata="prob"),
+           dense.replace(basis="lp2"),
+           W.cos_model("d9", d=9, N=2, C=1, a=2.0, M=64, s0=0.3, lam=0.2, kap=0.5).replace(
+               sigma=[[0.3 if l == r else (0.01 if r == l + 1 else 0.0) for r in range(9)] for l in range(9)])]
+    for w in bad:
+        with pytest.raises(srmc.SrmcError) as e:
+            srmc.Solver(w)
+        assert e.value.status == 4, w.name
+    s = srmc.Solver(dense)
+    s.srmc_solve()
+    with pytest.raises(srmc.SrmcError) as e:
+        s.closed_form_error()
+    assert e.value.status == 4
+    with pytest.raises(srmc.SrmcError) as e:
+        srmc.Batch([s])
+    assert e.value.status == 4
+    s.close()
+
+
 def test_d19_teacher_forced(dev, orc):
     # d = 19 at the M of the paper's d = 19 row (3200 paths per stratum, dt = 0.2)
     # on 2^10 strata (2 cells in ten dimensions), with z in the driver: steps 0,

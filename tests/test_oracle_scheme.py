@@ -79,6 +79,10 @@ BF_CASES = [
     dict(d=1, N=2, C=4, M=7, kapz=0.0, basis="lp0", b=[0.0], theta=[2.0], dynamics="exact"),
     dict(d=1, N=3, C=3, M=8, kapz=0.2, basis="lp2"),
     dict(d=2, N=2, C=2, M=12, kapz=0.1, basis="lp2", strata="prob"),
+    # a non-diagonal sigma (correlated coordinates), with and without a drift
+    dict(d=2, N=3, C=2, M=6, kapz=0.3, basis="lp1", sigma=[[0.5, 0.2], [-0.3, 0.4]]),
+    dict(d=3, N=2, C=2, M=5, kapz=0.0, basis="lp1", sigma=[[0.5, 0.1, 0.0], [0.2, 0.4, -0.1], [0.0, 0.3, 0.6]],
+         b=[0.1, 0.0, -0.2], theta=[0.3, 0.0, 0.0]),
 ]
 _BF = {}
 
@@ -88,7 +92,8 @@ def _bf_workload(case):
                     lam=0.5, kap=0.4, kapz=case["kapz"], basis=case["basis"], seed=11, instance=3)
     return w.replace(Cy=1.5, Cz=1.2, strata=case.get("strata", "size"),   # active truncation somewhere
                      M_strata=case.get("M_strata"), b=case.get("b", [0.0] * case["d"]),
-                     theta=case.get("theta", []), dynamics=case.get("dynamics", "euler"))
+                     theta=case.get("theta", []), dynamics=case.get("dynamics", "euler"),
+                     sigma=case.get("sigma", w.sigma))
 
 
 def _brute_force_mismatch(orc, n, library=None):
