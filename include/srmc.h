@@ -243,10 +243,11 @@ srmc_status srmc_read_table(const srmc_solver *s, double *dst_y, double *dst_z, 
  * srmc_table (centred basis; e.g. the step-i slice of another solver's tables
  * on the same strata and basis), caller-owned, device or host (pinned or
  * pageable).  The FP32 form's copies of the rows are refreshed (round to
- * nearest).  If the rows of steps i+1..N-1 are present (solved or installed),
- * srmc_solve_step(i - 1) may follow: with installed rows the fit of step i-1
- * reads the given functions (teacher forcing).  Asynchronous on stream;
- * SRMC_ERR_INVALID_ARG for a NULL argument or i outside [0, N). */
+ * nearest).  Steps count as present from the last one down: installing step i
+ * when steps i+1..N-1 are present (solved or installed; none for i = N-1)
+ * makes steps i..N-1 present, after which srmc_solve_step(i - 1) may follow
+ * and fits step i-1 from the given functions (teacher forcing).  Asynchronous
+ * on stream; SRMC_ERR_INVALID_ARG for a NULL argument or i outside [0, N). */
 srmc_status srmc_set_rows(srmc_solver *s, int i, const double *src_y, const double *src_z, void *stream);
 
 /* Martingale control variate (an extension of Alg. SRMDP, not in the

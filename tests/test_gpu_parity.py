@@ -404,10 +404,10 @@ def test_invalid_arguments(dev):
         srmc.Solver(W.cfg2(M=2))                 # M < d + 1
     assert e.value.status == 1
     bad = W.cfg2(M=64)
-    bad.sigma = [[0.3, 0.1], [0.0, 0.3]]
+    bad.sigma = [[0.3, float("nan")], [0.0, 0.3]]
     with pytest.raises(srmc.SrmcError) as e:
-        srmc.Solver(bad)                         # non-diagonal sigma
-    assert e.value.status == 4
+        srmc.Solver(bad)                         # non-finite sigma
+    assert e.value.status == 1
     with pytest.raises(srmc.SrmcError) as e:
         srmc.Solver(W.cfg2(M=64), block_threads=48)
     assert e.value.status == 1
