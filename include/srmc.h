@@ -84,13 +84,15 @@ typedef enum { SRMC_MODEL_COS = 0, SRMC_MODEL_LOGISTIC = 1, SRMC_MODEL_AFFINE = 
  * Drift b_l(x) = b_l - theta_l x_l (theta = 0: constant drift; theta > 0:
  * Ornstein-Uhlenbeck, mean reverting to b_l/theta_l).  b: [d] (host).
  * theta: [d] (host) or NULL for 0.  sigma: [d*q] row-major constant diffusion
- * (host, finite); this build requires q == d (else SRMC_ERR_UNSUPPORTED).  A
- * diagonal sigma moves each coordinate by its own increment; a non-diagonal one
- * (sigma_lr != 0 for some l != r: correlated coordinates, the general constant
- * diffusion of Sec. 1) is built for d <= 8 with Euler dynamics, equal-size
- * strata, LP0/LP1 and the built-in models (else SRMC_ERR_UNSUPPORTED), and
- * takes X_{j+1,l} = X_{j,l} + b_l(X_j) dt + sum_r sigma_lr dW_{j,r}; the
- * closed-form error metrics and the batched form do not take it.
+ * (host, finite), q the number of Brownian components (1 <= q <= 19).  A
+ * diagonal d x d sigma moves each coordinate by its own increment; any other
+ * (an off-diagonal sigma_lr != 0: correlated coordinates, or q != d: the general
+ * constant diffusion of Sec. 1) is built for d <= 8 (d, q <= 4 when q != d) with
+ * Euler dynamics, equal-size strata, LP0/LP1 and the built-in models, without a
+ * drift in the cos model when q != d (else SRMC_ERR_UNSUPPORTED), and takes
+ * X_{j+1,l} = X_{j,l} + b_l(X_j) dt + sum_r sigma_lr dW_{j,r}; z and the Z fits
+ * then have q components.  The closed-form error metrics, the batched form and
+ * (for q != d) the network tabulation do not take it.
  * params: [n_params <= SRMC_PMAX] (host).
  * dynamics: how X moves between grid times (assumption HX):
  *   SRMC_DYN_EULER (Alg. 2): X_{j+1} = X_j + b(X_j) dt + sigma dW_j;

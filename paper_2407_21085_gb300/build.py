@@ -3,7 +3,8 @@
 The step kernel is compiled once per dimension D = 1..19 (-DSRMC_STEP_D=D) so
 that per-path state stays in registers, and once per kind of strata
 (-DSRMC_STEP_KIND: equal size, equal probability), of dynamics
-(-DSRMC_STEP_DYN: Euler, exact, Euler with a non-diagonal sigma) and of basis
+(-DSRMC_STEP_DYN: Euler, exact, Euler with a non-diagonal sigma, also as a d x q
+matrix with -DSRMC_STEP_Q=q) and of basis
 (-DSRMC_STEP_BASIS=2: quadratic local polynomials, d <= 3) so that each kernel
 carries only its own cell location, chain step and basis; the objects are
 compiled in parallel and linked with the C-ABI translation unit into one shared
@@ -26,6 +27,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 DIMS = range(1, 20)             # equal-size strata, Euler dynamics: d <= 19
 NARROW_DIMS = range(1, 9)       # equal-probability strata, exact dynamics: d <= 8
 LP2_DIMS = range(1, 4)          # quadratic local polynomials: d <= 3
+DENSEQ_DIMS = range(1, 5)       # a d x q sigma with q != d: d, q <= 4
 
 
 def _nvcc() -> str:
@@ -102,6 +104,9 @@ def build(force: bool = False, verbose: bool = False, jobs: int | None = None,
                [f"-DSRMC_STEP_D={D}", "-DSRMC_STEP_DYN=1"] + extra_defs) for D in NARROW_DIMS]
     units += [(os.path.join(CSRC, "srmc_step.cu"), os.path.join(out, f"step_dense_d{D}.o"),
                [f"-DSRMC_STEP_D={D}", "-DSRMC_STEP_DYN=2"] + extra_defs) for D in NARROW_DIMS]
+    units += [(os.path.join(CSRC, "srmc_step.cu"), os.path.join(out, f"step_dense_d{D}_q{Q}.o"),
+               [f"-DSRMC_STEP_D={D}", f"-DSRMC_STEP_Q={Q}", "-DSRMC_STEP_DYN=2"] + extra_defs)
+              for D in DENSEQ_DIMS for Q in DENSEQ_DIMS if Q != D]
     units += [(os.path.join(CSRC, "srmc_step.cu"), os.path.join(out, f"step_quad_d{D}.o"),
                [f"-DSRMC_STEP_D={D}", "-DSRMC_STEP_BASIS=2"] + extra_defs) for D in LP2_DIMS]
     for name in sorted(os.listdir(CSRC)):

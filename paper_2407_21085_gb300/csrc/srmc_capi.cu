@@ -159,6 +159,23 @@ cudaError_t launch_step(const srmc_solver *s, int i, cudaStream_t st)
         }
         return cudaErrorInvalidValue;
     }
+    if (s->dense && P.q != P.d) {
+        switch (P.d * 8 + P.q) {
+        case 1 * 8 + 2: return srmc::launch_step_dense_d1_q2(P, i, s->fp64, s->lp1, mv, grid, s->threads, st);
+        case 1 * 8 + 3: return srmc::launch_step_dense_d1_q3(P, i, s->fp64, s->lp1, mv, grid, s->threads, st);
+        case 1 * 8 + 4: return srmc::launch_step_dense_d1_q4(P, i, s->fp64, s->lp1, mv, grid, s->threads, st);
+        case 2 * 8 + 1: return srmc::launch_step_dense_d2_q1(P, i, s->fp64, s->lp1, mv, grid, s->threads, st);
+        case 2 * 8 + 3: return srmc::launch_step_dense_d2_q3(P, i, s->fp64, s->lp1, mv, grid, s->threads, st);
+        case 2 * 8 + 4: return srmc::launch_step_dense_d2_q4(P, i, s->fp64, s->lp1, mv, grid, s->threads, st);
+        case 3 * 8 + 1: return srmc::launch_step_dense_d3_q1(P, i, s->fp64, s->lp1, mv, grid, s->threads, st);
+        case 3 * 8 + 2: return srmc::launch_step_dense_d3_q2(P, i, s->fp64, s->lp1, mv, grid, s->threads, st);
+        case 3 * 8 + 4: return srmc::launch_step_dense_d3_q4(P, i, s->fp64, s->lp1, mv, grid, s->threads, st);
+        case 4 * 8 + 1: return srmc::launch_step_dense_d4_q1(P, i, s->fp64, s->lp1, mv, grid, s->threads, st);
+        case 4 * 8 + 2: return srmc::launch_step_dense_d4_q2(P, i, s->fp64, s->lp1, mv, grid, s->threads, st);
+        case 4 * 8 + 3: return srmc::launch_step_dense_d4_q3(P, i, s->fp64, s->lp1, mv, grid, s->threads, st);
+        }
+        return cudaErrorInvalidValue;
+    }
     if (s->dense) {
         switch (P.d) {
         case 1: return srmc::launch_step_dense_d1(P, i, s->fp64, s->lp1, mv, grid, s->threads, st);
@@ -403,11 +420,11 @@ srmc_status srmc_create(const srmc_problem *pr, const srmc_strata *sa, const srm
     if (!pr || !sa || !cf) return fail(SRMC_ERR_INVALID_ARG, "srmc_create: NULL argument");
     const int d = pr->d, q = pr->q;
     if (d < 1 || d > SRMC_DMAX) return fail(SRMC_ERR_INVALID_ARG, "d must be in [1, 19]");
-    if (q != d) return fail(SRMC_ERR_UNSUPPORTED, "this build requires q == d");
+    if (q < 1 || q > SRMC_DMAX) return fail(SRMC_ERR_INVALID_ARG, "q must be in [1, 19]");
     if (pr->N < 1 || pr->N > 1000000) return fail(SRMC_ERR_INVALID_ARG, "N must be in [1, 1e6]");
     if (!(pr->T > 0.0) || !std::isfinite(pr->T)) return fail(SRMC_ERR_INVALID_ARG, "T must be > 0");
     if (!pr->b || !pr->sigma) return fail(SRMC_ERR_INVALID_ARG, "b and sigma are required");
-    bool dense = false;                  // sigma has an off-diagonal entry
+    bool dense = q != d;                 // sigma is not a diagonal d x d matrix
     for (int l = 0; l < d; ++l)
         for (int r = 0; r < q; ++r) {
             if (!std::isfinite(pr->sigma[l * q + r])) return fail(SRMC_ERR_INVALID_ARG, "sigma must be finite");
@@ -417,6 +434,8 @@ srmc_status srmc_create(const srmc_problem *pr, const srmc_strata *sa, const srm
                   cf->basis == SRMC_LP2 || sa->kind != SRMC_STRATA_EQUAL_SIZE))
         return fail(SRMC_ERR_UNSUPPORTED, "a non-diagonal sigma is built for d <= 8, Euler dynamics, "
                                           "equal-size strata, LP0/LP1 and the built-in models");
+    if (q != d && (d > SRMC_DENSEQ_MAX || q > SRMC_DENSEQ_MAX))
+        return fail(SRMC_ERR_UNSUPPORTED, "q != d is built for d, q <= 4");
     if (pr->model < SRMC_MODEL_COS || pr->model > SRMC_MODEL_USER)
         return fail(SRMC_ERR_INVALID_ARG, "unknown model");
     if (pr->model == SRMC_MODEL_USER && (!pr->user_source || !pr->user_source[0]))
@@ -431,6 +450,8 @@ srmc_status srmc_create(const srmc_problem *pr, const srmc_strata *sa, const srm
         if (!std::isfinite(th) || !std::isfinite(pr->b[l])) return fail(SRMC_ERR_INVALID_ARG, "b and theta must be finite");
         has_drift = has_drift || th != 0.0 || pr->b[l] != 0.0;
     }
+    if (q != d && has_drift && pr->model == SRMC_MODEL_COS)
+        return fail(SRMC_ERR_UNSUPPORTED, "the cos model's drift term needs q == d");
     if (pr->n_params < 0 || pr->n_params > SRMC_PMAX || (pr->n_params > 0 && !pr->params))
         return fail(SRMC_ERR_INVALID_ARG, "params: n_params must be in [0, 24]");
     const int need = pr->model == SRMC_MODEL_COS ? 4 : pr->model == SRMC_MODEL_AFFINE ? 3 + 2 * d : 0;
@@ -556,7 +577,7 @@ srmc_status srmc_create(const srmc_problem *pr, const srmc_strata *sa, const srm
         P.lo[l] = lo;
         P.h[l] = (hi - lo) / (double)sa->cells[l];
         P.b[l] = pr->b[l];
-        P.sig[l] = pr->sigma[l * q + l];
+        P.sig[l] = l < q ? pr->sigma[l * q + l] : 0.0;
         P.lo_f[l] = (float)lo;
         P.r_f[l] = (float)((double)sa->cells[l] / (hi - lo));
         P.b_f[l] = (float)pr->b[l];
@@ -577,12 +598,12 @@ srmc_status srmc_create(const srmc_problem *pr, const srmc_strata *sa, const srm
         P.A_f[l] = (float)P.A[l]; P.c_f[l] = (float)P.c[l];
         P.s1_f[l] = (float)P.s1[l]; P.s2_f[l] = (float)P.s2[l]; P.theta_f[l] = (float)th;
     }
-    if (dense) {
+    if (dense) {                         // row-major d x q, read at l q + r
         P.dense = 1;
         for (int l = 0; l < d; ++l)
-            for (int r = 0; r < d; ++r) {
-                P.sd[l * d + r] = pr->sigma[l * q + r];
-                P.sd_f[l * d + r] = (float)pr->sigma[l * q + r];
+            for (int r = 0; r < q; ++r) {
+                P.sd[l * q + r] = pr->sigma[l * q + r];
+                P.sd_f[l * q + r] = (float)pr->sigma[l * q + r];
             }
     }
     P.unit_drift = 1;

@@ -590,8 +590,8 @@ __device__ __forceinline__ R logistic_f(R y, R zsum)
     return zsum * (y - (R)(2 + D) / (R)(2 * D));
 }
 
-// f_j(x, y, z); z is used only when ZIN.
-template <typename R, int D, int MODEL, bool ZIN>
+// f_j(x, y, z); z (Q components) is used only when ZIN.
+template <typename R, int D, int MODEL, bool ZIN, int Q = D>
 __device__ __forceinline__ R model_f(const Params &P, int j, const R (&x)[D], R y, const R *z)
 {
 #ifdef SRMC_USER_MODEL
@@ -612,13 +612,15 @@ __device__ __forceinline__ R model_f(const Params &P, int j, const R (&x)[D], R 
             sincos_r(s, &sn, &cs);
             R zz = (R)0;
 #pragma unroll
-            for (int l = 0; l < D; ++l) zz += z[l] * z[l];
+            for (int l = 0; l < Q; ++l) zz += z[l] * z[l];
             v += Form<R>::prm(P, 2) * zz - c1 * cs * cs - c2 * sn * sn;
-            if (P.drift) {          // uniform: cancels the drift b(x).grad u = b(x).z / s0
-                R bz = (R)0;
+            if constexpr (Q == D) {
+                if (P.drift) {      // uniform: cancels the drift b(x).grad u = b(x).z / s0
+                    R bz = (R)0;
 #pragma unroll
-                for (int l = 0; l < D; ++l) bz += (Form<R>::b(P, l) - Form<R>::theta(P, l) * x[l]) * z[l];
-                v -= bz * Form<R>::inv_s0(P);
+                    for (int l = 0; l < D; ++l) bz += (Form<R>::b(P, l) - Form<R>::theta(P, l) * x[l]) * z[l];
+                    v -= bz * Form<R>::inv_s0(P);
+                }
             }
         } else {
             const R cs = cos_r(s);
@@ -628,8 +630,8 @@ __device__ __forceinline__ R model_f(const Params &P, int j, const R (&x)[D], R 
     } else if (MODEL == MODEL_LOGISTIC) {
         R sz = (R)0;
 #pragma unroll
-        for (int l = 0; l < D; ++l) sz += z[l];
-        return logistic_f<R, D>(y, sz);
+        for (int l = 0; l < Q; ++l) sz += z[l];
+        return logistic_f<R, Q>(y, sz);
     } else {
         return model_f_y<R, D, MODEL>(P, y, model_f_x<R, D, MODEL>(P, j, x));
     }

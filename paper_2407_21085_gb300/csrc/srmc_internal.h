@@ -74,6 +74,8 @@ struct FlowPlan {
 #define SRMC_LAUNCH_STEP_EXACT_NAME_(D) launch_step_exact_d##D
 #define SRMC_LAUNCH_STEP_DENSE_NAME(D) SRMC_LAUNCH_STEP_DENSE_NAME_(D)
 #define SRMC_LAUNCH_STEP_DENSE_NAME_(D) launch_step_dense_d##D
+#define SRMC_LAUNCH_STEP_DENSEQ_NAME(D, Q) SRMC_LAUNCH_STEP_DENSEQ_NAME_(D, Q)
+#define SRMC_LAUNCH_STEP_DENSEQ_NAME_(D, Q) launch_step_dense_d##D##_q##Q
 #define SRMC_LAUNCH_STEP_QUAD_NAME(D) SRMC_LAUNCH_STEP_QUAD_NAME_(D)
 #define SRMC_LAUNCH_STEP_QUAD_NAME_(D) launch_step_quad_d##D
 // LP2 step kernels are built for d <= SRMC_LP2_DMAX.
@@ -97,6 +99,16 @@ SRMC_DECLARE_STEP(6)
 SRMC_DECLARE_STEP(7)
 SRMC_DECLARE_STEP(8)
 #undef SRMC_DECLARE_STEP
+// A d x q sigma with q != d (non-diagonal-sigma dynamics): d, q <= SRMC_DENSEQ_MAX.
+#define SRMC_DENSEQ_MAX 4
+#define SRMC_DECLARE_STEP_Q(D, Q)                                                                \
+    cudaError_t launch_step_dense_d##D##_q##Q(const Params &P, int i, bool fp64, bool lp1, int mv, \
+                                              int grid, int threads, cudaStream_t st);
+SRMC_DECLARE_STEP_Q(1, 2) SRMC_DECLARE_STEP_Q(1, 3) SRMC_DECLARE_STEP_Q(1, 4)
+SRMC_DECLARE_STEP_Q(2, 1) SRMC_DECLARE_STEP_Q(2, 3) SRMC_DECLARE_STEP_Q(2, 4)
+SRMC_DECLARE_STEP_Q(3, 1) SRMC_DECLARE_STEP_Q(3, 2) SRMC_DECLARE_STEP_Q(3, 4)
+SRMC_DECLARE_STEP_Q(4, 1) SRMC_DECLARE_STEP_Q(4, 2) SRMC_DECLARE_STEP_Q(4, 3)
+#undef SRMC_DECLARE_STEP_Q
 // d = 9..11: equal-size strata, Euler dynamics, the FP32 form, no controls.
 constexpr int SRMC_WIDE_DMIN_V = 9;
 cudaError_t launch_step_d9(const Params &P, int i, bool fp64, bool lp1, int mv, int grid, int threads,

@@ -533,7 +533,7 @@ __global__ void __launch_bounds__(WARPS * 32) mlp_tabulate_kernel(Net net, const
             double v;
             if (P.dense) {
                 v = 0.0;
-                for (int m = 0; m < d; ++m) v += P.sd[m * d + l] * g(m);
+                for (int m = 0; m < d; ++m) v += P.sd[m * P.q + l] * g(m);
             } else {
                 v = P.sig[l] * g(l);
             }
@@ -838,8 +838,8 @@ srmc_status srmc_mlp_fit_noalloc(srmc_mlp *m, const srmc_solver *s, long long n_
 srmc_status srmc_cv_tabulate(const srmc_mlp *m, srmc_solver *s, void *stream)
 {
     if (!m || !s) return mfail(SRMC_ERR_INVALID_ARG, "srmc_cv_tabulate: NULL argument");
-    if (!s->lp1 || s->lp2 || s->P.d > 7 || m->nin != s->P.d + 1 || s->mv == srmc::MV_AFFINE)
-        return mfail(SRMC_ERR_UNSUPPORTED, "srmc_cv_tabulate: LP1, d <= 7, n_in = d + 1 only");
+    if (!s->lp1 || s->lp2 || s->P.d > 7 || m->nin != s->P.d + 1 || s->mv == srmc::MV_AFFINE || s->P.q != s->P.d)
+        return mfail(SRMC_ERR_UNSUPPORTED, "srmc_cv_tabulate: LP1, d <= 7, q = d, n_in = d + 1 only");
     if (const int st = srmc_prepare_user_control(s)) return (srmc_status)st;
     const size_t nrow = (size_t)s->P.N * (size_t)s->P.K;
     if (!s->C64) {

@@ -53,11 +53,24 @@
 #ifndef SRMC_STEP_BASIS
 #define SRMC_STEP_BASIS 1
 #endif
+// Brownian components q of the unit: q = d, except in the units of the
+// non-diagonal-sigma dynamics compiled with -DSRMC_STEP_Q=q (a d x q sigma).
+#ifndef SRMC_STEP_Q
+#define SRMC_STEP_Q SRMC_STEP_D
+#endif
+static_assert(SRMC_STEP_Q == SRMC_STEP_D || SRMC_STEP_DYN == 2, "q != d is built for the dense-sigma units only");
 
 namespace srmc {
 namespace {
 
 constexpr int FLUSH = 16;
+
+// q of a d-dimensional kernel in this unit (dW_j, z, the Z fits and the
+// control rows have q components; x, the strata and the basis have d).
+template <int D>
+struct QOf {
+    static constexpr int value = D == SRMC_STEP_D ? SRMC_STEP_Q : D;
+};
 constexpr int NW = SRMC_STEP_DYN == 1 ? 2 : 1;     // blocks of q normals per step
 
 // Basis dimension: 1 (LP0), d + 1 (LP1) or 1 + d + d(d+1)/2 (LP2 units).
@@ -118,17 +131,18 @@ __device__ __forceinline__ R next_coord(const Params &P, int j, int l, const R (
 
 // X_{j+1} from X_j = x and the increments dw (the whole vector).
 template <typename R, int D>
-__device__ __forceinline__ void advance(const Params &P, int j, const R (&x)[D], const R (&dw)[D],
-                                        R (&xn)[D])
+__device__ __forceinline__ void advance(const Params &P, int j, const R (&x)[D],
+                                        const R (&dw)[QOf<D>::value], R (&xn)[D])
 {
 #if SRMC_STEP_DYN == 2
-    static_assert(D <= SD_DMAX, "non-diagonal sigma units are built for d <= SD_DMAX");
-    // the full matrix: coordinate l takes every increment
+    constexpr int Q = QOf<D>::value;
+    static_assert(D <= SD_DMAX && Q <= SD_DMAX, "non-diagonal sigma units are built for d, q <= SD_DMAX");
+    // the full d x q matrix: coordinate l takes every increment
 #pragma unroll
     for (int l = 0; l < D; ++l) {
         R v = fma(Form<R>::A(P, l), x[l], Form<R>::c(P, l));
 #pragma unroll
-        for (int r = 0; r < D; ++r) v = fma(Form<R>::sd(P, l * D + r), dw[r], v);
+        for (int r = 0; r < Q; ++r) v = fma(Form<R>::sd(P, l * Q + r), dw[r], v);
         xn[l] = v;
     }
 #else
@@ -457,10 +471,12 @@ __host__ __device__ constexpr int row_pad(int n) { return sizeof(R) == 4 ? (n + 
 // With CV, also hands back phi(x) and the row index of (j, stratum of x), from
 // which the control of the next increment is evaluated.
 template <typename R, int D, bool LP1, int MODEL, bool ZIN, bool CV, bool FLOW = false>
-__device__ __forceinline__ void eval_at(const Params &P, int j, const R (&x)[D], R &y, R (&z)[D],
-                                        R (&phio)[BasisDim<D, LP1>::value], unsigned &rowo)
+__device__ __forceinline__ void eval_at(const Params &P, int j, const R (&x)[D], R &y,
+                                        R (&z)[QOf<D>::value], R (&phio)[BasisDim<D, LP1>::value],
+                                        unsigned &rowo)
 {
     constexpr int p = BasisDim<D, LP1>::value;
+    constexpr int Q = QOf<D>::value;
     if (j == P.N) {
         y = model_g<R, D, MODEL>(P, x);
         return;
@@ -484,7 +500,7 @@ __device__ __forceinline__ void eval_at(const Params &P, int j, const R (&x)[D],
     const unsigned row = (unsigned)j * (unsigned)P.K + kk;     // N K < 2^32 (checked at create)
     // The row strides are those srmc_create sets (rows padded to 16 bytes),
     // as constants of the kernel's basis dimension.
-    constexpr unsigned RY = (unsigned)row_pad<R>(p), RZ = (unsigned)row_pad<R>(D * p);
+    constexpr unsigned RY = (unsigned)row_pad<R>(p), RZ = (unsigned)row_pad<R>(Q * p);
     R a[p];
     load_row<p, FLOW>(Form<R>::Ytab(P) + row * RY, a);
     R v = a[0];
@@ -492,30 +508,30 @@ __device__ __forceinline__ void eval_at(const Params &P, int j, const R (&x)[D],
     for (int c = 1; c < p; ++c) v += a[c] * phi[c];
     y = clamp_r(v, Form<R>::Cy(P));
     if (ZIN) {
-        if constexpr (sizeof(R) == 4 && D * p > 64) {
+        if constexpr (sizeof(R) == 4 && Q * p > 64) {
             // long rows (d >= 8): each 16-byte vector is folded into z as it
             // arrives, so that the row never sits in registers whole
             const float4 *z4 = reinterpret_cast<const float4 *>(Form<R>::Ztab(P) + row * RZ);
-            R w[D];
+            R w[Q];
 #pragma unroll
-            for (int l = 0; l < D; ++l) w[l] = (R)0;
+            for (int l = 0; l < Q; ++l) w[l] = (R)0;
 #pragma unroll
-            for (int v = 0; v < (D * p + 3) / 4; ++v) {
+            for (int v = 0; v < (Q * p + 3) / 4; ++v) {
                 const float4 t = ld_row4<FLOW>(z4 + v);
                 const float tv[4] = {t.x, t.y, t.z, t.w};
 #pragma unroll
                 for (int u = 0; u < 4; ++u) {
                     const int e = 4 * v + u;
-                    if (e < D * p) w[e / p] = (e % p == 0) ? w[e / p] + tv[u] : fmaf(tv[u], phi[e % p], w[e / p]);
+                    if (e < Q * p) w[e / p] = (e % p == 0) ? w[e / p] + tv[u] : fmaf(tv[u], phi[e % p], w[e / p]);
                 }
             }
 #pragma unroll
-            for (int l = 0; l < D; ++l) z[l] = clamp_r(w[l], Form<R>::Cz(P));
+            for (int l = 0; l < Q; ++l) z[l] = clamp_r(w[l], Form<R>::Cz(P));
         } else {
-            R bz[D * p];
-            load_row<D * p, FLOW>(Form<R>::Ztab(P) + row * RZ, bz);
+            R bz[Q * p];
+            load_row<Q * p, FLOW>(Form<R>::Ztab(P) + row * RZ, bz);
 #pragma unroll
-            for (int l = 0; l < D; ++l) {
+            for (int l = 0; l < Q; ++l) {
                 R w = bz[l * p];
 #pragma unroll
                 for (int c = 1; c < p; ++c) w += bz[l * p + c] * phi[c];
@@ -533,8 +549,10 @@ __device__ __forceinline__ void eval_at(const Params &P, int j, const R (&x)[D],
 // zc(x) = T_Cz(beta_l . phi) for the control row `row` and the basis values
 // phi of x: the values of the martingale control's integrand (clamped).
 template <typename R, int D, int p>
-__device__ __forceinline__ void control_vals(const Params &P, unsigned row, const R (&phi)[p], R (&zc)[D])
+__device__ __forceinline__ void control_vals(const Params &P, unsigned row, const R (&phi)[p],
+                                             R (&zc)[QOf<D>::value])
 {
+    constexpr int Q = QOf<D>::value;
     if constexpr (sizeof(R) == 4) {
         // FP32 form: binary16 rows, coefficient-major (the halves of a 32-bit
         // word are coefficient a of components 2m and 2m + 1, c16_index), read
@@ -542,7 +560,7 @@ __device__ __forceinline__ void control_vals(const Params &P, unsigned row, cons
         // an FP32 pair that enters both components' dot products with one
         // packed FMA; the order of the terms of each component is that of the
         // scalar form (constant first, then a = 1 .. p - 1).
-        constexpr int QH = (D + 1) / 2;                  // component pairs
+        constexpr int QH = (Q + 1) / 2;                  // component pairs
         constexpr int NWD = p * QH;                      // 32-bit words of a row in use
         constexpr int RCW = (2 * NWD + 7) / 8 * 4;       // 32-bit words per row (16-byte rows)
         const uint4 *b4 = reinterpret_cast<const uint4 *>(reinterpret_cast<const unsigned *>(P.C16) +
@@ -566,12 +584,12 @@ __device__ __forceinline__ void control_vals(const Params &P, unsigned row, cons
 #pragma unroll
         for (int m = 0; m < QH; ++m) {
             zc[2 * m] = clamp_r(w2[m].x, L);
-            if (2 * m + 1 < D) zc[2 * m + 1] = clamp_r(w2[m].y, L);
+            if (2 * m + 1 < Q) zc[2 * m + 1] = clamp_r(w2[m].y, L);
         }
     } else {
         const double *b = P.C64 + row * (unsigned)P.rz64;
 #pragma unroll
-        for (int l = 0; l < D; ++l) {
+        for (int l = 0; l < Q; ++l) {
             double w = __ldg(b + l * p);
 #pragma unroll
             for (int a = 1; a < p; ++a) w += __ldg(b + l * p + a) * phi[a];
@@ -601,11 +619,12 @@ __device__ __forceinline__ R control_apply(const R (&zc)[D], const R (&dw)[D])
 }
 
 template <typename R, int D, int p>
-__device__ __forceinline__ R control_dot(const Params &P, unsigned row, const R (&phi)[p], const R (&dw)[D])
+__device__ __forceinline__ R control_dot(const Params &P, unsigned row, const R (&phi)[p],
+                                         const R (&dw)[QOf<D>::value])
 {
-    R zc[D];
+    R zc[QOf<D>::value];
     control_vals<R, D, p>(P, row, phi, zc);
-    return control_apply<R, D>(zc, dw);
+    return control_apply<R, QOf<D>::value>(zc, dw);
 }
 
 // Blocks per SM the compiler must fit (register budget): FP32 forms of
@@ -683,7 +702,7 @@ struct TileMoments {
 template <typename R, int D, bool LP1>
 struct StepSmem {
     static constexpr int p = BasisDim<D, LP1>::value;
-    static constexpr int q = D;
+    static constexpr int q = QOf<D>::value;
     static constexpr int EG = LP1 ? p * (p + 1) / 2 : 0;
     static constexpr int EA = EG + q * p + p;
     // Path columns (one per thread; rows padded by four words, so that rows
@@ -718,7 +737,7 @@ __device__ __forceinline__ void solve_stratum(const Params &P, const int i, cons
                                               StepSmem<R, D, LP1> &sm)
 {
     constexpr int p = BasisDim<D, LP1>::value;
-    constexpr int q = D;
+    constexpr int q = QOf<D>::value;                 // Brownian components
     constexpr int EG = LP1 ? p * (p + 1) / 2 : 0;
     constexpr int EZ = q * p;
     constexpr int EA = EG + EZ + p;
@@ -823,7 +842,7 @@ __device__ __forceinline__ void solve_stratum(const Params &P, const int i, cons
         const bool valid = m < Mk;
         Words W;
         W.init(P, (unsigned)m, (unsigned)k, (unsigned)i);
-        R x[D], phi[p], dwi[D], xj[D], zj[D], yn;
+        R x[D], phi[p], dwi[q], xj[D], zj[q], yn;
         phi[0] = (R)1;
         {
             unsigned ws[D];
@@ -836,10 +855,10 @@ __device__ __forceinline__ void solve_stratum(const Params &P, const int i, cons
             add_quadratic<R, D, p>(phi);
         }
         {
-            unsigned wd[D], we[D];
-            W.template take<D % 4, D, false>(P, wd);
-            if constexpr (NW == 2) W.template take<(2 * D) % 4, D, false>(P, we);
-            scaled_normals<D>(wd, sdt, dwi);
+            unsigned wd[q], we[q];
+            W.template take<D % 4, q, false>(P, wd);
+            if constexpr (NW == 2) W.template take<(D + q) % 4, q, false>(P, we);
+            scaled_normals<q>(wd, sdt, dwi);
             if constexpr (SRMC_STEP_DYN == 2) {
                 advance<R, D>(P, i, x, dwi, xj);
             } else {
@@ -858,7 +877,7 @@ __device__ __forceinline__ void solve_stratum(const Params &P, const int i, cons
 #pragma unroll
             for (int a = 1; a < p; ++a) sm.tile[a][threadIdx.x] = (float)phi[a];
 #pragma unroll
-            for (int l = 0; l < D; ++l) sm.tile[p + l][threadIdx.x] = (float)dwi[l];
+            for (int l = 0; l < q; ++l) sm.tile[p + l][threadIdx.x] = (float)dwi[l];
         }
         // Martingale control: CI = zc_i(x_i).dW_i (stratum k), CZ = sum_{j>i} zc_j(X_j).dW_j,
         // zc_j evaluated at X_j from the control row of (j, stratum of X_j); with the
@@ -867,7 +886,7 @@ __device__ __forceinline__ void solve_stratum(const Params &P, const int i, cons
         // of X_j)), evaluated when X_j is located and carried to step j
         [[maybe_unused]] R phij[p];
         [[maybe_unused]] unsigned rowj = 0;
-        [[maybe_unused]] R zcj[D];
+        [[maybe_unused]] R zcj[q];
         // A driver that does not read z: f_i(x_i, y_{i+1}(X_{i+1})) is known
         // after this first step, so the Y response is complete in phase A (no
         // phase B).  Its part in x_i is taken before X_{i+1} is located.
@@ -881,23 +900,23 @@ __device__ __forceinline__ void solve_stratum(const Params &P, const int i, cons
         [[maybe_unused]] R zsum = (R)0;
         if constexpr (ZSUM) {
 #pragma unroll
-            for (int l = 0; l < D; ++l) zsum += zj[l];
+            for (int l = 0; l < q; ++l) zsum += zj[l];
         }
         R S = (R)0;
         // Steps j = i+1 .. N-1 in groups of G, so that the word phase of
         // every step in a group is a compile-time constant.
-        constexpr int G = 4 / gcd_c(NW * D, 4);
+        constexpr int G = 4 / gcd_c(NW * q, 4);
         for (int j0 = i + 1; j0 < P.N; j0 += G) {
             static_for<0, G>([&](auto gc) {
                 constexpr int g = decltype(gc)::value;
                 const int j = j0 + g;
                 if (j >= P.N) return;
-                unsigned wn[D];
-                [[maybe_unused]] unsigned we[D];
-                W.template take<(D + NW * D * (1 + g)) % 4, D, false>(P, wn);
-                if constexpr (NW == 2) W.template take<(2 * D + NW * D * (1 + g)) % 4, D, false>(P, we);
-                R xn[D], zn[D], dw[D];
-                scaled_normals<D>(wn, sdt, dw);
+                unsigned wn[q];
+                [[maybe_unused]] unsigned we[q];
+                W.template take<(D + NW * q * (1 + g)) % 4, q, false>(P, wn);
+                if constexpr (NW == 2) W.template take<(D + q + NW * q * (1 + g)) % 4, q, false>(P, we);
+                R xn[D], zn[q], dw[q];
+                scaled_normals<q>(wn, sdt, dw);
                 if constexpr (NW == 1) {
                     advance<R, D>(P, j, xj, dw, xn);
                 } else {
@@ -912,10 +931,10 @@ __device__ __forceinline__ void solve_stratum(const Params &P, const int i, cons
                         if (P.cv_own) {
                             own = true;
 #pragma unroll
-                            for (int l = 0; l < D; ++l) CZ += zj[l] * dw[l];
+                            for (int l = 0; l < q; ++l) CZ += zj[l] * dw[l];
                         }
                     }
-                    if (!own) CZ += control_apply<R, D>(zcj, dw);
+                    if (!own) CZ += control_apply<R, q>(zcj, dw);
                 }
                 [[maybe_unused]] R fx = (R)0;
                 if constexpr (!ZIN) fx = model_f_x<R, D, MODEL>(P, j, xj);
@@ -924,17 +943,19 @@ __device__ __forceinline__ void solve_stratum(const Params &P, const int i, cons
                     if (!P.cv_own && j + 1 < P.N) control_vals<R, D, p>(P, rowj, phij, zcj);
                 }
                 if constexpr (ZSUM) {
-                    S += dt * logistic_f<R, D>(yn, zsum);
+                    S += dt * logistic_f<R, q>(yn, zsum);
                     zsum = (R)0;
 #pragma unroll
-                    for (int l = 0; l < D; ++l) zsum += zn[l];
+                    for (int l = 0; l < q; ++l) zsum += zn[l];
                 } else if constexpr (ZIN) {
-                    S += dt * model_f<R, D, MODEL, ZIN>(P, j, xj, yn, zj);
+                    S += dt * model_f<R, D, MODEL, ZIN, q>(P, j, xj, yn, zj);
                 } else {
                     S += dt * model_f_y<R, D, MODEL>(P, yn, fx);
                 }
 #pragma unroll
-                for (int l = 0; l < D; ++l) { xj[l] = xn[l]; zj[l] = zn[l]; }
+                for (int l = 0; l < D; ++l) xj[l] = xn[l];
+#pragma unroll
+                for (int l = 0; l < q; ++l) zj[l] = zn[l];
             });
         }
         S += model_g<R, D, MODEL>(P, xj);
@@ -945,7 +966,7 @@ __device__ __forceinline__ void solve_stratum(const Params &P, const int i, cons
                 for (int a = 1; a < p; ++a) phi[a] = (R)st[a * TS];
             }
 #pragma unroll
-            for (int l = 0; l < D; ++l) dwi[l] = (R)st[(p + l) * TS];
+            for (int l = 0; l < q; ++l) dwi[l] = (R)st[(p + l) * TS];
         }
         // Z response uses S - CZ; the phase-A part of the Y response S - CZ - CI.
         R SZ = S, SY = S;
@@ -1088,7 +1109,7 @@ __device__ __forceinline__ void solve_stratum(const Params &P, const int i, cons
             const bool valid = m < Mk;
             Words W;
             W.init(P, (unsigned)m, (unsigned)k, (unsigned)i);
-            R x[D], phi[p], x1[D], y1, z1[D], zi[D];
+            R x[D], phi[p], x1[D], y1, z1[q], zi[q];
             phi[0] = (R)1;
             {
                 unsigned ws[D];
@@ -1101,11 +1122,11 @@ __device__ __forceinline__ void solve_stratum(const Params &P, const int i, cons
                 add_quadratic<R, D, p>(phi);
             }
             {
-                unsigned wd[D], we[D];
-                W.template take<D % 4, D, false>(P, wd);
-                if constexpr (NW == 2) W.template take<(2 * D) % 4, D, false>(P, we);
-                R dwb[D];
-                scaled_normals<D>(wd, sdt, dwb);
+                unsigned wd[q], we[q];
+                W.template take<D % 4, q, false>(P, wd);
+                if constexpr (NW == 2) W.template take<(D + q) % 4, q, false>(P, we);
+                R dwb[q];
+                scaled_normals<q>(wd, sdt, dwb);
                 if constexpr (SRMC_STEP_DYN == 2) {
                     advance<R, D>(P, i, x, dwb, x1);
                 } else {
@@ -1134,7 +1155,7 @@ __device__ __forceinline__ void solve_stratum(const Params &P, const int i, cons
                     zi[l] = clamp_r(w, Form<R>::Cz(P));
                 }
             }
-            const R fi = model_f<R, D, MODEL, ZIN>(P, i, x, y1, zi);
+            const R fi = model_f<R, D, MODEL, ZIN, q>(P, i, x, y1, zi);
             if (valid) {
 #pragma unroll
                 for (int a = 0; a < p; ++a) mB.add(a, phi[a] * fi);
@@ -1499,6 +1520,9 @@ cudaError_t SRMC_LAUNCH_STEP_QUAD_NAME(SRMC_STEP_D)(const Params &P, int i, bool
 #elif SRMC_STEP_DYN == 1
 cudaError_t SRMC_LAUNCH_STEP_EXACT_NAME(SRMC_STEP_D)(const Params &P, int i, bool fp64, bool lp1, int mv,
                                                       int grid, int threads, cudaStream_t st)
+#elif SRMC_STEP_DYN == 2 && SRMC_STEP_Q != SRMC_STEP_D
+cudaError_t SRMC_LAUNCH_STEP_DENSEQ_NAME(SRMC_STEP_D, SRMC_STEP_Q)(const Params &P, int i, bool fp64, bool lp1,
+                                                                    int mv, int grid, int threads, cudaStream_t st)
 #elif SRMC_STEP_DYN == 2
 cudaError_t SRMC_LAUNCH_STEP_DENSE_NAME(SRMC_STEP_D)(const Params &P, int i, bool fp64, bool lp1, int mv,
                                                       int grid, int threads, cudaStream_t st)

@@ -163,6 +163,61 @@ def test_non_diagonal_sigma(dev, orc, prec, case):
     _full_parity(dev, orc, w.replace(sigma=SIGMA_DENSE[w.d], precision=prec))
 
 
+# q != d: a d x q sigma (fewer or more Brownian components than coordinates)
+SIGMA_DQ = {
+    (2, 1): [[0.3], [-0.2]],
+    (1, 2): [[0.25, -0.2]],
+    (3, 2): [[0.3, 0.05], [-0.1, 0.25], [0.08, 0.2]],
+    (2, 3): [[0.25, 0.1, -0.05], [0.0, 0.2, 0.15]],
+    (4, 3): [[0.3 if l == r else 0.04 * (l - r) for r in range(3)] for l in range(4)],
+}
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("case", ["cos_z_d2_q1", "cos_z_d1_q2", "logistic_d3_q2", "affine_d2_q3", "lp0_d4_q3"])
+def test_q_not_d(dev, orc, prec, case):
+    if case == "cos_z_d2_q1":
+        w, dq = W.cfg2(C=4, N=4, M=256, kapz=0.2), (2, 1)
+    elif case == "cos_z_d1_q2":
+        w, dq = W.cfg1(C=8, N=4, M=256).replace(params=[0.5, 0.3, 0.2, 0.4]), (1, 2)
+    elif case == "logistic_d3_q2":
+        w, dq = W.logistic_paper(d=3, N=3, C=3, M=128), (3, 2)
+    elif case == "affine_d2_q3":
+        w, dq = W.affine(d=2, N=3, C=3, M=64, g0=0.5, gv=[0.3, -0.2], f0=0.1, fv=[0.05, 0.02], a=-0.3), (2, 3)
+    else:
+        w, dq = W.cos_model("d4", d=4, N=3, C=2, a=2.0, M=512, s0=0.3, lam=0.2, kap=0.5, basis="lp0"), (4, 3)
+    _full_parity(dev, orc, w.replace(q=dq[1], sigma=SIGMA_DQ[dq], precision=prec))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_controls_with_q_not_d(dev, orc, prec):
+    from tests import controls as CT
+    from tests.test_gpu_cv import _cv_parity, _own_parity
+    w = W.cfg2(C=6, N=4, M=256, precision=prec, kapz=0.2).replace(q=1, sigma=SIGMA_DQ[(2, 1)])
+    _cv_parity(dev, orc, w, CT.random_smooth_z(w, seed=8))
+    _own_parity(dev, orc, w)
+
+
+def test_q_not_d_limits(dev):
+    torch, srmc = dev
+    w = W.cfg2(C=4, N=2, M=64).replace(q=1, sigma=SIGMA_DQ[(2, 1)])
+    bad = [W.cos_model("d5", d=5, N=2, C=1, a=2.0, M=64, s0=0.3, lam=0.2, kap=0.5).replace(
+               q=2, sigma=[[0.3, 0.0]] * 5),
+           w.replace(b=[0.1, 0.0]),                              # the cos drift term needs q == d
+           w.replace(theta=[1.0, 1.0], dynamics="exact")]
+    for b in bad:
+        with pytest.raises(srmc.SrmcError) as e:
+            srmc.Solver(b)
+        assert e.value.status == 4, b.name
+    s = srmc.Solver(w)
+    net = srmc.MLP(3)
+    with pytest.raises(srmc.SrmcError) as e:
+        net.srmc_cv_tabulate(s)
+    assert e.value.status == 4
+    net.close()
+    s.close()
+
+
 def test_non_diagonal_sigma_limits(dev):
     torch, srmc = dev
     dense = W.cfg2(C=4, N=2, M=64).replace(sigma=SIGMA_DENSE[2])

@@ -83,6 +83,9 @@ BF_CASES = [
     dict(d=2, N=3, C=2, M=6, kapz=0.3, basis="lp1", sigma=[[0.5, 0.2], [-0.3, 0.4]]),
     dict(d=3, N=2, C=2, M=5, kapz=0.0, basis="lp1", sigma=[[0.5, 0.1, 0.0], [0.2, 0.4, -0.1], [0.0, 0.3, 0.6]],
          b=[0.1, 0.0, -0.2], theta=[0.3, 0.0, 0.0]),
+    # q != d: fewer and more Brownian components than coordinates (d x q sigma)
+    dict(d=2, N=3, C=2, M=6, kapz=0.3, basis="lp1", q=1, sigma=[[0.5], [-0.3]]),
+    dict(d=1, N=3, C=3, M=5, kapz=0.2, basis="lp1", q=2, sigma=[[0.4, -0.25]]),
 ]
 _BF = {}
 
@@ -93,7 +96,7 @@ def _bf_workload(case):
     return w.replace(Cy=1.5, Cz=1.2, strata=case.get("strata", "size"),   # active truncation somewhere
                      M_strata=case.get("M_strata"), b=case.get("b", [0.0] * case["d"]),
                      theta=case.get("theta", []), dynamics=case.get("dynamics", "euler"),
-                     sigma=case.get("sigma", w.sigma))
+                     q=case.get("q", w.q), sigma=case.get("sigma", w.sigma))
 
 
 def _brute_force_mismatch(orc, n, library=None):
